@@ -1,0 +1,205 @@
+/*
+ * liboctax: data-parallel CHIP-8 environment step on one GB300 (sm_103a).
+ *
+ * C-ABI boundary of the vectorised environment step described by the Octax
+ * paper (arXiv 2510.01764): many independent CHIP-8 emulator instances, each
+ * stepping with fetch/decode/execute of the 35 instructions (§3.2
+ * "Fetch-decode-execute cycle", App. B), an XOR sprite blit with VF collision
+ * into a 64x32 1-bit display (App. B "Sprite Drawing"), 60 Hz delay/sound
+ * timers, K instructions per frame with frame skip and a stacked observation
+ * (§3.2 "Environment integration", §4.2), and reward/termination read from
+ * game registers or memory with automatic reset (§3.3).
+ *
+ * Conventions (every entry point):
+ *  - Plain pointers and sizes only. "_dev" pointers are CUDA device memory
+ *    owned by the caller (e.g. a torch tensor's data_ptr()); "_host" pointers
+ *    are host memory owned by the caller (pinned memory copies fastest).
+ *    The library owns the emulator state and the ROM images; `rom` bytes are
+ *    copied at creation.
+ *  - Return value: OCTAX_OK (0) or a negative OCTAX_E* code; the message of
+ *    the last failure on the calling thread is octax_last_error().
+ *  - Work is enqueued on the environment's CUDA stream and the call returns
+ *    without waiting, except where a function says it is synchronous.
+ *  - Device-side faults never trap: stack over/underflow, invalid opcodes and
+ *    out-of-range action indices set per-instance status bits.
+ *  - Results are bit-exact and independent of launch configuration, batch
+ *    composition and instance placement.
+ */
+#ifndef OCTAX_H
+#define OCTAX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes --------------------------------------------------------- */
+#define OCTAX_OK 0
+#define OCTAX_EINVAL (-1)   /* bad argument: sizes, descriptor fields, null pointer */
+#define OCTAX_ENOMEM (-2)   /* device or host allocation failed / over budget       */
+#define OCTAX_ECUDA (-3)    /* a CUDA runtime call failed (message has the detail)  */
+#define OCTAX_ETIMEOUT (-4) /* octax_sync / server wait deadline passed             */
+#define OCTAX_ENOTFOUND (-5) /* unknown request id                                 */
+
+/* ---- quirk bits (one env-wide bit set; 0 = the classic set) -------------- */
+#define OCTAX_QUIRK_SHIFT_USES_VY 0x01u   /* 8XY6/8XYE shift VY into VX          */
+#define OCTAX_QUIRK_LOADSTORE_INC_I 0x02u /* FX55/FX65 leave I = I + X + 1       */
+#define OCTAX_QUIRK_LOGIC_RESETS_VF 0x04u /* 8XY1/8XY2/8XY3 set VF = 0           */
+#define OCTAX_QUIRK_JUMP_VX 0x08u         /* BXNN jumps to XNN + VX              */
+#define OCTAX_QUIRK_WRAP_SPRITES 0x10u    /* DXYN wraps at the display edges     */
+#define OCTAX_QUIRK_FX1E_VF 0x20u         /* FX1E sets VF = (I + VX > 0xFFF)     */
+
+/* ---- per-instance status bits (sticky since creation) -------------------- */
+#define OCTAX_STATUS_BAD_OP 0x01u      /* an undefined opcode was executed (no-op) */
+#define OCTAX_STATUS_STACK_FAULT 0x02u /* CALL on a full / RET on an empty stack   */
+#define OCTAX_STATUS_BAD_ACTION 0x04u  /* action index > n_actions (no key held)   */
+
+/* ---- reward / termination descriptor (§3.3 score_fn / terminated_fn) ----- */
+enum { OCTAX_SRC_REG = 0, OCTAX_SRC_MEM = 1 };
+enum {
+  OCTAX_X_RAW = 0,                 /* v                                  */
+  OCTAX_X_NEG = 1,                 /* -v                                 */
+  OCTAX_X_DEC_TENS = 2,            /* v / 10                             */
+  OCTAX_X_DEC_ONES = 3,            /* v % 10                             */
+  OCTAX_X_DEC_TENS_MINUS_ONES = 4, /* v/10 - v%10 (Pong, §3.3)          */
+  OCTAX_X_NIB_HI_MINUS_LO = 5,     /* (v >> 4) - (v & 15)               */
+  OCTAX_X_ZERO_IF_GT = 6           /* v > arg ? 0 : v (App. C)          */
+};
+enum { OCTAX_CMP_EQ = 0, OCTAX_CMP_NE, OCTAX_CMP_GE, OCTAX_CMP_GT, OCTAX_CMP_LE, OCTAX_CMP_LT };
+
+typedef struct {
+  uint8_t src;   /* OCTAX_SRC_REG: V[idx & 15]; OCTAX_SRC_MEM: RAM[idx & 0xFFF] */
+  uint8_t xform; /* OCTAX_X_*                                                  */
+  uint16_t idx;
+  int32_t arg;   /* threshold of OCTAX_X_ZERO_IF_GT                            */
+} octax_term;    /* 8 bytes */
+
+typedef struct {
+  octax_term lhs;
+  uint8_t cmp;   /* OCTAX_CMP_*: lhs <cmp> rhs */
+  uint8_t pad[3];
+  int32_t rhs;
+} octax_clause;  /* 16 bytes */
+
+/* One game (§3.2-§3.3): ROM, timing, action set, reward and termination. */
+typedef struct {
+  const uint8_t *rom;        /* host pointer, 1..3584 bytes, loaded at 0x200; copied */
+  uint32_t rom_len;
+  uint8_t instr_per_frame;   /* K >= 1 (the paper's ~700 Hz is ~11.7 per frame)       */
+  uint8_t frameskip;         /* frames per env step >= 1 (paper default 4)            */
+  uint8_t stack_frames;      /* frames in the observation, 1..frameskip; same for all
+                                games of one environment                             */
+  uint8_t n_actions;         /* 0..16; action index n_actions means "no key"          */
+  uint8_t action_set[16];    /* action index -> CHIP-8 key (0..15)                    */
+  uint8_t n_score_terms;     /* 0..4: score = sum of terms                            */
+  uint8_t n_term_clauses;    /* 0..4: terminated = OR of clauses (0 = never)          */
+  uint8_t pad[2];
+  octax_term score[4];
+  octax_clause term[4];
+  uint32_t max_episode_steps; /* truncation after this many steps; 0 = none           */
+  uint32_t startup_instrs;    /* instructions run at every reset with no key held,
+                                 0..2^20                                             */
+} octax_game;
+
+/* Canonical state of one instance: the unit of comparison and checkpointing.
+ * RAM is the full 4 KB as the program sees it (font, ROM and all writes). */
+typedef struct {
+  uint8_t V[16];
+  uint16_t I, PC;
+  uint8_t SP;                /* occupied call-stack entries, 0..16 */
+  uint8_t DT, ST, status;
+  uint16_t stack[16];
+  uint64_t display[32];      /* bit x of word y = pixel (x, y) */
+  uint8_t ram[4096];
+  uint32_t episode_steps;    /* steps since the last reset */
+  uint32_t env_steps;        /* steps since creation (random-number counter) */
+} octax_state_record;        /* 4416 bytes */
+
+/* Launch configuration (chosen by octax_autotune or set by hand). */
+typedef struct {
+  int32_t block;             /* instances per CTA: 32, 64, 128 or 256            */
+  int32_t steps_per_launch;  /* octax_step_n: env steps per kernel launch 1..64  */
+  int32_t persistent;        /* 1: resident CTAs pull instance groups off a queue */
+  int32_t use_graph;         /* 1: octax_step_n replays a captured CUDA graph     */
+} octax_launch;
+
+typedef struct octax_env octax_env;
+
+/* Create n_envs instances over n_games games and reset them all (§3.2 "ROM
+ * loading and initialization"). game_of_env[i] (host, nullable = all 0) picks
+ * instance i's game; uid_of_env[i] (host, nullable = i) is its random-number
+ * identity, so an instance's trajectory depends only on (seed, uid, actions).
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream). Synchronous.
+ * EINVAL: n_games < 1, n_envs < 1, a descriptor field out of range, unknown
+ * quirk bits, stack_frames differing between games. */
+int octax_create(const octax_game *games, int n_games, const uint16_t *game_of_env,
+                 const uint32_t *uid_of_env, int64_t n_envs, uint32_t quirks,
+                 uint64_t seed, void *cuda_stream, octax_env **out);
+
+/* Reset the instances with mask_dev[i] != 0 (mask_dev NULL = all) and write
+ * their observation (the reset display in every stack slot) to
+ * obs_dev[i][stack_frames][32][64] (uint8 0/1; NULL = no write). */
+int octax_reset(octax_env *env, const uint8_t *mask_dev, uint8_t *obs_dev);
+
+/* One environment step for every instance (§3.2, §4.2).
+ * actions_dev: uint8 [n_envs], index into the game's action_set.
+ * obs_dev: uint8 [n_envs][stack_frames][32][64], the last stack_frames frames
+ *   of the step, oldest first; for a done instance the reset display.
+ * reward_dev: float32 [n_envs], score after minus score before the step.
+ * done_dev: uint8 [n_envs], terminated or truncated; done instances are reset. */
+int octax_step(octax_env *env, const uint8_t *actions_dev, uint8_t *obs_dev,
+               float *reward_dev, uint8_t *done_dev);
+
+/* n_steps steps in as few launches as the launch configuration allows
+ * (steps_per_launch per launch, CUDA-graph replay, persistent scheduling).
+ * actions_dev [n_steps][n_envs]; obs_dev [n_steps][n_envs][S][32][64];
+ * reward_dev, done_dev [n_steps][n_envs]. Same results as n_steps octax_step. */
+int octax_step_n(octax_env *env, int n_steps, const uint8_t *actions_dev, uint8_t *obs_dev,
+                 float *reward_dev, uint8_t *done_dev);
+
+/* octax_step with host buffers: copies actions in, steps, copies obs, reward
+ * and done out, and waits. Synchronous. */
+int octax_step_host(octax_env *env, const uint8_t *actions_host, uint8_t *obs_host,
+                    float *reward_host, uint8_t *done_host);
+
+/* FNV-1a 64-bit hash of each instance's canonical record (octax_state_record
+ * bytes in field order, little-endian) into hash_dev [n_envs]. */
+int octax_state_hash(octax_env *env, uint64_t *hash_dev);
+
+/* Copy the canonical records of instances [first, first+count) to host
+ * memory. Synchronous. EINVAL if the range is outside [0, n_envs). */
+int octax_get_state(octax_env *env, int64_t first, int64_t count, octax_state_record *out_host);
+
+/* Overwrite instances [first, first+count) from records (checkpoint resume).
+ * Synchronous. EINVAL if the range is outside [0, n_envs) or SP > 16. */
+int octax_set_state(octax_env *env, int64_t first, int64_t count,
+                    const octax_state_record *in_host);
+
+/* Wait until all enqueued work finished; OCTAX_ETIMEOUT after timeout_ms
+ * (negative = no limit). */
+int octax_sync(octax_env *env, int timeout_ms);
+
+int octax_get_launch(const octax_env *env, octax_launch *out);
+/* EINVAL for unsupported values. */
+int octax_set_launch(octax_env *env, const octax_launch *cfg);
+
+/* Time candidate launch configurations on a scratch copy of this environment
+ * (results unaffected) and keep the fastest for octax_step_n with n_steps
+ * steps per call. Synchronous. best_ms_out (nullable) receives its time. */
+int octax_autotune(octax_env *env, int n_steps, float *best_ms_out);
+
+int64_t octax_num_envs(const octax_env *env);
+int octax_stack_frames(const octax_env *env);
+/* Device bytes owned by the environment. */
+size_t octax_device_bytes(const octax_env *env);
+void octax_destroy(octax_env *env);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *octax_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

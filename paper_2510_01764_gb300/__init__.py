@@ -4,11 +4,12 @@
 binding (``octax``) loads the in-tree ``liboctax.so`` on first use and raises if
 it is missing: there is no CPU fallback.
 """
-__all__ = ["workloads", "octax"]
+import importlib
+
+__all__ = ["workloads", "octax", "Env"]
 
 
 def __getattr__(name):
-    if name in ("octax", "Env", "Server"):
-        from . import octax as _o
-        return _o if name == "octax" else getattr(_o, name)
+    if name == "Env":
+        return importlib.import_module(__name__ + ".octax").Env
     raise AttributeError(name)

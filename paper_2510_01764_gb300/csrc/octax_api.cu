@@ -1,0 +1,725 @@
+// liboctax host side: the C-ABI declared in include/octax.h.
+//
+// An environment owns its emulator state (structure-of-arrays over "slots";
+// slots are instances sorted by game so that every CTA runs one game), the
+// per-game descriptors and 4 KB initial RAM images, the group tables for each
+// CTA size, and a cache of explicitly built CUDA graphs for octax_step_n.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "octax_internal.h"
+
+namespace octax {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char *what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return OCTAX_ECUDA;
+}
+
+// The conventional 4x5 hexadecimal font, 5 bytes per glyph, loaded at 0x050
+// (the paper fixes the location 0x050-0x09F; the glyph shapes are the
+// customary CHIP-8 ones).
+static const uint8_t kFont[80] = {
+    0xF0, 0x90, 0x90, 0x90, 0xF0, 0x20, 0x60, 0x20, 0x20, 0x70, 0xF0, 0x10, 0xF0, 0x80,
+    0xF0, 0xF0, 0x10, 0xF0, 0x10, 0xF0, 0x90, 0x90, 0xF0, 0x10, 0x10, 0xF0, 0x80, 0xF0,
+    0x10, 0xF0, 0xF0, 0x80, 0xF0, 0x90, 0xF0, 0xF0, 0x10, 0x20, 0x40, 0x40, 0xF0, 0x90,
+    0xF0, 0x90, 0xF0, 0xF0, 0x90, 0xF0, 0x10, 0xF0, 0xF0, 0x90, 0xF0, 0x90, 0x90, 0xE0,
+    0x90, 0xE0, 0x90, 0xE0, 0xF0, 0x80, 0x80, 0x80, 0xF0, 0xE0, 0x90, 0x90, 0x90, 0xE0,
+    0xF0, 0x80, 0xF0, 0x80, 0xF0, 0xF0, 0x80, 0xF0, 0x80, 0x80};
+
+}  // namespace octax
+
+using namespace octax;
+
+struct GroupTable {
+  Group *dev = nullptr;
+  int count = 0;
+};
+
+struct GraphKey {
+  int n_steps, block, spl, persistent;
+  bool operator<(const GraphKey &o) const {
+    return std::tie(n_steps, block, spl, persistent) < std::tie(o.n_steps, o.block, o.spl, o.persistent);
+  }
+};
+
+struct octax_env {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t n = 0;
+  int n_games = 0;
+  int S = 4;
+  uint32_t quirks = 0;
+  uint64_t seed = 0;
+  std::vector<GameDev> games_h;
+  std::vector<uint16_t> game_of_slot;
+  GameDev *games_d = nullptr;
+  uint8_t *images_d = nullptr;
+  DevState st{};
+  uint32_t *slot_of_row_d = nullptr;
+  std::vector<void *> allocs;
+  size_t bytes = 0;
+  octax_launch cfg{64, 4, 0, 1};
+  std::map<int, GroupTable> groups;
+  unsigned int *counters_d = nullptr;
+  int counters_cap = 0;
+  IO *io_d = nullptr;
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+  // octax_step_host staging
+  uint8_t *hs_act = nullptr, *hs_obs = nullptr, *hs_done = nullptr;
+  float *hs_rew = nullptr;
+  cudaEvent_t ev = nullptr;
+};
+
+namespace {
+
+template <class T>
+cudaError_t dalloc(octax_env *e, T **p, size_t count) {
+  void *q = nullptr;
+  const size_t bytes = count * sizeof(T);
+  cudaError_t r = cudaMalloc(&q, bytes > 0 ? bytes : 16);
+  if (r != cudaSuccess) return r;
+  e->allocs.push_back(q);
+  e->bytes += bytes;
+  *p = static_cast<T *>(q);
+  return cudaSuccess;
+}
+
+int validate_game(const octax_game &g, int S) {
+  char buf[160];
+  if (!g.rom || g.rom_len < 1 || g.rom_len > 3584) {
+    set_error("game rom must be 1..3584 bytes");
+    return OCTAX_EINVAL;
+  }
+  if (g.instr_per_frame < 1 || g.frameskip < 1 || g.stack_frames < 1 || g.stack_frames > g.frameskip) {
+    set_error("need instr_per_frame >= 1, frameskip >= 1, 1 <= stack_frames <= frameskip");
+    return OCTAX_EINVAL;
+  }
+  if (g.stack_frames != S) {
+    set_error("all games of one environment need the same stack_frames");
+    return OCTAX_EINVAL;
+  }
+  if (g.startup_instrs > (1u << 20)) {
+    set_error("startup_instrs must be <= 2^20");
+    return OCTAX_EINVAL;
+  }
+  if (g.n_actions > 16 || g.n_score_terms > 4 || g.n_term_clauses > 4) {
+    set_error("n_actions <= 16, n_score_terms <= 4, n_term_clauses <= 4");
+    return OCTAX_EINVAL;
+  }
+  for (int i = 0; i < g.n_actions; ++i)
+    if (g.action_set[i] > 15) {
+      snprintf(buf, sizeof buf, "action_set[%d] = %d is not a CHIP-8 key", i, g.action_set[i]);
+      set_error(buf);
+      return OCTAX_EINVAL;
+    }
+  auto bad_term = [](const octax_term &t) { return t.src > OCTAX_SRC_MEM || t.xform > OCTAX_X_ZERO_IF_GT; };
+  for (int i = 0; i < g.n_score_terms; ++i)
+    if (bad_term(g.score[i])) {
+      set_error("score term: bad src or xform");
+      return OCTAX_EINVAL;
+    }
+  for (int i = 0; i < g.n_term_clauses; ++i)
+    if (bad_term(g.term[i].lhs) || g.term[i].cmp > OCTAX_CMP_LT) {
+      set_error("termination clause: bad src, xform or cmp");
+      return OCTAX_EINVAL;
+    }
+  return OCTAX_OK;
+}
+
+GameDev to_dev(const octax_game &g) {
+  GameDev d;
+  memset(&d, 0, sizeof d);
+  d.K = g.instr_per_frame;
+  d.frameskip = g.frameskip;
+  d.n_actions = g.n_actions;
+  d.n_score = g.n_score_terms;
+  d.n_term = g.n_term_clauses;
+  d.max_steps = g.max_episode_steps;
+  d.startup = g.startup_instrs;
+  memcpy(d.action_set, g.action_set, 16);
+  for (int i = 0; i < 4; ++i) {
+    d.score[i] = TermDev{g.score[i].src, g.score[i].xform, g.score[i].idx, g.score[i].arg};
+    d.term[i].lhs = TermDev{g.term[i].lhs.src, g.term[i].lhs.xform, g.term[i].lhs.idx, g.term[i].lhs.arg};
+    d.term[i].cmp = g.term[i].cmp;
+    d.term[i].rhs = g.term[i].rhs;
+  }
+  return d;
+}
+
+int block_ok(int b) { return b == 32 || b == 64 || b == 128 || b == 256; }
+
+// Groups of up to `block` consecutive same-game slots.
+int get_groups(octax_env *e, int block, GroupTable **out) {
+  auto it = e->groups.find(block);
+  if (it != e->groups.end()) {
+    *out = &it->second;
+    return OCTAX_OK;
+  }
+  std::vector<Group> gs;
+  int64_t s = 0;
+  while (s < e->n) {
+    int64_t end = s;
+    const uint16_t g = e->game_of_slot[s];
+    while (end < e->n && e->game_of_slot[end] == g && end - s < block) ++end;
+    gs.push_back(Group{(uint32_t)s, (uint16_t)(end - s), g, 0u, 0u});
+    s = end;
+  }
+  GroupTable t;
+  t.count = (int)gs.size();
+  cudaError_t r = dalloc(e, &t.dev, gs.size());
+  if (r != cudaSuccess) return cuda_fail(r, "group table");
+  r = cudaMemcpy(t.dev, gs.data(), gs.size() * sizeof(Group), cudaMemcpyHostToDevice);
+  if (r != cudaSuccess) return cuda_fail(r, "group table upload");
+  e->groups[block] = t;
+  *out = &e->groups[block];
+  return OCTAX_OK;
+}
+
+int ensure_counters(octax_env *e, int count) {
+  if (count <= e->counters_cap) return OCTAX_OK;
+  unsigned int *p = nullptr;
+  cudaError_t r = dalloc(e, &p, (size_t)count);
+  if (r != cudaSuccess) return cuda_fail(r, "work counters");
+  e->counters_d = p;
+  e->counters_cap = count;
+  return OCTAX_OK;
+}
+
+StepLaunch base_launch(octax_env *e, const GroupTable *gt) {
+  StepLaunch p;
+  memset(&p, 0, sizeof p);
+  p.st = e->st;
+  p.games = e->games_d;
+  p.images = e->images_d;
+  p.groups = gt->dev;
+  p.n_groups = gt->count;
+  p.S = e->S;
+  p.quirks = e->quirks;
+  return p;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int check_io(const uint8_t *actions, const uint8_t *obs, const float *reward, const uint8_t *done) {
+  if (!actions || !obs || !reward || !done) {
+    set_error("actions, obs, reward and done must be non-null device pointers");
+    return OCTAX_EINVAL;
+  }
+  if (!aligned16(obs)) {
+    set_error("obs must be 16-byte aligned");
+    return OCTAX_EINVAL;
+  }
+  return OCTAX_OK;
+}
+
+// Enqueue n_steps steps as a chain of launches of `spl` steps each.
+int enqueue_steps(octax_env *e, const octax_launch &cfg, int n_steps, const IO &io) {
+  GroupTable *gt = nullptr;
+  int rc = get_groups(e, cfg.block, &gt);
+  if (rc) return rc;
+  const int spl = cfg.steps_per_launch;
+  const int launches = (n_steps + spl - 1) / spl;
+  const int grid = cfg.persistent ? std::min(gt->count, std::max(1, max_resident_ctas(cfg.block))) : gt->count;
+  if (cfg.persistent) {
+    rc = ensure_counters(e, launches);
+    if (rc) return rc;
+  }
+  if (!cfg.use_graph || launches == 1) {
+    if (cfg.persistent) {
+      cudaError_t r = cudaMemsetAsync(e->counters_d, 0, sizeof(unsigned) * launches, e->stream);
+      if (r != cudaSuccess) return cuda_fail(r, "counter reset");
+    }
+    for (int j = 0; j < launches; ++j) {
+      StepLaunch p = base_launch(e, gt);
+      p.io0 = io;
+      p.step0 = j * spl;
+      p.steps = std::min(spl, n_steps - j * spl);
+      p.work_counter = cfg.persistent ? e->counters_d + j : nullptr;
+      cudaError_t r = launch_step(p, grid, cfg.block, e->stream);
+      if (r != cudaSuccess) return cuda_fail(r, "step launch");
+    }
+    return OCTAX_OK;
+  }
+  // CUDA graph: the kernels read their IO from io_d, refreshed before replay.
+  const GraphKey key{n_steps, cfg.block, spl, cfg.persistent};
+  auto it = e->graphs.find(key);
+  if (it == e->graphs.end()) {
+    cudaGraph_t g;
+    cudaError_t r = cudaGraphCreate(&g, 0);
+    if (r != cudaSuccess) return cuda_fail(r, "graph create");
+    cudaGraphNode_t prev = nullptr;
+    if (cfg.persistent) {
+      cudaMemsetParams mp;
+      memset(&mp, 0, sizeof mp);
+      mp.dst = e->counters_d;
+      mp.value = 0;
+      mp.elementSize = 4;
+      mp.width = (size_t)launches;
+      mp.height = 1;
+      mp.pitch = 0;
+      r = cudaGraphAddMemsetNode(&prev, g, nullptr, 0, &mp);
+      if (r != cudaSuccess) return cuda_fail(r, "graph memset node");
+    }
+    for (int j = 0; j < launches; ++j) {
+      StepLaunch p = base_launch(e, gt);
+      p.io_table = e->io_d;
+      p.step0 = j * spl;
+      p.steps = std::min(spl, n_steps - j * spl);
+      p.work_counter = cfg.persistent ? e->counters_d + j : nullptr;
+      cudaGraphNode_t node;
+      r = add_step_node(g, &node, prev, p, grid, cfg.block);
+      if (r != cudaSuccess) return cuda_fail(r, "graph kernel node");
+      prev = node;
+    }
+    cudaGraphExec_t ex;
+    r = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (r != cudaSuccess) return cuda_fail(r, "graph instantiate");
+    it = e->graphs.emplace(key, ex).first;
+  }
+  // Pageable source: the runtime stages it before returning, so the stack copy is safe.
+  IO io_copy = io;
+  cudaError_t r = cudaMemcpyAsync(e->io_d, &io_copy, sizeof(IO), cudaMemcpyHostToDevice, e->stream);
+  if (r != cudaSuccess) return cuda_fail(r, "io upload");
+  r = cudaGraphLaunch(it->second, e->stream);
+  if (r != cudaSuccess) return cuda_fail(r, "graph launch");
+  return OCTAX_OK;
+}
+
+void free_env(octax_env *e) {
+  if (!e) return;
+  cudaSetDevice(e->device);
+  if (e->stream) cudaStreamSynchronize(e->stream);
+  for (auto &kv : e->graphs) cudaGraphExecDestroy(kv.second);
+  for (void *p : e->allocs) cudaFree(p);
+  if (e->ev) cudaEventDestroy(e->ev);
+  if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
+  delete e;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *octax_last_error(void) { return g_last_error.c_str(); }
+
+int octax_create(const octax_game *games, int n_games, const uint16_t *game_of_env,
+                 const uint32_t *uid_of_env, int64_t n_envs, uint32_t quirks, uint64_t seed,
+                 void *cuda_stream, octax_env **out) {
+  if (!out || !games || n_games < 1 || n_games > 65535 || n_envs < 1 || n_envs > (int64_t)1 << 31) {
+    set_error("octax_create: need out, games, 1 <= n_games <= 65535, 1 <= n_envs <= 2^31");
+    return OCTAX_EINVAL;
+  }
+  *out = nullptr;
+  if (quirks & ~0x3Fu) {
+    set_error("octax_create: unknown quirk bits");
+    return OCTAX_EINVAL;
+  }
+  for (int g = 0; g < n_games; ++g) {
+    int rc = validate_game(games[g], games[0].stack_frames);
+    if (rc) return rc;
+  }
+  if (game_of_env)
+    for (int64_t i = 0; i < n_envs; ++i)
+      if (game_of_env[i] >= n_games) {
+        set_error("octax_create: game_of_env entry out of range");
+        return OCTAX_EINVAL;
+      }
+  octax_env *e = new octax_env();
+  cudaGetDevice(&e->device);
+  e->n = n_envs;
+  e->n_games = n_games;
+  e->S = games[0].stack_frames;
+  e->quirks = quirks;
+  e->seed = seed;
+  if (cuda_stream) {
+    e->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {  // blocking stream: ordered with the legacy default stream
+    cudaError_t r = cudaStreamCreate(&e->stream);
+    if (r != cudaSuccess) {
+      free_env(e);
+      return cuda_fail(r, "stream create");
+    }
+    e->own_stream = true;
+  }
+  // slots: instances stably sorted by game
+  std::vector<uint32_t> slot_of_row(n_envs), row_of_slot(n_envs);
+  std::iota(row_of_slot.begin(), row_of_slot.end(), 0u);
+  if (game_of_env)
+    std::stable_sort(row_of_slot.begin(), row_of_slot.end(),
+                     [&](uint32_t a, uint32_t b) { return game_of_env[a] < game_of_env[b]; });
+  e->game_of_slot.resize(n_envs);
+  std::vector<uint32_t> uid_of_slot(n_envs);
+  for (int64_t s = 0; s < n_envs; ++s) {
+    const uint32_t row = row_of_slot[s];
+    slot_of_row[row] = (uint32_t)s;
+    e->game_of_slot[s] = game_of_env ? game_of_env[row] : 0;
+    uid_of_slot[s] = uid_of_env ? uid_of_env[row] : row;
+  }
+  // descriptors and initial RAM images
+  std::vector<uint8_t> images((size_t)n_games * kRamBytes, 0);
+  for (int g = 0; g < n_games; ++g) {
+    e->games_h.push_back(to_dev(games[g]));
+    memcpy(&images[(size_t)g * kRamBytes + 0x50], kFont, sizeof kFont);
+    memcpy(&images[(size_t)g * kRamBytes + 0x200], games[g].rom, games[g].rom_len);
+  }
+  const size_t n = (size_t)n_envs;
+  DevState &st = e->st;
+  st.n = n_envs;
+  cudaError_t r = cudaSuccess;
+  uint32_t *uid_tmp = nullptr;
+#define ALLOC(ptr, cnt) \
+  if (r == cudaSuccess) r = dalloc(e, &(ptr), (cnt))
+  ALLOC(e->games_d, (size_t)n_games);
+  ALLOC(e->images_d, images.size());
+  ALLOC(st.v, 4 * n);
+  ALLOC(st.pcI, n);
+  ALLOC(st.misc, n);
+  ALLOC(st.stack, 16 * n);
+  ALLOC(st.disp, 32 * n);
+  ALLOC(st.dirty, n);
+  ALLOC(st.ram, n * kRamBytes);
+  ALLOC(st.ep, n);
+  ALLOC(st.env_steps, n);
+  ALLOC(st.prev_score, n);
+  ALLOC(st.key, 2 * n);
+  ALLOC(st.uid, n);
+  ALLOC(st.out_row, n);
+  ALLOC(st.game, n);
+  ALLOC(e->slot_of_row_d, n);
+  ALLOC(e->io_d, 1);
+  ALLOC(uid_tmp, n);
+#undef ALLOC
+  if (r != cudaSuccess) {
+    free_env(e);
+    set_error(std::string("octax_create: device allocation failed: ") + cudaGetErrorString(r));
+    return OCTAX_ENOMEM;
+  }
+  r = cudaMemcpy(e->games_d, e->games_h.data(), e->games_h.size() * sizeof(GameDev), cudaMemcpyHostToDevice);
+  if (r == cudaSuccess) r = cudaMemcpy(e->images_d, images.data(), images.size(), cudaMemcpyHostToDevice);
+  if (r == cudaSuccess) r = cudaMemcpy(st.out_row, row_of_slot.data(), n * 4, cudaMemcpyHostToDevice);
+  if (r == cudaSuccess) r = cudaMemcpy(st.game, e->game_of_slot.data(), n * 2, cudaMemcpyHostToDevice);
+  if (r == cudaSuccess) r = cudaMemcpy(e->slot_of_row_d, slot_of_row.data(), n * 4, cudaMemcpyHostToDevice);
+  if (r == cudaSuccess) r = cudaMemcpy(uid_tmp, uid_of_slot.data(), n * 4, cudaMemcpyHostToDevice);
+  if (r == cudaSuccess) r = cudaEventCreateWithFlags(&e->ev, cudaEventDisableTiming);
+  if (r != cudaSuccess) {
+    int rc = cuda_fail(r, "octax_create upload");
+    free_env(e);
+    return rc;
+  }
+  GroupTable *gt = nullptr;
+  int rc = get_groups(e, e->cfg.block, &gt);
+  if (rc) {
+    free_env(e);
+    return rc;
+  }
+  ResetLaunch p;
+  memset(&p, 0, sizeof p);
+  p.st = st;
+  p.games = e->games_d;
+  p.images = e->images_d;
+  p.groups = gt->dev;
+  p.n_groups = gt->count;
+  p.S = e->S;
+  p.quirks = quirks;
+  p.init = 1;
+  p.seed = seed;
+  p.uid_of_slot = uid_tmp;
+  r = launch_reset(p, e->cfg.block, e->stream);
+  if (r == cudaSuccess) r = cudaStreamSynchronize(e->stream);
+  if (r != cudaSuccess) {
+    rc = cuda_fail(r, "octax_create reset");
+    free_env(e);
+    return rc;
+  }
+  *out = e;
+  return OCTAX_OK;
+}
+
+int octax_reset(octax_env *e, const uint8_t *mask_dev, uint8_t *obs_dev) {
+  if (!e) {
+    set_error("octax_reset: null env");
+    return OCTAX_EINVAL;
+  }
+  if (obs_dev && !aligned16(obs_dev)) {
+    set_error("octax_reset: obs must be 16-byte aligned");
+    return OCTAX_EINVAL;
+  }
+  GroupTable *gt = nullptr;
+  int rc = get_groups(e, e->cfg.block, &gt);
+  if (rc) return rc;
+  ResetLaunch p;
+  memset(&p, 0, sizeof p);
+  p.st = e->st;
+  p.games = e->games_d;
+  p.images = e->images_d;
+  p.groups = gt->dev;
+  p.n_groups = gt->count;
+  p.mask = mask_dev;
+  p.obs = obs_dev;
+  p.S = e->S;
+  p.quirks = e->quirks;
+  cudaError_t r = launch_reset(p, e->cfg.block, e->stream);
+  return r == cudaSuccess ? OCTAX_OK : cuda_fail(r, "octax_reset");
+}
+
+int octax_step(octax_env *e, const uint8_t *actions_dev, uint8_t *obs_dev, float *reward_dev,
+               uint8_t *done_dev) {
+  if (!e) {
+    set_error("octax_step: null env");
+    return OCTAX_EINVAL;
+  }
+  int rc = check_io(actions_dev, obs_dev, reward_dev, done_dev);
+  if (rc) return rc;
+  IO io{actions_dev, obs_dev, reward_dev, done_dev, e->n};
+  octax_launch cfg = e->cfg;
+  cfg.steps_per_launch = 1;
+  cfg.use_graph = 0;
+  return enqueue_steps(e, cfg, 1, io);
+}
+
+int octax_step_n(octax_env *e, int n_steps, const uint8_t *actions_dev, uint8_t *obs_dev,
+                 float *reward_dev, uint8_t *done_dev) {
+  if (!e || n_steps < 1) {
+    set_error("octax_step_n: need env and n_steps >= 1");
+    return OCTAX_EINVAL;
+  }
+  int rc = check_io(actions_dev, obs_dev, reward_dev, done_dev);
+  if (rc) return rc;
+  IO io{actions_dev, obs_dev, reward_dev, done_dev, e->n};
+  return enqueue_steps(e, e->cfg, n_steps, io);
+}
+
+int octax_step_host(octax_env *e, const uint8_t *actions_host, uint8_t *obs_host, float *reward_host,
+                    uint8_t *done_host) {
+  if (!e || !actions_host || !obs_host || !reward_host || !done_host) {
+    set_error("octax_step_host: null argument");
+    return OCTAX_EINVAL;
+  }
+  const size_t n = (size_t)e->n, obs_bytes = n * (size_t)e->S * kFrameBytes;
+  if (!e->hs_act) {
+    cudaError_t r = dalloc(e, &e->hs_act, n);
+    if (r == cudaSuccess) r = dalloc(e, &e->hs_obs, obs_bytes);
+    if (r == cudaSuccess) r = dalloc(e, &e->hs_rew, n);
+    if (r == cudaSuccess) r = dalloc(e, &e->hs_done, n);
+    if (r != cudaSuccess) {
+      set_error("octax_step_host: staging allocation failed");
+      return OCTAX_ENOMEM;
+    }
+  }
+  cudaError_t r = cudaMemcpyAsync(e->hs_act, actions_host, n, cudaMemcpyHostToDevice, e->stream);
+  if (r != cudaSuccess) return cuda_fail(r, "octax_step_host actions");
+  int rc = octax_step(e, e->hs_act, e->hs_obs, e->hs_rew, e->hs_done);
+  if (rc) return rc;
+  r = cudaMemcpyAsync(obs_host, e->hs_obs, obs_bytes, cudaMemcpyDeviceToHost, e->stream);
+  if (r == cudaSuccess) r = cudaMemcpyAsync(reward_host, e->hs_rew, n * 4, cudaMemcpyDeviceToHost, e->stream);
+  if (r == cudaSuccess) r = cudaMemcpyAsync(done_host, e->hs_done, n, cudaMemcpyDeviceToHost, e->stream);
+  if (r == cudaSuccess) r = cudaStreamSynchronize(e->stream);
+  return r == cudaSuccess ? OCTAX_OK : cuda_fail(r, "octax_step_host");
+}
+
+int octax_state_hash(octax_env *e, uint64_t *hash_dev) {
+  if (!e || !hash_dev) {
+    set_error("octax_state_hash: null argument");
+    return OCTAX_EINVAL;
+  }
+  cudaError_t r = launch_hash(e->st, e->images_d, e->slot_of_row_d, e->n, hash_dev, e->stream);
+  return r == cudaSuccess ? OCTAX_OK : cuda_fail(r, "octax_state_hash");
+}
+
+int octax_get_state(octax_env *e, int64_t first, int64_t count, octax_state_record *out_host) {
+  if (!e || !out_host || first < 0 || count < 0 || first + count > e->n) {
+    set_error("octax_get_state: range outside [0, n_envs) or null output");
+    return OCTAX_EINVAL;
+  }
+  if (count == 0) return OCTAX_OK;
+  octax_state_record *tmp = nullptr;
+  cudaError_t r = cudaMallocAsync(&tmp, count * sizeof(octax_state_record), e->stream);
+  if (r != cudaSuccess) return cuda_fail(r, "octax_get_state alloc");
+  r = launch_records(e->st, e->images_d, e->slot_of_row_d, first, count, tmp, e->stream);
+  if (r == cudaSuccess)
+    r = cudaMemcpyAsync(out_host, tmp, count * sizeof(octax_state_record), cudaMemcpyDeviceToHost, e->stream);
+  cudaFreeAsync(tmp, e->stream);
+  if (r == cudaSuccess) r = cudaStreamSynchronize(e->stream);
+  return r == cudaSuccess ? OCTAX_OK : cuda_fail(r, "octax_get_state");
+}
+
+int octax_set_state(octax_env *e, int64_t first, int64_t count, const octax_state_record *in_host) {
+  if (!e || !in_host || first < 0 || count < 0 || first + count > e->n) {
+    set_error("octax_set_state: range outside [0, n_envs) or null input");
+    return OCTAX_EINVAL;
+  }
+  for (int64_t i = 0; i < count; ++i)
+    if (in_host[i].SP > 16) {
+      set_error("octax_set_state: SP > 16");
+      return OCTAX_EINVAL;
+    }
+  if (count == 0) return OCTAX_OK;
+  octax_state_record *tmp = nullptr;
+  cudaError_t r = cudaMallocAsync(&tmp, count * sizeof(octax_state_record), e->stream);
+  if (r != cudaSuccess) return cuda_fail(r, "octax_set_state alloc");
+  r = cudaMemcpyAsync(tmp, in_host, count * sizeof(octax_state_record), cudaMemcpyHostToDevice, e->stream);
+  if (r == cudaSuccess)
+    r = launch_set_records(e->st, e->games_d, e->images_d, e->slot_of_row_d, first, count, tmp, e->stream);
+  cudaFreeAsync(tmp, e->stream);
+  if (r == cudaSuccess) r = cudaStreamSynchronize(e->stream);
+  return r == cudaSuccess ? OCTAX_OK : cuda_fail(r, "octax_set_state");
+}
+
+int octax_sync(octax_env *e, int timeout_ms) {
+  if (!e) {
+    set_error("octax_sync: null env");
+    return OCTAX_EINVAL;
+  }
+  cudaError_t r = cudaEventRecord(e->ev, e->stream);
+  if (r != cudaSuccess) return cuda_fail(r, "octax_sync record");
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    r = cudaEventQuery(e->ev);
+    if (r == cudaSuccess) return OCTAX_OK;
+    if (r != cudaErrorNotReady) return cuda_fail(r, "octax_sync");
+    if (timeout_ms >= 0 &&
+        std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms)) {
+      set_error("octax_sync: timed out");
+      return OCTAX_ETIMEOUT;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+int octax_get_launch(const octax_env *e, octax_launch *out) {
+  if (!e || !out) {
+    set_error("octax_get_launch: null argument");
+    return OCTAX_EINVAL;
+  }
+  *out = e->cfg;
+  return OCTAX_OK;
+}
+
+int octax_set_launch(octax_env *e, const octax_launch *cfg) {
+  if (!e || !cfg || !block_ok(cfg->block) || cfg->steps_per_launch < 1 || cfg->steps_per_launch > 64 ||
+      (cfg->persistent != 0 && cfg->persistent != 1) || (cfg->use_graph != 0 && cfg->use_graph != 1)) {
+    set_error("octax_set_launch: block in {32,64,128,256}, steps_per_launch 1..64, flags 0/1");
+    return OCTAX_EINVAL;
+  }
+  e->cfg = *cfg;
+  return OCTAX_OK;
+}
+
+int octax_autotune(octax_env *e, int n_steps, float *best_ms_out) {
+  if (!e || n_steps < 1) {
+    set_error("octax_autotune: need env and n_steps >= 1");
+    return OCTAX_EINVAL;
+  }
+  const size_t n = (size_t)e->n;
+  // back up the mutable state so that tuning leaves no trace
+  const DevState &st = e->st;
+  struct Piece {
+    void *p;
+    size_t bytes;
+  };
+  const Piece pieces[] = {{st.v, 16 * n},     {st.pcI, 4 * n},    {st.misc, 4 * n},
+                          {st.stack, 32 * n}, {st.disp, 256 * n}, {st.dirty, 8 * n},
+                          {st.ram, 4096 * n}, {st.ep, 4 * n},     {st.env_steps, 4 * n},
+                          {st.prev_score, 4 * n}};
+  size_t total = 0;
+  for (const Piece &pc : pieces) total += pc.bytes;
+  uint8_t *backup = nullptr, *acts = nullptr, *obs = nullptr, *done = nullptr;
+  float *rew = nullptr;
+  const size_t obs_bytes = (size_t)n_steps * n * e->S * kFrameBytes;
+  cudaError_t r = cudaMalloc(&backup, total);
+  if (r == cudaSuccess) r = cudaMalloc(&acts, (size_t)n_steps * n);
+  if (r == cudaSuccess) r = cudaMalloc(&obs, obs_bytes);
+  if (r == cudaSuccess) r = cudaMalloc((void **)&rew, (size_t)n_steps * n * 4);
+  if (r == cudaSuccess) r = cudaMalloc(&done, (size_t)n_steps * n);
+  if (r != cudaSuccess) {
+    cudaFree(backup);
+    cudaFree(acts);
+    cudaFree(obs);
+    cudaFree(rew);
+    cudaFree(done);
+    set_error("octax_autotune: scratch allocation failed");
+    return OCTAX_ENOMEM;
+  }
+  size_t off = 0;
+  for (const Piece &pc : pieces) {
+    cudaMemcpyAsync(backup + off, pc.p, pc.bytes, cudaMemcpyDeviceToDevice, e->stream);
+    off += pc.bytes;
+  }
+  cudaMemsetAsync(acts, 0, (size_t)n_steps * n, e->stream);
+  IO io{acts, obs, rew, done, e->n};
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  const octax_launch saved = e->cfg;
+  octax_launch best = saved;
+  float best_ms = 1e30f;
+  int rc = OCTAX_OK;
+  const int blocks[] = {32, 64, 128, 256};
+  const int spls[] = {1, 2, 4, 8};
+  for (int b : blocks) {
+    for (int pers = 0; pers < 2 && rc == OCTAX_OK; ++pers) {
+      for (int spl : spls) {
+        if (spl > n_steps) continue;
+        octax_launch c{b, spl, pers, 1};
+        rc = enqueue_steps(e, c, n_steps, io);  // warm-up (graph build)
+        if (rc) break;
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 3 && rc == OCTAX_OK; ++rep) {
+          cudaEventRecord(t0, e->stream);
+          rc = enqueue_steps(e, c, n_steps, io);
+          cudaEventRecord(t1, e->stream);
+          cudaEventSynchronize(t1);
+          float ms = 0;
+          cudaEventElapsedTime(&ms, t0, t1);
+          ms_min = std::min(ms_min, ms);
+        }
+        if (rc == OCTAX_OK && ms_min < best_ms) {
+          best_ms = ms_min;
+          best = c;
+        }
+      }
+    }
+  }
+  off = 0;
+  for (const Piece &pc : pieces) {
+    cudaMemcpyAsync(pc.p, backup + off, pc.bytes, cudaMemcpyDeviceToDevice, e->stream);
+    off += pc.bytes;
+  }
+  r = cudaStreamSynchronize(e->stream);
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  cudaFree(backup);
+  cudaFree(acts);
+  cudaFree(obs);
+  cudaFree(rew);
+  cudaFree(done);
+  if (rc) return rc;
+  if (r != cudaSuccess) return cuda_fail(r, "octax_autotune");
+  e->cfg = best;
+  if (best_ms_out) *best_ms_out = best_ms;
+  return OCTAX_OK;
+}
+
+int64_t octax_num_envs(const octax_env *e) { return e ? e->n : -1; }
+int octax_stack_frames(const octax_env *e) { return e ? e->S : -1; }
+size_t octax_device_bytes(const octax_env *e) { return e ? e->bytes : 0; }
+
+void octax_destroy(octax_env *e) { free_env(e); }
+
+}  // extern "C"

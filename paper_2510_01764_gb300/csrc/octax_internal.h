@@ -1,0 +1,124 @@
+// Internal declarations shared by the liboctax translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "octax.h"
+
+namespace octax {
+
+constexpr int kRamBytes = 4096;
+constexpr int kPageShift = 6;               // 64-byte RAM pages: 64 pages -> one u64 mask
+constexpr int kFrameBytes = 32 * 64;        // one uint8 observation frame
+constexpr int kMaxBlock = 256;
+
+// Game descriptor as the kernels read it (one per game, device memory).
+struct TermDev {
+  uint8_t src, xform;
+  uint16_t idx;
+  int32_t arg;
+};
+struct ClauseDev {
+  TermDev lhs;
+  int32_t cmp;
+  int32_t rhs;
+};
+struct alignas(16) GameDev {
+  uint32_t K, frameskip, n_actions, n_score, n_term, max_steps, startup, pad;
+  uint8_t action_set[16];
+  TermDev score[4];
+  ClauseDev term[4];
+};
+static_assert(sizeof(GameDev) <= 192, "GameDev must fit its shared-memory slot");
+constexpr int kGameSmem = 192;
+
+// Emulator state, structure-of-arrays over slots (slot = index in these arrays).
+struct DevState {
+  int64_t n;              // slots
+  uint32_t *v;            // [4][n]   V[4j..4j+3] little-endian in word j
+  uint32_t *pcI;          // [n]      PC | I << 16
+  uint32_t *misc;         // [n]      SP | DT << 8 | ST << 16 | status << 24
+  uint16_t *stack;        // [16][n]
+  uint64_t *disp;         // [32][n]  bit x of word y = pixel (x, y)
+  uint64_t *dirty;        // [n]      RAM pages that differ from the ROM image
+  uint8_t *ram;           // [n][4096] per-instance RAM (valid on dirty pages only)
+  uint32_t *ep;           // [n]      steps since reset
+  uint32_t *env_steps;    // [n]      steps since creation
+  int32_t *prev_score;    // [n]      score at the end of the last step / reset
+  uint32_t *key;          // [2][n]   Philox key
+  uint32_t *uid;          // [n]      Philox counter word 0
+  uint32_t *out_row;      // [n]      row of this slot in its request's outputs
+  uint16_t *game;         // [n]
+};
+
+// A group: up to `block` consecutive slots that share one game (one CTA's work).
+struct Group {
+  uint32_t slot0;
+  uint16_t count;
+  uint16_t game;
+  uint32_t io;            // index into the IO table (0 when launched with io0)
+  uint32_t pad;
+};
+
+// Where one request's per-step inputs and outputs live.
+struct IO {
+  const uint8_t *actions;  // [steps][rows]
+  uint8_t *obs;            // [steps][rows][S][32][64]
+  float *reward;           // [steps][rows]
+  uint8_t *done;           // [steps][rows]
+  int64_t rows;            // rows per step
+};
+
+struct StepLaunch {
+  DevState st;
+  const GameDev *games;
+  const uint8_t *images;   // [n_games][4096] initial RAM image (font + ROM)
+  const Group *groups;
+  int n_groups;
+  IO io0;                  // used when io_table == nullptr
+  const IO *io_table;
+  int step0;               // output step index of this launch's first step
+  int steps;               // env steps in this launch
+  int S;                   // stack frames
+  uint32_t quirks;
+  unsigned int *work_counter;  // non-null: persistent CTAs pull groups from it
+};
+
+struct ResetLaunch {
+  DevState st;
+  const GameDev *games;
+  const uint8_t *images;
+  const Group *groups;
+  int n_groups;
+  const uint8_t *mask;     // [n_out_rows] by out_row, nullable = all
+  uint8_t *obs;            // [rows][S][32][64] by out_row, nullable
+  int S;
+  uint32_t quirks;
+  int init;                // 1: also set key/uid/env_steps/status (creation)
+  uint64_t seed;
+  const uint32_t *uid_of_slot;  // used when init (nullable = out_row)
+};
+
+size_t step_smem_bytes(int block);
+cudaError_t launch_step(const StepLaunch &p, int grid, int block, cudaStream_t s);
+cudaError_t launch_reset(const ResetLaunch &p, int block, cudaStream_t s);
+cudaError_t launch_hash(const DevState &st, const uint8_t *images, const uint32_t *slot_of_row,
+                        int64_t rows, uint64_t *out, cudaStream_t s);
+cudaError_t launch_records(const DevState &st, const uint8_t *images, const uint32_t *slot_of_row,
+                           int64_t first, int64_t count, octax_state_record *out, cudaStream_t s);
+cudaError_t launch_set_records(const DevState &st, const GameDev *games, const uint8_t *images,
+                               const uint32_t *slot_of_row, int64_t first, int64_t count,
+                               const octax_state_record *in, cudaStream_t s);
+int max_resident_ctas(int block);
+// Append one step launch to a graph (after `dep`, if non-null).
+cudaError_t add_step_node(cudaGraph_t g, cudaGraphNode_t *node, cudaGraphNode_t dep, const StepLaunch &p,
+                          int grid, int block);
+
+// Error reporting (thread-local message).
+void set_error(const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+}  // namespace octax

@@ -1,0 +1,845 @@
+// liboctax device code: the vectorised CHIP-8 environment step for sm_103a.
+//
+// Mapping (one CTA = one group of up to `block` instances of one game):
+//  - one thread emulates one instance; V0-VF live in four 32-bit registers,
+//    PC/I/SP/timers/status in registers, the call stack and the bit-packed
+//    64x32 display (one u64 per row, bit x = pixel x) in shared memory, laid
+//    out [row][instance] so a warp touching its own rows never bank-conflicts;
+//  - the game's initial 4 KB RAM image (font + ROM) is staged once per CTA in
+//    shared memory and is read-only; an instance's writes go to 64-byte pages
+//    of its own RAM in global memory, tracked by a 64-bit dirty mask kept in a
+//    register. Fetches and loads read the shared image unless the page is
+//    dirty, and a reset only clears the mask;
+//  - observation frames are expanded from the packed rows by the whole warp
+//    together: every store is a 16-byte streaming store and each store
+//    instruction writes eight complete 64-byte image rows.
+// Each instance runs exactly K instructions per frame, so all lanes of a warp
+// meet at every frame boundary.
+#include <cstring>
+
+#include "octax_internal.h"
+
+namespace octax {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+struct Regs {
+  uint32_t v0, v1, v2, v3;  // V0..VF, byte j of vk = V[4k + j]
+  uint32_t pc, I, sp, dt, st, status;
+  uint64_t dirty;
+  uint32_t draws, phase, env_steps;
+  uint32_t key0, key1, uid;
+};
+
+struct Ctx {
+  const uint8_t *img;  // shared: initial RAM image of this CTA's game
+  uint64_t *disp;      // shared: this instance's row 0; row r at disp[r * B]
+  uint32_t *stack;     // shared: this instance's entry 0; entry i at stack[i * B]
+  uint8_t *ram;        // global: this instance's 4 KB RAM (dirty pages)
+  int B;
+};
+
+__device__ __forceinline__ uint32_t getV(const Regs &R, uint32_t x) {
+  uint32_t lo = (x & 8u) ? R.v2 : R.v0;
+  uint32_t hi = (x & 8u) ? R.v3 : R.v1;
+  return __byte_perm(lo, hi, x & 7u) & 0xFFu;
+}
+
+__device__ __forceinline__ void setV(Regs &R, uint32_t x, uint32_t val) {
+  const uint32_t sh = (x & 3u) * 8u;
+  const uint32_t keep = ~(0xFFu << sh), ins = (val & 0xFFu) << sh;
+  const uint32_t w = x >> 2;
+  R.v0 = (w == 0) ? ((R.v0 & keep) | ins) : R.v0;
+  R.v1 = (w == 1) ? ((R.v1 & keep) | ins) : R.v1;
+  R.v2 = (w == 2) ? ((R.v2 & keep) | ins) : R.v2;
+  R.v3 = (w == 3) ? ((R.v3 & keep) | ins) : R.v3;
+}
+
+__device__ __forceinline__ void setVF(Regs &R, uint32_t f) { R.v3 = (R.v3 & 0x00FFFFFFu) | (f << 24); }
+
+__device__ __forceinline__ uint32_t rd8(const Regs &R, const Ctx &C, uint32_t a) {
+  a &= 0xFFFu;
+  return ((R.dirty >> (a >> kPageShift)) & 1u) ? (uint32_t)C.ram[a] : (uint32_t)C.img[a];
+}
+
+__device__ __forceinline__ void wr8(Regs &R, const Ctx &C, uint32_t a, uint32_t val) {
+  a &= 0xFFFu;
+  const uint32_t page = a >> kPageShift;
+  if (!((R.dirty >> page) & 1u)) {  // first write to this page: copy it from the image
+    const uint4 *src = reinterpret_cast<const uint4 *>(C.img + (page << kPageShift));
+    uint4 *dst = reinterpret_cast<uint4 *>(C.ram + (page << kPageShift));
+    dst[0] = src[0];
+    dst[1] = src[1];
+    dst[2] = src[2];
+    dst[3] = src[3];
+    R.dirty |= 1ull << page;
+  }
+  C.ram[a] = (uint8_t)val;
+}
+
+// Philox4x32-10 (Salmon et al., SC'11); word 0 of the output block.
+__device__ __forceinline__ uint32_t philox_w0(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                              uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return c0;
+}
+
+__device__ __forceinline__ void tick(Regs &R) {
+  R.dt -= (R.dt > 0);
+  R.st -= (R.st > 0);
+}
+
+// DXYN: XOR an 8-wide, n-row sprite at (vx mod 64, vy mod 32); VF = collision.
+__device__ __forceinline__ void draw(Regs &R, const Ctx &C, uint32_t vx, uint32_t vy, uint32_t n,
+                                     uint32_t quirks) {
+  const uint32_t x0 = vx & 63u, y0 = vy & 31u;
+  const bool wrap = quirks & OCTAX_QUIRK_WRAP_SPRITES;
+  uint32_t coll = 0;
+  for (uint32_t r = 0; r < n; ++r) {
+    uint32_t py = y0 + r;
+    if (py >= 32u) {
+      if (!wrap) break;
+      py &= 31u;
+    }
+    const uint32_t rev = __brev(rd8(R, C, R.I + r)) >> 24;  // pixel j of the sprite -> bit j
+    uint64_t s = (uint64_t)rev << x0;                      // right edge clips
+    if (wrap && x0 > 56u) s |= (uint64_t)rev >> (64u - x0);
+    uint64_t *row = C.disp + py * C.B;
+    const uint64_t old = *row;
+    coll |= (old & s) != 0ull;
+    *row = old ^ s;
+  }
+  setVF(R, coll);
+}
+
+// One fetch / decode / execute cycle. key: held CHIP-8 key or -1.
+__device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_t quirks) {
+  const uint32_t pc = R.pc;
+  uint32_t op;
+  if (!((pc & 1u) | (uint32_t)((R.dirty >> (pc >> kPageShift)) & 1u))) {
+    op = __byte_perm(*reinterpret_cast<const uint16_t *>(C.img + pc), 0u, 0x4401);
+  } else {
+    op = (rd8(R, C, pc) << 8) | rd8(R, C, pc + 1u);
+  }
+  R.pc = (pc + 2u) & 0xFFFu;
+  const uint32_t x = (op >> 8) & 15u, y = (op >> 4) & 15u, n = op & 15u, nn = op & 0xFFu;
+  const uint32_t nnn = op & 0xFFFu;
+  const uint32_t vx = getV(R, x), vy = getV(R, y);
+  switch (op >> 12) {
+    case 0x0:
+      if (op == 0x00E0u) {
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) C.disp[r * C.B] = 0ull;
+      } else if (op == 0x00EEu) {
+        if (R.sp == 0) {
+          R.status |= OCTAX_STATUS_STACK_FAULT;
+          R.sp = 16;
+        }
+        R.sp -= 1;
+        R.pc = C.stack[R.sp * C.B];
+      }
+      break;
+    case 0x1:
+      R.pc = nnn;
+      break;
+    case 0x2:
+      if (R.sp == 16) {
+        R.status |= OCTAX_STATUS_STACK_FAULT;
+        R.sp = 0;
+      }
+      C.stack[R.sp * C.B] = R.pc;
+      R.sp += 1;
+      R.pc = nnn;
+      break;
+    case 0x3:
+      if (vx == nn) R.pc = (R.pc + 2u) & 0xFFFu;
+      break;
+    case 0x4:
+      if (vx != nn) R.pc = (R.pc + 2u) & 0xFFFu;
+      break;
+    case 0x5:
+      if (n) R.status |= OCTAX_STATUS_BAD_OP;
+      else if (vx == vy) R.pc = (R.pc + 2u) & 0xFFFu;
+      break;
+    case 0x6:
+      setV(R, x, nn);
+      break;
+    case 0x7:
+      setV(R, x, vx + nn);
+      break;
+    case 0x8:
+      switch (n) {
+        case 0x0: setV(R, x, vy); break;
+        case 0x1:
+          setV(R, x, vx | vy);
+          if (quirks & OCTAX_QUIRK_LOGIC_RESETS_VF) setVF(R, 0);
+          break;
+        case 0x2:
+          setV(R, x, vx & vy);
+          if (quirks & OCTAX_QUIRK_LOGIC_RESETS_VF) setVF(R, 0);
+          break;
+        case 0x3:
+          setV(R, x, vx ^ vy);
+          if (quirks & OCTAX_QUIRK_LOGIC_RESETS_VF) setVF(R, 0);
+          break;
+        case 0x4: {
+          const uint32_t s = vx + vy;
+          setV(R, x, s);
+          setVF(R, s >> 8);
+          break;
+        }
+        case 0x5:
+          setV(R, x, vx - vy);
+          setVF(R, vx >= vy);
+          break;
+        case 0x6: {
+          const uint32_t src = (quirks & OCTAX_QUIRK_SHIFT_USES_VY) ? vy : vx;
+          setV(R, x, src >> 1);
+          setVF(R, src & 1u);
+          break;
+        }
+        case 0x7:
+          setV(R, x, vy - vx);
+          setVF(R, vy >= vx);
+          break;
+        case 0xE: {
+          const uint32_t src = (quirks & OCTAX_QUIRK_SHIFT_USES_VY) ? vy : vx;
+          setV(R, x, src << 1);
+          setVF(R, src >> 7);
+          break;
+        }
+        default:
+          R.status |= OCTAX_STATUS_BAD_OP;
+          break;
+      }
+      break;
+    case 0x9:
+      if (n) R.status |= OCTAX_STATUS_BAD_OP;
+      else if (vx != vy) R.pc = (R.pc + 2u) & 0xFFFu;
+      break;
+    case 0xA:
+      R.I = nnn;
+      break;
+    case 0xB:
+      R.pc = (nnn + ((quirks & OCTAX_QUIRK_JUMP_VX) ? vx : (R.v0 & 0xFFu))) & 0xFFFu;
+      break;
+    case 0xC: {
+      const uint32_t rnd = philox_w0(R.uid, R.env_steps, pc | ((R.draws & 0xFFFFu) << 16), R.phase,
+                                     R.key0, R.key1);
+      R.draws += 1;
+      setV(R, x, rnd & nn);
+      break;
+    }
+    case 0xD:
+      draw(R, C, vx, vy, n, quirks);
+      break;
+    case 0xE: {
+      const bool pressed = key >= 0 && (uint32_t)key == (vx & 15u);
+      if (nn == 0x9Eu) {
+        if (pressed) R.pc = (R.pc + 2u) & 0xFFFu;
+      } else if (nn == 0xA1u) {
+        if (!pressed) R.pc = (R.pc + 2u) & 0xFFFu;
+      } else {
+        R.status |= OCTAX_STATUS_BAD_OP;
+      }
+      break;
+    }
+    default:  // 0xF
+      switch (nn) {
+        case 0x07: setV(R, x, R.dt); break;
+        case 0x0A:
+          if (key >= 0) setV(R, x, (uint32_t)key);
+          else R.pc = pc;
+          break;
+        case 0x15: R.dt = vx; break;
+        case 0x18: R.st = vx; break;
+        case 0x1E: {
+          const uint32_t s = R.I + vx;
+          R.I = s & 0xFFFFu;
+          if (quirks & OCTAX_QUIRK_FX1E_VF) setVF(R, s > 0xFFFu);
+          break;
+        }
+        case 0x29: R.I = 0x50u + 5u * (vx & 15u); break;
+        case 0x33:
+          wr8(R, C, R.I, vx / 100u);
+          wr8(R, C, R.I + 1u, (vx / 10u) % 10u);
+          wr8(R, C, R.I + 2u, vx % 10u);
+          break;
+        case 0x55:
+          for (uint32_t i = 0; i <= x; ++i) wr8(R, C, R.I + i, getV(R, i));
+          if (quirks & OCTAX_QUIRK_LOADSTORE_INC_I) R.I = (R.I + x + 1u) & 0xFFFFu;
+          break;
+        case 0x65:
+          for (uint32_t i = 0; i <= x; ++i) setV(R, i, rd8(R, C, R.I + i));
+          if (quirks & OCTAX_QUIRK_LOADSTORE_INC_I) R.I = (R.I + x + 1u) & 0xFFFFu;
+          break;
+        default:
+          R.status |= OCTAX_STATUS_BAD_OP;
+          break;
+      }
+      break;
+  }
+}
+
+__device__ __forceinline__ int32_t term_value(const Regs &R, const Ctx &C, const TermDev &t) {
+  const int32_t v = t.src == OCTAX_SRC_REG ? (int32_t)getV(R, t.idx & 15u) : (int32_t)rd8(R, C, t.idx);
+  switch (t.xform) {
+    case OCTAX_X_RAW: return v;
+    case OCTAX_X_NEG: return -v;
+    case OCTAX_X_DEC_TENS: return v / 10;
+    case OCTAX_X_DEC_ONES: return v % 10;
+    case OCTAX_X_DEC_TENS_MINUS_ONES: return v / 10 - v % 10;
+    case OCTAX_X_NIB_HI_MINUS_LO: return (v >> 4) - (v & 15);
+    case OCTAX_X_ZERO_IF_GT: return v > t.arg ? 0 : v;
+    default: return 0;
+  }
+}
+
+__device__ __forceinline__ int32_t score(const Regs &R, const Ctx &C, const GameDev &G) {
+  int32_t s = 0;
+  for (uint32_t i = 0; i < G.n_score; ++i) s += term_value(R, C, G.score[i]);
+  return s;
+}
+
+__device__ __forceinline__ bool terminated(const Regs &R, const Ctx &C, const GameDev &G) {
+  bool hit = false;
+  for (uint32_t i = 0; i < G.n_term; ++i) {
+    const ClauseDev &c = G.term[i];
+    const int32_t v = term_value(R, C, c.lhs);
+    switch (c.cmp) {
+      case OCTAX_CMP_EQ: hit |= v == c.rhs; break;
+      case OCTAX_CMP_NE: hit |= v != c.rhs; break;
+      case OCTAX_CMP_GE: hit |= v >= c.rhs; break;
+      case OCTAX_CMP_GT: hit |= v > c.rhs; break;
+      case OCTAX_CMP_LE: hit |= v <= c.rhs; break;
+      case OCTAX_CMP_LT: hit |= v < c.rhs; break;
+      default: break;
+    }
+  }
+  return hit;
+}
+
+// Power-on state + the game's startup instructions (no key, timers tick every K).
+__device__ __forceinline__ void reset_instance(Regs &R, const Ctx &C, const GameDev &G, uint32_t quirks) {
+  R.v0 = R.v1 = R.v2 = R.v3 = 0;
+  R.pc = 0x200;
+  R.I = 0;
+  R.sp = 0;
+  R.dt = 0;
+  R.st = 0;
+  R.dirty = 0;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) C.stack[i * C.B] = 0;
+#pragma unroll 8
+  for (int r = 0; r < 32; ++r) C.disp[r * C.B] = 0ull;
+  R.phase = 1;
+  R.draws = 0;
+  uint32_t in_frame = 0;
+  for (uint32_t i = 0; i < G.startup; ++i) {
+    exec_one(R, C, -1, quirks);
+    if (++in_frame == G.K) {
+      tick(R);
+      in_frame = 0;
+    }
+  }
+  R.phase = 0;
+  R.draws = 0;
+}
+
+// 4 pixels (bits 0..3) -> 4 bytes of value 0/1 (byte j = bit j).
+__device__ __forceinline__ uint32_t spread4(uint32_t nib) { return (nib * 0x00204081u) & 0x01010101u; }
+
+__device__ __forceinline__ uint4 expand16(uint64_t row, uint32_t q) {
+  const uint32_t bits = (uint32_t)(row >> (16u * q)) & 0xFFFFu;
+  uint4 o;
+  o.x = spread4(bits & 15u);
+  o.y = spread4((bits >> 4) & 15u);
+  o.z = spread4((bits >> 8) & 15u);
+  o.w = spread4(bits >> 12);
+  return o;
+}
+
+// Whole-warp frame write: lane -> instance 8m + lane/4 of the warp, quarter
+// lane%4 of every row. frame (per lane, 0 = skip) points at the 2 KB frame of
+// that lane's own instance.
+__device__ __forceinline__ void capture_frame(const uint64_t *disp_warp, int B, uint8_t *frame,
+                                              int lane) {
+  const uint64_t mine = reinterpret_cast<uint64_t>(frame);
+  const uint32_t q = lane & 3;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int src = 8 * m + (lane >> 2);
+    const uint64_t base = __shfl_sync(kFull, mine, src);
+    if (base) {
+      const uint64_t *col = disp_warp + src;
+      uint8_t *dst = reinterpret_cast<uint8_t *>(base) + q * 16u;
+#pragma unroll 8
+      for (int r = 0; r < 32; ++r) __stcs(reinterpret_cast<uint4 *>(dst + r * 64), expand16(col[r * B], q));
+    }
+  }
+}
+
+// Whole-warp write of the reset observation (display repeated S times) for
+// every lane whose bit is set in `which`. obs: that lane's S-frame block.
+__device__ __forceinline__ void write_reset_obs(const uint64_t *disp_warp, int B, uint8_t *obs, int S,
+                                                unsigned which, int lane) {
+  const uint64_t mine = reinterpret_cast<uint64_t>(obs);
+  while (which) {
+    const int src = __ffs(which) - 1;
+    which &= which - 1;
+    const uint64_t base = __shfl_sync(kFull, mine, src);
+    const uint64_t *col = disp_warp + src;
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int c = it * 32 + lane;  // 16-byte chunk of the 2 KB frame
+      const uint4 o = expand16(col[(c >> 2) * B], c & 3);
+      for (int s = 0; s < S; ++s)
+        __stcs(reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(base) + s * kFrameBytes + c * 16), o);
+    }
+  }
+}
+
+struct Smem {
+  uint8_t *img;
+  GameDev *game;
+  uint64_t *disp;
+  uint32_t *stack;
+};
+
+__device__ __forceinline__ Smem carve(uint8_t *smem, int B) {
+  Smem s;
+  s.img = smem;
+  s.game = reinterpret_cast<GameDev *>(smem + kRamBytes);
+  s.disp = reinterpret_cast<uint64_t *>(smem + kRamBytes + kGameSmem);
+  s.stack = reinterpret_cast<uint32_t *>(s.disp + 32 * B);
+  return s;
+}
+
+__device__ __forceinline__ void stage_game(const Smem &S, const GameDev *games, const uint8_t *images,
+                                           int game) {
+  const uint4 *src = reinterpret_cast<const uint4 *>(images + (size_t)game * kRamBytes);
+  uint4 *dst = reinterpret_cast<uint4 *>(S.img);
+  for (int i = threadIdx.x; i < kRamBytes / 16; i += blockDim.x) dst[i] = src[i];
+  const uint4 *gs = reinterpret_cast<const uint4 *>(games + game);
+  uint4 *gd = reinterpret_cast<uint4 *>(S.game);
+  for (int i = threadIdx.x; i < (int)(sizeof(GameDev) / 16); i += blockDim.x) gd[i] = gs[i];
+}
+
+__device__ __forceinline__ void load_regs(Regs &R, const DevState &st, int64_t slot) {
+  const int64_t n = st.n;
+  R.v0 = st.v[slot];
+  R.v1 = st.v[n + slot];
+  R.v2 = st.v[2 * n + slot];
+  R.v3 = st.v[3 * n + slot];
+  const uint32_t pcI = st.pcI[slot], misc = st.misc[slot];
+  R.pc = pcI & 0xFFFFu;
+  R.I = pcI >> 16;
+  R.sp = misc & 0xFFu;
+  R.dt = (misc >> 8) & 0xFFu;
+  R.st = (misc >> 16) & 0xFFu;
+  R.status = misc >> 24;
+  R.dirty = st.dirty[slot];
+  R.env_steps = st.env_steps[slot];
+  R.key0 = st.key[slot];
+  R.key1 = st.key[n + slot];
+  R.uid = st.uid[slot];
+  R.draws = 0;
+  R.phase = 0;
+}
+
+__device__ __forceinline__ void store_regs(const Regs &R, const DevState &st, int64_t slot) {
+  const int64_t n = st.n;
+  st.v[slot] = R.v0;
+  st.v[n + slot] = R.v1;
+  st.v[2 * n + slot] = R.v2;
+  st.v[3 * n + slot] = R.v3;
+  st.pcI[slot] = R.pc | (R.I << 16);
+  st.misc[slot] = R.sp | (R.dt << 8) | (R.st << 16) | (R.status << 24);
+  st.dirty[slot] = R.dirty;
+  st.env_steps[slot] = R.env_steps;
+}
+
+__device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
+  const int B = blockDim.x, t = threadIdx.x, lane = t & 31, wbase = t & ~31;
+  const DevState &st = p.st;
+  const int64_t n = st.n;
+  const GameDev &G = *S.game;
+  const bool active = t < (int)g.count;
+  const int64_t slot = (int64_t)g.slot0 + (active ? t : 0);
+  const IO io = p.io_table ? p.io_table[g.io] : p.io0;
+  const uint32_t quirks = p.quirks;
+
+  Regs R;
+  load_regs(R, st, slot);
+  const int64_t row = active ? (int64_t)st.out_row[slot] : 0;
+  uint32_t ep = st.ep[slot];
+  int32_t prev = st.prev_score[slot];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) S.stack[i * B + t] = st.stack[i * n + slot];
+#pragma unroll 8
+  for (int r = 0; r < 32; ++r) S.disp[r * B + t] = st.disp[r * n + slot];
+  const Ctx C{S.img, S.disp + t, S.stack + t, st.ram + slot * (int64_t)kRamBytes, B};
+  const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
+  __syncwarp();
+
+  for (int s = 0; s < p.steps; ++s) {
+    const int64_t io_row = (int64_t)(p.step0 + s) * io.rows + row;
+    int key = -1;
+    uint8_t *my_obs = nullptr;
+    if (active) {
+      const uint32_t a = io.actions[io_row];
+      if (a < G.n_actions) key = G.action_set[a] & 15;
+      else if (a > G.n_actions) R.status |= OCTAX_STATUS_BAD_ACTION;
+      my_obs = io.obs + io_row * (int64_t)p.S * kFrameBytes;
+    }
+    R.draws = 0;
+    R.phase = 0;
+    for (uint32_t f = 0; f < FS; ++f) {
+      if (active) {
+        for (uint32_t k = 0; k < K; ++k) exec_one(R, C, key, quirks);
+        tick(R);
+      }
+      if (f >= first_kept) {
+        __syncwarp();
+        capture_frame(S.disp + wbase, B, my_obs ? my_obs + (f - first_kept) * kFrameBytes : nullptr,
+                      lane);
+        __syncwarp();
+      }
+    }
+    bool done = false;
+    if (active) {
+      const int32_t sc = score(R, C, G);
+      ep += 1;
+      R.env_steps += 1;
+      done = terminated(R, C, G) || (G.max_steps != 0 && ep >= G.max_steps);
+      io.reward[io_row] = (float)(sc - prev);
+      io.done[io_row] = done ? 1 : 0;
+      if (done) {
+        reset_instance(R, C, G, quirks);
+        ep = 0;
+        prev = score(R, C, G);
+      } else {
+        prev = sc;
+      }
+    }
+    const unsigned which = __ballot_sync(kFull, done);
+    if (which) {
+      __syncwarp();
+      write_reset_obs(S.disp + wbase, B, my_obs, p.S, which, lane);
+      __syncwarp();
+    }
+  }
+
+  if (active) {
+    store_regs(R, st, slot);
+    st.ep[slot] = ep;
+    st.prev_score[slot] = prev;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) st.stack[i * n + slot] = (uint16_t)S.stack[i * B + t];
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) st.disp[r * n + slot] = S.disp[r * B + t];
+  }
+}
+
+__global__ void __launch_bounds__(kMaxBlock) step_kernel(const StepLaunch p) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const Smem S = carve(smem, blockDim.x);
+  __shared__ int s_group;
+  int cur_game = -1;
+  int gi = blockIdx.x;
+  for (;;) {
+    if (p.work_counter) {
+      if (threadIdx.x == 0) s_group = (int)atomicAdd(p.work_counter, 1u);
+      __syncthreads();
+      gi = s_group;
+    }
+    if (gi >= p.n_groups) break;
+    const Group g = p.groups[gi];
+    if ((int)g.game != cur_game) {
+      stage_game(S, p.games, p.images, g.game);
+      cur_game = g.game;
+    }
+    __syncthreads();
+    run_group(p, g, S);
+    __syncthreads();  // shared memory is reused by the next group
+    if (!p.work_counter) break;
+  }
+}
+
+__global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const Smem S = carve(smem, blockDim.x);
+  const Group g = p.groups[blockIdx.x];
+  stage_game(S, p.games, p.images, g.game);
+  __syncthreads();
+  const int B = blockDim.x, t = threadIdx.x, lane = t & 31, wbase = t & ~31;
+  const DevState &st = p.st;
+  const int64_t n = st.n;
+  const GameDev &G = *S.game;
+  const bool active = t < (int)g.count;
+  const int64_t slot = (int64_t)g.slot0 + (active ? t : 0);
+  const int64_t row = active ? (int64_t)st.out_row[slot] : 0;
+  const bool doit = active && (p.mask == nullptr || p.mask[row] != 0);
+  Regs R;
+  if (p.init) {
+    R.status = 0;
+    R.env_steps = 0;
+    R.key0 = (uint32_t)(p.seed & 0xFFFFFFFFu);
+    R.key1 = (uint32_t)(p.seed >> 32);
+    R.uid = p.uid_of_slot ? p.uid_of_slot[slot] : (uint32_t)row;
+  } else {
+    load_regs(R, st, slot);
+  }
+  const Ctx C{S.img, S.disp + t, S.stack + t, st.ram + slot * (int64_t)kRamBytes, B};
+  if (doit) reset_instance(R, C, G, p.quirks);
+  const unsigned which = __ballot_sync(kFull, doit);
+  if (p.obs && which) {
+    __syncwarp();
+    write_reset_obs(S.disp + wbase, B, doit ? p.obs + row * (int64_t)p.S * kFrameBytes : nullptr, p.S,
+                    which, lane);
+    __syncwarp();
+  }
+  if (doit) {
+    store_regs(R, st, slot);
+    st.ep[slot] = 0;
+    st.prev_score[slot] = score(R, C, G);
+    if (p.init) {
+      st.key[slot] = R.key0;
+      st.key[n + slot] = R.key1;
+      st.uid[slot] = R.uid;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) st.stack[i * n + slot] = (uint16_t)S.stack[i * B + t];
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) st.disp[r * n + slot] = S.disp[r * B + t];
+  }
+}
+
+// RAM byte of a slot as the program sees it.
+__device__ __forceinline__ uint8_t ram_byte(const DevState &st, const uint8_t *img, int64_t slot,
+                                            uint64_t dirty, uint32_t a) {
+  return ((dirty >> (a >> kPageShift)) & 1u) ? st.ram[slot * (int64_t)kRamBytes + a] : img[a];
+}
+
+__device__ __forceinline__ uint64_t fnv_byte(uint64_t h, uint32_t b) {
+  return (h ^ (uint64_t)(b & 0xFFu)) * 1099511628211ull;
+}
+
+__global__ void hash_kernel(const DevState st, const uint8_t *images, const uint32_t *slot_of_row,
+                            int64_t rows, uint64_t *out) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= rows) return;
+  const int64_t slot = slot_of_row[row];
+  const int64_t n = st.n;
+  const uint8_t *img = images + (size_t)st.game[slot] * kRamBytes;
+  uint64_t h = 14695981039346656037ull;
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t w = st.v[j * n + slot];
+    for (int b = 0; b < 4; ++b) h = fnv_byte(h, w >> (8 * b));
+  }
+  const uint32_t pcI = st.pcI[slot], misc = st.misc[slot];
+  const uint32_t I = pcI >> 16, PC = pcI & 0xFFFFu;
+  h = fnv_byte(h, I);
+  h = fnv_byte(h, I >> 8);
+  h = fnv_byte(h, PC);
+  h = fnv_byte(h, PC >> 8);
+  for (int b = 0; b < 4; ++b) h = fnv_byte(h, misc >> (8 * b));  // SP DT ST status
+  for (int i = 0; i < 16; ++i) {
+    const uint32_t e = st.stack[i * n + slot];
+    h = fnv_byte(h, e);
+    h = fnv_byte(h, e >> 8);
+  }
+  for (int r = 0; r < 32; ++r) {
+    const uint64_t w = st.disp[r * n + slot];
+    for (int b = 0; b < 8; ++b) h = fnv_byte(h, (uint32_t)(w >> (8 * b)));
+  }
+  const uint64_t dirty = st.dirty[slot];
+  for (uint32_t a = 0; a < (uint32_t)kRamBytes; ++a) h = fnv_byte(h, ram_byte(st, img, slot, dirty, a));
+  const uint32_t ep = st.ep[slot], es = st.env_steps[slot];
+  for (int b = 0; b < 4; ++b) h = fnv_byte(h, ep >> (8 * b));
+  for (int b = 0; b < 4; ++b) h = fnv_byte(h, es >> (8 * b));
+  out[row] = h;
+}
+
+__global__ void records_kernel(const DevState st, const uint8_t *images, const uint32_t *slot_of_row,
+                               int64_t first, int64_t count, octax_state_record *out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int64_t slot = slot_of_row[first + i];
+  const int64_t n = st.n;
+  octax_state_record &rec = out[i];
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t w = st.v[j * n + slot];
+    for (int b = 0; b < 4; ++b) rec.V[4 * j + b] = (uint8_t)(w >> (8 * b));
+  }
+  const uint32_t pcI = st.pcI[slot], misc = st.misc[slot];
+  rec.PC = (uint16_t)(pcI & 0xFFFFu);
+  rec.I = (uint16_t)(pcI >> 16);
+  rec.SP = (uint8_t)misc;
+  rec.DT = (uint8_t)(misc >> 8);
+  rec.ST = (uint8_t)(misc >> 16);
+  rec.status = (uint8_t)(misc >> 24);
+  for (int k = 0; k < 16; ++k) rec.stack[k] = st.stack[k * n + slot];
+  for (int r = 0; r < 32; ++r) rec.display[r] = st.disp[r * n + slot];
+  const uint8_t *img = images + (size_t)st.game[slot] * kRamBytes;
+  const uint64_t dirty = st.dirty[slot];
+  for (uint32_t a = 0; a < (uint32_t)kRamBytes; ++a) rec.ram[a] = ram_byte(st, img, slot, dirty, a);
+  rec.episode_steps = st.ep[slot];
+  rec.env_steps = st.env_steps[slot];
+}
+
+__global__ void set_records_kernel(const DevState st, const GameDev *games, const uint8_t *images,
+                                   const uint32_t *slot_of_row, int64_t first, int64_t count,
+                                   const octax_state_record *in) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int64_t slot = slot_of_row[first + i];
+  const int64_t n = st.n;
+  const octax_state_record &rec = in[i];
+  for (int j = 0; j < 4; ++j) {
+    uint32_t w = 0;
+    for (int b = 0; b < 4; ++b) w |= (uint32_t)rec.V[4 * j + b] << (8 * b);
+    st.v[j * n + slot] = w;
+  }
+  st.pcI[slot] = (uint32_t)(rec.PC & 0xFFFu) | ((uint32_t)rec.I << 16);
+  st.misc[slot] = (uint32_t)rec.SP | ((uint32_t)rec.DT << 8) | ((uint32_t)rec.ST << 16) |
+                  ((uint32_t)rec.status << 24);
+  for (int k = 0; k < 16; ++k) st.stack[k * n + slot] = rec.stack[k];
+  for (int r = 0; r < 32; ++r) st.disp[r * n + slot] = rec.display[r];
+  const int game = st.game[slot];
+  const uint8_t *img = images + (size_t)game * kRamBytes;
+  uint64_t dirty = 0;
+  uint8_t *ram = st.ram + slot * (int64_t)kRamBytes;
+  for (int page = 0; page < kRamBytes >> kPageShift; ++page) {
+    bool differs = false;
+    for (int b = 0; b < (1 << kPageShift); ++b)
+      differs |= rec.ram[(page << kPageShift) + b] != img[(page << kPageShift) + b];
+    if (differs) {
+      dirty |= 1ull << page;
+      for (int b = 0; b < (1 << kPageShift); ++b) ram[(page << kPageShift) + b] = rec.ram[(page << kPageShift) + b];
+    }
+  }
+  st.dirty[slot] = dirty;
+  st.ep[slot] = rec.episode_steps;
+  st.env_steps[slot] = rec.env_steps;
+  // score of the restored state (the next step's reward baseline)
+  const GameDev &G = games[game];
+  int32_t s = 0;
+  for (uint32_t k = 0; k < G.n_score; ++k) {
+    const TermDev &t = G.score[k];
+    const int32_t v = t.src == OCTAX_SRC_REG ? (int32_t)rec.V[t.idx & 15] : (int32_t)rec.ram[t.idx & 0xFFF];
+    switch (t.xform) {
+      case OCTAX_X_RAW: s += v; break;
+      case OCTAX_X_NEG: s -= v; break;
+      case OCTAX_X_DEC_TENS: s += v / 10; break;
+      case OCTAX_X_DEC_ONES: s += v % 10; break;
+      case OCTAX_X_DEC_TENS_MINUS_ONES: s += v / 10 - v % 10; break;
+      case OCTAX_X_NIB_HI_MINUS_LO: s += (v >> 4) - (v & 15); break;
+      case OCTAX_X_ZERO_IF_GT: s += v > t.arg ? 0 : v; break;
+      default: break;
+    }
+  }
+  st.prev_score[slot] = s;
+}
+
+}  // namespace
+
+size_t step_smem_bytes(int block) {
+  return (size_t)kRamBytes + kGameSmem + (size_t)block * (32 * sizeof(uint64_t) + 16 * sizeof(uint32_t));
+}
+
+static cudaError_t ensure_smem_attr() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)step_smem_bytes(kMaxBlock));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(reset_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)step_smem_bytes(kMaxBlock));
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+cudaError_t launch_step(const StepLaunch &p, int grid, int block, cudaStream_t s) {
+  cudaError_t e = ensure_smem_attr();
+  if (e != cudaSuccess) return e;
+  if (grid <= 0) return cudaSuccess;
+  step_kernel<<<grid, block, step_smem_bytes(block), s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reset(const ResetLaunch &p, int block, cudaStream_t s) {
+  cudaError_t e = ensure_smem_attr();
+  if (e != cudaSuccess) return e;
+  if (p.n_groups <= 0) return cudaSuccess;
+  reset_kernel<<<p.n_groups, block, step_smem_bytes(block), s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hash(const DevState &st, const uint8_t *images, const uint32_t *slot_of_row,
+                        int64_t rows, uint64_t *out, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  const int tb = 128;
+  hash_kernel<<<(unsigned)((rows + tb - 1) / tb), tb, 0, s>>>(st, images, slot_of_row, rows, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_records(const DevState &st, const uint8_t *images, const uint32_t *slot_of_row,
+                           int64_t first, int64_t count, octax_state_record *out, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const int tb = 128;
+  records_kernel<<<(unsigned)((count + tb - 1) / tb), tb, 0, s>>>(st, images, slot_of_row, first, count,
+                                                                   out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_records(const DevState &st, const GameDev *games, const uint8_t *images,
+                               const uint32_t *slot_of_row, int64_t first, int64_t count,
+                               const octax_state_record *in, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const int tb = 128;
+  set_records_kernel<<<(unsigned)((count + tb - 1) / tb), tb, 0, s>>>(st, games, images, slot_of_row,
+                                                                       first, count, in);
+  return cudaGetLastError();
+}
+
+cudaError_t add_step_node(cudaGraph_t g, cudaGraphNode_t *node, cudaGraphNode_t dep, const StepLaunch &p,
+                          int grid, int block) {
+  cudaError_t e = ensure_smem_attr();
+  if (e != cudaSuccess) return e;
+  StepLaunch copy = p;
+  void *args[] = {&copy};
+  cudaKernelNodeParams kp;
+  memset(&kp, 0, sizeof kp);
+  kp.func = reinterpret_cast<void *>(step_kernel);
+  kp.gridDim = dim3((unsigned)grid);
+  kp.blockDim = dim3((unsigned)block);
+  kp.sharedMemBytes = (unsigned)step_smem_bytes(block);
+  kp.kernelParams = args;
+  return cudaGraphAddKernelNode(node, g, dep ? &dep : nullptr, dep ? 1 : 0, &kp);
+}
+
+int max_resident_ctas(int block) {
+  if (ensure_smem_attr() != cudaSuccess) return 0;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel, block, step_smem_bytes(block));
+  return sms * per_sm;
+}
+
+}  // namespace octax

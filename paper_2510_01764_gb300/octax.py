@@ -1,0 +1,307 @@
+"""Python binding of liboctax (include/octax.h): argument marshalling only.
+
+Every step of the environment runs in the hand-written CUDA kernels of the
+in-tree ``_build/liboctax.so``; this module converts game descriptions into
+the C structs, allocates output tensors with PyTorch and passes raw pointers
+and the CUDA stream. There is no CPU fallback: if the library is missing the
+import of ``Env`` fails with instructions to build it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liboctax.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTFOUND = 0, -1, -2, -3, -4, -5
+QUIRK_SHIFT_USES_VY, QUIRK_LOADSTORE_INC_I, QUIRK_LOGIC_RESETS_VF = 0x01, 0x02, 0x04
+QUIRK_JUMP_VX, QUIRK_WRAP_SPRITES, QUIRK_FX1E_VF = 0x08, 0x10, 0x20
+STATUS_BAD_OP, STATUS_STACK_FAULT, STATUS_BAD_ACTION = 0x01, 0x02, 0x04
+
+_XFORM = {"raw": 0, "neg": 1, "dec_tens": 2, "dec_ones": 3, "dec_tens_minus_ones": 4,
+          "nib_hi_minus_lo": 5, "zero_if_gt": 6}
+_CMP = {"==": 0, "!=": 1, ">=": 2, ">": 3, "<=": 4, "<": 5}
+
+
+class OctaxError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"liboctax error {code}: {msg}")
+        self.code = code
+
+
+class CTerm(C.Structure):
+    _fields_ = [("src", C.c_uint8), ("xform", C.c_uint8), ("idx", C.c_uint16), ("arg", C.c_int32)]
+
+
+class CClause(C.Structure):
+    _fields_ = [("lhs", CTerm), ("cmp", C.c_uint8), ("pad", C.c_uint8 * 3), ("rhs", C.c_int32)]
+
+
+class CGame(C.Structure):
+    _fields_ = [("rom", C.POINTER(C.c_uint8)), ("rom_len", C.c_uint32),
+                ("instr_per_frame", C.c_uint8), ("frameskip", C.c_uint8),
+                ("stack_frames", C.c_uint8), ("n_actions", C.c_uint8),
+                ("action_set", C.c_uint8 * 16), ("n_score_terms", C.c_uint8),
+                ("n_term_clauses", C.c_uint8), ("pad", C.c_uint8 * 2), ("score", CTerm * 4),
+                ("term", CClause * 4), ("max_episode_steps", C.c_uint32),
+                ("startup_instrs", C.c_uint32)]
+
+
+class CLaunch(C.Structure):
+    _fields_ = [("block", C.c_int32), ("steps_per_launch", C.c_int32),
+                ("persistent", C.c_int32), ("use_graph", C.c_int32)]
+
+
+RECORD_DTYPE = np.dtype([("V", np.uint8, 16), ("I", "<u2"), ("PC", "<u2"), ("SP", np.uint8),
+                         ("DT", np.uint8), ("ST", np.uint8), ("status", np.uint8),
+                         ("stack", "<u2", 16), ("display", "<u8", 32), ("ram", np.uint8, 4096),
+                         ("episode_steps", "<u4"), ("env_steps", "<u4")])
+assert RECORD_DTYPE.itemsize == 4416
+
+EXPORTS = ("octax_create", "octax_reset", "octax_step", "octax_step_n", "octax_step_host",
+           "octax_state_hash", "octax_get_state", "octax_set_state", "octax_sync",
+           "octax_get_launch", "octax_set_launch", "octax_autotune", "octax_num_envs",
+           "octax_stack_frames", "octax_device_bytes", "octax_destroy", "octax_last_error")
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH):
+    """Load liboctax.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError(f"{path} not found: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(path)
+        P, I64, I32 = C.c_void_p, C.c_int64, C.c_int
+        sig = {
+            "octax_create": (I32, [C.POINTER(CGame), I32, P, P, I64, C.c_uint32, C.c_uint64, P,
+                                   C.POINTER(P)]),
+            "octax_reset": (I32, [P, P, P]),
+            "octax_step": (I32, [P, P, P, P, P]),
+            "octax_step_n": (I32, [P, I32, P, P, P, P]),
+            "octax_step_host": (I32, [P, P, P, P, P]),
+            "octax_state_hash": (I32, [P, P]),
+            "octax_get_state": (I32, [P, I64, I64, P]),
+            "octax_set_state": (I32, [P, I64, I64, P]),
+            "octax_sync": (I32, [P, I32]),
+            "octax_get_launch": (I32, [P, C.POINTER(CLaunch)]),
+            "octax_set_launch": (I32, [P, C.POINTER(CLaunch)]),
+            "octax_autotune": (I32, [P, I32, C.POINTER(C.c_float)]),
+            "octax_num_envs": (I64, [P]),
+            "octax_stack_frames": (I32, [P]),
+            "octax_device_bytes": (C.c_size_t, [P]),
+            "octax_destroy": (None, [P]),
+            "octax_last_error": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+def check(rc: int) -> None:
+    if rc != OK:
+        raise OctaxError(rc, load_library().octax_last_error().decode())
+
+
+def _term(t) -> CTerm:
+    return CTerm(0 if t.src == "reg" else 1, _XFORM[t.xform], int(t.idx) & 0xFFFF, int(t.arg))
+
+
+def make_game(spec) -> tuple[CGame, object]:
+    """Marshal a GameSpec-like object into an octax_game (+ keep-alive buffer)."""
+    rom = np.frombuffer(bytes(spec.rom), dtype=np.uint8).copy()
+    g = CGame()
+    g.rom = rom.ctypes.data_as(C.POINTER(C.c_uint8))
+    g.rom_len = len(rom)
+    g.instr_per_frame = spec.instr_per_frame
+    g.frameskip = spec.frameskip
+    g.stack_frames = spec.stack_frames
+    g.n_actions = len(spec.action_set)
+    for i, k in enumerate(spec.action_set):
+        g.action_set[i] = k
+    g.n_score_terms = len(spec.score)
+    for i, t in enumerate(spec.score):
+        g.score[i] = _term(t)
+    g.n_term_clauses = len(spec.term)
+    for i, c in enumerate(spec.term):
+        g.term[i] = CClause(_term(c.lhs), _CMP[c.cmp], (C.c_uint8 * 3)(), int(c.rhs))
+    g.max_episode_steps = spec.max_episode_steps
+    g.startup_instrs = spec.startup_instrs
+    return g, rom
+
+
+def _ptr(t) -> C.c_void_p | None:
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+class Env:
+    """n_envs CHIP-8 environments stepped by the CUDA kernels on one GPU."""
+
+    def __init__(self, games, n_envs: int, *, game_of_env=None, uid_of_env=None,
+                 quirks: int = 0, seed: int = 0, device=None, stream=None):
+        import torch
+
+        self._torch = torch
+        L = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("liboctax needs a CUDA device")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        torch.cuda.set_device(self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.games = list(games)
+        self.n = int(n_envs)
+        self.S = int(self.games[0].stack_frames)
+        keep = [make_game(g) for g in self.games]
+        arr = (CGame * len(keep))(*[k[0] for k in keep])
+        goe = None if game_of_env is None else np.ascontiguousarray(game_of_env, dtype=np.uint16)
+        uoe = None if uid_of_env is None else np.ascontiguousarray(uid_of_env, dtype=np.uint32)
+        if goe is not None and goe.shape != (self.n,):
+            raise ValueError("game_of_env must have shape (n_envs,)")
+        if uoe is not None and uoe.shape != (self.n,):
+            raise ValueError("uid_of_env must have shape (n_envs,)")
+        h = C.c_void_p()
+        check(L.octax_create(arr, len(keep), None if goe is None else C.c_void_p(goe.ctypes.data),
+                             None if uoe is None else C.c_void_p(uoe.ctypes.data), self.n, quirks,
+                             seed & 0xFFFFFFFFFFFFFFFF, C.c_void_p(self.stream.cuda_stream),
+                             C.byref(h)))
+        self._h = h
+        self._keep = keep
+
+    # ------------------------------------------------------------------ helpers
+    def _u8(self, *shape):
+        return self._torch.empty(shape, dtype=self._torch.uint8, device=self.device)
+
+    def _check_dev(self, t, dtype, shape, name):
+        if t.device != self.device or t.dtype != dtype or tuple(t.shape) != tuple(shape) \
+                or not t.is_contiguous():
+            raise ValueError(f"{name}: need contiguous {dtype} {tuple(shape)} on {self.device}, "
+                             f"got {t.dtype} {tuple(t.shape)} on {t.device}")
+
+    @property
+    def obs_shape(self):
+        return (self.n, self.S, 32, 64)
+
+    # ------------------------------------------------------------------ API
+    def reset(self, mask=None, out=None):
+        torch = self._torch
+        obs = out if out is not None else self._u8(*self.obs_shape)
+        self._check_dev(obs, torch.uint8, self.obs_shape, "obs")
+        if mask is not None:
+            mask = mask.to(device=self.device, dtype=torch.uint8).contiguous()
+            self._check_dev(mask, torch.uint8, (self.n,), "mask")
+        check(load_library().octax_reset(self._h, _ptr(mask), _ptr(obs)))
+        return obs
+
+    def step(self, actions, out=None):
+        torch = self._torch
+        self._check_dev(actions, torch.uint8, (self.n,), "actions")
+        if out is None:
+            out = (self._u8(*self.obs_shape),
+                   torch.empty(self.n, dtype=torch.float32, device=self.device),
+                   self._u8(self.n))
+        obs, rew, done = out
+        self._check_dev(obs, torch.uint8, self.obs_shape, "obs")
+        self._check_dev(rew, torch.float32, (self.n,), "reward")
+        self._check_dev(done, torch.uint8, (self.n,), "done")
+        check(load_library().octax_step(self._h, _ptr(actions), _ptr(obs), _ptr(rew), _ptr(done)))
+        return obs, rew, done
+
+    def step_n(self, actions, out=None):
+        torch = self._torch
+        T = int(actions.shape[0])
+        self._check_dev(actions, torch.uint8, (T, self.n), "actions")
+        if out is None:
+            out = (self._u8(T, *self.obs_shape),
+                   torch.empty((T, self.n), dtype=torch.float32, device=self.device),
+                   self._u8(T, self.n))
+        obs, rew, done = out
+        self._check_dev(obs, torch.uint8, (T, *self.obs_shape), "obs")
+        self._check_dev(rew, torch.float32, (T, self.n), "reward")
+        self._check_dev(done, torch.uint8, (T, self.n), "done")
+        check(load_library().octax_step_n(self._h, T, _ptr(actions), _ptr(obs), _ptr(rew),
+                                          _ptr(done)))
+        return obs, rew, done
+
+    def step_host(self, actions, out=None):
+        """Host buffers in and out (pinned CPU tensors copy fastest); synchronous."""
+        torch = self._torch
+        if out is None:
+            out = (torch.empty(self.obs_shape, dtype=torch.uint8, pin_memory=True),
+                   torch.empty(self.n, dtype=torch.float32, pin_memory=True),
+                   torch.empty(self.n, dtype=torch.uint8, pin_memory=True))
+        obs, rew, done = out
+        for t, dt, shp, nm in ((actions, torch.uint8, (self.n,), "actions"),
+                               (obs, torch.uint8, self.obs_shape, "obs"),
+                               (rew, torch.float32, (self.n,), "reward"),
+                               (done, torch.uint8, (self.n,), "done")):
+            if t.device.type != "cpu" or t.dtype != dt or tuple(t.shape) != shp or not t.is_contiguous():
+                raise ValueError(f"{nm}: need contiguous host {dt} {shp}")
+        check(load_library().octax_step_host(self._h, _ptr(actions), _ptr(obs), _ptr(rew),
+                                             _ptr(done)))
+        return obs, rew, done
+
+    def state_hash(self, out=None):
+        torch = self._torch
+        h = out if out is not None else torch.empty(self.n, dtype=torch.int64, device=self.device)
+        check(load_library().octax_state_hash(self._h, _ptr(h)))
+        return h
+
+    def get_state(self, first: int = 0, count: int | None = None) -> np.ndarray:
+        count = self.n - first if count is None else count
+        out = np.zeros(count, dtype=RECORD_DTYPE)
+        check(load_library().octax_get_state(self._h, first, count, C.c_void_p(out.ctypes.data)))
+        return out
+
+    def set_state(self, records: np.ndarray, first: int = 0) -> None:
+        rec = np.ascontiguousarray(records, dtype=RECORD_DTYPE)
+        check(load_library().octax_set_state(self._h, first, len(rec), C.c_void_p(rec.ctypes.data)))
+
+    def sync(self, timeout_ms: int = -1) -> None:
+        check(load_library().octax_sync(self._h, timeout_ms))
+
+    @property
+    def launch(self) -> dict:
+        c = CLaunch()
+        check(load_library().octax_get_launch(self._h, C.byref(c)))
+        return {"block": c.block, "steps_per_launch": c.steps_per_launch,
+                "persistent": c.persistent, "use_graph": c.use_graph}
+
+    def set_launch(self, **kw) -> None:
+        cur = self.launch
+        cur.update(kw)
+        c = CLaunch(cur["block"], cur["steps_per_launch"], cur["persistent"], cur["use_graph"])
+        check(load_library().octax_set_launch(self._h, C.byref(c)))
+
+    def autotune(self, n_steps: int = 8) -> float:
+        ms = C.c_float()
+        check(load_library().octax_autotune(self._h, n_steps, C.byref(ms)))
+        return ms.value
+
+    @property
+    def device_bytes(self) -> int:
+        return int(load_library().octax_device_bytes(self._h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load_library().octax_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -137,6 +137,15 @@ class TemplateParams:
 
 def template_rom(p: TemplateParams) -> bytes:
     """Seeded arcade-shaped CHIP-8 program (see module docstring)."""
+    return _template(p)[0]
+
+
+def template_labels(p: TemplateParams) -> dict:
+    """Addresses of the template's labels (e.g. ``scratch``, the BCD buffer)."""
+    return _template(p)[1]
+
+
+def _template(p: TemplateParams) -> tuple:
     rng = np.random.Generator(np.random.Philox(key=p.seed))
     a = Asm()
     # ---- init
@@ -249,7 +258,7 @@ def template_rom(p: TemplateParams) -> bytes:
     rom = bytearray(a.assemble())
     if len(rom) < p.size:
         rom += rng.integers(0, 256, size=p.size - len(rom), dtype=np.uint8).tobytes()
-    return bytes(rom)
+    return bytes(rom), dict(a.labels)
 
 
 def template_game(p: TemplateParams, *, instr_per_frame: int = 10, frameskip: int = 4,

@@ -1,0 +1,367 @@
+"""Bit-exact parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Small configurations are compared in full: every register, RAM byte, display
+bit (via the per-step state hash and the canonical records), every
+observation byte, reward and done flag. Full-size configurations run the
+whole workload on the GPU in the launch configuration the benchmark uses and
+compare a sample of instances, which the oracle steps one by one, at every
+step.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from chip8_prog import prog
+from paper_2510_01764_gb300 import workloads as W
+from paper_2510_01764_gb300.workloads import Clause, GameSpec, Term
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_01764_gb300 import build
+
+    build.build()
+    oracle.build()
+
+
+def octax():
+    from paper_2510_01764_gb300 import octax as o
+
+    return o
+
+
+def hashes(env):
+    return env.state_hash().cpu().numpy().view(np.uint64)
+
+
+def full_compare(games, n, steps, *, seed=1, action_seed=1, game_of_env=None, quirks=0,
+                 n_actions=None, launch=None, use_step_n=False, uid_of_env=None):
+    """Step GPU and oracle side by side; compare everything at every step."""
+    o = octax()
+    env = o.Env(games, n, seed=seed, quirks=quirks, game_of_env=game_of_env, uid_of_env=uid_of_env)
+    if launch:
+        env.set_launch(**launch)
+    ref = oracle.OracleEnv(games, n, seed=seed, quirks=quirks, game_of_env=game_of_env,
+                           uid_of_env=uid_of_env)
+    na = n_actions or games[0].n_actions
+    acts = W.actions(action_seed, 0, steps, n, na + 1 if n_actions is None else n_actions)
+    assert np.array_equal(env.reset().cpu().numpy(), ref.reset())
+    assert np.array_equal(hashes(env), ref.hashes())
+    a_dev = torch.from_numpy(acts).cuda()
+    if use_step_n:
+        obs, rew, done = env.step_n(a_dev)
+        o2, r2, d2, _ = ref.rollout(acts, obs=True)
+        assert np.array_equal(obs.cpu().numpy(), o2)
+        assert np.array_equal(rew.cpu().numpy(), r2)
+        assert np.array_equal(done.cpu().numpy(), d2)
+        assert np.array_equal(hashes(env), ref.hashes())
+    else:
+        for s in range(steps):
+            obs, rew, done = env.step(a_dev[s])
+            o2, r2, d2 = ref.step(acts[s])
+            assert np.array_equal(obs.cpu().numpy(), o2), f"obs step {s}"
+            assert np.array_equal(rew.cpu().numpy(), r2), f"reward step {s}"
+            assert np.array_equal(done.cpu().numpy(), d2), f"done step {s}"
+            assert np.array_equal(hashes(env), ref.hashes()), f"state step {s}"
+    g = env.get_state()
+    r = ref.records()
+    for f in oracle.RECORD_DTYPE.names:
+        assert np.array_equal(g[f], r[f]), f
+    return env, ref
+
+
+# ----------------------------------------------------------------- small, full
+def test_config_small_full_parity():
+    """64 instances of the ~600 B template ROM, K = 10, frame skip 4, 1,000
+    steps: every state, observation, reward and done flag."""
+    w = W.cfg_small()
+    full_compare(w.games, w.n_envs, w.n_steps, seed=w.seed, action_seed=w.action_seed,
+                 n_actions=4)
+
+
+@pytest.mark.parametrize("launch", [
+    dict(block=32, steps_per_launch=1, persistent=0, use_graph=0),
+    dict(block=64, steps_per_launch=4, persistent=0, use_graph=1),
+    dict(block=128, steps_per_launch=3, persistent=1, use_graph=1),
+    dict(block=256, steps_per_launch=8, persistent=1, use_graph=0),
+])
+def test_launch_configurations_agree(launch):
+    w = W.cfg_small()
+    full_compare(w.games, 200, 64, seed=3, action_seed=5, launch=launch, use_step_n=True)
+
+
+def test_random_opcode_roms():
+    """Random programs: every opcode, self-modifying code, stack faults, odd PCs."""
+    games = [W.random_game(1000 + r) for r in range(32)]
+    n = 256
+    goe = (np.arange(n) % 32).astype(np.uint16)
+    env, _ = full_compare(games, n, 150, seed=4, action_seed=4, game_of_env=goe)
+    assert (env.get_state()["status"] & octax().STATUS_STACK_FAULT).any()
+
+
+@pytest.mark.parametrize("quirks", [0x01, 0x02, 0x04, 0x08, 0x10, 0x20, 0x3F])
+def test_quirk_bits(quirks):
+    games = [W.random_game(2000 + r) for r in range(8)]
+    n = 96
+    goe = (np.arange(n) % 8).astype(np.uint16)
+    full_compare(games, n, 80, seed=9, action_seed=9, game_of_env=goe, quirks=quirks)
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 100])
+def test_ragged_instance_counts(n):
+    w = W.cfg_small()
+    full_compare(w.games, n, 40, seed=2, action_seed=2, launch=dict(block=64))
+
+
+def test_mixed_games_timing_and_stacks():
+    """Different K and frame skip per game, stack_frames < frame skip,
+    startup instructions that draw random numbers, shuffled instance order."""
+    ts = [W.TemplateParams(seed=50 + i, size=300 + 100 * i, alu_ops=i, deco_pairs=i % 3,
+                           wait_frames=i % 3) for i in range(4)]
+    games = [
+        W.replace(W.template_game(ts[0], instr_per_frame=5, frameskip=2), stack_frames=2),
+        W.replace(W.template_game(ts[1], instr_per_frame=20, frameskip=3, score_limit=2),
+                  stack_frames=2),
+        W.replace(W.template_game(ts[2], instr_per_frame=7, frameskip=5, max_episode_steps=13),
+                  stack_frames=2, startup_instrs=57),
+        W.replace(W.random_game(77, frameskip=2), stack_frames=2, startup_instrs=33),
+    ]
+    n = 300
+    goe = np.random.default_rng(0).integers(0, 4, n).astype(np.uint16)
+    full_compare(games, n, 120, seed=11, action_seed=12, game_of_env=goe)
+
+
+def test_reward_descriptor_memory_and_transforms():
+    """Score from memory bytes written by FX33, several transforms, compound
+    termination, truncation."""
+    tp = W.TemplateParams(seed=5)
+    g = W.template_game(tp)
+    scratch = W.template_labels(tp)["scratch"]  # BCD buffer written by FX33
+    g = W.replace(g, score=(Term("mem", scratch + 2, "raw"), Term("reg", 6, "dec_tens_minus_ones"),
+                            Term("reg", 9, "zero_if_gt", 20), Term("reg", 8, "neg")),
+                  term=(Clause(Term("reg", 6, "dec_ones"), "==", 3),
+                        Clause(Term("mem", scratch + 1, "raw"), ">", 0),
+                        Clause(Term("reg", 8, "nib_hi_minus_lo"), "<", -10)),
+                  max_episode_steps=150)
+    full_compare([g], 128, 200, seed=6, action_seed=6)
+
+
+def test_out_of_range_actions():
+    w = W.cfg_small()
+    env, _ = full_compare(w.games, 64, 30, seed=1, action_seed=3, n_actions=7)
+    assert (env.get_state()["status"] & octax().STATUS_BAD_ACTION).any()
+
+
+def test_identity_independent_of_placement():
+    """An instance's trajectory depends on (seed, uid, actions) only."""
+    w = W.cfg_small()
+    n = 96
+    perm = np.random.default_rng(1).permutation(n).astype(np.uint32)
+    full_compare(w.games, n, 50, seed=7, action_seed=7, uid_of_env=perm)
+
+
+def test_reset_with_mask():
+    o = octax()
+    w = W.cfg_small()
+    n = 80
+    env = o.Env(w.games, n, seed=3)
+    ref = oracle.OracleEnv(w.games, n, seed=3)
+    env.reset()
+    ref.reset()
+    acts = W.actions(3, 0, 30, n)
+    a_dev = torch.from_numpy(acts).cuda()
+    for s in range(30):
+        env.step(a_dev[s])
+        ref.step(acts[s])
+        if s in (10, 20):
+            mask = (np.arange(n) % 3 == s % 2).astype(np.uint8)
+            go = env.reset(mask=torch.from_numpy(mask).cuda(), out=torch.zeros((n, 4, 32, 64),
+                                                                               dtype=torch.uint8,
+                                                                               device="cuda"))
+            ro = np.zeros((n, 4, 32, 64), dtype=np.uint8)
+            ro_sel = ref.reset(mask)
+            ro[mask == 1] = ro_sel[mask == 1]
+            assert np.array_equal(go.cpu().numpy(), ro)
+        assert np.array_equal(hashes(env), ref.hashes())
+
+
+def test_checkpoint_roundtrip():
+    """get_state / set_state: resuming from a checkpoint replays identically."""
+    o = octax()
+    games = [W.random_game(31), W.template_game(W.TemplateParams(seed=8))]
+    n = 130
+    goe = (np.arange(n) % 2).astype(np.uint16)
+    env = o.Env(games, n, seed=5, game_of_env=goe)
+    acts = torch.from_numpy(W.actions(8, 0, 60, n)).cuda()
+    for s in range(30):
+        env.step(acts[s])
+    ck = env.get_state()
+    h_ck = hashes(env)
+    first = [tuple(t.cpu() for t in env.step(acts[s])) for s in range(30, 60)]
+    env.set_state(ck)
+    assert np.array_equal(hashes(env), h_ck)
+    second = [tuple(t.cpu() for t in env.step(acts[s])) for s in range(30, 60)]
+    for a, b in zip(first, second):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+    # records restore into a fresh environment too (different launch config)
+    env2 = o.Env(games, n, seed=5, game_of_env=goe)
+    env2.set_launch(block=32)
+    env2.set_state(ck)
+    assert np.array_equal(hashes(env2), h_ck)
+
+
+def test_memory_map_and_font_match_oracle():
+    o = octax()
+    g = GameSpec(rom=bytes(range(256)) * 14)
+    env = o.Env([g], 2)
+    ref = oracle.OracleEnv([g], 2)
+    assert np.array_equal(env.get_state()["ram"], ref.records()["ram"])
+
+
+def test_hand_programs_through_gpu():
+    """The oracle's hand-assembled multiply program also runs on the GPU."""
+    from test_oracle_pins import MUL8, RAMP
+    g = prog(MUL8, instr_per_frame=20, frameskip=4)
+    full_compare([g], 40, 8, seed=1)
+    g = prog(RAMP, instr_per_frame=10, frameskip=4, score=(Term("reg", 6),),
+             term=(Clause(Term("reg", 6), ">=", 20),))
+    env, _ = full_compare([g], 40, 12, seed=1)
+
+
+def test_autotune_leaves_no_trace():
+    o = octax()
+    w = W.cfg_small()
+    n = 256
+    env = o.Env(w.games, n, seed=1)
+    acts = torch.from_numpy(W.actions(1, 0, 40, n)).cuda()
+    env.step_n(acts[:20])
+    h0 = hashes(env)
+    ms = env.autotune(8)
+    assert ms > 0
+    assert np.array_equal(hashes(env), h0)
+    o1 = env.step_n(acts[20:])
+    ref = o.Env(w.games, n, seed=1)
+    ref.set_launch(block=32, steps_per_launch=1, persistent=0, use_graph=0)
+    ref.step_n(acts[:20])
+    o2 = ref.step_n(acts[20:])
+    for x, y in zip(o1, o2):
+        assert torch.equal(x, y)
+
+
+def test_host_buffer_step_matches_device_step():
+    o = octax()
+    w = W.cfg_small()
+    n = 128
+    a = W.actions(1, 0, 10, n)
+    e1 = o.Env(w.games, n, seed=1)
+    e2 = o.Env(w.games, n, seed=1)
+    for s in range(10):
+        d = e1.step(torch.from_numpy(a[s]).cuda())
+        h = e2.step_host(torch.from_numpy(a[s]).pin_memory())
+        for x, y in zip(d, h):
+            assert torch.equal(x.cpu(), y)
+
+
+def test_sync_timeout_is_reported():
+    """octax_sync returns ETIMEOUT (not a hang) while work is still running."""
+    o = octax()
+    w = W.cfg_divergence(n_envs=16384, n_steps=48)
+    env = o.Env(w.games, w.n_envs, seed=1, game_of_env=w.game_of_env)
+    acts = torch.zeros((48, w.n_envs), dtype=torch.uint8, device="cuda")
+    out = env.step_n(acts)
+    with pytest.raises(o.OctaxError) as ei:
+        env.sync(timeout_ms=0)
+    assert ei.value.code in (o.ETIMEOUT,)
+    env.sync(timeout_ms=-1)
+    del out
+
+
+# ----------------------------------------------------------------- full size, sampled
+def sampled_run(w, *, chunk, sample, launch=None, use_step_n=True):
+    """Run the whole workload on the GPU; compare `sample` rows with the
+    oracle at every step (obs, reward, done) and the state hash at every
+    chunk boundary."""
+    o = octax()
+    env = o.Env(w.games, w.n_envs, seed=w.seed, quirks=w.quirks, game_of_env=w.game_of_env)
+    if launch:
+        env.set_launch(**launch)
+    goe = None if w.game_of_env is None else w.game_of_env[sample]
+    ref = oracle.OracleEnv(w.games, len(sample), seed=w.seed, quirks=w.quirks, game_of_env=goe,
+                           uid_of_env=sample.astype(np.uint32))
+    idx = torch.from_numpy(sample.astype(np.int64)).cuda()
+    assert np.array_equal(env.reset()[idx].cpu().numpy(), ref.reset())
+    n_actions = w.games[0].n_actions
+    T = chunk
+    obs_buf = torch.empty((T, w.n_envs, 4, 32, 64), dtype=torch.uint8, device="cuda")
+    rew_buf = torch.empty((T, w.n_envs), dtype=torch.float32, device="cuda")
+    done_buf = torch.empty((T, w.n_envs), dtype=torch.uint8, device="cuda")
+    n_done = 0
+    for lo in range(0, w.n_steps, T):
+        hi = min(lo + T, w.n_steps)
+        acts = W.actions(w.action_seed, lo, hi, w.n_envs, n_actions)
+        a_dev = torch.from_numpy(acts).cuda()
+        c = hi - lo
+        out = (obs_buf[:c], rew_buf[:c], done_buf[:c])
+        if use_step_n:
+            env.step_n(a_dev, out=out)
+        else:
+            for s in range(c):
+                env.step(a_dev[s], out=(obs_buf[s], rew_buf[s], done_buf[s]))
+        o2, r2, d2, h2 = ref.rollout(acts[:, sample], obs=True, hashes=True)
+        assert np.array_equal(obs_buf[:c][:, idx].cpu().numpy(), o2), f"obs in steps {lo}..{hi}"
+        assert np.array_equal(rew_buf[:c][:, idx].cpu().numpy(), r2), f"reward in {lo}..{hi}"
+        assert np.array_equal(done_buf[:c][:, idx].cpu().numpy(), d2), f"done in {lo}..{hi}"
+        gh = env.state_hash()[idx].cpu().numpy().view(np.uint64)
+        assert np.array_equal(gh, h2[-1]), f"state after step {hi}"
+        n_done += int(done_buf[:c].sum().item())
+    return env, n_done
+
+
+def pick(n, k, seed=0, extra=()):
+    rng = np.random.default_rng(seed)
+    s = set(int(v) for v in rng.choice(n, size=k, replace=False))
+    s.update(e for e in extra if 0 <= e < n)
+    return np.array(sorted(s), dtype=np.int64)
+
+
+def test_config_scale_sampled():
+    """16,384 template instances x 20,000 steps with auto-reset (score >= 20
+    or 5,000 steps), plain one-launch-per-step kernel."""
+    w = W.cfg_scale()
+    sample = pick(w.n_envs, 24, 1, extra=(0, 31, 32, 63, 64, w.n_envs - 1))
+    env, n_done = sampled_run(w, chunk=50, sample=sample, use_step_n=False)
+    assert n_done > 0
+
+
+def test_config_scale_sampled_persistent_graph():
+    """Same workload through octax_step_n (CUDA graph, 4 steps per launch)."""
+    w = W.cfg_scale(n_steps=6000)
+    sample = pick(w.n_envs, 16, 2, extra=(5, w.n_envs - 2))
+    sampled_run(w, chunk=40, sample=sample,
+                launch=dict(block=64, steps_per_launch=4, persistent=1, use_graph=1))
+
+
+def test_config_batch_sampled():
+    """65,536 instances over 16 ROMs (K from {5,8,10,15,20}, uneven episodes),
+    16 frames per persistent graph-captured launch."""
+    w = W.cfg_batch()
+    goe = w.game_of_env
+    per_game = [np.nonzero(goe == g)[0][:2] for g in range(16)]
+    sample = np.unique(np.concatenate(per_game + [pick(w.n_envs, 16, 3)]))
+    sampled_run(w, chunk=32, sample=sample,
+                launch=dict(block=64, steps_per_launch=4, persistent=1, use_graph=1))
+
+
+def test_config_divergence_sampled():
+    """262,144 instances of random-opcode ROMs x 2,000 steps."""
+    w = W.cfg_divergence()
+    sample = pick(w.n_envs, 32, 4, extra=(0, 1, w.n_envs - 1))
+    sampled_run(w, chunk=8, sample=sample,
+                launch=dict(block=64, steps_per_launch=4, persistent=0, use_graph=1))
