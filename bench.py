@@ -1,0 +1,416 @@
+"""Benchmark of the vectorised CHIP-8 environment step on GB300.
+
+Default workload (N = 1): 16,384 instances of one seeded template ROM (seed
+2), K = 10 instructions per frame, frame skip 4, uint8 [4,32,64] observation
+stack, auto-reset on score >= 20 or 5,000 steps; K timed env steps (default
+20,000 = the whole workload) from the freshly reset state.
+
+One JSON line on stdout (rank 0). ``value`` is whole-job env steps/s with the
+actions already in HBM, through octax_step_n (CUDA-graph replay, launch
+configuration from octax_autotune); ``plain_kernel`` is the same workload with
+one plain kernel launch per env step; ``e2e`` goes through octax_step_host
+with pinned host buffers (actions in, obs/reward/done out, every step).
+``--impl reference`` times the CPU oracle (the plain-C reference interpreter)
+on the host cores instead. Multi-GPU runs are independent replicas (the
+environments never exchange data); rank 0 prints the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2510_01764_gb300 import workloads as W  # noqa: E402
+
+METRIC = "env steps/s on 1 GB300 (bit-exact vs oracle) vs plain kernel; serving p50/p99 ms"
+OBS_BYTES = 4 * 32 * 64
+# algorithmic HBM bytes of the step kernel ("roofline"):
+STEP_IO_BYTES = OBS_BYTES + 1 + 4 + 1            # obs + action + reward + done, per env step
+STATE_BYTES = 348 + 332                          # per instance per launch: state read + write
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload(name: str) -> W.Workload:
+    return {"scale": W.cfg_scale, "small": W.cfg_small, "batch": W.cfg_batch,
+            "divergence": W.cfg_divergence}[name]()
+
+
+def describe(config: str, w: W.Workload) -> str:
+    g = w.games[0]
+    return {
+        "scale": f"plain-scale: {w.n_envs} instances of the template ROM (seed 2, {len(g.rom)} B), "
+                 "K=10, frameskip 4, obs uint8 [4,32,64], auto-reset at score>=20 or 5,000 steps",
+        "small": f"plain-small: {w.n_envs} instances of the template ROM (seed 1), K=10, frameskip 4",
+        "batch": f"batch: {w.n_envs} instances over 16 template ROMs (200-3,000 B), K per ROM in "
+                 "{5,8,10,15,20}, uneven episodes, 16 frames per persistent graph launch",
+        "divergence": f"divergence: {w.n_envs} instances of 64 random-opcode ROMs (3,584 B), K=10",
+    }[config]
+
+
+class Clocks:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks() -> tuple[float, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("octax_kernels.cu", "octax_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2510_01764_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(config: str, launch: dict) -> dict | None:
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source and the same launch shape."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    e = d.get(config)
+    if not e or e.get("kernel_source") != kernel_source_hash():
+        return None
+    if e.get("steps_per_launch") != launch.get("steps_per_launch"):
+        return None
+    return e
+
+
+# --------------------------------------------------------------------------- GPU arm
+def run_gpu(args) -> dict | None:
+    import torch
+
+    from paper_2510_01764_gb300 import octax
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    w = workload(args.config)
+    K, Wm = args.steps if args.steps else w.n_steps, args.warmup
+    n = w.n_envs
+    with torch.cuda.stream(stream):
+        env = octax.Env(w.games, n, seed=w.seed, quirks=w.quirks, game_of_env=w.game_of_env,
+                        device=local, stream=stream)
+        T = args.rollout
+        acts_h = W.actions(w.action_seed, 0, K, n, w.games[0].n_actions)
+        acts = torch.from_numpy(acts_h).to(dev)
+        obs = torch.empty((T, n, 4, 32, 64), dtype=torch.uint8, device=dev)
+        rew = torch.empty((T, n), dtype=torch.float32, device=dev)
+        done = torch.empty((T, n), dtype=torch.uint8, device=dev)
+        init_state = env.get_state()
+
+        # ---- launch configuration: autotuned for T-step calls
+        if args.launch:
+            b, spl, pers, gr = (int(x) for x in args.launch.split(","))
+            env.set_launch(block=b, steps_per_launch=spl, persistent=pers, use_graph=gr)
+        else:
+            env.autotune(T)
+        launch = env.launch
+        calls = [(lo, min(lo + T, K)) for lo in range(0, K, T)]
+
+        def run_calls(cfg: dict | None):
+            if cfg:
+                env.set_launch(**cfg)
+            for lo, hi in calls:
+                c = hi - lo
+                env.step_n(acts[lo:hi], out=(obs[:c], rew[:c], done[:c]))
+
+        def timed(cfg: dict | None) -> tuple[float, int]:
+            # warm-up (graph build, caches) then restore the fresh state
+            if cfg:
+                env.set_launch(**cfg)
+            for lo in range(0, max(Wm, 1)):
+                s = lo % K
+                env.step_n(acts[s:s + 1], out=(obs[:1], rew[:1], done[:1]))
+            for lo, hi in calls[:2]:
+                env.step_n(acts[lo:hi], out=(obs[:hi - lo], rew[:hi - lo], done[:hi - lo]))
+            env.set_state(init_state)
+            torch.cuda.synchronize(dev)
+            if world > 1:
+                torch.distributed.barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run_calls(None)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            dn = int(done.sum().item())
+            return ms, dn
+
+        with Clocks(local) as clk:
+            ms_best, _ = timed(launch)
+        clocks = clk.summary()
+        plain_cfg = dict(block=launch["block"], steps_per_launch=1, persistent=0, use_graph=0)
+        ms_plain, _ = timed(plain_cfg)
+        env.set_launch(**launch)
+
+        # ---- end to end through the host-buffer entry point
+        Ke = min(K, args.e2e_steps)
+        a_h = torch.from_numpy(acts_h[:Ke].copy()).pin_memory()
+        o_h = torch.empty((n, 4, 32, 64), dtype=torch.uint8, pin_memory=True)
+        r_h = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        d_h = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+        env.set_launch(**plain_cfg)
+        for s in range(min(3, Ke)):
+            env.step_host(a_h[s], out=(o_h, r_h, d_h))
+        env.set_state(init_state)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for s in range(Ke):
+            env.step_host(a_h[s], out=(o_h, r_h, d_h))
+        e2e_s = time.perf_counter() - t0
+        env.set_launch(**launch)
+
+    times = torch.tensor([ms_best, ms_plain, e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+    ms_best, ms_plain, e2e_s = (float(x) for x in times.tolist())
+    if rank != 0:
+        return None
+
+    value = world * n * K / (ms_best / 1e3)
+    spl = launch["steps_per_launch"]
+    n_launch = sum((hi - lo + spl - 1) // spl for lo, hi in calls)
+    launch_ms = ms_best / n_launch
+    alg_bytes = n * (STEP_IO_BYTES * (K / n_launch) + STATE_BYTES)
+    peak, peak_src = measured_peaks()
+    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    prof = profiled_traffic(args.config, launch)
+    line = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": "env steps/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": Wm,
+        "ms_per_step": round(ms_best / K, 6),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic (seeded template ROM, Philox actions)",
+        "frames_per_s": round(value * w.games[0].frameskip, 1),
+        "config": {
+            "workload": describe(args.config, w),
+            "n_envs_per_gpu": n,
+            "steps": K,
+            "rollout_buffer_steps": T,
+            "launch": launch,
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": "no flush: each step writes 134 MB of observations into a 32-step rollout ring "
+                  "and touches 72 MB of emulator state, more than the 126 MB L2",
+        },
+        "plain_kernel": {
+            "value": round(world * n * K / (ms_plain / 1e3), 1),
+            "unit": "env steps/s",
+            "ms_per_step": round(ms_plain / K, 6),
+            "launch": plain_cfg,
+        },
+        "speedup_vs_plain": round(ms_plain / ms_best, 3),
+        "gpu_launches": n_launch,
+        "roofline": {
+            "bound": "hbm",
+            "achieved": round(achieved, 1),
+            "peak": peak,
+            "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "peak_source": peak_src,
+            "kernel": "step_kernel",
+            "bytes_per_launch": int(alg_bytes),
+            "launch_ms": round(launch_ms, 5),
+            "traffic": None if prof is None else prof["traffic_per_launch"],
+        },
+        "e2e": {
+            "value": round(world * n * Ke / e2e_s, 1),
+            "unit": "env steps/s",
+            "steps": Ke,
+            "h2d_bytes_per_step": n,
+            "d2h_bytes_per_step": n * (OBS_BYTES + 4 + 1),
+        },
+        "clocks": clocks,
+    }
+    if prof and prof.get("issue"):
+        line["issue_roofline"] = prof["issue"]
+    return line
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def cpu_oracle(w: W.Workload, budget_s: float, threads: int, steps_hint: int | None = None) -> dict:
+    import oracle
+
+    oracle.build()
+    n = w.n_envs
+    env = oracle.OracleEnv(w.games, n, seed=w.seed, quirks=w.quirks, game_of_env=w.game_of_env)
+    env.reset()
+    acts = W.actions(w.action_seed, 0, 3, n, w.games[0].n_actions)
+    t0 = time.perf_counter()
+    env.step(acts[0], threads=threads)
+    per_step = time.perf_counter() - t0
+    steps = max(1, int(budget_s / max(per_step, 1e-6)))
+    if steps_hint:
+        steps = min(steps, steps_hint)
+    acts = W.actions(w.action_seed, 1, 1 + steps, n, w.games[0].n_actions)
+    t0 = time.perf_counter()
+    for s in range(steps):
+        env.step(acts[s], threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": round(n * steps / dt, 1), "unit": "env steps/s", "cores": threads,
+            "kind": "oracle", "seconds": round(dt, 2),
+            "sample": f"{n} instances x {steps} steps of the same workload (obs materialised)"}
+
+
+def run_reference(args) -> dict | None:
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    w = workload(args.config)
+    threads = os.cpu_count() or 1
+    K, Wm = args.steps if args.steps else w.n_steps, args.warmup
+    import oracle
+
+    oracle.build()
+    # each step: one env step over a bounded sample of the instances, sized so
+    # that warm-up + K steps take about args.ref_budget seconds
+    probe = oracle.OracleEnv(w.games, min(w.n_envs, 4096), seed=w.seed,
+                             game_of_env=None if w.game_of_env is None else w.game_of_env[:4096])
+    a = W.actions(w.action_seed, 0, 2, probe.n, w.games[0].n_actions)
+    probe.step(a[0], threads=threads)
+    t0 = time.perf_counter()
+    probe.step(a[1], threads=threads)
+    rate = probe.n / (time.perf_counter() - t0)
+    probe.close()
+    m = int(max(64, min(w.n_envs, rate * args.ref_budget / max(1, K + Wm))))
+    goe = None if w.game_of_env is None else w.game_of_env[:m]
+    env = oracle.OracleEnv(w.games, m, seed=w.seed, game_of_env=goe)
+    env.reset()
+    for s in range(Wm):
+        env.step(W.actions(w.action_seed, s, s + 1, m, w.games[0].n_actions)[0], threads=threads)
+    acts = W.actions(w.action_seed, 0, K, m, w.games[0].n_actions) if K * m <= 2e9 else None
+    t0 = time.perf_counter()
+    for s in range(K):
+        row = acts[s] if acts is not None else W.actions(w.action_seed, s, s + 1, m)[0]
+        env.step(row, threads=threads)
+    dt = time.perf_counter() - t0
+    value = m * K / dt
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "env steps/s",
+            "n_gpus": world, "steps": K, "warmup": Wm, "ms_per_step": round(dt * 1e3 / K, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic (seeded template ROM, Philox actions)",
+            "config": {"workload": describe(args.config, w), "n_envs_sampled": m},
+            "cpu_baseline": {"value": round(value, 1), "unit": "env steps/s", "cores": threads,
+                             "kind": "oracle",
+                             "sample": f"{m} of {w.n_envs} instances per step, {K} steps"},
+            "e2e": {"value": round(value, 1), "unit": "env steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=0, help="timed env steps (0 = the workload's)")
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="octax", choices=["octax", "reference"])
+    ap.add_argument("--config", default="scale", choices=["scale", "small", "batch", "divergence"])
+    ap.add_argument("--rollout", type=int, default=32, help="steps per octax_step_n call")
+    ap.add_argument("--launch", default="", help="block,steps_per_launch,persistent,graph")
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=90.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        line = run_reference(args)
+        if line:
+            print(json.dumps(line), flush=True)
+        return
+    line = run_gpu(args)
+    if line is None:
+        return
+    if not args.no_cpu and line["n_gpus"] == 1:
+        w = workload(args.config)
+        line["cpu_baseline"] = cpu_oracle(w, args.cpu_budget, os.cpu_count() or 1)
+        line["cpu_baseline"]["single_core"] = cpu_oracle(w, args.cpu_budget / 3, 1)["value"]
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()
