@@ -117,12 +117,15 @@ typedef struct {
   uint32_t env_steps;        /* steps since creation (random-number counter) */
 } octax_state_record;        /* 4416 bytes */
 
-/* Launch configuration (chosen by octax_autotune or set by hand). */
+/* Launch configuration (chosen by octax_autotune or set by hand). A CTA of
+ * `block` threads runs block/32 * inst_per_warp instances of one game. */
 typedef struct {
-  int32_t block;             /* instances per CTA: 32, 64, 128 or 256            */
+  int32_t block;             /* threads per CTA: 32, 64, 128 or 256             */
+  int32_t inst_per_warp;     /* instances emulated per warp: 1, 2, 4, 8, 16, 32 */
   int32_t steps_per_launch;  /* octax_step_n: env steps per kernel launch 1..64  */
   int32_t persistent;        /* 1: resident CTAs pull instance groups off a queue */
   int32_t use_graph;         /* 1: octax_step_n replays a captured CUDA graph     */
+  int32_t reserved;          /* 0                                                */
 } octax_launch;
 
 typedef struct octax_env octax_env;
@@ -195,6 +198,69 @@ int octax_stack_frames(const octax_env *env);
 /* Device bytes owned by the environment. */
 size_t octax_device_bytes(const octax_env *env);
 void octax_destroy(octax_env *env);
+
+/* ---- serving: continuous batching of step requests ------------------------
+ * A server keeps a pool of resident emulator slots sized by a device-memory
+ * budget and runs its own thread and CUDA stream. Each request asks for
+ * n_envs fresh instances of one game (reset with its own seed; instance i has
+ * random-number identity i) stepped n_steps times with the given actions.
+ * Queued requests are admitted first-in first-out as slots free up; every
+ * scheduling tick launches one step kernel over all admitted requests, each
+ * at its own step, so requests that arrive while others run join the next
+ * tick. Results are identical to running the request alone (octax_create +
+ * octax_step with the same seed). */
+typedef struct octax_server octax_server;
+
+typedef struct {
+  int64_t memory_budget_bytes; /* device bytes for resident instance state; the
+                                  slot pool holds budget / 4,454 instances    */
+  int32_t block;               /* threads per CTA: 32, 64, 128, 256 (0 = 64)    */
+  int32_t inst_per_warp;       /* 1, 2, 4, 8, 16, 32 (0 = 8)                    */
+  int32_t max_inflight_ticks;  /* batched launches enqueued ahead, 1..8 (0 = 2) */
+  int32_t reserved;
+} octax_server_config;
+
+typedef struct {
+  uint16_t game;               /* index into the server's games               */
+  uint16_t pad;
+  uint32_t n_envs;             /* 1..4096                                     */
+  uint32_t n_steps;            /* 1..8                                        */
+  uint32_t pad2;
+  uint64_t seed;               /* Philox key of this request's instances     */
+  const uint8_t *actions_host; /* [n_steps][n_envs] action indices, copied    */
+  uint8_t *obs_dev;            /* [n_steps][n_envs][S][32][64], 16-byte aligned */
+  float *reward_dev;           /* [n_steps][n_envs]                           */
+  uint8_t *done_dev;           /* [n_steps][n_envs]                           */
+} octax_request;               /* the caller keeps the device buffers alive until done */
+
+typedef struct {
+  int32_t state;               /* 0 queued, 1 running, 2 done                 */
+  int32_t pad;
+  int64_t submit_ns, admit_ns, done_ns; /* steady-clock timestamps (ns)       */
+} octax_request_info;
+
+typedef struct {
+  int64_t submitted, completed, env_steps, ticks;
+  int64_t peak_active_envs, peak_active_requests;
+  int64_t slots_capacity, slots_in_use, queued;
+} octax_server_stats;
+
+/* Start a server over n_games games (same descriptor rules as octax_create).
+ * EINVAL: bad descriptors / config; ENOMEM: the budget cannot be allocated. */
+int octax_server_create(const octax_game *games, int n_games, uint32_t quirks,
+                        const octax_server_config *cfg, octax_server **out);
+/* Queue a request (thread-safe, returns at once). EINVAL: bad fields;
+ * ENOMEM: n_envs exceeds the whole slot pool. */
+int octax_server_submit(octax_server *s, const octax_request *req, uint64_t *id_out);
+/* Wait until request id is done (its outputs are then complete in device
+ * memory). timeout_ms < 0 waits without limit; ETIMEOUT, ENOTFOUND. */
+int octax_server_wait(octax_server *s, uint64_t id, int timeout_ms, octax_request_info *info_out);
+int octax_server_query(octax_server *s, uint64_t id, octax_request_info *info_out);
+/* Forget a finished request's bookkeeping. EINVAL if it is not done. */
+int octax_server_release(octax_server *s, uint64_t id);
+int octax_server_get_stats(octax_server *s, octax_server_stats *out);
+/* Finish enqueued work, stop the thread, free the pool. */
+void octax_server_destroy(octax_server *s);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *octax_last_error(void);

@@ -50,9 +50,10 @@ struct GroupTable {
 };
 
 struct GraphKey {
-  int n_steps, block, spl, persistent;
+  int n_steps, block, ipw, spl, persistent;
   bool operator<(const GraphKey &o) const {
-    return std::tie(n_steps, block, spl, persistent) < std::tie(o.n_steps, o.block, o.spl, o.persistent);
+    return std::tie(n_steps, block, ipw, spl, persistent) <
+           std::tie(o.n_steps, o.block, o.ipw, o.spl, o.persistent);
   }
 };
 
@@ -73,7 +74,7 @@ struct octax_env {
   uint32_t *slot_of_row_d = nullptr;
   std::vector<void *> allocs;
   size_t bytes = 0;
-  octax_launch cfg{64, 4, 0, 1};
+  octax_launch cfg{64, 8, 4, 0, 1, 0};
   std::map<int, GroupTable> groups;
   unsigned int *counters_d = nullptr;
   int counters_cap = 0;
@@ -162,8 +163,31 @@ GameDev to_dev(const octax_game &g) {
 }
 
 int block_ok(int b) { return b == 32 || b == 64 || b == 128 || b == 256; }
+int ipw_ok(int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32; }
+int per_cta(const octax_launch &c) { return c.block / 32 * c.inst_per_warp; }
 
-// Groups of up to `block` consecutive same-game slots.
+}  // namespace
+
+// Validate the descriptors and build the device descriptors + initial RAM images.
+int octax::build_games(const octax_game *games, int n_games, std::vector<GameDev> &dev,
+                       std::vector<uint8_t> &images) {
+  for (int g = 0; g < n_games; ++g) {
+    int rc = validate_game(games[g], games[0].stack_frames);
+    if (rc) return rc;
+  }
+  dev.clear();
+  images.assign((size_t)n_games * kRamBytes, 0);
+  for (int g = 0; g < n_games; ++g) {
+    dev.push_back(to_dev(games[g]));
+    memcpy(&images[(size_t)g * kRamBytes + 0x50], kFont, sizeof kFont);
+    memcpy(&images[(size_t)g * kRamBytes + 0x200], games[g].rom, games[g].rom_len);
+  }
+  return OCTAX_OK;
+}
+
+namespace {
+
+// Groups of up to `block` (instances per CTA) consecutive same-game slots.
 int get_groups(octax_env *e, int block, GroupTable **out) {
   auto it = e->groups.find(block);
   if (it != e->groups.end()) {
@@ -210,6 +234,7 @@ StepLaunch base_launch(octax_env *e, const GroupTable *gt) {
   p.n_groups = gt->count;
   p.S = e->S;
   p.quirks = e->quirks;
+  p.ipw = e->cfg.inst_per_warp;
   return p;
 }
 
@@ -230,11 +255,13 @@ int check_io(const uint8_t *actions, const uint8_t *obs, const float *reward, co
 // Enqueue n_steps steps as a chain of launches of `spl` steps each.
 int enqueue_steps(octax_env *e, const octax_launch &cfg, int n_steps, const IO &io) {
   GroupTable *gt = nullptr;
-  int rc = get_groups(e, cfg.block, &gt);
+  int rc = get_groups(e, per_cta(cfg), &gt);
   if (rc) return rc;
   const int spl = cfg.steps_per_launch;
   const int launches = (n_steps + spl - 1) / spl;
-  const int grid = cfg.persistent ? std::min(gt->count, std::max(1, max_resident_ctas(cfg.block))) : gt->count;
+  const int grid = cfg.persistent
+                       ? std::min(gt->count, std::max(1, max_resident_ctas(cfg.block, cfg.inst_per_warp)))
+                       : gt->count;
   if (cfg.persistent) {
     rc = ensure_counters(e, launches);
     if (rc) return rc;
@@ -246,6 +273,7 @@ int enqueue_steps(octax_env *e, const octax_launch &cfg, int n_steps, const IO &
     }
     for (int j = 0; j < launches; ++j) {
       StepLaunch p = base_launch(e, gt);
+      p.ipw = cfg.inst_per_warp;
       p.io0 = io;
       p.step0 = j * spl;
       p.steps = std::min(spl, n_steps - j * spl);
@@ -256,7 +284,7 @@ int enqueue_steps(octax_env *e, const octax_launch &cfg, int n_steps, const IO &
     return OCTAX_OK;
   }
   // CUDA graph: the kernels read their IO from io_d, refreshed before replay.
-  const GraphKey key{n_steps, cfg.block, spl, cfg.persistent};
+  const GraphKey key{n_steps, cfg.block, cfg.inst_per_warp, spl, cfg.persistent};
   auto it = e->graphs.find(key);
   if (it == e->graphs.end()) {
     cudaGraph_t g;
@@ -277,6 +305,7 @@ int enqueue_steps(octax_env *e, const octax_launch &cfg, int n_steps, const IO &
     }
     for (int j = 0; j < launches; ++j) {
       StepLaunch p = base_launch(e, gt);
+      p.ipw = cfg.inst_per_warp;
       p.io_table = e->io_d;
       p.step0 = j * spl;
       p.steps = std::min(spl, n_steps - j * spl);
@@ -330,8 +359,10 @@ int octax_create(const octax_game *games, int n_games, const uint16_t *game_of_e
     set_error("octax_create: unknown quirk bits");
     return OCTAX_EINVAL;
   }
-  for (int g = 0; g < n_games; ++g) {
-    int rc = validate_game(games[g], games[0].stack_frames);
+  std::vector<GameDev> games_dev;
+  std::vector<uint8_t> images;
+  {
+    int rc = build_games(games, n_games, games_dev, images);
     if (rc) return rc;
   }
   if (game_of_env)
@@ -371,13 +402,7 @@ int octax_create(const octax_game *games, int n_games, const uint16_t *game_of_e
     e->game_of_slot[s] = game_of_env ? game_of_env[row] : 0;
     uid_of_slot[s] = uid_of_env ? uid_of_env[row] : row;
   }
-  // descriptors and initial RAM images
-  std::vector<uint8_t> images((size_t)n_games * kRamBytes, 0);
-  for (int g = 0; g < n_games; ++g) {
-    e->games_h.push_back(to_dev(games[g]));
-    memcpy(&images[(size_t)g * kRamBytes + 0x50], kFont, sizeof kFont);
-    memcpy(&images[(size_t)g * kRamBytes + 0x200], games[g].rom, games[g].rom_len);
-  }
+  e->games_h = games_dev;
   const size_t n = (size_t)n_envs;
   DevState &st = e->st;
   st.n = n_envs;
@@ -423,7 +448,7 @@ int octax_create(const octax_game *games, int n_games, const uint16_t *game_of_e
     return rc;
   }
   GroupTable *gt = nullptr;
-  int rc = get_groups(e, e->cfg.block, &gt);
+  int rc = get_groups(e, per_cta(e->cfg), &gt);
   if (rc) {
     free_env(e);
     return rc;
@@ -437,6 +462,7 @@ int octax_create(const octax_game *games, int n_games, const uint16_t *game_of_e
   p.n_groups = gt->count;
   p.S = e->S;
   p.quirks = quirks;
+  p.ipw = e->cfg.inst_per_warp;
   p.init = 1;
   p.seed = seed;
   p.uid_of_slot = uid_tmp;
@@ -461,7 +487,7 @@ int octax_reset(octax_env *e, const uint8_t *mask_dev, uint8_t *obs_dev) {
     return OCTAX_EINVAL;
   }
   GroupTable *gt = nullptr;
-  int rc = get_groups(e, e->cfg.block, &gt);
+  int rc = get_groups(e, per_cta(e->cfg), &gt);
   if (rc) return rc;
   ResetLaunch p;
   memset(&p, 0, sizeof p);
@@ -474,6 +500,7 @@ int octax_reset(octax_env *e, const uint8_t *mask_dev, uint8_t *obs_dev) {
   p.obs = obs_dev;
   p.S = e->S;
   p.quirks = e->quirks;
+  p.ipw = e->cfg.inst_per_warp;
   cudaError_t r = launch_reset(p, e->cfg.block, e->stream);
   return r == cudaSuccess ? OCTAX_OK : cuda_fail(r, "octax_reset");
 }
@@ -612,9 +639,11 @@ int octax_get_launch(const octax_env *e, octax_launch *out) {
 }
 
 int octax_set_launch(octax_env *e, const octax_launch *cfg) {
-  if (!e || !cfg || !block_ok(cfg->block) || cfg->steps_per_launch < 1 || cfg->steps_per_launch > 64 ||
-      (cfg->persistent != 0 && cfg->persistent != 1) || (cfg->use_graph != 0 && cfg->use_graph != 1)) {
-    set_error("octax_set_launch: block in {32,64,128,256}, steps_per_launch 1..64, flags 0/1");
+  if (!e || !cfg || !block_ok(cfg->block) || !ipw_ok(cfg->inst_per_warp) || cfg->steps_per_launch < 1 ||
+      cfg->steps_per_launch > 64 || (cfg->persistent != 0 && cfg->persistent != 1) ||
+      (cfg->use_graph != 0 && cfg->use_graph != 1)) {
+    set_error("octax_set_launch: block in {32,64,128,256}, inst_per_warp in {1,2,4,8,16,32}, "
+              "steps_per_launch 1..64, flags 0/1");
     return OCTAX_EINVAL;
   }
   e->cfg = *cfg;
@@ -671,27 +700,33 @@ int octax_autotune(octax_env *e, int n_steps, float *best_ms_out) {
   float best_ms = 1e30f;
   int rc = OCTAX_OK;
   const int blocks[] = {32, 64, 128, 256};
+  const int ipws[] = {32, 16, 8, 4};
   const int spls[] = {1, 2, 4, 8};
   for (int b : blocks) {
-    for (int pers = 0; pers < 2 && rc == OCTAX_OK; ++pers) {
-      for (int spl : spls) {
-        if (spl > n_steps) continue;
-        octax_launch c{b, spl, pers, 1};
-        rc = enqueue_steps(e, c, n_steps, io);  // warm-up (graph build)
-        if (rc) break;
-        float ms_min = 1e30f;
-        for (int rep = 0; rep < 3 && rc == OCTAX_OK; ++rep) {
-          cudaEventRecord(t0, e->stream);
-          rc = enqueue_steps(e, c, n_steps, io);
-          cudaEventRecord(t1, e->stream);
-          cudaEventSynchronize(t1);
-          float ms = 0;
-          cudaEventElapsedTime(&ms, t0, t1);
-          ms_min = std::min(ms_min, ms);
-        }
-        if (rc == OCTAX_OK && ms_min < best_ms) {
-          best_ms = ms_min;
-          best = c;
+    for (int ipw : ipws) {
+      const int J = b / 32 * ipw;
+      if (J < 8 || J > 256) continue;
+      for (int pers = 0; pers < 2 && rc == OCTAX_OK; ++pers) {
+        for (int spl : spls) {
+          if (spl > n_steps) continue;
+          octax_launch c{b, ipw, spl, pers, 1, 0};
+          e->cfg = c;
+          rc = enqueue_steps(e, c, n_steps, io);  // warm-up (graph build)
+          if (rc) break;
+          float ms_min = 1e30f;
+          for (int rep = 0; rep < 3 && rc == OCTAX_OK; ++rep) {
+            cudaEventRecord(t0, e->stream);
+            rc = enqueue_steps(e, c, n_steps, io);
+            cudaEventRecord(t1, e->stream);
+            cudaEventSynchronize(t1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, t0, t1);
+            ms_min = std::min(ms_min, ms);
+          }
+          if (rc == OCTAX_OK && ms_min < best_ms) {
+            best_ms = ms_min;
+            best = c;
+          }
         }
       }
     }

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "octax.h"
 
@@ -54,13 +55,13 @@ struct DevState {
   uint16_t *game;         // [n]
 };
 
-// A group: up to `block` consecutive slots that share one game (one CTA's work).
+// A group: up to block/32*ipw consecutive slots that share one game (one CTA's work).
 struct Group {
   uint32_t slot0;
   uint16_t count;
   uint16_t game;
   uint32_t io;            // index into the IO table (0 when launched with io0)
-  uint32_t pad;
+  uint32_t row0;          // output row of slot0 within its request (serving resets)
 };
 
 // Where one request's per-step inputs and outputs live.
@@ -84,6 +85,7 @@ struct StepLaunch {
   int steps;               // env steps in this launch
   int S;                   // stack frames
   uint32_t quirks;
+  int ipw;                 // instances emulated per warp (1..32)
   unsigned int *work_counter;  // non-null: persistent CTAs pull groups from it
 };
 
@@ -97,12 +99,15 @@ struct ResetLaunch {
   uint8_t *obs;            // [rows][S][32][64] by out_row, nullable
   int S;
   uint32_t quirks;
+  int ipw;
   int init;                // 1: also set key/uid/env_steps/status (creation)
   uint64_t seed;
   const uint32_t *uid_of_slot;  // used when init (nullable = out_row)
+  const uint64_t *seed_of_group;  // init: per-group seed (nullable = seed)
+  int set_rows;            // init: out_row = group.row0 + lane, game = group.game
 };
 
-size_t step_smem_bytes(int block);
+size_t step_smem_bytes(int block, int ipw);
 cudaError_t launch_step(const StepLaunch &p, int grid, int block, cudaStream_t s);
 cudaError_t launch_reset(const ResetLaunch &p, int block, cudaStream_t s);
 cudaError_t launch_hash(const DevState &st, const uint8_t *images, const uint32_t *slot_of_row,
@@ -112,10 +117,17 @@ cudaError_t launch_records(const DevState &st, const uint8_t *images, const uint
 cudaError_t launch_set_records(const DevState &st, const GameDev *games, const uint8_t *images,
                                const uint32_t *slot_of_row, int64_t first, int64_t count,
                                const octax_state_record *in, cudaStream_t s);
-int max_resident_ctas(int block);
+int max_resident_ctas(int block, int ipw);
+// Bytes of device state per slot (all DevState arrays).
+constexpr size_t kSlotStateBytes = 16 + 4 + 4 + 32 + 256 + 8 + 4096 + 4 + 4 + 4 + 8 + 4 + 4 + 2;
+cudaError_t alloc_state(DevState &st, int64_t n, void **block_out, size_t *bytes_out);
 // Append one step launch to a graph (after `dep`, if non-null).
 cudaError_t add_step_node(cudaGraph_t g, cudaGraphNode_t *node, cudaGraphNode_t dep, const StepLaunch &p,
                           int grid, int block);
+
+// Validate game descriptors; build device descriptors and 4 KB RAM images.
+int build_games(const octax_game *games, int n_games, std::vector<GameDev> &dev,
+                std::vector<uint8_t> &images);
 
 // Error reporting (thread-local message).
 void set_error(const std::string &msg);

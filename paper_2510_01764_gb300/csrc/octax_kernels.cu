@@ -374,28 +374,28 @@ __device__ __forceinline__ uint4 expand16(uint64_t row, uint32_t q) {
 }
 
 // Whole-warp frame write: lane -> instance 8m + lane/4 of the warp, quarter
-// lane%4 of every row. frame (per lane, 0 = skip) points at the 2 KB frame of
-// that lane's own instance.
-__device__ __forceinline__ void capture_frame(const uint64_t *disp_warp, int B, uint8_t *frame,
-                                              int lane) {
+// lane%4 of every row, for the warp's `ipw` instances. frame (per lane, 0 =
+// skip) points at the 2 KB frame of that lane's own instance.
+__device__ __forceinline__ void capture_frame(const uint64_t *disp_warp, int J, uint8_t *frame,
+                                              int lane, int ipw) {
   const uint64_t mine = reinterpret_cast<uint64_t>(frame);
   const uint32_t q = lane & 3;
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
+  const int passes = (ipw + 7) >> 3;
+  for (int m = 0; m < passes; ++m) {
     const int src = 8 * m + (lane >> 2);
     const uint64_t base = __shfl_sync(kFull, mine, src);
     if (base) {
       const uint64_t *col = disp_warp + src;
       uint8_t *dst = reinterpret_cast<uint8_t *>(base) + q * 16u;
 #pragma unroll 8
-      for (int r = 0; r < 32; ++r) __stcs(reinterpret_cast<uint4 *>(dst + r * 64), expand16(col[r * B], q));
+      for (int r = 0; r < 32; ++r) __stcs(reinterpret_cast<uint4 *>(dst + r * 64), expand16(col[r * J], q));
     }
   }
 }
 
 // Whole-warp write of the reset observation (display repeated S times) for
 // every lane whose bit is set in `which`. obs: that lane's S-frame block.
-__device__ __forceinline__ void write_reset_obs(const uint64_t *disp_warp, int B, uint8_t *obs, int S,
+__device__ __forceinline__ void write_reset_obs(const uint64_t *disp_warp, int J, uint8_t *obs, int S,
                                                 unsigned which, int lane) {
   const uint64_t mine = reinterpret_cast<uint64_t>(obs);
   while (which) {
@@ -406,7 +406,7 @@ __device__ __forceinline__ void write_reset_obs(const uint64_t *disp_warp, int B
 #pragma unroll
     for (int it = 0; it < 4; ++it) {
       const int c = it * 32 + lane;  // 16-byte chunk of the 2 KB frame
-      const uint4 o = expand16(col[(c >> 2) * B], c & 3);
+      const uint4 o = expand16(col[(c >> 2) * J], c & 3);
       for (int s = 0; s < S; ++s)
         __stcs(reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(base) + s * kFrameBytes + c * 16), o);
     }
@@ -420,12 +420,13 @@ struct Smem {
   uint32_t *stack;
 };
 
-__device__ __forceinline__ Smem carve(uint8_t *smem, int B) {
+// Shared memory of a CTA with J instances: image | game | display [32][J] | stack [16][J].
+__device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
   Smem s;
   s.img = smem;
   s.game = reinterpret_cast<GameDev *>(smem + kRamBytes);
   s.disp = reinterpret_cast<uint64_t *>(smem + kRamBytes + kGameSmem);
-  s.stack = reinterpret_cast<uint32_t *>(s.disp + 32 * B);
+  s.stack = reinterpret_cast<uint32_t *>(s.disp + 32 * J);
   return s;
 }
 
@@ -474,25 +475,32 @@ __device__ __forceinline__ void store_regs(const Regs &R, const DevState &st, in
 }
 
 __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
-  const int B = blockDim.x, t = threadIdx.x, lane = t & 31, wbase = t & ~31;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, ipw = p.ipw;
+  const int J = (blockDim.x >> 5) * ipw;  // instances per CTA
+  const int j = w * ipw + lane;           // this lane's instance (if lane < ipw)
   const DevState &st = p.st;
   const int64_t n = st.n;
   const GameDev &G = *S.game;
-  const bool active = t < (int)g.count;
-  const int64_t slot = (int64_t)g.slot0 + (active ? t : 0);
+  const bool mine = lane < ipw;
+  const bool active = mine && j < (int)g.count;
+  const int64_t slot = (int64_t)g.slot0 + (active ? j : 0);
   const IO io = p.io_table ? p.io_table[g.io] : p.io0;
   const uint32_t quirks = p.quirks;
+  uint64_t *disp_warp = S.disp + w * ipw;
 
   Regs R;
   load_regs(R, st, slot);
   const int64_t row = active ? (int64_t)st.out_row[slot] : 0;
   uint32_t ep = st.ep[slot];
   int32_t prev = st.prev_score[slot];
+  if (mine) {
 #pragma unroll
-  for (int i = 0; i < 16; ++i) S.stack[i * B + t] = st.stack[i * n + slot];
+    for (int i = 0; i < 16; ++i) S.stack[i * J + j] = st.stack[i * n + slot];
 #pragma unroll 8
-  for (int r = 0; r < 32; ++r) S.disp[r * B + t] = st.disp[r * n + slot];
-  const Ctx C{S.img, S.disp + t, S.stack + t, st.ram + slot * (int64_t)kRamBytes, B};
+    for (int r = 0; r < 32; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
+  }
+  const Ctx C{S.img, S.disp + (mine ? j : 0), S.stack + (mine ? j : 0),
+              st.ram + slot * (int64_t)kRamBytes, J};
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
   __syncwarp();
 
@@ -515,8 +523,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
       }
       if (f >= first_kept) {
         __syncwarp();
-        capture_frame(S.disp + wbase, B, my_obs ? my_obs + (f - first_kept) * kFrameBytes : nullptr,
-                      lane);
+        capture_frame(disp_warp, J, my_obs ? my_obs + (f - first_kept) * kFrameBytes : nullptr, lane, ipw);
         __syncwarp();
       }
     }
@@ -539,7 +546,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
     const unsigned which = __ballot_sync(kFull, done);
     if (which) {
       __syncwarp();
-      write_reset_obs(S.disp + wbase, B, my_obs, p.S, which, lane);
+      write_reset_obs(disp_warp, J, my_obs, p.S, which, lane);
       __syncwarp();
     }
   }
@@ -549,15 +556,15 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
     st.ep[slot] = ep;
     st.prev_score[slot] = prev;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) st.stack[i * n + slot] = (uint16_t)S.stack[i * B + t];
+    for (int i = 0; i < 16; ++i) st.stack[i * n + slot] = (uint16_t)S.stack[i * J + j];
 #pragma unroll 8
-    for (int r = 0; r < 32; ++r) st.disp[r * n + slot] = S.disp[r * B + t];
+    for (int r = 0; r < 32; ++r) st.disp[r * n + slot] = S.disp[r * J + j];
   }
 }
 
 __global__ void __launch_bounds__(kMaxBlock) step_kernel(const StepLaunch p) {
   extern __shared__ __align__(16) uint8_t smem[];
-  const Smem S = carve(smem, blockDim.x);
+  const Smem S = carve(smem, (blockDim.x >> 5) * p.ipw);
   __shared__ int s_group;
   int cur_game = -1;
   int gi = blockIdx.x;
@@ -582,34 +589,38 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const StepLaunch p) {
 
 __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
   extern __shared__ __align__(16) uint8_t smem[];
-  const Smem S = carve(smem, blockDim.x);
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, ipw = p.ipw;
+  const int J = (blockDim.x >> 5) * ipw;
+  const int j = w * ipw + lane;
+  const Smem S = carve(smem, J);
   const Group g = p.groups[blockIdx.x];
   stage_game(S, p.games, p.images, g.game);
   __syncthreads();
-  const int B = blockDim.x, t = threadIdx.x, lane = t & 31, wbase = t & ~31;
   const DevState &st = p.st;
   const int64_t n = st.n;
   const GameDev &G = *S.game;
-  const bool active = t < (int)g.count;
-  const int64_t slot = (int64_t)g.slot0 + (active ? t : 0);
-  const int64_t row = active ? (int64_t)st.out_row[slot] : 0;
+  const bool mine = lane < ipw;
+  const bool active = mine && j < (int)g.count;
+  const int64_t slot = (int64_t)g.slot0 + (active ? j : 0);
+  const int64_t row = !active ? 0 : (p.init && p.set_rows) ? (int64_t)(g.row0 + j) : (int64_t)st.out_row[slot];
   const bool doit = active && (p.mask == nullptr || p.mask[row] != 0);
   Regs R;
   if (p.init) {
+    const uint64_t seed = p.seed_of_group ? p.seed_of_group[blockIdx.x] : p.seed;
     R.status = 0;
     R.env_steps = 0;
-    R.key0 = (uint32_t)(p.seed & 0xFFFFFFFFu);
-    R.key1 = (uint32_t)(p.seed >> 32);
+    R.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
+    R.key1 = (uint32_t)(seed >> 32);
     R.uid = p.uid_of_slot ? p.uid_of_slot[slot] : (uint32_t)row;
   } else {
     load_regs(R, st, slot);
   }
-  const Ctx C{S.img, S.disp + t, S.stack + t, st.ram + slot * (int64_t)kRamBytes, B};
+  const Ctx C{S.img, S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), st.ram + slot * (int64_t)kRamBytes, J};
   if (doit) reset_instance(R, C, G, p.quirks);
   const unsigned which = __ballot_sync(kFull, doit);
   if (p.obs && which) {
     __syncwarp();
-    write_reset_obs(S.disp + wbase, B, doit ? p.obs + row * (int64_t)p.S * kFrameBytes : nullptr, p.S,
+    write_reset_obs(S.disp + w * ipw, J, doit ? p.obs + row * (int64_t)p.S * kFrameBytes : nullptr, p.S,
                     which, lane);
     __syncwarp();
   }
@@ -621,11 +632,15 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
       st.key[slot] = R.key0;
       st.key[n + slot] = R.key1;
       st.uid[slot] = R.uid;
+      if (p.set_rows) {
+        st.out_row[slot] = (uint32_t)row;
+        st.game[slot] = g.game;
+      }
     }
 #pragma unroll
-    for (int i = 0; i < 16; ++i) st.stack[i * n + slot] = (uint16_t)S.stack[i * B + t];
+    for (int i = 0; i < 16; ++i) st.stack[i * n + slot] = (uint16_t)S.stack[i * J + j];
 #pragma unroll 8
-    for (int r = 0; r < 32; ++r) st.disp[r * n + slot] = S.disp[r * B + t];
+    for (int r = 0; r < 32; ++r) st.disp[r * n + slot] = S.disp[r * J + j];
   }
 }
 
@@ -758,18 +773,19 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
 
 }  // namespace
 
-size_t step_smem_bytes(int block) {
-  return (size_t)kRamBytes + kGameSmem + (size_t)block * (32 * sizeof(uint64_t) + 16 * sizeof(uint32_t));
+size_t step_smem_bytes(int block, int ipw) {
+  const size_t J = (size_t)(block / 32) * ipw;
+  return (size_t)kRamBytes + kGameSmem + J * (32 * sizeof(uint64_t) + 16 * sizeof(uint32_t));
 }
 
 static cudaError_t ensure_smem_attr() {
   static bool done = false;
   if (done) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)step_smem_bytes(kMaxBlock));
+                                       (int)step_smem_bytes(kMaxBlock, 32));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(reset_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)step_smem_bytes(kMaxBlock));
+                           (int)step_smem_bytes(kMaxBlock, 32));
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -778,7 +794,7 @@ cudaError_t launch_step(const StepLaunch &p, int grid, int block, cudaStream_t s
   cudaError_t e = ensure_smem_attr();
   if (e != cudaSuccess) return e;
   if (grid <= 0) return cudaSuccess;
-  step_kernel<<<grid, block, step_smem_bytes(block), s>>>(p);
+  step_kernel<<<grid, block, step_smem_bytes(block, p.ipw), s>>>(p);
   return cudaGetLastError();
 }
 
@@ -786,7 +802,7 @@ cudaError_t launch_reset(const ResetLaunch &p, int block, cudaStream_t s) {
   cudaError_t e = ensure_smem_attr();
   if (e != cudaSuccess) return e;
   if (p.n_groups <= 0) return cudaSuccess;
-  reset_kernel<<<p.n_groups, block, step_smem_bytes(block), s>>>(p);
+  reset_kernel<<<p.n_groups, block, step_smem_bytes(block, p.ipw), s>>>(p);
   return cudaGetLastError();
 }
 
@@ -828,17 +844,43 @@ cudaError_t add_step_node(cudaGraph_t g, cudaGraphNode_t *node, cudaGraphNode_t 
   kp.func = reinterpret_cast<void *>(step_kernel);
   kp.gridDim = dim3((unsigned)grid);
   kp.blockDim = dim3((unsigned)block);
-  kp.sharedMemBytes = (unsigned)step_smem_bytes(block);
+  kp.sharedMemBytes = (unsigned)step_smem_bytes(block, p.ipw);
   kp.kernelParams = args;
   return cudaGraphAddKernelNode(node, g, dep ? &dep : nullptr, dep ? 1 : 0, &kp);
 }
 
-int max_resident_ctas(int block) {
+cudaError_t alloc_state(DevState &st, int64_t n, void **block_out, size_t *bytes_out) {
+  const size_t N = (size_t)n;
+  // every array starts on a 256-byte boundary
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t sizes[] = {16 * N, 4 * N, 4 * N, 32 * N, 256 * N, 8 * N, 4096 * N,
+                          4 * N,  4 * N, 4 * N, 8 * N,  4 * N,   4 * N, 2 * N};
+  size_t total = 0;
+  for (size_t b : sizes) total += up(b);
+  uint8_t *base = nullptr;
+  cudaError_t e = cudaMalloc(&base, total);
+  if (e != cudaSuccess) return e;
+  size_t off = 0;
+  void **dst[] = {(void **)&st.v,   (void **)&st.pcI,        (void **)&st.misc,      (void **)&st.stack,
+                  (void **)&st.disp, (void **)&st.dirty,     (void **)&st.ram,       (void **)&st.ep,
+                  (void **)&st.env_steps, (void **)&st.prev_score, (void **)&st.key, (void **)&st.uid,
+                  (void **)&st.out_row, (void **)&st.game};
+  for (int i = 0; i < 14; ++i) {
+    *dst[i] = base + off;
+    off += up(sizes[i]);
+  }
+  st.n = n;
+  *block_out = base;
+  *bytes_out = total;
+  return cudaSuccess;
+}
+
+int max_resident_ctas(int block, int ipw) {
   if (ensure_smem_attr() != cudaSuccess) return 0;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel, block, step_smem_bytes(block));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel, block, step_smem_bytes(block, ipw));
   return sms * per_sm;
 }
 

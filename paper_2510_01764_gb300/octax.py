@@ -52,8 +52,9 @@ class CGame(C.Structure):
 
 
 class CLaunch(C.Structure):
-    _fields_ = [("block", C.c_int32), ("steps_per_launch", C.c_int32),
-                ("persistent", C.c_int32), ("use_graph", C.c_int32)]
+    _fields_ = [("block", C.c_int32), ("inst_per_warp", C.c_int32),
+                ("steps_per_launch", C.c_int32), ("persistent", C.c_int32),
+                ("use_graph", C.c_int32), ("reserved", C.c_int32)]
 
 
 RECORD_DTYPE = np.dtype([("V", np.uint8, 16), ("I", "<u2"), ("PC", "<u2"), ("SP", np.uint8),
@@ -62,10 +63,37 @@ RECORD_DTYPE = np.dtype([("V", np.uint8, 16), ("I", "<u2"), ("PC", "<u2"), ("SP"
                          ("episode_steps", "<u4"), ("env_steps", "<u4")])
 assert RECORD_DTYPE.itemsize == 4416
 
+class CServerConfig(C.Structure):
+    _fields_ = [("memory_budget_bytes", C.c_int64), ("block", C.c_int32),
+                ("inst_per_warp", C.c_int32), ("max_inflight_ticks", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class CRequest(C.Structure):
+    _fields_ = [("game", C.c_uint16), ("pad", C.c_uint16), ("n_envs", C.c_uint32),
+                ("n_steps", C.c_uint32), ("pad2", C.c_uint32), ("seed", C.c_uint64),
+                ("actions_host", C.c_void_p), ("obs_dev", C.c_void_p),
+                ("reward_dev", C.c_void_p), ("done_dev", C.c_void_p)]
+
+
+class CRequestInfo(C.Structure):
+    _fields_ = [("state", C.c_int32), ("pad", C.c_int32), ("submit_ns", C.c_int64),
+                ("admit_ns", C.c_int64), ("done_ns", C.c_int64)]
+
+
+class CServerStats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("submitted", "completed", "env_steps", "ticks",
+                                         "peak_active_envs", "peak_active_requests",
+                                         "slots_capacity", "slots_in_use", "queued")]
+
+
 EXPORTS = ("octax_create", "octax_reset", "octax_step", "octax_step_n", "octax_step_host",
            "octax_state_hash", "octax_get_state", "octax_set_state", "octax_sync",
            "octax_get_launch", "octax_set_launch", "octax_autotune", "octax_num_envs",
-           "octax_stack_frames", "octax_device_bytes", "octax_destroy", "octax_last_error")
+           "octax_stack_frames", "octax_device_bytes", "octax_destroy", "octax_last_error",
+           "octax_server_create", "octax_server_submit", "octax_server_wait",
+           "octax_server_query", "octax_server_release", "octax_server_get_stats",
+           "octax_server_destroy")
 
 _lib = None
 _lock = threading.Lock()
@@ -101,6 +129,14 @@ def load_library(path: str = LIB_PATH):
             "octax_device_bytes": (C.c_size_t, [P]),
             "octax_destroy": (None, [P]),
             "octax_last_error": (C.c_char_p, []),
+            "octax_server_create": (I32, [C.POINTER(CGame), I32, C.c_uint32,
+                                          C.POINTER(CServerConfig), C.POINTER(P)]),
+            "octax_server_submit": (I32, [P, C.POINTER(CRequest), C.POINTER(C.c_uint64)]),
+            "octax_server_wait": (I32, [P, C.c_uint64, I32, C.POINTER(CRequestInfo)]),
+            "octax_server_query": (I32, [P, C.c_uint64, C.POINTER(CRequestInfo)]),
+            "octax_server_release": (I32, [P, C.c_uint64]),
+            "octax_server_get_stats": (I32, [P, C.POINTER(CServerStats)]),
+            "octax_server_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -277,13 +313,15 @@ class Env:
     def launch(self) -> dict:
         c = CLaunch()
         check(load_library().octax_get_launch(self._h, C.byref(c)))
-        return {"block": c.block, "steps_per_launch": c.steps_per_launch,
-                "persistent": c.persistent, "use_graph": c.use_graph}
+        return {"block": c.block, "inst_per_warp": c.inst_per_warp,
+                "steps_per_launch": c.steps_per_launch, "persistent": c.persistent,
+                "use_graph": c.use_graph}
 
     def set_launch(self, **kw) -> None:
         cur = self.launch
         cur.update(kw)
-        c = CLaunch(cur["block"], cur["steps_per_launch"], cur["persistent"], cur["use_graph"])
+        c = CLaunch(cur["block"], cur["inst_per_warp"], cur["steps_per_launch"], cur["persistent"],
+                    cur["use_graph"], 0)
         check(load_library().octax_set_launch(self._h, C.byref(c)))
 
     def autotune(self, n_steps: int = 8) -> float:
@@ -298,6 +336,89 @@ class Env:
     def close(self) -> None:
         if getattr(self, "_h", None):
             load_library().octax_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server (octax_server_*) on one GPU.
+
+    ``submit`` queues a request for ``n_envs`` fresh instances of one game,
+    stepped ``n_steps`` times with ``actions`` (uint8 [n_steps, n_envs]); the
+    outputs land in device tensors that stay referenced here until the
+    request is released."""
+
+    def __init__(self, games, *, memory_budget_bytes: int, block: int = 64,
+                 inst_per_warp: int = 8, max_inflight_ticks: int = 2, quirks: int = 0,
+                 device=None):
+        import torch
+
+        self._torch = torch
+        L = load_library()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        torch.cuda.set_device(self.device)
+        self.games = list(games)
+        self.S = int(self.games[0].stack_frames)
+        keep = [make_game(g) for g in self.games]
+        arr = (CGame * len(keep))(*[k[0] for k in keep])
+        cfg = CServerConfig(int(memory_budget_bytes), block, inst_per_warp, max_inflight_ticks, 0)
+        h = C.c_void_p()
+        check(L.octax_server_create(arr, len(keep), quirks, C.byref(cfg), C.byref(h)))
+        self._h = h
+        self._keep = keep
+        self._outs: dict[int, tuple] = {}
+
+    def submit(self, game: int, actions: np.ndarray, seed: int, out=None) -> int:
+        torch = self._torch
+        a = np.ascontiguousarray(actions, dtype=np.uint8)
+        T, n = a.shape
+        if out is None:
+            out = (torch.empty((T, n, self.S, 32, 64), dtype=torch.uint8, device=self.device),
+                   torch.empty((T, n), dtype=torch.float32, device=self.device),
+                   torch.empty((T, n), dtype=torch.uint8, device=self.device))
+        obs, rew, done = out
+        req = CRequest(game, 0, n, T, 0, seed & 0xFFFFFFFFFFFFFFFF, a.ctypes.data,
+                       obs.data_ptr(), rew.data_ptr(), done.data_ptr())
+        rid = C.c_uint64()
+        check(load_library().octax_server_submit(self._h, C.byref(req), C.byref(rid)))
+        self._outs[rid.value] = out
+        return rid.value
+
+    def outputs(self, rid: int) -> tuple:
+        return self._outs[rid]
+
+    @staticmethod
+    def _info(i: CRequestInfo) -> dict:
+        return {"state": i.state, "submit_ns": i.submit_ns, "admit_ns": i.admit_ns,
+                "done_ns": i.done_ns}
+
+    def wait(self, rid: int, timeout_ms: int = -1) -> dict:
+        info = CRequestInfo()
+        check(load_library().octax_server_wait(self._h, rid, timeout_ms, C.byref(info)))
+        return self._info(info)
+
+    def query(self, rid: int) -> dict:
+        info = CRequestInfo()
+        check(load_library().octax_server_query(self._h, rid, C.byref(info)))
+        return self._info(info)
+
+    def release(self, rid: int) -> None:
+        check(load_library().octax_server_release(self._h, rid))
+        self._outs.pop(rid, None)
+
+    def stats(self) -> dict:
+        st = CServerStats()
+        check(load_library().octax_server_get_stats(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in CServerStats._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load_library().octax_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

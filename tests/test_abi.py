@@ -42,15 +42,76 @@ def test_binding_covers_the_header():
     assert set(octax.EXPORTS) <= set(declared_functions())
 
 
-def test_struct_layouts_match_header():
-    from paper_2510_01764_gb300 import octax
+LAYOUT_C = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "octax.h"
+#define P(T) printf(#T " %zu\n", sizeof(T))
+#define O(T, f) printf(#T "." #f " %zu\n", offsetof(T, f))
+int main(void) {
+  P(octax_term); P(octax_clause); P(octax_game); P(octax_state_record); P(octax_launch);
+  P(octax_server_config); P(octax_request); P(octax_request_info); P(octax_server_stats);
+  O(octax_game, rom_len); O(octax_game, action_set); O(octax_game, score); O(octax_game, term);
+  O(octax_game, max_episode_steps); O(octax_game, startup_instrs);
+  O(octax_state_record, display); O(octax_state_record, ram); O(octax_state_record, env_steps);
+  O(octax_request, seed); O(octax_request, actions_host); O(octax_request, done_dev);
+  return 0;
+}
+"""
 
-    assert C.sizeof(octax.CTerm) == 8
-    assert C.sizeof(octax.CClause) == 16
-    assert octax.CGame.score.offset == 36 and octax.CGame.term.offset == 68
-    assert C.sizeof(octax.CGame) == 144
-    assert octax.RECORD_DTYPE.itemsize == 4416
-    assert C.sizeof(octax.CLaunch) == 16
+
+def test_struct_layouts_match_header(tmp_path):
+    """Compile the header with gcc and compare every size/offset with ctypes."""
+    import subprocess
+
+    from paper_2510_01764_gb300 import octax as o
+
+    src = tmp_path / "layout.c"
+    src.write_text(LAYOUT_C)
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src),
+                           "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    sizes = {"octax_term": o.CTerm, "octax_clause": o.CClause, "octax_game": o.CGame,
+             "octax_launch": o.CLaunch, "octax_server_config": o.CServerConfig,
+             "octax_request": o.CRequest, "octax_request_info": o.CRequestInfo,
+             "octax_server_stats": o.CServerStats}
+    for name, cls in sizes.items():
+        assert int(got[name]) == C.sizeof(cls), name
+    assert int(got["octax_state_record"]) == o.RECORD_DTYPE.itemsize
+    for key, val in got.items():
+        if "." not in key:
+            continue
+        struct, field = key.split(".")
+        if struct == "octax_state_record":
+            assert int(val) == o.RECORD_DTYPE.fields[field][1], key
+        else:
+            cls = {"octax_game": o.CGame, "octax_request": o.CRequest}[struct]
+            assert int(val) == getattr(cls, field).offset, key
+
+
+def test_descriptor_validation_without_gpu(lib):
+    """octax_create rejects bad descriptors before touching the device."""
+    from paper_2510_01764_gb300 import octax as o
+    from paper_2510_01764_gb300.workloads import GameSpec
+
+    L = o.load_library()
+    bad = [GameSpec(rom=b""), GameSpec(rom=b"\x00" * 3585), GameSpec(rom=b"\x12\x00", frameskip=2),
+           GameSpec(rom=b"\x12\x00", instr_per_frame=0), GameSpec(rom=b"\x12\x00", action_set=(16,)),
+           GameSpec(rom=b"\x12\x00", startup_instrs=(1 << 20) + 1)]
+    for g in bad:
+        cg, keep = o.make_game(g) if len(g.rom) else (o.CGame(), None)
+        arr = (o.CGame * 1)(cg)
+        h = C.c_void_p()
+        rc = L.octax_create(arr, 1, None, None, 4, 0, 0, None, C.byref(h))
+        assert rc == o.EINVAL, g
+        assert L.octax_last_error()
+    cg, keep = o.make_game(GameSpec(rom=b"\x12\x00"))
+    arr = (o.CGame * 1)(cg)
+    h = C.c_void_p()
+    assert L.octax_create(arr, 1, None, None, 0, 0, 0, None, C.byref(h)) == o.EINVAL
+    assert L.octax_create(arr, 1, None, None, 4, 0x40, 0, None, C.byref(h)) == o.EINVAL
+    assert L.octax_create(arr, 0, None, None, 4, 0, 0, None, C.byref(h)) == o.EINVAL
 
 
 def test_binding_refuses_without_library(tmp_path):

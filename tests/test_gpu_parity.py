@@ -86,10 +86,13 @@ def test_config_small_full_parity():
 
 
 @pytest.mark.parametrize("launch", [
-    dict(block=32, steps_per_launch=1, persistent=0, use_graph=0),
-    dict(block=64, steps_per_launch=4, persistent=0, use_graph=1),
-    dict(block=128, steps_per_launch=3, persistent=1, use_graph=1),
-    dict(block=256, steps_per_launch=8, persistent=1, use_graph=0),
+    dict(block=32, inst_per_warp=32, steps_per_launch=1, persistent=0, use_graph=0),
+    dict(block=64, inst_per_warp=32, steps_per_launch=4, persistent=0, use_graph=1),
+    dict(block=128, inst_per_warp=8, steps_per_launch=3, persistent=1, use_graph=1),
+    dict(block=256, inst_per_warp=4, steps_per_launch=8, persistent=1, use_graph=0),
+    dict(block=64, inst_per_warp=1, steps_per_launch=2, persistent=0, use_graph=1),
+    dict(block=256, inst_per_warp=16, steps_per_launch=5, persistent=0, use_graph=1),
+    dict(block=32, inst_per_warp=2, steps_per_launch=1, persistent=1, use_graph=0),
 ])
 def test_launch_configurations_agree(launch):
     w = W.cfg_small()
@@ -116,7 +119,7 @@ def test_quirk_bits(quirks):
 @pytest.mark.parametrize("n", [1, 31, 33, 100])
 def test_ragged_instance_counts(n):
     w = W.cfg_small()
-    full_compare(w.games, n, 40, seed=2, action_seed=2, launch=dict(block=64))
+    full_compare(w.games, n, 40, seed=2, action_seed=2, launch=dict(block=64, inst_per_warp=32))
 
 
 def test_mixed_games_timing_and_stacks():
@@ -212,7 +215,7 @@ def test_checkpoint_roundtrip():
             assert torch.equal(x, y)
     # records restore into a fresh environment too (different launch config)
     env2 = o.Env(games, n, seed=5, game_of_env=goe)
-    env2.set_launch(block=32)
+    env2.set_launch(block=32, inst_per_warp=4)
     env2.set_state(ck)
     assert np.array_equal(hashes(env2), h_ck)
 
@@ -248,7 +251,7 @@ def test_autotune_leaves_no_trace():
     assert np.array_equal(hashes(env), h0)
     o1 = env.step_n(acts[20:])
     ref = o.Env(w.games, n, seed=1)
-    ref.set_launch(block=32, steps_per_launch=1, persistent=0, use_graph=0)
+    ref.set_launch(block=32, inst_per_warp=32, steps_per_launch=1, persistent=0, use_graph=0)
     ref.step_n(acts[:20])
     o2 = ref.step_n(acts[20:])
     for x, y in zip(o1, o2):
@@ -345,7 +348,8 @@ def test_config_scale_sampled_persistent_graph():
     w = W.cfg_scale(n_steps=6000)
     sample = pick(w.n_envs, 16, 2, extra=(5, w.n_envs - 2))
     sampled_run(w, chunk=40, sample=sample,
-                launch=dict(block=64, steps_per_launch=4, persistent=1, use_graph=1))
+                launch=dict(block=128, inst_per_warp=8, steps_per_launch=4, persistent=1,
+                            use_graph=1))
 
 
 def test_config_batch_sampled():
@@ -356,7 +360,8 @@ def test_config_batch_sampled():
     per_game = [np.nonzero(goe == g)[0][:2] for g in range(16)]
     sample = np.unique(np.concatenate(per_game + [pick(w.n_envs, 16, 3)]))
     sampled_run(w, chunk=32, sample=sample,
-                launch=dict(block=64, steps_per_launch=4, persistent=1, use_graph=1))
+                launch=dict(block=64, inst_per_warp=16, steps_per_launch=4, persistent=1,
+                            use_graph=1))
 
 
 def test_config_divergence_sampled():
@@ -364,4 +369,5 @@ def test_config_divergence_sampled():
     w = W.cfg_divergence()
     sample = pick(w.n_envs, 32, 4, extra=(0, 1, w.n_envs - 1))
     sampled_run(w, chunk=8, sample=sample,
-                launch=dict(block=64, steps_per_launch=4, persistent=0, use_graph=1))
+                launch=dict(block=128, inst_per_warp=32, steps_per_launch=4, persistent=0,
+                            use_graph=1))
