@@ -179,10 +179,11 @@ def run_gpu(args) -> dict | None:
 
         # ---- launch configuration: autotuned for T-step calls
         if args.launch:
-            b, spl, pers, gr = (int(x) for x in args.launch.split(","))
-            env.set_launch(block=b, steps_per_launch=spl, persistent=pers, use_graph=gr)
+            b, ipw, spl, pers, gr = (int(x) for x in args.launch.split(","))
+            env.set_launch(block=b, inst_per_warp=ipw, steps_per_launch=spl, persistent=pers,
+                           use_graph=gr)
         else:
-            env.autotune(T)
+            env.autotune(T, acts[:T])
         launch = env.launch
         calls = [(lo, min(lo + T, K)) for lo in range(0, K, T)]
 
@@ -218,7 +219,8 @@ def run_gpu(args) -> dict | None:
         with Clocks(local) as clk:
             ms_best, _ = timed(launch)
         clocks = clk.summary()
-        plain_cfg = dict(block=launch["block"], steps_per_launch=1, persistent=0, use_graph=0)
+        plain_cfg = dict(block=launch["block"], inst_per_warp=launch["inst_per_warp"],
+                         steps_per_launch=1, persistent=0, use_graph=0)
         ms_plain, _ = timed(plain_cfg)
         env.set_launch(**launch)
 
@@ -391,7 +393,8 @@ def main():
     ap.add_argument("--impl", default="octax", choices=["octax", "reference"])
     ap.add_argument("--config", default="scale", choices=["scale", "small", "batch", "divergence"])
     ap.add_argument("--rollout", type=int, default=32, help="steps per octax_step_n call")
-    ap.add_argument("--launch", default="", help="block,steps_per_launch,persistent,graph")
+    ap.add_argument("--launch", default="",
+                    help="block,inst_per_warp,steps_per_launch,persistent,graph (default: autotune)")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=90.0)

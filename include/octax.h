@@ -188,10 +188,13 @@ int octax_get_launch(const octax_env *env, octax_launch *out);
 /* EINVAL for unsupported values. */
 int octax_set_launch(octax_env *env, const octax_launch *cfg);
 
-/* Time candidate launch configurations on a scratch copy of this environment
- * (results unaffected) and keep the fastest for octax_step_n with n_steps
- * steps per call. Synchronous. best_ms_out (nullable) receives its time. */
-int octax_autotune(octax_env *env, int n_steps, float *best_ms_out);
+/* Time candidate launch configurations (CTA size, instances per warp, steps
+ * per launch, persistence) for octax_step_n calls of n_steps steps, starting
+ * from the current state, then restore that state: results are unaffected.
+ * actions_dev [n_steps][n_envs] (nullable: pseudo-random indices 0..4) should
+ * be representative, since divergence depends on them. Keeps the fastest
+ * configuration. Synchronous. best_ms_out (nullable) receives its time. */
+int octax_autotune(octax_env *env, int n_steps, const uint8_t *actions_dev, float *best_ms_out);
 
 int64_t octax_num_envs(const octax_env *env);
 int octax_stack_frames(const octax_env *env);

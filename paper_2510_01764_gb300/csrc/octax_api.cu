@@ -650,7 +650,7 @@ int octax_set_launch(octax_env *e, const octax_launch *cfg) {
   return OCTAX_OK;
 }
 
-int octax_autotune(octax_env *e, int n_steps, float *best_ms_out) {
+int octax_autotune(octax_env *e, int n_steps, const uint8_t *actions_dev, float *best_ms_out) {
   if (!e || n_steps < 1) {
     set_error("octax_autotune: need env and n_steps >= 1");
     return OCTAX_EINVAL;
@@ -690,7 +690,21 @@ int octax_autotune(octax_env *e, int n_steps, float *best_ms_out) {
     cudaMemcpyAsync(backup + off, pc.p, pc.bytes, cudaMemcpyDeviceToDevice, e->stream);
     off += pc.bytes;
   }
-  cudaMemsetAsync(acts, 0, (size_t)n_steps * n, e->stream);
+  if (actions_dev) {
+    cudaMemcpyAsync(acts, actions_dev, (size_t)n_steps * n, cudaMemcpyDeviceToDevice, e->stream);
+  } else {  // uniform over each game's action indices (including the no-op)
+    std::vector<uint8_t> h((size_t)n_steps * n);
+    uint64_t x = 0x9E3779B97F4A7C15ull;
+    for (size_t i = 0; i < h.size(); ++i) {
+      x += 0x9E3779B97F4A7C15ull;  // splitmix64
+      uint64_t z = x;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      h[i] = (uint8_t)(z % 5u);
+    }
+    cudaMemcpy(acts, h.data(), h.size(), cudaMemcpyHostToDevice);
+  }
   IO io{acts, obs, rew, done, e->n};
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);

@@ -123,7 +123,7 @@ def load_library(path: str = LIB_PATH):
             "octax_sync": (I32, [P, I32]),
             "octax_get_launch": (I32, [P, C.POINTER(CLaunch)]),
             "octax_set_launch": (I32, [P, C.POINTER(CLaunch)]),
-            "octax_autotune": (I32, [P, I32, C.POINTER(C.c_float)]),
+            "octax_autotune": (I32, [P, I32, P, C.POINTER(C.c_float)]),
             "octax_num_envs": (I64, [P]),
             "octax_stack_frames": (I32, [P]),
             "octax_device_bytes": (C.c_size_t, [P]),
@@ -324,9 +324,13 @@ class Env:
                     cur["use_graph"], 0)
         check(load_library().octax_set_launch(self._h, C.byref(c)))
 
-    def autotune(self, n_steps: int = 8) -> float:
+    def autotune(self, n_steps: int = 8, actions=None) -> float:
+        """Pick the fastest launch configuration for step_n calls of n_steps
+        steps (actions: representative uint8 [n_steps, n] device tensor)."""
+        if actions is not None:
+            self._check_dev(actions, self._torch.uint8, (n_steps, self.n), "actions")
         ms = C.c_float()
-        check(load_library().octax_autotune(self._h, n_steps, C.byref(ms)))
+        check(load_library().octax_autotune(self._h, n_steps, _ptr(actions), C.byref(ms)))
         return ms.value
 
     @property
