@@ -312,7 +312,87 @@ def run_gpu(args) -> dict | None:
     }
     if prof and prof.get("issue"):
         line["issue_roofline"] = prof["issue"]
+    if not args.no_serve and world == 1:
+        line["serving"] = run_serving(args, dev)
+        line["serving_p50_ms"] = line["serving"]["poisson"]["p50_ms"]
+        line["serving_p99_ms"] = line["serving"]["poisson"]["p99_ms"]
     return line
+
+
+# --------------------------------------------------------------------------- serving
+def serving_trace(total_steps: int, seed: int = 55):
+    """Poisson arrivals per game at mixed rates (10, 100, 1000 /s), each request
+    (game, 1-4,096 envs log-uniform, 1-8 steps, uniform actions, seed), until
+    the requests add up to total_steps env steps."""
+    rng = np.random.Generator(np.random.Philox(key=seed))
+    rates = [(10.0, 100.0, 1000.0)[g % 3] for g in range(16)]
+    t = [float(rng.exponential(1.0 / r)) for r in rates]
+    reqs, steps = [], 0
+    while steps < total_steps:
+        g = int(np.argmin(t))
+        n = int(min(4096, max(1, round(float(np.exp(rng.uniform(0.0, np.log(4096.0))))))))
+        T = int(rng.integers(1, 9))
+        acts = rng.integers(0, 4, size=(T, n), dtype=np.uint8)
+        reqs.append(dict(t=t[g], game=g, actions=acts, seed=int(rng.integers(0, 2**62))))
+        steps += n * T
+        t[g] += float(rng.exponential(1.0 / rates[g]))
+    t0 = reqs[0]["t"]
+    for r in reqs:
+        r["t"] -= t0
+    return reqs
+
+
+def run_serving(args, dev) -> dict:
+    import torch
+
+    from paper_2510_01764_gb300 import octax
+
+    games = W.cfg_batch(n_envs=64, n_steps=1).games
+    reqs = serving_trace(args.serve_steps)
+    total = sum(int(np.prod(r["actions"].shape)) for r in reqs)
+    obs = torch.empty((total, 4, 32, 64), dtype=torch.uint8, device=dev)
+    rew = torch.empty(total, dtype=torch.float32, device=dev)
+    done = torch.empty(total, dtype=torch.uint8, device=dev)
+    outs, off = [], 0
+    for r in reqs:
+        T, n = r["actions"].shape
+        k = T * n
+        outs.append((obs[off:off + k].view(T, n, 4, 32, 64), rew[off:off + k].view(T, n),
+                     done[off:off + k].view(T, n)))
+        off += k
+    res = {}
+    for mode in ("poisson", "saturated"):
+        srv = octax.Server(games, memory_budget_bytes=int(args.serve_budget_gb * 1e9), block=64,
+                           inst_per_warp=8, max_inflight_ticks=2, device=dev.index)
+        # warm-up: one small request per game
+        for g in range(16):
+            srv.wait(srv.submit(g, np.zeros((1, 8), np.uint8), 1, out=None))
+        torch.cuda.synchronize(dev)
+        base = srv.stats()
+        ids = []
+        t_start = time.perf_counter()
+        for r, out in zip(reqs, outs):
+            if mode == "poisson":
+                while time.perf_counter() - t_start < r["t"]:
+                    pass
+            ids.append(srv.submit(r["game"], r["actions"], r["seed"], out=out))
+        infos = [srv.wait(i) for i in ids]
+        st = srv.stats()
+        srv.close()
+        lat = np.array([(i["done_ns"] - i["submit_ns"]) / 1e6 for i in infos])
+        qwait = np.array([(i["admit_ns"] - i["submit_ns"]) / 1e6 for i in infos])
+        span = (max(i["done_ns"] for i in infos) - min(i["submit_ns"] for i in infos)) / 1e9
+        res[mode] = {"env_steps_per_s": round(total / span, 1), "p50_ms": round(float(np.percentile(lat, 50)), 4),
+                     "p99_ms": round(float(np.percentile(lat, 99)), 4),
+                     "mean_admission_wait_ms": round(float(qwait.mean()), 4),
+                     "makespan_s": round(span, 4), "ticks": st["ticks"] - base["ticks"],
+                     "peak_active_requests": st["peak_active_requests"],
+                     "peak_active_envs": st["peak_active_envs"]}
+    del obs, rew, done
+    return {"requests": len(reqs), "env_steps": total, "games": 16,
+            "arrivals": "Poisson per game, rates 10/100/1000 per s; envs log-uniform 1-4096; "
+                        "1-8 steps; budget %.0f GB" % args.serve_budget_gb,
+            **{f"{m}": v for m, v in res.items()}}
 
 
 # --------------------------------------------------------------------------- CPU oracle
@@ -399,6 +479,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=90.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-steps", type=int, default=1_000_000)
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     args = ap.parse_args()
     if args.impl == "reference":
         line = run_reference(args)

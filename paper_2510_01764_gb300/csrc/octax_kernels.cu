@@ -1,15 +1,21 @@
 // liboctax device code: the vectorised CHIP-8 environment step for sm_103a.
 //
-// Mapping (one CTA = one group of up to `block` instances of one game):
-//  - one thread emulates one instance; V0-VF live in four 32-bit registers,
-//    PC/I/SP/timers/status in registers, the call stack and the bit-packed
-//    64x32 display (one u64 per row, bit x = pixel x) in shared memory, laid
-//    out [row][instance] so a warp touching its own rows never bank-conflicts;
+// Mapping (one CTA = one group of block/32 * ipw instances of one game):
+//  - each warp emulates `ipw` instances, one per lane; PC/I/SP/timers/status
+//    and the 64-bit dirty-page mask live in registers; V0-VF (one u32 each),
+//    the call stack and the bit-packed 64x32 display (one u64 per row, bit x =
+//    pixel x) live in shared memory laid out [register|entry|row][instance],
+//    so lanes touching their own instance never bank-conflict;
 //  - the game's initial 4 KB RAM image (font + ROM) is staged once per CTA in
 //    shared memory and is read-only; an instance's writes go to 64-byte pages
-//    of its own RAM in global memory, tracked by a 64-bit dirty mask kept in a
-//    register. Fetches and loads read the shared image unless the page is
-//    dirty, and a reset only clears the mask;
+//    of its own RAM in global memory, tracked by the dirty mask. Fetches and
+//    loads read the shared image unless the page is dirty, and a reset only
+//    clears the mask;
+//  - dispatch limits divergence: the common opcodes (jumps, skips, loads,
+//    adds, ALU, key tests, timer and index ops) run through one branch-free
+//    predicated datapath that every lane executes together; only the rare or
+//    heavy ones (DXYN, CXNN, calls/returns, 00E0, BCD and bulk memory ops,
+//    quirk variants, undefined encodings) take a divergent switch;
 //  - observation frames are expanded from the packed rows by the whole warp
 //    together: every store is a 16-byte streaming store and each store
 //    instruction writes eight complete 64-byte image rows.
@@ -25,7 +31,6 @@ namespace {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 struct Regs {
-  uint32_t v0, v1, v2, v3;  // V0..VF, byte j of vk = V[4k + j]
   uint32_t pc, I, sp, dt, st, status;
   uint64_t dirty;
   uint32_t draws, phase, env_steps;
@@ -34,33 +39,24 @@ struct Regs {
 
 struct Ctx {
   const uint8_t *img;  // shared: initial RAM image of this CTA's game
-  uint64_t *disp;      // shared: this instance's row 0; row r at disp[r * B]
-  uint32_t *stack;     // shared: this instance's entry 0; entry i at stack[i * B]
+  uint64_t *disp;      // shared: this instance's row 0; row r at disp[r * J]
+  uint32_t *stack;     // shared: this instance's entry 0; entry i at stack[i * J]
+  uint32_t *V;         // shared: this instance's V0; Vx at V[x * J]
   uint8_t *ram;        // global: this instance's 4 KB RAM (dirty pages)
-  int B;
+  int J;
 };
 
-__device__ __forceinline__ uint32_t getV(const Regs &R, uint32_t x) {
-  uint32_t lo = (x & 8u) ? R.v2 : R.v0;
-  uint32_t hi = (x & 8u) ? R.v3 : R.v1;
-  return __byte_perm(lo, hi, x & 7u) & 0xFFu;
-}
+__device__ __forceinline__ uint32_t getV(const Ctx &C, uint32_t x) { return C.V[x * C.J]; }
+__device__ __forceinline__ void setV(const Ctx &C, uint32_t x, uint32_t val) { C.V[x * C.J] = val & 0xFFu; }
+__device__ __forceinline__ void setVF(const Ctx &C, uint32_t f) { C.V[15 * C.J] = f; }
 
-__device__ __forceinline__ void setV(Regs &R, uint32_t x, uint32_t val) {
-  const uint32_t sh = (x & 3u) * 8u;
-  const uint32_t keep = ~(0xFFu << sh), ins = (val & 0xFFu) << sh;
-  const uint32_t w = x >> 2;
-  R.v0 = (w == 0) ? ((R.v0 & keep) | ins) : R.v0;
-  R.v1 = (w == 1) ? ((R.v1 & keep) | ins) : R.v1;
-  R.v2 = (w == 2) ? ((R.v2 & keep) | ins) : R.v2;
-  R.v3 = (w == 3) ? ((R.v3 & keep) | ins) : R.v3;
+__device__ __forceinline__ uint32_t dirty_bit(uint64_t dirty, uint32_t a) {
+  return (uint32_t)(dirty >> ((a & 0xFFFu) >> kPageShift)) & 1u;
 }
-
-__device__ __forceinline__ void setVF(Regs &R, uint32_t f) { R.v3 = (R.v3 & 0x00FFFFFFu) | (f << 24); }
 
 __device__ __forceinline__ uint32_t rd8(const Regs &R, const Ctx &C, uint32_t a) {
   a &= 0xFFFu;
-  return ((R.dirty >> (a >> kPageShift)) & 1u) ? (uint32_t)C.ram[a] : (uint32_t)C.img[a];
+  return dirty_bit(R.dirty, a) ? (uint32_t)C.ram[a] : (uint32_t)C.img[a];
 }
 
 __device__ __forceinline__ void wr8(Regs &R, const Ctx &C, uint32_t a, uint32_t val) {
@@ -106,8 +102,10 @@ __device__ __forceinline__ void tick(Regs &R) {
 // DXYN: XOR an 8-wide, n-row sprite at (vx mod 64, vy mod 32); VF = collision.
 __device__ __forceinline__ void draw(Regs &R, const Ctx &C, uint32_t vx, uint32_t vy, uint32_t n,
                                      uint32_t quirks) {
-  const uint32_t x0 = vx & 63u, y0 = vy & 31u;
+  const uint32_t x0 = vx & 63u, y0 = vy & 31u, I = R.I;
   const bool wrap = quirks & OCTAX_QUIRK_WRAP_SPRITES;
+  // the sprite spans at most two pages: read it from the image unless one is dirty
+  const bool clean = n == 0 || !(dirty_bit(R.dirty, I) | dirty_bit(R.dirty, I + n - 1u));
   uint32_t coll = 0;
   for (uint32_t r = 0; r < n; ++r) {
     uint32_t py = y0 + r;
@@ -115,42 +113,38 @@ __device__ __forceinline__ void draw(Regs &R, const Ctx &C, uint32_t vx, uint32_
       if (!wrap) break;
       py &= 31u;
     }
-    const uint32_t rev = __brev(rd8(R, C, R.I + r)) >> 24;  // pixel j of the sprite -> bit j
-    uint64_t s = (uint64_t)rev << x0;                      // right edge clips
+    const uint32_t a = (I + r) & 0xFFFu;
+    const uint32_t b = clean ? (uint32_t)C.img[a] : rd8(R, C, a);
+    const uint32_t rev = __brev(b) >> 24;   // pixel j of the sprite -> bit j
+    uint64_t s = (uint64_t)rev << x0;        // right edge clips
     if (wrap && x0 > 56u) s |= (uint64_t)rev >> (64u - x0);
-    uint64_t *row = C.disp + py * C.B;
+    uint64_t *row = C.disp + py * C.J;
     const uint64_t old = *row;
     coll |= (old & s) != 0ull;
     *row = old ^ s;
   }
-  setVF(R, coll);
+  setVF(C, coll);
 }
 
-// One fetch / decode / execute cycle. key: held CHIP-8 key or -1.
-__device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_t quirks) {
-  const uint32_t pc = R.pc;
-  uint32_t op;
-  if (!((pc & 1u) | (uint32_t)((R.dirty >> (pc >> kPageShift)) & 1u))) {
-    op = __byte_perm(*reinterpret_cast<const uint16_t *>(C.img + pc), 0u, 0x4401);
-  } else {
-    op = (rd8(R, C, pc) << 8) | rd8(R, C, pc + 1u);
-  }
-  R.pc = (pc + 2u) & 0xFFFu;
+// The rare / heavy instructions and every variant the fast datapath leaves
+// out (quirk bits, undefined encodings). PC has already been advanced.
+__device__ __forceinline__ void exec_slow(Regs &R, const Ctx &C, uint32_t op, uint32_t pc, int key,
+                                       uint32_t quirks) {
   const uint32_t x = (op >> 8) & 15u, y = (op >> 4) & 15u, n = op & 15u, nn = op & 0xFFu;
   const uint32_t nnn = op & 0xFFFu;
-  const uint32_t vx = getV(R, x), vy = getV(R, y);
+  const uint32_t vx = getV(C, x), vy = getV(C, y);
   switch (op >> 12) {
     case 0x0:
       if (op == 0x00E0u) {
 #pragma unroll 8
-        for (int r = 0; r < 32; ++r) C.disp[r * C.B] = 0ull;
+        for (int r = 0; r < 32; ++r) C.disp[r * C.J] = 0ull;
       } else if (op == 0x00EEu) {
         if (R.sp == 0) {
           R.status |= OCTAX_STATUS_STACK_FAULT;
           R.sp = 16;
         }
         R.sp -= 1;
-        R.pc = C.stack[R.sp * C.B];
+        R.pc = C.stack[R.sp * C.J];
       }
       break;
     case 0x1:
@@ -161,7 +155,7 @@ __device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_
         R.status |= OCTAX_STATUS_STACK_FAULT;
         R.sp = 0;
       }
-      C.stack[R.sp * C.B] = R.pc;
+      C.stack[R.sp * C.J] = R.pc;
       R.sp += 1;
       R.pc = nnn;
       break;
@@ -176,50 +170,50 @@ __device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_
       else if (vx == vy) R.pc = (R.pc + 2u) & 0xFFFu;
       break;
     case 0x6:
-      setV(R, x, nn);
+      setV(C, x, nn);
       break;
     case 0x7:
-      setV(R, x, vx + nn);
+      setV(C, x, vx + nn);
       break;
     case 0x8:
       switch (n) {
-        case 0x0: setV(R, x, vy); break;
+        case 0x0: setV(C, x, vy); break;
         case 0x1:
-          setV(R, x, vx | vy);
-          if (quirks & OCTAX_QUIRK_LOGIC_RESETS_VF) setVF(R, 0);
+          setV(C, x, vx | vy);
+          if (quirks & OCTAX_QUIRK_LOGIC_RESETS_VF) setVF(C, 0);
           break;
         case 0x2:
-          setV(R, x, vx & vy);
-          if (quirks & OCTAX_QUIRK_LOGIC_RESETS_VF) setVF(R, 0);
+          setV(C, x, vx & vy);
+          if (quirks & OCTAX_QUIRK_LOGIC_RESETS_VF) setVF(C, 0);
           break;
         case 0x3:
-          setV(R, x, vx ^ vy);
-          if (quirks & OCTAX_QUIRK_LOGIC_RESETS_VF) setVF(R, 0);
+          setV(C, x, vx ^ vy);
+          if (quirks & OCTAX_QUIRK_LOGIC_RESETS_VF) setVF(C, 0);
           break;
         case 0x4: {
           const uint32_t s = vx + vy;
-          setV(R, x, s);
-          setVF(R, s >> 8);
+          setV(C, x, s);
+          setVF(C, s >> 8);
           break;
         }
         case 0x5:
-          setV(R, x, vx - vy);
-          setVF(R, vx >= vy);
+          setV(C, x, vx - vy);
+          setVF(C, vx >= vy);
           break;
         case 0x6: {
           const uint32_t src = (quirks & OCTAX_QUIRK_SHIFT_USES_VY) ? vy : vx;
-          setV(R, x, src >> 1);
-          setVF(R, src & 1u);
+          setV(C, x, src >> 1);
+          setVF(C, src & 1u);
           break;
         }
         case 0x7:
-          setV(R, x, vy - vx);
-          setVF(R, vy >= vx);
+          setV(C, x, vy - vx);
+          setVF(C, vy >= vx);
           break;
         case 0xE: {
           const uint32_t src = (quirks & OCTAX_QUIRK_SHIFT_USES_VY) ? vy : vx;
-          setV(R, x, src << 1);
-          setVF(R, src >> 7);
+          setV(C, x, src << 1);
+          setVF(C, src >> 7);
           break;
         }
         default:
@@ -235,13 +229,13 @@ __device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_
       R.I = nnn;
       break;
     case 0xB:
-      R.pc = (nnn + ((quirks & OCTAX_QUIRK_JUMP_VX) ? vx : (R.v0 & 0xFFu))) & 0xFFFu;
+      R.pc = (nnn + ((quirks & OCTAX_QUIRK_JUMP_VX) ? vx : getV(C, 0))) & 0xFFFu;
       break;
     case 0xC: {
       const uint32_t rnd = philox_w0(R.uid, R.env_steps, pc | ((R.draws & 0xFFFFu) << 16), R.phase,
                                      R.key0, R.key1);
       R.draws += 1;
-      setV(R, x, rnd & nn);
+      setV(C, x, rnd & nn);
       break;
     }
     case 0xD:
@@ -260,9 +254,9 @@ __device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_
     }
     default:  // 0xF
       switch (nn) {
-        case 0x07: setV(R, x, R.dt); break;
+        case 0x07: setV(C, x, R.dt); break;
         case 0x0A:
-          if (key >= 0) setV(R, x, (uint32_t)key);
+          if (key >= 0) setV(C, x, (uint32_t)key);
           else R.pc = pc;
           break;
         case 0x15: R.dt = vx; break;
@@ -270,7 +264,7 @@ __device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_
         case 0x1E: {
           const uint32_t s = R.I + vx;
           R.I = s & 0xFFFFu;
-          if (quirks & OCTAX_QUIRK_FX1E_VF) setVF(R, s > 0xFFFu);
+          if (quirks & OCTAX_QUIRK_FX1E_VF) setVF(C, s > 0xFFFu);
           break;
         }
         case 0x29: R.I = 0x50u + 5u * (vx & 15u); break;
@@ -280,11 +274,11 @@ __device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_
           wr8(R, C, R.I + 2u, vx % 10u);
           break;
         case 0x55:
-          for (uint32_t i = 0; i <= x; ++i) wr8(R, C, R.I + i, getV(R, i));
+          for (uint32_t i = 0; i <= x; ++i) wr8(R, C, R.I + i, getV(C, i));
           if (quirks & OCTAX_QUIRK_LOADSTORE_INC_I) R.I = (R.I + x + 1u) & 0xFFFFu;
           break;
         case 0x65:
-          for (uint32_t i = 0; i <= x; ++i) setV(R, i, rd8(R, C, R.I + i));
+          for (uint32_t i = 0; i <= x; ++i) setV(C, i, rd8(R, C, R.I + i));
           if (quirks & OCTAX_QUIRK_LOADSTORE_INC_I) R.I = (R.I + x + 1u) & 0xFFFFu;
           break;
         default:
@@ -295,8 +289,72 @@ __device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_
   }
 }
 
+// One fetch / decode / execute cycle. key: held CHIP-8 key or -1.
+__device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_t quirks) {
+  const uint32_t pc = R.pc;
+  uint32_t op;
+  if (!((pc & 1u) | dirty_bit(R.dirty, pc))) {
+    op = __byte_perm(*reinterpret_cast<const uint16_t *>(C.img + pc), 0u, 0x4401);
+  } else {
+    op = (rd8(R, C, pc) << 8) | rd8(R, C, pc + 1u);
+  }
+  const uint32_t cls = op >> 12, x = (op >> 8) & 15u, y = (op >> 4) & 15u, n = op & 15u;
+  const uint32_t nn = op & 0xFFu, nnn = op & 0xFFFu;
+  // classes the predicated datapath covers (bit c set = class c):
+  // 1 3 4 6 7 A always; 5 9 with N = 0; 8 with N in 0-7,E (classic shifts and
+  // logic); E with 9E/A1; F with 07 0A 15 18 29, and 1E without its quirk.
+  const uint32_t cbit = 1u << cls;
+  bool fast = (cbit & 0x04DAu) != 0;
+  fast |= ((cbit & 0x0220u) != 0) & (n == 0);
+  fast |= (cls == 8) & ((n <= 7) | (n == 14)) &
+          ((quirks & (OCTAX_QUIRK_SHIFT_USES_VY | OCTAX_QUIRK_LOGIC_RESETS_VF)) == 0);
+  fast |= (cls == 14) & ((nn == 0x9Eu) | (nn == 0xA1u));
+  fast |= (cls == 15) & ((nn == 0x07u) | (nn == 0x0Au) | (nn == 0x15u) | (nn == 0x18u) | (nn == 0x29u) |
+                         ((nn == 0x1Eu) & ((quirks & OCTAX_QUIRK_FX1E_VF) == 0)));
+  uint32_t *const Vx = C.V + x * C.J;
+  if (fast) {
+    const uint32_t vx = *Vx, vy = C.V[y * C.J];
+    // next PC: skips, jump, wait-for-key
+    const bool pressed = key >= 0 && (uint32_t)key == (vx & 15u);
+    const bool skip = ((cls == 3) & (vx == nn)) | ((cls == 4) & (vx != nn)) | ((cls == 5) & (vx == vy)) |
+                      ((cls == 9) & (vx != vy)) | ((cls == 14) & ((nn == 0x9Eu) == pressed));
+    uint32_t npc = (pc + (skip ? 4u : 2u)) & 0xFFFu;
+    npc = (cls == 1) ? nnn : npc;
+    npc = ((cls == 15) & (nn == 0x0Au) & (key < 0)) ? pc : npc;
+    R.pc = npc;
+    // 8XYN result and flag (N in 0-7, E)
+    const uint32_t sum = vx + vy;
+    const uint32_t a0 = (n & 1u) ? (vx | vy) : vy, a1 = (n & 1u) ? (vx ^ vy) : (vx & vy);
+    const uint32_t b0 = (n & 1u) ? (vx - vy) : sum, b1 = (n & 1u) ? (vy - vx) : (vx >> 1);
+    uint32_t alu = (n & 4u) ? ((n & 2u) ? b1 : b0) : ((n & 2u) ? a1 : a0);
+    alu = (n == 14) ? (vx << 1) : alu;
+    const uint32_t f0 = (n & 1u) ? (uint32_t)(vx >= vy) : (sum >> 8);
+    const uint32_t f1 = (n & 1u) ? (uint32_t)(vy >= vx) : (vx & 1u);
+    uint32_t flag = (n & 2u) ? f1 : f0;
+    flag = (n == 14) ? (vx >> 7) : flag;
+    // VX write: 6XNN, 7XNN, 8XYN, FX07, FX0A (with a key held)
+    uint32_t val = (cls == 7) ? (vx + nn) : nn;
+    val = (cls == 8) ? alu : val;
+    val = (cls == 15) ? ((nn == 0x07u) ? R.dt : (uint32_t)key) : val;
+    const bool wen = (cls == 6) | (cls == 7) | (cls == 8) |
+                     ((cls == 15) & ((nn == 0x07u) | ((nn == 0x0Au) & (key >= 0))));
+    if (wen) *Vx = val & 0xFFu;
+    if ((cls == 8) & (n >= 4u)) C.V[15 * C.J] = flag;  // after VX: with X = F the flag wins
+    // index register and timers
+    uint32_t I = (cls == 10) ? nnn : R.I;
+    I = ((cls == 15) & (nn == 0x1Eu)) ? ((I + vx) & 0xFFFFu) : I;
+    I = ((cls == 15) & (nn == 0x29u)) ? (0x50u + 5u * (vx & 15u)) : I;
+    R.I = I;
+    R.dt = ((cls == 15) & (nn == 0x15u)) ? vx : R.dt;
+    R.st = ((cls == 15) & (nn == 0x18u)) ? vx : R.st;
+  } else {
+    R.pc = (pc + 2u) & 0xFFFu;
+    exec_slow(R, C, op, pc, key, quirks);
+  }
+}
+
 __device__ __forceinline__ int32_t term_value(const Regs &R, const Ctx &C, const TermDev &t) {
-  const int32_t v = t.src == OCTAX_SRC_REG ? (int32_t)getV(R, t.idx & 15u) : (int32_t)rd8(R, C, t.idx);
+  const int32_t v = t.src == OCTAX_SRC_REG ? (int32_t)getV(C, t.idx & 15u) : (int32_t)rd8(R, C, t.idx);
   switch (t.xform) {
     case OCTAX_X_RAW: return v;
     case OCTAX_X_NEG: return -v;
@@ -335,7 +393,8 @@ __device__ __forceinline__ bool terminated(const Regs &R, const Ctx &C, const Ga
 
 // Power-on state + the game's startup instructions (no key, timers tick every K).
 __device__ __forceinline__ void reset_instance(Regs &R, const Ctx &C, const GameDev &G, uint32_t quirks) {
-  R.v0 = R.v1 = R.v2 = R.v3 = 0;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) C.V[i * C.J] = 0;
   R.pc = 0x200;
   R.I = 0;
   R.sp = 0;
@@ -343,9 +402,9 @@ __device__ __forceinline__ void reset_instance(Regs &R, const Ctx &C, const Game
   R.st = 0;
   R.dirty = 0;
 #pragma unroll
-  for (int i = 0; i < 16; ++i) C.stack[i * C.B] = 0;
+  for (int i = 0; i < 16; ++i) C.stack[i * C.J] = 0;
 #pragma unroll 8
-  for (int r = 0; r < 32; ++r) C.disp[r * C.B] = 0ull;
+  for (int r = 0; r < 32; ++r) C.disp[r * C.J] = 0ull;
   R.phase = 1;
   R.draws = 0;
   uint32_t in_frame = 0;
@@ -418,15 +477,18 @@ struct Smem {
   GameDev *game;
   uint64_t *disp;
   uint32_t *stack;
+  uint32_t *V;
 };
 
-// Shared memory of a CTA with J instances: image | game | display [32][J] | stack [16][J].
+// Shared memory of a CTA with J instances:
+// image | game | display [32][J] u64 | stack [16][J] u32 | V [16][J] u32.
 __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
   Smem s;
   s.img = smem;
   s.game = reinterpret_cast<GameDev *>(smem + kRamBytes);
   s.disp = reinterpret_cast<uint64_t *>(smem + kRamBytes + kGameSmem);
   s.stack = reinterpret_cast<uint32_t *>(s.disp + 32 * J);
+  s.V = s.stack + 16 * J;
   return s;
 }
 
@@ -441,12 +503,8 @@ __device__ __forceinline__ void stage_game(const Smem &S, const GameDev *games, 
 }
 
 __device__ __forceinline__ void load_regs(Regs &R, const DevState &st, int64_t slot) {
-  const int64_t n = st.n;
-  R.v0 = st.v[slot];
-  R.v1 = st.v[n + slot];
-  R.v2 = st.v[2 * n + slot];
-  R.v3 = st.v[3 * n + slot];
   const uint32_t pcI = st.pcI[slot], misc = st.misc[slot];
+  const int64_t n = st.n;
   R.pc = pcI & 0xFFFFu;
   R.I = pcI >> 16;
   R.sp = misc & 0xFFu;
@@ -463,15 +521,30 @@ __device__ __forceinline__ void load_regs(Regs &R, const DevState &st, int64_t s
 }
 
 __device__ __forceinline__ void store_regs(const Regs &R, const DevState &st, int64_t slot) {
-  const int64_t n = st.n;
-  st.v[slot] = R.v0;
-  st.v[n + slot] = R.v1;
-  st.v[2 * n + slot] = R.v2;
-  st.v[3 * n + slot] = R.v3;
   st.pcI[slot] = R.pc | (R.I << 16);
   st.misc[slot] = R.sp | (R.dt << 8) | (R.st << 16) | (R.status << 24);
   st.dirty[slot] = R.dirty;
   st.env_steps[slot] = R.env_steps;
+}
+
+// V0-VF: packed 4 per u32 in global memory, one per u32 in shared memory.
+__device__ __forceinline__ void load_V(const Ctx &C, const DevState &st, int64_t slot) {
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    const uint32_t word = st.v[w * st.n + slot];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) C.V[(4 * w + b) * C.J] = (word >> (8 * b)) & 0xFFu;
+  }
+}
+
+__device__ __forceinline__ void store_V(const Ctx &C, const DevState &st, int64_t slot) {
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    uint32_t word = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) word |= C.V[(4 * w + b) * C.J] << (8 * b);
+    st.v[w * st.n + slot] = word;
+  }
 }
 
 __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
@@ -499,8 +572,9 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
 #pragma unroll 8
     for (int r = 0; r < 32; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
   }
-  const Ctx C{S.img, S.disp + (mine ? j : 0), S.stack + (mine ? j : 0),
+  const Ctx C{S.img, S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
               st.ram + slot * (int64_t)kRamBytes, J};
+  if (mine) load_V(C, st, slot);
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
   __syncwarp();
 
@@ -553,6 +627,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
 
   if (active) {
     store_regs(R, st, slot);
+    store_V(C, st, slot);
     st.ep[slot] = ep;
     st.prev_score[slot] = prev;
 #pragma unroll
@@ -615,7 +690,8 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
   } else {
     load_regs(R, st, slot);
   }
-  const Ctx C{S.img, S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), st.ram + slot * (int64_t)kRamBytes, J};
+  const Ctx C{S.img, S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
+              st.ram + slot * (int64_t)kRamBytes, J};
   if (doit) reset_instance(R, C, G, p.quirks);
   const unsigned which = __ballot_sync(kFull, doit);
   if (p.obs && which) {
@@ -626,6 +702,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
   }
   if (doit) {
     store_regs(R, st, slot);
+    store_V(C, st, slot);
     st.ep[slot] = 0;
     st.prev_score[slot] = score(R, C, G);
     if (p.init) {
@@ -775,7 +852,7 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
 
 size_t step_smem_bytes(int block, int ipw) {
   const size_t J = (size_t)(block / 32) * ipw;
-  return (size_t)kRamBytes + kGameSmem + J * (32 * sizeof(uint64_t) + 16 * sizeof(uint32_t));
+  return (size_t)kRamBytes + kGameSmem + J * (32 * sizeof(uint64_t) + 32 * sizeof(uint32_t));
 }
 
 static cudaError_t ensure_smem_attr() {
