@@ -265,6 +265,31 @@ int octax_server_get_stats(octax_server *s, octax_server_stats *out);
 /* Finish enqueued work, stop the thread, free the pool. */
 void octax_server_destroy(octax_server *s);
 
+/* ---- no-allocation entry point ---------------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that may
+ * not allocate device memory: code running inside another framework's
+ * memory pool or a pre-reserved arena, plugins whose host forbids
+ * allocation after start-up, and real-time loops where an allocation (which
+ * can synchronise the device) would break the timing budget.
+ * Runs n_envs fresh instances of one game (reset with `seed`; instance i has
+ * random-number identity i) for n_steps steps, exactly what octax_create +
+ * octax_step_n compute, but with every piece of scratch state in one
+ * library-owned static device array of fixed size, so the call allocates
+ * nothing. Inputs and outputs are the caller's device buffers, as in
+ * octax_step_n: actions_dev [n_steps][n_envs]; obs_dev
+ * [n_steps][n_envs][stack_frames][32][64] (16-byte aligned); reward_dev and
+ * done_dev [n_steps][n_envs]. Asynchronous on cuda_stream (NULL = legacy
+ * default stream).
+ * Limits: 1 <= n_envs <= 1024 (EINVAL beyond); every device that loads the
+ * library holds the array (about 4.6 MB) until the process exits.
+ * The first call on a device looks up the array's device address, so make it
+ * before any stream capture. Every call reuses the same array: calls whose
+ * work overlaps on the GPU (other streams, other threads) race with each
+ * other and must be serialised by the caller. */
+int octax_rollout_static(const octax_game *game, int64_t n_envs, uint32_t quirks, uint64_t seed,
+                         int n_steps, const uint8_t *actions_dev, uint8_t *obs_dev,
+                         float *reward_dev, uint8_t *done_dev, void *cuda_stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *octax_last_error(void);
 

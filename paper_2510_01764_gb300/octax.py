@@ -93,7 +93,7 @@ EXPORTS = ("octax_create", "octax_reset", "octax_step", "octax_step_n", "octax_s
            "octax_stack_frames", "octax_device_bytes", "octax_destroy", "octax_last_error",
            "octax_server_create", "octax_server_submit", "octax_server_wait",
            "octax_server_query", "octax_server_release", "octax_server_get_stats",
-           "octax_server_destroy")
+           "octax_server_destroy", "octax_rollout_static")
 
 _lib = None
 _lock = threading.Lock()
@@ -137,6 +137,8 @@ def load_library(path: str = LIB_PATH):
             "octax_server_release": (I32, [P, C.c_uint64]),
             "octax_server_get_stats": (I32, [P, C.POINTER(CServerStats)]),
             "octax_server_destroy": (None, [P]),
+            "octax_rollout_static": (I32, [C.POINTER(CGame), I64, C.c_uint32, C.c_uint64, I32,
+                                           P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
