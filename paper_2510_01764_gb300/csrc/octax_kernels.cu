@@ -44,6 +44,13 @@ struct Ctx {
   uint32_t *V;         // shared: this instance's V0; Vx at V[x * J]
   uint8_t *ram;        // global: this instance's 4 KB RAM (dirty pages)
   int J;
+  const uint32_t *fastmap;  // shared: bit a/2 set = the image opcode at even address a is fast
+};
+
+// A sprite draw handed to the warp (see coop_draw).
+struct DrawReq {
+  bool pend;
+  uint32_t x0, y0, rows, I;
 };
 
 __device__ __forceinline__ uint32_t getV(const Ctx &C, uint32_t x) { return C.V[x * C.J]; }
@@ -126,10 +133,29 @@ __device__ __forceinline__ void draw(Regs &R, const Ctx &C, uint32_t vx, uint32_
   setVF(C, coll);
 }
 
+// Opcodes the predicated datapath covers: classes 1 3 4 6 7 A always; 5 9
+// with N = 0; 8 with N in 0-7,E (classic shifts and logic); E with 9E/A1;
+// F with 07 0A 15 18 29, and 1E without its quirk.
+__device__ __forceinline__ bool is_fast_op(uint32_t op, uint32_t quirks) {
+  const uint32_t cls = op >> 12, n = op & 15u, nn = op & 0xFFu;
+  const uint32_t cbit = 1u << cls;
+  bool fast = (cbit & 0x04DAu) != 0;
+  fast |= ((cbit & 0x0220u) != 0) & (n == 0);
+  fast |= (cls == 8) & ((n <= 7) | (n == 14)) &
+          ((quirks & (OCTAX_QUIRK_SHIFT_USES_VY | OCTAX_QUIRK_LOGIC_RESETS_VF)) == 0);
+  fast |= (cls == 14) & ((nn == 0x9Eu) | (nn == 0xA1u));
+  fast |= (cls == 15) & ((nn == 0x07u) | (nn == 0x0Au) | (nn == 0x15u) | (nn == 0x18u) | (nn == 0x29u) |
+                         ((nn == 0x1Eu) & ((quirks & OCTAX_QUIRK_FX1E_VF) == 0)));
+  return fast;
+}
+
 // The rare / heavy instructions and every variant the fast datapath leaves
 // out (quirk bits, undefined encodings). PC has already been advanced.
+// kCoop: a DXYN whose sprite bytes come from the image is handed to the warp
+// (dr.pend) instead of being drawn here.
+template <bool kCoop>
 __device__ __forceinline__ void exec_slow(Regs &R, const Ctx &C, uint32_t op, uint32_t pc, int key,
-                                       uint32_t quirks) {
+                                       uint32_t quirks, DrawReq &dr) {
   const uint32_t x = (op >> 8) & 15u, y = (op >> 4) & 15u, n = op & 15u, nn = op & 0xFFu;
   const uint32_t nnn = op & 0xFFFu;
   const uint32_t vx = getV(C, x), vy = getV(C, y);
@@ -239,7 +265,15 @@ __device__ __forceinline__ void exec_slow(Regs &R, const Ctx &C, uint32_t op, ui
       break;
     }
     case 0xD:
-      draw(R, C, vx, vy, n, quirks);
+      if (kCoop && n != 0 && !(dirty_bit(R.dirty, R.I) | dirty_bit(R.dirty, R.I + n - 1u))) {
+        dr.pend = true;
+        dr.x0 = vx & 63u;
+        dr.y0 = vy & 31u;
+        dr.rows = (quirks & OCTAX_QUIRK_WRAP_SPRITES) ? n : min(n, 32u - dr.y0);
+        dr.I = R.I;
+      } else {
+        draw(R, C, vx, vy, n, quirks);
+      }
       break;
     case 0xE: {
       const bool pressed = key >= 0 && (uint32_t)key == (vx & 15u);
@@ -290,27 +324,20 @@ __device__ __forceinline__ void exec_slow(Regs &R, const Ctx &C, uint32_t op, ui
 }
 
 // One fetch / decode / execute cycle. key: held CHIP-8 key or -1.
-__device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_t quirks) {
+template <bool kCoop>
+__device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_t quirks, DrawReq &dr) {
   const uint32_t pc = R.pc;
   uint32_t op;
+  bool fast;
   if (!((pc & 1u) | dirty_bit(R.dirty, pc))) {
     op = __byte_perm(*reinterpret_cast<const uint16_t *>(C.img + pc), 0u, 0x4401);
-  } else {
+    fast = (C.fastmap[pc >> 6] >> ((pc >> 1) & 31u)) & 1u;
+  } else {  // odd PC or a written page: the general path
     op = (rd8(R, C, pc) << 8) | rd8(R, C, pc + 1u);
+    fast = false;
   }
   const uint32_t cls = op >> 12, x = (op >> 8) & 15u, y = (op >> 4) & 15u, n = op & 15u;
   const uint32_t nn = op & 0xFFu, nnn = op & 0xFFFu;
-  // classes the predicated datapath covers (bit c set = class c):
-  // 1 3 4 6 7 A always; 5 9 with N = 0; 8 with N in 0-7,E (classic shifts and
-  // logic); E with 9E/A1; F with 07 0A 15 18 29, and 1E without its quirk.
-  const uint32_t cbit = 1u << cls;
-  bool fast = (cbit & 0x04DAu) != 0;
-  fast |= ((cbit & 0x0220u) != 0) & (n == 0);
-  fast |= (cls == 8) & ((n <= 7) | (n == 14)) &
-          ((quirks & (OCTAX_QUIRK_SHIFT_USES_VY | OCTAX_QUIRK_LOGIC_RESETS_VF)) == 0);
-  fast |= (cls == 14) & ((nn == 0x9Eu) | (nn == 0xA1u));
-  fast |= (cls == 15) & ((nn == 0x07u) | (nn == 0x0Au) | (nn == 0x15u) | (nn == 0x18u) | (nn == 0x29u) |
-                         ((nn == 0x1Eu) & ((quirks & OCTAX_QUIRK_FX1E_VF) == 0)));
   uint32_t *const Vx = C.V + x * C.J;
   if (fast) {
     const uint32_t vx = *Vx, vy = C.V[y * C.J];
@@ -349,8 +376,60 @@ __device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_
     R.st = ((cls == 15) & (nn == 0x18u)) ? vx : R.st;
   } else {
     R.pc = (pc + 2u) & 0xFFFu;
-    exec_slow(R, C, op, pc, key, quirks);
+    exec_slow<kCoop>(R, C, op, pc, key, quirks, dr);
   }
+}
+
+// Whole-warp sprite drawing: the rows of every pending draw become work
+// items spread over all 32 lanes (row r of the draw of lane i is item
+// start_i + r), each XORed into its owner's display column; the collision
+// flag of a draw is the OR of its rows' flags. Returns the caller's flag.
+__device__ __forceinline__ uint32_t coop_draw(const DrawReq &d, const uint8_t *img, uint64_t *disp_warp,
+                                              int J, int lane, bool wrap) {
+  const uint32_t cnt = d.pend ? d.rows : 0u;
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const uint32_t total = __shfl_sync(kFull, incl, 31), excl = incl - cnt;
+  uint32_t coll = 0;
+  for (uint32_t base = 0; base < total; base += 32) {
+    const uint32_t item = base + lane;
+    int lo = -1;  // largest lane whose inclusive count is <= item
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+      const int cand = lo + step;
+      if (__shfl_sync(kFull, incl, cand) <= item) lo = cand;
+    }
+    const int owner = lo + 1;
+    const uint32_t o_excl = __shfl_sync(kFull, excl, owner & 31);
+    const uint32_t o_x0 = __shfl_sync(kFull, d.x0, owner & 31);
+    const uint32_t o_y0 = __shfl_sync(kFull, d.y0, owner & 31);
+    const uint32_t o_I = __shfl_sync(kFull, d.I, owner & 31);
+    bool hit = false;
+    if (item < total) {
+      const uint32_t r = item - o_excl;
+      const uint32_t rev = __brev(img[(o_I + r) & 0xFFFu]) >> 24;
+      uint64_t s = (uint64_t)rev << o_x0;
+      if (wrap && o_x0 > 56u) s |= (uint64_t)rev >> (64u - o_x0);
+      uint64_t *row = disp_warp + owner + ((o_y0 + r) & 31u) * J;
+      const uint64_t old = *row;
+      hit = (old & s) != 0ull;
+      *row = old ^ s;
+    }
+    const unsigned hits = __ballot_sync(kFull, hit);
+    if (d.pend) {
+      const int lo_b = max((int)excl - (int)base, 0), hi_b = min((int)incl - (int)base, 32);
+      if (hi_b > lo_b) {
+        const unsigned width = (unsigned)(hi_b - lo_b);
+        const unsigned mask = (width == 32u ? kFull : ((1u << width) - 1u)) << lo_b;
+        coll |= (hits & mask) != 0u;
+      }
+    }
+  }
+  return coll;
 }
 
 __device__ __forceinline__ int32_t term_value(const Regs &R, const Ctx &C, const TermDev &t) {
@@ -408,8 +487,9 @@ __device__ __forceinline__ void reset_instance(Regs &R, const Ctx &C, const Game
   R.phase = 1;
   R.draws = 0;
   uint32_t in_frame = 0;
+  DrawReq dr;
   for (uint32_t i = 0; i < G.startup; ++i) {
-    exec_one(R, C, -1, quirks);
+    exec_one<false>(R, C, -1, quirks, dr);
     if (++in_frame == G.K) {
       tick(R);
       in_frame = 0;
@@ -475,31 +555,45 @@ __device__ __forceinline__ void write_reset_obs(const uint64_t *disp_warp, int J
 struct Smem {
   uint8_t *img;
   GameDev *game;
+  uint32_t *fastmap;
   uint64_t *disp;
   uint32_t *stack;
   uint32_t *V;
 };
 
-// Shared memory of a CTA with J instances:
-// image | game | display [32][J] u64 | stack [16][J] u32 | V [16][J] u32.
+// Shared memory of a CTA with J instances: image | game | fast-op bitmap |
+// display [32][J] u64 | stack [16][J] u32 | V [16][J] u32.
 __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
   Smem s;
   s.img = smem;
   s.game = reinterpret_cast<GameDev *>(smem + kRamBytes);
-  s.disp = reinterpret_cast<uint64_t *>(smem + kRamBytes + kGameSmem);
+  s.fastmap = reinterpret_cast<uint32_t *>(smem + kRamBytes + kGameSmem);
+  s.disp = reinterpret_cast<uint64_t *>(smem + kRamBytes + kGameSmem + kFastmapSmem);
   s.stack = reinterpret_cast<uint32_t *>(s.disp + 32 * J);
   s.V = s.stack + 16 * J;
   return s;
 }
 
+// Every thread of the CTA calls this (it contains a barrier).
 __device__ __forceinline__ void stage_game(const Smem &S, const GameDev *games, const uint8_t *images,
-                                           int game) {
+                                           int game, uint32_t quirks) {
   const uint4 *src = reinterpret_cast<const uint4 *>(images + (size_t)game * kRamBytes);
   uint4 *dst = reinterpret_cast<uint4 *>(S.img);
   for (int i = threadIdx.x; i < kRamBytes / 16; i += blockDim.x) dst[i] = src[i];
   const uint4 *gs = reinterpret_cast<const uint4 *>(games + game);
   uint4 *gd = reinterpret_cast<uint4 *>(S.game);
   for (int i = threadIdx.x; i < (int)(sizeof(GameDev) / 16); i += blockDim.x) gd[i] = gs[i];
+  __syncthreads();
+  // classify the opcode at every even address of the image once
+  for (int w = threadIdx.x; w < kRamBytes / 64; w += blockDim.x) {
+    uint32_t bits = 0;
+    for (int b = 0; b < 32; ++b) {
+      const int a = (w * 32 + b) * 2;
+      const uint32_t op = ((uint32_t)S.img[a] << 8) | S.img[a + 1];
+      bits |= (uint32_t)is_fast_op(op, quirks) << b;
+    }
+    S.fastmap[w] = bits;
+  }
 }
 
 __device__ __forceinline__ void load_regs(Regs &R, const DevState &st, int64_t slot) {
@@ -573,7 +667,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
     for (int r = 0; r < 32; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
   }
   const Ctx C{S.img, S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, J};
+              st.ram + slot * (int64_t)kRamBytes, J, S.fastmap};
   if (mine) load_V(C, st, slot);
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
   __syncwarp();
@@ -590,11 +684,20 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
     }
     R.draws = 0;
     R.phase = 0;
+    const bool wrap = quirks & OCTAX_QUIRK_WRAP_SPRITES;
     for (uint32_t f = 0; f < FS; ++f) {
-      if (active) {
-        for (uint32_t k = 0; k < K; ++k) exec_one(R, C, key, quirks);
-        tick(R);
+      for (uint32_t k = 0; k < K; ++k) {  // every lane runs the loop: draws are warp-wide
+        DrawReq dr;
+        dr.pend = false;
+        if (active) exec_one<true>(R, C, key, quirks, dr);
+        if (__any_sync(kFull, dr.pend)) {
+          __syncwarp();
+          const uint32_t coll = coop_draw(dr, S.img, disp_warp, J, lane, wrap);
+          __syncwarp();
+          if (dr.pend) setVF(C, coll);
+        }
       }
+      if (active) tick(R);
       if (f >= first_kept) {
         __syncwarp();
         capture_frame(disp_warp, J, my_obs ? my_obs + (f - first_kept) * kFrameBytes : nullptr, lane, ipw);
@@ -637,7 +740,10 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
   }
 }
 
-__global__ void __launch_bounds__(kMaxBlock) step_kernel(const StepLaunch p) {
+// No __launch_bounds__: with it ptxas caps the kernel at 128 registers and
+// spills; without it the kernel takes 140 registers, which still admits a
+// 256-thread CTA.
+__global__ void step_kernel(const StepLaunch p) {
   extern __shared__ __align__(16) uint8_t smem[];
   const Smem S = carve(smem, (blockDim.x >> 5) * p.ipw);
   __shared__ int s_group;
@@ -652,7 +758,7 @@ __global__ void __launch_bounds__(kMaxBlock) step_kernel(const StepLaunch p) {
     if (gi >= p.n_groups) break;
     const Group g = p.groups[gi];
     if ((int)g.game != cur_game) {
-      stage_game(S, p.games, p.images, g.game);
+      stage_game(S, p.games, p.images, g.game, p.quirks);
       cur_game = g.game;
     }
     __syncthreads();
@@ -669,7 +775,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
   const int j = w * ipw + lane;
   const Smem S = carve(smem, J);
   const Group g = p.groups[blockIdx.x];
-  stage_game(S, p.games, p.images, g.game);
+  stage_game(S, p.games, p.images, g.game, p.quirks);
   __syncthreads();
   const DevState &st = p.st;
   const int64_t n = st.n;
@@ -691,7 +797,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
     load_regs(R, st, slot);
   }
   const Ctx C{S.img, S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, J};
+              st.ram + slot * (int64_t)kRamBytes, J, S.fastmap};
   if (doit) reset_instance(R, C, G, p.quirks);
   const unsigned which = __ballot_sync(kFull, doit);
   if (p.obs && which) {
@@ -852,7 +958,7 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
 
 size_t step_smem_bytes(int block, int ipw) {
   const size_t J = (size_t)(block / 32) * ipw;
-  return (size_t)kRamBytes + kGameSmem + J * (32 * sizeof(uint64_t) + 32 * sizeof(uint32_t));
+  return (size_t)kRamBytes + kGameSmem + kFastmapSmem + J * (32 * sizeof(uint64_t) + 32 * sizeof(uint32_t));
 }
 
 static cudaError_t ensure_smem_attr() {
