@@ -45,6 +45,24 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(values: list, device=None) -> list:
+    """Element-wise maximum over all ranks (identity on one process). The
+    environments never exchange data; this is only the timing reduction."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(world: int, n_envs: int, steps: int, ms: float) -> float:
+    """Env steps/s of the whole job: every replica ran n_envs x steps."""
+    return world * n_envs * steps / (ms / 1e3)
+
+
 def workload(name: str) -> W.Workload:
     return {"scale": W.cfg_scale, "small": W.cfg_small, "batch": W.cfg_batch,
             "divergence": W.cfg_divergence}[name]()
@@ -241,15 +259,13 @@ def run_gpu(args) -> dict | None:
         e2e_s = time.perf_counter() - t0
         env.set_launch(**launch)
 
-    times = torch.tensor([ms_best, ms_plain, e2e_s], dtype=torch.float64, device=dev)
+    ms_best, ms_plain, e2e_s = max_over_ranks([ms_best, ms_plain, e2e_s], dev)
     if world > 1:
-        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
         torch.distributed.barrier()
-    ms_best, ms_plain, e2e_s = (float(x) for x in times.tolist())
     if rank != 0:
         return None
 
-    value = world * n * K / (ms_best / 1e3)
+    value = whole_job_rate(world, n, K, ms_best)
     spl = launch["steps_per_launch"]
     n_launch = sum((hi - lo + spl - 1) // spl for lo, hi in calls)
     launch_ms = ms_best / n_launch
@@ -282,7 +298,7 @@ def run_gpu(args) -> dict | None:
                   "and touches 72 MB of emulator state, more than the 126 MB L2",
         },
         "plain_kernel": {
-            "value": round(world * n * K / (ms_plain / 1e3), 1),
+            "value": round(whole_job_rate(world, n, K, ms_plain), 1),
             "unit": "env steps/s",
             "ms_per_step": round(ms_plain / K, 6),
             "launch": plain_cfg,
@@ -420,9 +436,14 @@ def cpu_oracle(w: W.Workload, budget_s: float, threads: int, steps_hint: int | N
             "sample": f"{n} instances x {steps} steps of the same workload (obs materialised)"}
 
 
+def run_reference_rank_gate() -> bool:
+    """The reference arm runs on rank 0 only; other ranks exit without work."""
+    return dist_env()[0] == 0
+
+
 def run_reference(args) -> dict | None:
     rank, world, _ = dist_env()
-    if rank != 0:
+    if not run_reference_rank_gate():
         return None
     w = workload(args.config)
     threads = os.cpu_count() or 1

@@ -162,8 +162,9 @@ int octax_step(octax_env *env, const uint8_t *actions_dev, uint8_t *obs_dev,
 int octax_step_n(octax_env *env, int n_steps, const uint8_t *actions_dev, uint8_t *obs_dev,
                  float *reward_dev, uint8_t *done_dev);
 
-/* octax_step with host buffers: copies actions in, steps, copies obs, reward
- * and done out, and waits. Synchronous. */
+/* octax_step with host buffers, synchronous. Page-locked (pinned) buffers are
+ * read and written by the kernel directly through their device mapping;
+ * pageable buffers go through device staging buffers and copies. */
 int octax_step_host(octax_env *env, const uint8_t *actions_host, uint8_t *obs_host,
                     float *reward_host, uint8_t *done_host);
 

@@ -532,11 +532,33 @@ int octax_step_n(octax_env *e, int n_steps, const uint8_t *actions_dev, uint8_t 
   return enqueue_steps(e, e->cfg, n_steps, io);
 }
 
+// Device-accessible address of a page-locked host buffer, or nullptr.
+static void *mapped_host(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+    return nullptr;
+  }
+  return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
+}
+
 int octax_step_host(octax_env *e, const uint8_t *actions_host, uint8_t *obs_host, float *reward_host,
                     uint8_t *done_host) {
   if (!e || !actions_host || !obs_host || !reward_host || !done_host) {
     set_error("octax_step_host: null argument");
     return OCTAX_EINVAL;
+  }
+  // Page-locked buffers are device-mapped: the kernel reads the actions and
+  // streams observations, rewards and flags straight into them over the
+  // host link, with no staging copy.
+  void *d_act = mapped_host(actions_host), *d_obs = mapped_host(obs_host);
+  void *d_rew = mapped_host(reward_host), *d_done = mapped_host(done_host);
+  if (d_act && d_obs && d_rew && d_done && aligned16(d_obs)) {
+    int rc = octax_step(e, static_cast<const uint8_t *>(d_act), static_cast<uint8_t *>(d_obs),
+                        static_cast<float *>(d_rew), static_cast<uint8_t *>(d_done));
+    if (rc) return rc;
+    cudaError_t r = cudaStreamSynchronize(e->stream);
+    return r == cudaSuccess ? OCTAX_OK : cuda_fail(r, "octax_step_host");
   }
   const size_t n = (size_t)e->n, obs_bytes = n * (size_t)e->S * kFrameBytes;
   if (!e->hs_act) {

@@ -258,16 +258,22 @@ def test_autotune_leaves_no_trace():
         assert torch.equal(x, y)
 
 
-def test_host_buffer_step_matches_device_step():
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_step_matches_device_step(pinned):
+    """Pinned buffers are written by the kernel directly; pageable ones are staged."""
     o = octax()
     w = W.cfg_small()
     n = 128
     a = W.actions(1, 0, 10, n)
     e1 = o.Env(w.games, n, seed=1)
     e2 = o.Env(w.games, n, seed=1)
+    out = (torch.empty((n, 4, 32, 64), dtype=torch.uint8, pin_memory=pinned),
+           torch.empty(n, dtype=torch.float32, pin_memory=pinned),
+           torch.empty(n, dtype=torch.uint8, pin_memory=pinned))
     for s in range(10):
         d = e1.step(torch.from_numpy(a[s]).cuda())
-        h = e2.step_host(torch.from_numpy(a[s]).pin_memory())
+        act = torch.from_numpy(a[s].copy())
+        h = e2.step_host(act.pin_memory() if pinned else act, out=out)
         for x, y in zip(d, h):
             assert torch.equal(x.cpu(), y)
 
