@@ -15,7 +15,9 @@
 //    adds, ALU, key tests, timer and index ops) run through one branch-free
 //    predicated datapath that every lane executes together; only the rare or
 //    heavy ones (DXYN, CXNN, calls/returns, 00E0, BCD and bulk memory ops,
-//    quirk variants, undefined encodings) take a divergent switch;
+//    quirk variants, undefined encodings) take a divergent switch. Which
+//    opcodes are "fast" is decided once per CTA for every even address of
+//    the image (a 2048-bit map in shared memory);
 //  - observation frames are expanded from the packed rows by the whole warp
 //    together: every store is a 16-byte streaming store and each store
 //    instruction writes eight complete 64-byte image rows.
@@ -45,12 +47,6 @@ struct Ctx {
   uint8_t *ram;        // global: this instance's 4 KB RAM (dirty pages)
   int J;
   const uint32_t *fastmap;  // shared: bit a/2 set = the image opcode at even address a is fast
-};
-
-// A sprite draw handed to the warp (see coop_draw).
-struct DrawReq {
-  bool pend;
-  uint32_t x0, y0, rows, I;
 };
 
 __device__ __forceinline__ uint32_t getV(const Ctx &C, uint32_t x) { return C.V[x * C.J]; }
@@ -122,8 +118,8 @@ __device__ __forceinline__ void draw(Regs &R, const Ctx &C, uint32_t vx, uint32_
     }
     const uint32_t a = (I + r) & 0xFFFu;
     const uint32_t b = clean ? (uint32_t)C.img[a] : rd8(R, C, a);
-    const uint32_t rev = __brev(b) >> 24;   // pixel j of the sprite -> bit j
-    uint64_t s = (uint64_t)rev << x0;        // right edge clips
+    const uint32_t rev = __brev(b) >> 24;  // pixel j of the sprite -> bit j
+    uint64_t s = (uint64_t)rev << x0;       // right edge clips
     if (wrap && x0 > 56u) s |= (uint64_t)rev >> (64u - x0);
     uint64_t *row = C.disp + py * C.J;
     const uint64_t old = *row;
@@ -151,11 +147,8 @@ __device__ __forceinline__ bool is_fast_op(uint32_t op, uint32_t quirks) {
 
 // The rare / heavy instructions and every variant the fast datapath leaves
 // out (quirk bits, undefined encodings). PC has already been advanced.
-// kCoop: a DXYN whose sprite bytes come from the image is handed to the warp
-// (dr.pend) instead of being drawn here.
-template <bool kCoop>
 __device__ __forceinline__ void exec_slow(Regs &R, const Ctx &C, uint32_t op, uint32_t pc, int key,
-                                       uint32_t quirks, DrawReq &dr) {
+                                       uint32_t quirks) {
   const uint32_t x = (op >> 8) & 15u, y = (op >> 4) & 15u, n = op & 15u, nn = op & 0xFFu;
   const uint32_t nnn = op & 0xFFFu;
   const uint32_t vx = getV(C, x), vy = getV(C, y);
@@ -265,15 +258,7 @@ __device__ __forceinline__ void exec_slow(Regs &R, const Ctx &C, uint32_t op, ui
       break;
     }
     case 0xD:
-      if (kCoop && n != 0 && !(dirty_bit(R.dirty, R.I) | dirty_bit(R.dirty, R.I + n - 1u))) {
-        dr.pend = true;
-        dr.x0 = vx & 63u;
-        dr.y0 = vy & 31u;
-        dr.rows = (quirks & OCTAX_QUIRK_WRAP_SPRITES) ? n : min(n, 32u - dr.y0);
-        dr.I = R.I;
-      } else {
-        draw(R, C, vx, vy, n, quirks);
-      }
+      draw(R, C, vx, vy, n, quirks);
       break;
     case 0xE: {
       const bool pressed = key >= 0 && (uint32_t)key == (vx & 15u);
@@ -324,8 +309,7 @@ __device__ __forceinline__ void exec_slow(Regs &R, const Ctx &C, uint32_t op, ui
 }
 
 // One fetch / decode / execute cycle. key: held CHIP-8 key or -1.
-template <bool kCoop>
-__device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_t quirks, DrawReq &dr) {
+__device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_t quirks) {
   const uint32_t pc = R.pc;
   uint32_t op;
   bool fast;
@@ -376,60 +360,8 @@ __device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_
     R.st = ((cls == 15) & (nn == 0x18u)) ? vx : R.st;
   } else {
     R.pc = (pc + 2u) & 0xFFFu;
-    exec_slow<kCoop>(R, C, op, pc, key, quirks, dr);
+    exec_slow(R, C, op, pc, key, quirks);
   }
-}
-
-// Whole-warp sprite drawing: the rows of every pending draw become work
-// items spread over all 32 lanes (row r of the draw of lane i is item
-// start_i + r), each XORed into its owner's display column; the collision
-// flag of a draw is the OR of its rows' flags. Returns the caller's flag.
-__device__ __forceinline__ uint32_t coop_draw(const DrawReq &d, const uint8_t *img, uint64_t *disp_warp,
-                                              int J, int lane, bool wrap) {
-  const uint32_t cnt = d.pend ? d.rows : 0u;
-  uint32_t incl = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t v = __shfl_up_sync(kFull, incl, o);
-    if (lane >= o) incl += v;
-  }
-  const uint32_t total = __shfl_sync(kFull, incl, 31), excl = incl - cnt;
-  uint32_t coll = 0;
-  for (uint32_t base = 0; base < total; base += 32) {
-    const uint32_t item = base + lane;
-    int lo = -1;  // largest lane whose inclusive count is <= item
-#pragma unroll
-    for (int step = 16; step >= 1; step >>= 1) {
-      const int cand = lo + step;
-      if (__shfl_sync(kFull, incl, cand) <= item) lo = cand;
-    }
-    const int owner = lo + 1;
-    const uint32_t o_excl = __shfl_sync(kFull, excl, owner & 31);
-    const uint32_t o_x0 = __shfl_sync(kFull, d.x0, owner & 31);
-    const uint32_t o_y0 = __shfl_sync(kFull, d.y0, owner & 31);
-    const uint32_t o_I = __shfl_sync(kFull, d.I, owner & 31);
-    bool hit = false;
-    if (item < total) {
-      const uint32_t r = item - o_excl;
-      const uint32_t rev = __brev(img[(o_I + r) & 0xFFFu]) >> 24;
-      uint64_t s = (uint64_t)rev << o_x0;
-      if (wrap && o_x0 > 56u) s |= (uint64_t)rev >> (64u - o_x0);
-      uint64_t *row = disp_warp + owner + ((o_y0 + r) & 31u) * J;
-      const uint64_t old = *row;
-      hit = (old & s) != 0ull;
-      *row = old ^ s;
-    }
-    const unsigned hits = __ballot_sync(kFull, hit);
-    if (d.pend) {
-      const int lo_b = max((int)excl - (int)base, 0), hi_b = min((int)incl - (int)base, 32);
-      if (hi_b > lo_b) {
-        const unsigned width = (unsigned)(hi_b - lo_b);
-        const unsigned mask = (width == 32u ? kFull : ((1u << width) - 1u)) << lo_b;
-        coll |= (hits & mask) != 0u;
-      }
-    }
-  }
-  return coll;
 }
 
 __device__ __forceinline__ int32_t term_value(const Regs &R, const Ctx &C, const TermDev &t) {
@@ -487,9 +419,8 @@ __device__ __forceinline__ void reset_instance(Regs &R, const Ctx &C, const Game
   R.phase = 1;
   R.draws = 0;
   uint32_t in_frame = 0;
-  DrawReq dr;
   for (uint32_t i = 0; i < G.startup; ++i) {
-    exec_one<false>(R, C, -1, quirks, dr);
+    exec_one(R, C, -1, quirks);
     if (++in_frame == G.K) {
       tick(R);
       in_frame = 0;
@@ -684,20 +615,11 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
     }
     R.draws = 0;
     R.phase = 0;
-    const bool wrap = quirks & OCTAX_QUIRK_WRAP_SPRITES;
     for (uint32_t f = 0; f < FS; ++f) {
-      for (uint32_t k = 0; k < K; ++k) {  // every lane runs the loop: draws are warp-wide
-        DrawReq dr;
-        dr.pend = false;
-        if (active) exec_one<true>(R, C, key, quirks, dr);
-        if (__any_sync(kFull, dr.pend)) {
-          __syncwarp();
-          const uint32_t coll = coop_draw(dr, S.img, disp_warp, J, lane, wrap);
-          __syncwarp();
-          if (dr.pend) setVF(C, coll);
-        }
+      if (active) {
+        for (uint32_t k = 0; k < K; ++k) exec_one(R, C, key, quirks);
+        tick(R);
       }
-      if (active) tick(R);
       if (f >= first_kept) {
         __syncwarp();
         capture_frame(disp_warp, J, my_obs ? my_obs + (f - first_kept) * kFrameBytes : nullptr, lane, ipw);
@@ -740,9 +662,8 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
   }
 }
 
-// No __launch_bounds__: with it ptxas caps the kernel at 128 registers and
-// spills; without it the kernel takes 140 registers, which still admits a
-// 256-thread CTA.
+// No __launch_bounds__: with it ptxas caps registers at 128 and may spill;
+// without it the register count still admits a 256-thread CTA.
 __global__ void step_kernel(const StepLaunch p) {
   extern __shared__ __align__(16) uint8_t smem[];
   const Smem S = carve(smem, (blockDim.x >> 5) * p.ipw);
