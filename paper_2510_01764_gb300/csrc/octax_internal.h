@@ -35,7 +35,7 @@ struct alignas(16) GameDev {
 };
 static_assert(sizeof(GameDev) <= 192, "GameDev must fit its shared-memory slot");
 constexpr int kGameSmem = 192;
-constexpr int kFastmapSmem = kRamBytes / 16;  // one bit per even address
+constexpr int kUopSmem = kRamBytes / 2 * 4;  // one decoded u32 per even address
 
 // Emulator state, structure-of-arrays over slots (slot = index in these arrays).
 struct DevState {

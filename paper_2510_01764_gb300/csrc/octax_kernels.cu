@@ -15,9 +15,10 @@
 //    adds, ALU, key tests, timer and index ops) run through one branch-free
 //    predicated datapath that every lane executes together; only the rare or
 //    heavy ones (DXYN, CXNN, calls/returns, 00E0, BCD and bulk memory ops,
-//    quirk variants, undefined encodings) take a divergent switch. Which
-//    opcodes are "fast" is decided once per CTA for every even address of
-//    the image (a 2048-bit map in shared memory);
+//    quirk variants, undefined encodings) take a divergent switch. Every
+//    even address of the image is decoded once per CTA into a 32-bit
+//    micro-op (operand fields plus what the datapath must do), so the hot
+//    loop does one shared load and a few bit tests per instruction;
 //  - observation frames are expanded from the packed rows by the whole warp
 //    together: every store is a 16-byte streaming store and each store
 //    instruction writes eight complete 64-byte image rows.
@@ -46,7 +47,7 @@ struct Ctx {
   uint32_t *V;         // shared: this instance's V0; Vx at V[x * J]
   uint8_t *ram;        // global: this instance's 4 KB RAM (dirty pages)
   int J;
-  const uint32_t *fastmap;  // shared: bit a/2 set = the image opcode at even address a is fast
+  const uint32_t *uops;  // shared: decoded opcode at every even image address (make_uop)
 };
 
 __device__ __forceinline__ uint32_t getV(const Ctx &C, uint32_t x) { return C.V[x * C.J]; }
@@ -143,6 +144,42 @@ __device__ __forceinline__ bool is_fast_op(uint32_t op, uint32_t quirks) {
   fast |= (cls == 15) & ((nn == 0x07u) | (nn == 0x0Au) | (nn == 0x15u) | (nn == 0x18u) | (nn == 0x29u) |
                          ((nn == 0x1Eu) & ((quirks & OCTAX_QUIRK_FX1E_VF) == 0)));
   return fast;
+}
+
+// Decoded form of the opcode at an even image address, built once per CTA.
+// A slow opcode is stored raw (bit 20 clear). A fast one is
+//   bits 0-11 NNN (NN, N in its low bits) | 12-15 X | 16-19 Y | 20 fast |
+//   21 skip negated | 22-23 skip source (1: VX vs NN, 2: VX vs VY, 3: key) |
+//   24 jump | 25-27 VX write (1 NN, 2 VX+NN, 3 8XYN, 4 DT, 5 key) |
+//   28-29 I write (1 NNN, 2 I+VX, 3 glyph) | 30-31 timer (1 DT, 2 ST) from VX.
+constexpr uint32_t kUopFast = 1u << 20;
+
+__device__ __forceinline__ uint32_t make_uop(uint32_t op, uint32_t quirks) {
+  if (!is_fast_op(op, quirks)) return op;
+  const uint32_t cls = op >> 12, nn = op & 0xFFu;
+  uint32_t u = (op & 0xFFFu) | (((op >> 8) & 15u) << 12) | (((op >> 4) & 15u) << 16) | kUopFast;
+  auto skip = [](uint32_t src, uint32_t neg) { return (src << 22) | (neg << 21); };
+  switch (cls) {
+    case 0x1: u |= 1u << 24; break;
+    case 0x3: u |= skip(1, 0); break;
+    case 0x4: u |= skip(1, 1); break;
+    case 0x5: u |= skip(2, 0); break;
+    case 0x9: u |= skip(2, 1); break;
+    case 0x6: u |= 1u << 25; break;
+    case 0x7: u |= 2u << 25; break;
+    case 0x8: u |= 3u << 25; break;
+    case 0xA: u |= 1u << 28; break;
+    case 0xE: u |= skip(3, nn == 0xA1u ? 1u : 0u); break;
+    default:  // 0xF
+      if (nn == 0x07u) u |= 4u << 25;
+      else if (nn == 0x0Au) u |= 5u << 25;
+      else if (nn == 0x15u) u |= 1u << 30;
+      else if (nn == 0x18u) u |= 2u << 30;
+      else if (nn == 0x1Eu) u |= 2u << 28;
+      else u |= 3u << 28;  // 0x29
+      break;
+  }
+  return u;
 }
 
 // The rare / heavy instructions and every variant the fast datapath leaves
@@ -311,27 +348,24 @@ __device__ __forceinline__ void exec_slow(Regs &R, const Ctx &C, uint32_t op, ui
 // One fetch / decode / execute cycle. key: held CHIP-8 key or -1.
 __device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_t quirks) {
   const uint32_t pc = R.pc;
-  uint32_t op;
-  bool fast;
+  uint32_t u;
   if (!((pc & 1u) | dirty_bit(R.dirty, pc))) {
-    op = __byte_perm(*reinterpret_cast<const uint16_t *>(C.img + pc), 0u, 0x4401);
-    fast = (C.fastmap[pc >> 6] >> ((pc >> 1) & 31u)) & 1u;
-  } else {  // odd PC or a written page: the general path
-    op = (rd8(R, C, pc) << 8) | rd8(R, C, pc + 1u);
-    fast = false;
+    u = C.uops[pc >> 1];
+  } else {  // odd PC or a written page: decode here, general path
+    u = (rd8(R, C, pc) << 8) | rd8(R, C, pc + 1u);
   }
-  const uint32_t cls = op >> 12, x = (op >> 8) & 15u, y = (op >> 4) & 15u, n = op & 15u;
-  const uint32_t nn = op & 0xFFu, nnn = op & 0xFFFu;
-  uint32_t *const Vx = C.V + x * C.J;
-  if (fast) {
-    const uint32_t vx = *Vx, vy = C.V[y * C.J];
+  if (u & kUopFast) {
+    const uint32_t nnn = u & 0xFFFu, nn = u & 0xFFu, n = u & 15u;
+    uint32_t *const Vx = C.V + ((u >> 12) & 15u) * C.J;
+    const uint32_t vx = *Vx, vy = C.V[((u >> 16) & 15u) * C.J];
     // next PC: skips, jump, wait-for-key
+    const uint32_t src = (u >> 22) & 3u, wk = (u >> 25) & 7u;
     const bool pressed = key >= 0 && (uint32_t)key == (vx & 15u);
-    const bool skip = ((cls == 3) & (vx == nn)) | ((cls == 4) & (vx != nn)) | ((cls == 5) & (vx == vy)) |
-                      ((cls == 9) & (vx != vy)) | ((cls == 14) & ((nn == 0x9Eu) == pressed));
+    const bool cond = (src == 3u) ? pressed : (vx == ((src == 2u) ? vy : nn));
+    const bool skip = (src != 0u) & (cond != (((u >> 21) & 1u) != 0u));
     uint32_t npc = (pc + (skip ? 4u : 2u)) & 0xFFFu;
-    npc = (cls == 1) ? nnn : npc;
-    npc = ((cls == 15) & (nn == 0x0Au) & (key < 0)) ? pc : npc;
+    npc = (u & (1u << 24)) ? nnn : npc;
+    npc = ((wk == 5u) & (key < 0)) ? pc : npc;
     R.pc = npc;
     // 8XYN result and flag (N in 0-7, E)
     const uint32_t sum = vx + vy;
@@ -344,23 +378,23 @@ __device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_
     uint32_t flag = (n & 2u) ? f1 : f0;
     flag = (n == 14) ? (vx >> 7) : flag;
     // VX write: 6XNN, 7XNN, 8XYN, FX07, FX0A (with a key held)
-    uint32_t val = (cls == 7) ? (vx + nn) : nn;
-    val = (cls == 8) ? alu : val;
-    val = (cls == 15) ? ((nn == 0x07u) ? R.dt : (uint32_t)key) : val;
-    const bool wen = (cls == 6) | (cls == 7) | (cls == 8) |
-                     ((cls == 15) & ((nn == 0x07u) | ((nn == 0x0Au) & (key >= 0))));
-    if (wen) *Vx = val & 0xFFu;
-    if ((cls == 8) & (n >= 4u)) C.V[15 * C.J] = flag;  // after VX: with X = F the flag wins
+    uint32_t val = (wk == 2u) ? (vx + nn) : nn;
+    val = (wk == 3u) ? alu : val;
+    val = (wk == 4u) ? R.dt : val;
+    val = (wk == 5u) ? (uint32_t)key : val;
+    if ((wk != 0u) & !((wk == 5u) & (key < 0))) *Vx = val & 0xFFu;
+    if ((wk == 3u) & (n >= 4u)) C.V[15 * C.J] = flag;  // after VX: with X = F the flag wins
     // index register and timers
-    uint32_t I = (cls == 10) ? nnn : R.I;
-    I = ((cls == 15) & (nn == 0x1Eu)) ? ((I + vx) & 0xFFFFu) : I;
-    I = ((cls == 15) & (nn == 0x29u)) ? (0x50u + 5u * (vx & 15u)) : I;
+    const uint32_t ik = (u >> 28) & 3u, tk = u >> 30;
+    uint32_t I = (ik == 1u) ? nnn : R.I;
+    I = (ik == 2u) ? ((I + vx) & 0xFFFFu) : I;
+    I = (ik == 3u) ? (0x50u + 5u * (vx & 15u)) : I;
     R.I = I;
-    R.dt = ((cls == 15) & (nn == 0x15u)) ? vx : R.dt;
-    R.st = ((cls == 15) & (nn == 0x18u)) ? vx : R.st;
+    R.dt = (tk == 1u) ? vx : R.dt;
+    R.st = (tk == 2u) ? vx : R.st;
   } else {
     R.pc = (pc + 2u) & 0xFFFu;
-    exec_slow(R, C, op, pc, key, quirks);
+    exec_slow(R, C, u & 0xFFFFu, pc, key, quirks);
   }
 }
 
@@ -486,20 +520,20 @@ __device__ __forceinline__ void write_reset_obs(const uint64_t *disp_warp, int J
 struct Smem {
   uint8_t *img;
   GameDev *game;
-  uint32_t *fastmap;
+  uint32_t *uops;
   uint64_t *disp;
   uint32_t *stack;
   uint32_t *V;
 };
 
-// Shared memory of a CTA with J instances: image | game | fast-op bitmap |
+// Shared memory of a CTA with J instances: image | game | decoded opcodes |
 // display [32][J] u64 | stack [16][J] u32 | V [16][J] u32.
 __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
   Smem s;
   s.img = smem;
   s.game = reinterpret_cast<GameDev *>(smem + kRamBytes);
-  s.fastmap = reinterpret_cast<uint32_t *>(smem + kRamBytes + kGameSmem);
-  s.disp = reinterpret_cast<uint64_t *>(smem + kRamBytes + kGameSmem + kFastmapSmem);
+  s.uops = reinterpret_cast<uint32_t *>(smem + kRamBytes + kGameSmem);
+  s.disp = reinterpret_cast<uint64_t *>(smem + kRamBytes + kGameSmem + kUopSmem);
   s.stack = reinterpret_cast<uint32_t *>(s.disp + 32 * J);
   s.V = s.stack + 16 * J;
   return s;
@@ -515,15 +549,10 @@ __device__ __forceinline__ void stage_game(const Smem &S, const GameDev *games, 
   uint4 *gd = reinterpret_cast<uint4 *>(S.game);
   for (int i = threadIdx.x; i < (int)(sizeof(GameDev) / 16); i += blockDim.x) gd[i] = gs[i];
   __syncthreads();
-  // classify the opcode at every even address of the image once
-  for (int w = threadIdx.x; w < kRamBytes / 64; w += blockDim.x) {
-    uint32_t bits = 0;
-    for (int b = 0; b < 32; ++b) {
-      const int a = (w * 32 + b) * 2;
-      const uint32_t op = ((uint32_t)S.img[a] << 8) | S.img[a + 1];
-      bits |= (uint32_t)is_fast_op(op, quirks) << b;
-    }
-    S.fastmap[w] = bits;
+  // decode the opcode at every even address of the image once
+  for (int w = threadIdx.x; w < kRamBytes / 2; w += blockDim.x) {
+    const uint32_t op = ((uint32_t)S.img[2 * w] << 8) | S.img[2 * w + 1];
+    S.uops[w] = make_uop(op, quirks);
   }
 }
 
@@ -598,7 +627,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
     for (int r = 0; r < 32; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
   }
   const Ctx C{S.img, S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, J, S.fastmap};
+              st.ram + slot * (int64_t)kRamBytes, J, S.uops};
   if (mine) load_V(C, st, slot);
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
   __syncwarp();
@@ -718,7 +747,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
     load_regs(R, st, slot);
   }
   const Ctx C{S.img, S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, J, S.fastmap};
+              st.ram + slot * (int64_t)kRamBytes, J, S.uops};
   if (doit) reset_instance(R, C, G, p.quirks);
   const unsigned which = __ballot_sync(kFull, doit);
   if (p.obs && which) {
@@ -879,7 +908,7 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
 
 size_t step_smem_bytes(int block, int ipw) {
   const size_t J = (size_t)(block / 32) * ipw;
-  return (size_t)kRamBytes + kGameSmem + kFastmapSmem + J * (32 * sizeof(uint64_t) + 32 * sizeof(uint32_t));
+  return (size_t)kRamBytes + kGameSmem + kUopSmem + J * (32 * sizeof(uint64_t) + 32 * sizeof(uint32_t));
 }
 
 static cudaError_t ensure_smem_attr() {
