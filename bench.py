@@ -197,9 +197,9 @@ def run_gpu(args) -> dict | None:
 
         # ---- launch configuration: autotuned for T-step calls
         if args.launch:
-            b, ipw, spl, pers, gr = (int(x) for x in args.launch.split(","))
-            env.set_launch(block=b, inst_per_warp=ipw, steps_per_launch=spl, persistent=pers,
-                           use_graph=gr)
+            f = [int(x) for x in args.launch.split(",")] + [0]
+            env.set_launch(block=f[0], inst_per_warp=f[1], steps_per_launch=f[2], persistent=f[3],
+                           use_graph=f[4], writer_warps=f[5])
         else:
             env.autotune(T, acts[:T])
         launch = env.launch
@@ -238,7 +238,7 @@ def run_gpu(args) -> dict | None:
             ms_best, _ = timed(launch)
         clocks = clk.summary()
         plain_cfg = dict(block=launch["block"], inst_per_warp=launch["inst_per_warp"],
-                         steps_per_launch=1, persistent=0, use_graph=0)
+                         steps_per_launch=1, persistent=0, use_graph=0, writer_warps=0)
         ms_plain, _ = timed(plain_cfg)
         env.set_launch(**launch)
 
@@ -495,7 +495,8 @@ def main():
     ap.add_argument("--config", default="scale", choices=["scale", "small", "batch", "divergence"])
     ap.add_argument("--rollout", type=int, default=32, help="steps per octax_step_n call")
     ap.add_argument("--launch", default="",
-                    help="block,inst_per_warp,steps_per_launch,persistent,graph (default: autotune)")
+                    help="block,inst_per_warp,steps_per_launch,persistent,graph[,writer_warps] "
+                         "(default: autotune)")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=90.0)

@@ -118,14 +118,16 @@ typedef struct {
 } octax_state_record;        /* 4416 bytes */
 
 /* Launch configuration (chosen by octax_autotune or set by hand). A CTA of
- * `block` threads runs block/32 * inst_per_warp instances of one game. */
+ * `block` emulator threads runs block/32 * inst_per_warp instances of one
+ * game; with writer_warps > 0 it also has that many warps that only write
+ * observations (block/32 * inst_per_warp / writer_warps must be 8, 16 or 32). */
 typedef struct {
-  int32_t block;             /* threads per CTA: 32, 64, 128 or 256             */
+  int32_t block;             /* emulator threads per CTA: 32, 64, 128 or 256    */
   int32_t inst_per_warp;     /* instances emulated per warp: 1, 2, 4, 8, 16, 32 */
   int32_t steps_per_launch;  /* octax_step_n: env steps per kernel launch 1..64  */
   int32_t persistent;        /* 1: resident CTAs pull instance groups off a queue */
   int32_t use_graph;         /* 1: octax_step_n replays a captured CUDA graph     */
-  int32_t reserved;          /* 0                                                */
+  int32_t writer_warps;      /* 0, 1, 2, 4 or 8 observation-writer warps         */
 } octax_launch;
 
 typedef struct octax_env octax_env;
@@ -182,7 +184,8 @@ int octax_set_state(octax_env *env, int64_t first, int64_t count,
                     const octax_state_record *in_host);
 
 /* Wait until all enqueued work finished; OCTAX_ETIMEOUT after timeout_ms
- * (negative = no limit). */
+ * (negative = no limit). OCTAX_ECUDA if a kernel reported an internal
+ * hand-over timeout (its outputs are then incomplete). */
 int octax_sync(octax_env *env, int timeout_ms);
 
 int octax_get_launch(const octax_env *env, octax_launch *out);

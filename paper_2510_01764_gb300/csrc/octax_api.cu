@@ -50,10 +50,10 @@ struct GroupTable {
 };
 
 struct GraphKey {
-  int n_steps, block, ipw, spl, persistent;
+  int n_steps, block, ipw, spl, persistent, writers;
   bool operator<(const GraphKey &o) const {
-    return std::tie(n_steps, block, ipw, spl, persistent) <
-           std::tie(o.n_steps, o.block, o.ipw, o.spl, o.persistent);
+    return std::tie(n_steps, block, ipw, spl, persistent, writers) <
+           std::tie(o.n_steps, o.block, o.ipw, o.spl, o.persistent, o.writers);
   }
 };
 
@@ -79,6 +79,7 @@ struct octax_env {
   unsigned int *counters_d = nullptr;
   int counters_cap = 0;
   IO *io_d = nullptr;
+  unsigned int *err_d = nullptr;  // set by a kernel whose bounded hand-over wait gave up
   std::map<GraphKey, cudaGraphExec_t> graphs;
   // octax_step_host staging
   uint8_t *hs_act = nullptr, *hs_obs = nullptr, *hs_done = nullptr;
@@ -166,6 +167,20 @@ int block_ok(int b) { return b == 32 || b == 64 || b == 128 || b == 256; }
 int ipw_ok(int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32; }
 int per_cta(const octax_launch &c) { return c.block / 32 * c.inst_per_warp; }
 
+const char *launch_problem(const octax_launch &c) {
+  if (!block_ok(c.block) || !ipw_ok(c.inst_per_warp)) return "block in {32,64,128,256}, inst_per_warp in {1,...,32}";
+  if (c.steps_per_launch < 1 || c.steps_per_launch > 64) return "steps_per_launch 1..64";
+  if ((c.persistent != 0 && c.persistent != 1) || (c.use_graph != 0 && c.use_graph != 1)) return "flags 0/1";
+  if (c.writer_warps != 0) {
+    const int W = c.writer_warps, J = per_cta(c);
+    if (!(W == 1 || W == 2 || W == 4 || W == 8)) return "writer_warps in {0,1,2,4,8}";
+    if (J % W != 0 || !(J / W == 8 || J / W == 16 || J / W == 32))
+      return "block/32*inst_per_warp/writer_warps must be 8, 16 or 32";
+    if (step_ws_smem_bytes(c.block, c.inst_per_warp) > 227 * 1024) return "too many instances per CTA for the writer ring";
+  }
+  return nullptr;
+}
+
 }  // namespace
 
 // Validate the descriptors and build the device descriptors + initial RAM images.
@@ -235,6 +250,7 @@ StepLaunch base_launch(octax_env *e, const GroupTable *gt) {
   p.S = e->S;
   p.quirks = e->quirks;
   p.ipw = e->cfg.inst_per_warp;
+  p.err = e->err_d;
   return p;
 }
 
@@ -259,9 +275,10 @@ int enqueue_steps(octax_env *e, const octax_launch &cfg, int n_steps, const IO &
   if (rc) return rc;
   const int spl = cfg.steps_per_launch;
   const int launches = (n_steps + spl - 1) / spl;
-  const int grid = cfg.persistent
-                       ? std::min(gt->count, std::max(1, max_resident_ctas(cfg.block, cfg.inst_per_warp)))
-                       : gt->count;
+  const int grid =
+      cfg.persistent
+          ? std::min(gt->count, std::max(1, max_resident_ctas(cfg.block, cfg.inst_per_warp, cfg.writer_warps)))
+          : gt->count;
   if (cfg.persistent) {
     rc = ensure_counters(e, launches);
     if (rc) return rc;
@@ -274,6 +291,7 @@ int enqueue_steps(octax_env *e, const octax_launch &cfg, int n_steps, const IO &
     for (int j = 0; j < launches; ++j) {
       StepLaunch p = base_launch(e, gt);
       p.ipw = cfg.inst_per_warp;
+      p.writers = cfg.writer_warps;
       p.io0 = io;
       p.step0 = j * spl;
       p.steps = std::min(spl, n_steps - j * spl);
@@ -284,7 +302,7 @@ int enqueue_steps(octax_env *e, const octax_launch &cfg, int n_steps, const IO &
     return OCTAX_OK;
   }
   // CUDA graph: the kernels read their IO from io_d, refreshed before replay.
-  const GraphKey key{n_steps, cfg.block, cfg.inst_per_warp, spl, cfg.persistent};
+  const GraphKey key{n_steps, cfg.block, cfg.inst_per_warp, spl, cfg.persistent, cfg.writer_warps};
   auto it = e->graphs.find(key);
   if (it == e->graphs.end()) {
     cudaGraph_t g;
@@ -306,6 +324,7 @@ int enqueue_steps(octax_env *e, const octax_launch &cfg, int n_steps, const IO &
     for (int j = 0; j < launches; ++j) {
       StepLaunch p = base_launch(e, gt);
       p.ipw = cfg.inst_per_warp;
+      p.writers = cfg.writer_warps;
       p.io_table = e->io_d;
       p.step0 = j * spl;
       p.steps = std::min(spl, n_steps - j * spl);
@@ -428,6 +447,7 @@ int octax_create(const octax_game *games, int n_games, const uint16_t *game_of_e
   ALLOC(st.game, n);
   ALLOC(e->slot_of_row_d, n);
   ALLOC(e->io_d, 1);
+  ALLOC(e->err_d, 1);
   ALLOC(uid_tmp, n);
 #undef ALLOC
   if (r != cudaSuccess) {
@@ -441,6 +461,7 @@ int octax_create(const octax_game *games, int n_games, const uint16_t *game_of_e
   if (r == cudaSuccess) r = cudaMemcpy(st.game, e->game_of_slot.data(), n * 2, cudaMemcpyHostToDevice);
   if (r == cudaSuccess) r = cudaMemcpy(e->slot_of_row_d, slot_of_row.data(), n * 4, cudaMemcpyHostToDevice);
   if (r == cudaSuccess) r = cudaMemcpy(uid_tmp, uid_of_slot.data(), n * 4, cudaMemcpyHostToDevice);
+  if (r == cudaSuccess) r = cudaMemset(e->err_d, 0, sizeof(unsigned int));
   if (r == cudaSuccess) r = cudaEventCreateWithFlags(&e->ev, cudaEventDisableTiming);
   if (r != cudaSuccess) {
     int rc = cuda_fail(r, "octax_create upload");
@@ -640,7 +661,16 @@ int octax_sync(octax_env *e, int timeout_ms) {
   const auto t0 = std::chrono::steady_clock::now();
   for (;;) {
     r = cudaEventQuery(e->ev);
-    if (r == cudaSuccess) return OCTAX_OK;
+    if (r == cudaSuccess) {
+      unsigned int err = 0;
+      r = cudaMemcpy(&err, e->err_d, sizeof err, cudaMemcpyDeviceToHost);
+      if (r != cudaSuccess) return cuda_fail(r, "octax_sync");
+      if (err) {
+        set_error("octax_sync: a kernel's shared-memory hand-over timed out; outputs are incomplete");
+        return OCTAX_ECUDA;
+      }
+      return OCTAX_OK;
+    }
     if (r != cudaErrorNotReady) return cuda_fail(r, "octax_sync");
     if (timeout_ms >= 0 &&
         std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms)) {
@@ -661,11 +691,12 @@ int octax_get_launch(const octax_env *e, octax_launch *out) {
 }
 
 int octax_set_launch(octax_env *e, const octax_launch *cfg) {
-  if (!e || !cfg || !block_ok(cfg->block) || !ipw_ok(cfg->inst_per_warp) || cfg->steps_per_launch < 1 ||
-      cfg->steps_per_launch > 64 || (cfg->persistent != 0 && cfg->persistent != 1) ||
-      (cfg->use_graph != 0 && cfg->use_graph != 1)) {
-    set_error("octax_set_launch: block in {32,64,128,256}, inst_per_warp in {1,2,4,8,16,32}, "
-              "steps_per_launch 1..64, flags 0/1");
+  if (!e || !cfg) {
+    set_error("octax_set_launch: null argument");
+    return OCTAX_EINVAL;
+  }
+  if (const char *why = launch_problem(*cfg)) {
+    set_error(std::string("octax_set_launch: ") + why);
     return OCTAX_EINVAL;
   }
   e->cfg = *cfg;
@@ -738,30 +769,34 @@ int octax_autotune(octax_env *e, int n_steps, const uint8_t *actions_dev, float 
   const int blocks[] = {32, 64, 128, 256};
   const int ipws[] = {32, 16, 8, 4};
   const int spls[] = {1, 2, 4, 8};
+  const int writers[] = {0, 1, 2, 4};
   for (int b : blocks) {
     for (int ipw : ipws) {
       const int J = b / 32 * ipw;
       if (J < 8 || J > 256) continue;
-      for (int pers = 0; pers < 2 && rc == OCTAX_OK; ++pers) {
-        for (int spl : spls) {
-          if (spl > n_steps) continue;
-          octax_launch c{b, ipw, spl, pers, 1, 0};
-          e->cfg = c;
-          rc = enqueue_steps(e, c, n_steps, io);  // warm-up (graph build)
-          if (rc) break;
-          float ms_min = 1e30f;
-          for (int rep = 0; rep < 3 && rc == OCTAX_OK; ++rep) {
-            cudaEventRecord(t0, e->stream);
-            rc = enqueue_steps(e, c, n_steps, io);
-            cudaEventRecord(t1, e->stream);
-            cudaEventSynchronize(t1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, t0, t1);
-            ms_min = std::min(ms_min, ms);
-          }
-          if (rc == OCTAX_OK && ms_min < best_ms) {
-            best_ms = ms_min;
-            best = c;
+      for (int W : writers) {
+        for (int pers = 0; pers < 2 && rc == OCTAX_OK; ++pers) {
+          for (int spl : spls) {
+            if (spl > n_steps) continue;
+            octax_launch c{b, ipw, spl, pers, 1, W};
+            if (launch_problem(c)) continue;
+            e->cfg = c;
+            rc = enqueue_steps(e, c, n_steps, io);  // warm-up (graph build)
+            if (rc) break;
+            float ms_min = 1e30f;
+            for (int rep = 0; rep < 3 && rc == OCTAX_OK; ++rep) {
+              cudaEventRecord(t0, e->stream);
+              rc = enqueue_steps(e, c, n_steps, io);
+              cudaEventRecord(t1, e->stream);
+              cudaEventSynchronize(t1);
+              float ms = 0;
+              cudaEventElapsedTime(&ms, t0, t1);
+              ms_min = std::min(ms_min, ms);
+            }
+            if (rc == OCTAX_OK && ms_min < best_ms) {
+              best_ms = ms_min;
+              best = c;
+            }
           }
         }
       }

@@ -87,7 +87,9 @@ struct StepLaunch {
   int S;                   // stack frames
   uint32_t quirks;
   int ipw;                 // instances emulated per warp (1..32)
+  int writers;             // >0: warp-specialised kernel with this many writer warps
   unsigned int *work_counter;  // non-null: persistent CTAs pull groups from it
+  unsigned int *err;       // set when a bounded barrier wait gives up (specialised kernel)
 };
 
 struct ResetLaunch {
@@ -109,6 +111,8 @@ struct ResetLaunch {
 };
 
 size_t step_smem_bytes(int block, int ipw);
+// Warp-specialised kernel: `block` emulator threads plus 32 * writers writer threads.
+size_t step_ws_smem_bytes(int block, int ipw);
 cudaError_t launch_step(const StepLaunch &p, int grid, int block, cudaStream_t s);
 cudaError_t launch_reset(const ResetLaunch &p, int block, cudaStream_t s);
 cudaError_t launch_hash(const DevState &st, const uint8_t *images, const uint32_t *slot_of_row,
@@ -118,7 +122,7 @@ cudaError_t launch_records(const DevState &st, const uint8_t *images, const uint
 cudaError_t launch_set_records(const DevState &st, const GameDev *games, const uint8_t *images,
                                const uint32_t *slot_of_row, int64_t first, int64_t count,
                                const octax_state_record *in, cudaStream_t s);
-int max_resident_ctas(int block, int ipw);
+int max_resident_ctas(int block, int ipw, int writers);
 // Bytes of device state per slot (all DevState arrays).
 constexpr size_t kSlotStateBytes = 16 + 4 + 4 + 32 + 256 + 8 + 4096 + 4 + 4 + 4 + 8 + 4 + 4 + 2;
 cudaError_t alloc_state(DevState &st, int64_t n, void **block_out, size_t *bytes_out);

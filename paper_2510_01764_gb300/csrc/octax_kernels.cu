@@ -718,6 +718,272 @@ __global__ void step_kernel(const StepLaunch p) {
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Warp-specialised step: the first block/32 warps emulate (as in run_group),
+// the last `writers` warps only write observations. At every kept frame the
+// emulators copy their packed display rows into one slot of a two-slot ring
+// in shared memory and go on emulating; the writers expand that slot to
+// uint8 frames and stream them out, so interpreter and stores overlap. After
+// each step a last message carries the done flags and reset displays; the
+// writer thread that wrote an address earlier in the step is the one that
+// overwrites it with the reset observation, so program order keeps them
+// ordered. Slots hand over through mbarriers (full: all emulator threads
+// arrive; empty: all writer threads arrive); every wait polls a bounded
+// number of times and, if it gives up, records the failure in p.err and
+// stops the thread's work instead of hanging.
+
+constexpr uint32_t kMaxPolls = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(b))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, unsigned int *err) {
+  for (uint32_t i = 0; i < kMaxPolls; ++i)
+    if (mbar_try(b, parity)) return true;
+  atomicOr(err, 1u);
+  return false;
+}
+
+struct WsSmem {
+  Smem base;
+  uint64_t *ring;    // [2][32][J] snapshots of packed display rows
+  uint8_t *done;     // [2][J] done flags of the end-of-step message
+  uint64_t *full;    // [2]
+  uint64_t *empty;   // [2]
+};
+
+// base layout | ring | done flags | barriers
+__device__ __forceinline__ WsSmem carve_ws(uint8_t *smem, int J) {
+  WsSmem w;
+  w.base = carve(smem, J);
+  w.ring = reinterpret_cast<uint64_t *>(w.base.V + 16 * J);
+  w.done = reinterpret_cast<uint8_t *>(w.ring + 2 * 32 * J);
+  w.full = reinterpret_cast<uint64_t *>(w.done + ((2 * J + 15) & ~15));
+  w.empty = w.full + 2;
+  return w;
+}
+
+// Emulator side of one group. `msg` counts messages of this CTA.
+__device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem &W, uint32_t &msg,
+                              bool &failed) {
+  const Smem &S = W.base;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, ipw = p.ipw;
+  const int E = (int)(blockDim.x >> 5) - p.writers;
+  const int J = E * ipw;
+  const int j = w * ipw + lane;
+  const DevState &st = p.st;
+  const int64_t n = st.n;
+  const GameDev &G = *S.game;
+  const bool mine = lane < ipw;
+  const bool active = mine && j < (int)g.count;
+  const int64_t slot = (int64_t)g.slot0 + (active ? j : 0);
+  const IO io = p.io_table ? p.io_table[g.io] : p.io0;
+  const uint32_t quirks = p.quirks;
+
+  Regs R;
+  load_regs(R, st, slot);
+  const int64_t row = active ? (int64_t)st.out_row[slot] : 0;
+  uint32_t ep = st.ep[slot];
+  int32_t prev = st.prev_score[slot];
+  if (mine) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) S.stack[i * J + j] = st.stack[i * n + slot];
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
+  }
+  const Ctx C{S.img, S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
+              st.ram + slot * (int64_t)kRamBytes, J, S.uops};
+  if (mine) load_V(C, st, slot);
+  const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
+
+  for (int s = 0; s < p.steps && !failed; ++s) {
+    const int64_t io_row = (int64_t)(p.step0 + s) * io.rows + row;
+    int key = -1;
+    if (active) {
+      const uint32_t a = io.actions[io_row];
+      if (a < G.n_actions) key = G.action_set[a] & 15;
+      else if (a > G.n_actions) R.status |= OCTAX_STATUS_BAD_ACTION;
+    }
+    R.draws = 0;
+    R.phase = 0;
+    for (uint32_t f = 0; f < FS && !failed; ++f) {
+      if (active) {
+        for (uint32_t k = 0; k < K; ++k) exec_one(R, C, key, quirks);
+        tick(R);
+      }
+      if (f >= first_kept) {  // hand the frame to the writers
+        const uint32_t b = msg & 1u, use = msg >> 1;
+        if (!mbar_wait(W.empty + b, (use & 1u) ^ 1u, p.err)) {
+          failed = true;
+          break;
+        }
+        if (mine) {
+          uint64_t *dst = W.ring + b * 32 * J + j;
+#pragma unroll 8
+          for (int r = 0; r < 32; ++r) dst[r * J] = S.disp[r * J + j];
+        }
+        mbar_arrive(W.full + b);
+        ++msg;
+      }
+    }
+    if (failed) break;
+    bool done = false;
+    if (active) {
+      const int32_t sc = score(R, C, G);
+      ep += 1;
+      R.env_steps += 1;
+      done = terminated(R, C, G) || (G.max_steps != 0 && ep >= G.max_steps);
+      io.reward[io_row] = (float)(sc - prev);
+      io.done[io_row] = done ? 1 : 0;
+      if (done) {
+        reset_instance(R, C, G, quirks);
+        ep = 0;
+        prev = score(R, C, G);
+      } else {
+        prev = sc;
+      }
+    }
+    // end-of-step message: done flags and the reset displays
+    const uint32_t b = msg & 1u, use = msg >> 1;
+    if (!mbar_wait(W.empty + b, (use & 1u) ^ 1u, p.err)) {
+      failed = true;
+      break;
+    }
+    if (mine) {
+      W.done[b * J + j] = done ? 1 : 0;
+      if (done) {
+        uint64_t *dst = W.ring + b * 32 * J + j;
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) dst[r * J] = S.disp[r * J + j];
+      }
+    }
+    mbar_arrive(W.full + b);
+    ++msg;
+  }
+
+  if (active && !failed) {
+    store_regs(R, st, slot);
+    store_V(C, st, slot);
+    st.ep[slot] = ep;
+    st.prev_score[slot] = prev;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) st.stack[i * n + slot] = (uint16_t)S.stack[i * J + j];
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) st.disp[r * n + slot] = S.disp[r * J + j];
+  }
+}
+
+// Writer side of one group: writer warp ww owns instances
+// [ww * J/W, (ww + 1) * J/W); lane -> instance 8m + lane/4, quarter lane%4.
+__device__ void run_group_writer(const StepLaunch &p, const Group &g, const WsSmem &W, uint32_t &msg,
+                                 bool &failed) {
+  const int t = threadIdx.x, lane = t & 31;
+  const int E = (int)(blockDim.x >> 5) - p.writers;
+  const int J = E * p.ipw;
+  const int per = J / p.writers, passes = per >> 3;  // per in {8, 16, 32}
+  const int ww = (t >> 5) - E;
+  const uint32_t q = lane & 3u;
+  const IO io = p.io_table ? p.io_table[g.io] : p.io0;
+  const int S_ = p.S;
+  int jj[4];
+  int64_t orow[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    jj[m] = ww * per + 8 * m + (lane >> 2);
+    const bool act = m < passes && jj[m] < (int)g.count;
+    orow[m] = act ? (int64_t)p.st.out_row[(int64_t)g.slot0 + jj[m]] : -1;
+  }
+  const GameDev &G = *W.base.game;
+  const uint32_t FS = G.frameskip, first_kept = FS - (uint32_t)S_;
+  for (int s = 0; s < p.steps && !failed; ++s) {
+    const int64_t step_row = (int64_t)(p.step0 + s) * io.rows;
+    for (uint32_t f = first_kept; f <= FS; ++f) {  // FS - S frames, then the end-of-step message
+      const uint32_t b = msg & 1u, use = msg >> 1;
+      if (!mbar_wait(W.full + b, use & 1u, p.err)) {
+        failed = true;
+        break;
+      }
+      const uint64_t *ring = W.ring + b * 32 * J;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        if (m >= passes || orow[m] < 0) continue;
+        uint8_t *obs = io.obs + (step_row + orow[m]) * (int64_t)S_ * kFrameBytes + q * 16u;
+        const uint64_t *col = ring + jj[m];
+        if (f < FS) {
+          uint8_t *dst = obs + (f - first_kept) * kFrameBytes;
+#pragma unroll 8
+          for (int r = 0; r < 32; ++r) __stcs(reinterpret_cast<uint4 *>(dst + r * 64), expand16(col[r * J], q));
+        } else if (W.done[b * J + jj[m]]) {
+          for (int r = 0; r < 32; ++r) {
+            const uint4 o = expand16(col[r * J], q);
+            for (int k = 0; k < S_; ++k)
+              __stcs(reinterpret_cast<uint4 *>(obs + k * kFrameBytes + r * 64), o);
+          }
+        }
+      }
+      mbar_arrive(W.empty + b);
+      ++msg;
+    }
+  }
+}
+
+__global__ void step_kernel_ws(const StepLaunch p) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int E = (int)(blockDim.x >> 5) - p.writers;
+  const int J = E * p.ipw;
+  const WsSmem W = carve_ws(smem, J);
+  __shared__ int s_group;
+  if (threadIdx.x == 0) {
+    mbar_init(W.full + 0, (uint32_t)E * 32u);
+    mbar_init(W.full + 1, (uint32_t)E * 32u);
+    mbar_init(W.empty + 0, (uint32_t)p.writers * 32u);
+    mbar_init(W.empty + 1, (uint32_t)p.writers * 32u);
+  }
+  __syncthreads();
+  const bool writer = (int)(threadIdx.x >> 5) >= E;
+  uint32_t msg = 0;
+  bool failed = false;
+  int cur_game = -1;
+  int gi = blockIdx.x;
+  for (;;) {
+    if (p.work_counter) {
+      if (threadIdx.x == 0) s_group = (int)atomicAdd(p.work_counter, 1u);
+      __syncthreads();
+      gi = s_group;
+    }
+    if (gi >= p.n_groups) break;
+    const Group g = p.groups[gi];
+    if ((int)g.game != cur_game) {
+      stage_game(W.base, p.games, p.images, g.game, p.quirks);
+      cur_game = g.game;
+    }
+    __syncthreads();
+    if (!failed) {
+      if (writer) run_group_writer(p, g, W, msg, failed);
+      else run_group_emu(p, g, W, msg, failed);
+    }
+    __syncthreads();  // shared memory is reused by the next group
+    if (!p.work_counter) break;
+  }
+}
+
 __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5, ipw = p.ipw;
@@ -911,11 +1177,19 @@ size_t step_smem_bytes(int block, int ipw) {
   return (size_t)kRamBytes + kGameSmem + kUopSmem + J * (32 * sizeof(uint64_t) + 32 * sizeof(uint32_t));
 }
 
+size_t step_ws_smem_bytes(int block, int ipw) {
+  const size_t J = (size_t)(block / 32) * ipw;
+  return step_smem_bytes(block, ipw) + 2 * 32 * 8 * J + ((2 * J + 15) & ~(size_t)15) + 4 * 8;
+}
+
 static cudaError_t ensure_smem_attr() {
   static bool done = false;
   if (done) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)step_smem_bytes(kMaxBlock, 32));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(step_kernel_ws, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           227 * 1024);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(reset_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)step_smem_bytes(kMaxBlock, 32));
@@ -927,7 +1201,10 @@ cudaError_t launch_step(const StepLaunch &p, int grid, int block, cudaStream_t s
   cudaError_t e = ensure_smem_attr();
   if (e != cudaSuccess) return e;
   if (grid <= 0) return cudaSuccess;
-  step_kernel<<<grid, block, step_smem_bytes(block, p.ipw), s>>>(p);
+  if (p.writers > 0)
+    step_kernel_ws<<<grid, block + 32 * p.writers, step_ws_smem_bytes(block, p.ipw), s>>>(p);
+  else
+    step_kernel<<<grid, block, step_smem_bytes(block, p.ipw), s>>>(p);
   return cudaGetLastError();
 }
 
@@ -974,10 +1251,11 @@ cudaError_t add_step_node(cudaGraph_t g, cudaGraphNode_t *node, cudaGraphNode_t 
   void *args[] = {&copy};
   cudaKernelNodeParams kp;
   memset(&kp, 0, sizeof kp);
-  kp.func = reinterpret_cast<void *>(step_kernel);
+  const bool ws = p.writers > 0;
+  kp.func = ws ? reinterpret_cast<void *>(step_kernel_ws) : reinterpret_cast<void *>(step_kernel);
   kp.gridDim = dim3((unsigned)grid);
-  kp.blockDim = dim3((unsigned)block);
-  kp.sharedMemBytes = (unsigned)step_smem_bytes(block, p.ipw);
+  kp.blockDim = dim3((unsigned)(ws ? block + 32 * p.writers : block));
+  kp.sharedMemBytes = (unsigned)(ws ? step_ws_smem_bytes(block, p.ipw) : step_smem_bytes(block, p.ipw));
   kp.kernelParams = args;
   return cudaGraphAddKernelNode(node, g, dep ? &dep : nullptr, dep ? 1 : 0, &kp);
 }
@@ -1008,12 +1286,16 @@ cudaError_t alloc_state(DevState &st, int64_t n, void **block_out, size_t *bytes
   return cudaSuccess;
 }
 
-int max_resident_ctas(int block, int ipw) {
+int max_resident_ctas(int block, int ipw, int writers) {
   if (ensure_smem_attr() != cudaSuccess) return 0;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel, block, step_smem_bytes(block, ipw));
+  if (writers > 0)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel_ws, block + 32 * writers,
+                                                  step_ws_smem_bytes(block, ipw));
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel, block, step_smem_bytes(block, ipw));
   return sms * per_sm;
 }
 

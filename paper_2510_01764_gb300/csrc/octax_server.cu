@@ -115,6 +115,7 @@ struct octax_server {
   DevState st{};
   void *state_block = nullptr;
   uint8_t *act_arena = nullptr;  // [capacity * kMaxSteps]
+  unsigned int *err_d = nullptr;
   RangeAlloc slots{0};
   std::vector<TickBuf> ticks;
   int64_t tick_no = 0;
@@ -268,6 +269,7 @@ bool tick(octax_server *s) {
   p.S = s->S;
   p.quirks = s->quirks;
   p.ipw = s->ipw;
+  p.err = s->err_d;
   if (r == cudaSuccess) r = launch_step(p, (int)g, s->block, s->stream);
   if (r == cudaSuccess) r = cudaEventRecord(t.ev, s->stream);
   if (r != cudaSuccess) {
@@ -380,6 +382,8 @@ int octax_server_create(const octax_game *games, int n_games, uint32_t quirks,
   cudaError_t r = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
   if (r == cudaSuccess) r = alloc_state(s->st, s->capacity, &s->state_block, &bytes);
   if (r == cudaSuccess) r = cudaMalloc(&s->act_arena, (size_t)s->capacity * kMaxSteps);
+  if (r == cudaSuccess) r = cudaMalloc(&s->err_d, sizeof(unsigned int));
+  if (r == cudaSuccess) r = cudaMemset(s->err_d, 0, sizeof(unsigned int));
   if (r == cudaSuccess) r = cudaMalloc(&s->games_d, s->games_h.size() * sizeof(GameDev));
   if (r == cudaSuccess) r = cudaMalloc(&s->images_d, images.size());
   if (r == cudaSuccess)
@@ -539,6 +543,7 @@ void octax_server_destroy(octax_server *s) {
   }
   cudaFree(s->state_block);
   cudaFree(s->act_arena);
+  cudaFree(s->err_d);
   cudaFree(s->games_d);
   cudaFree(s->images_d);
   if (s->stream) cudaStreamDestroy(s->stream);

@@ -93,6 +93,10 @@ def test_config_small_full_parity():
     dict(block=64, inst_per_warp=1, steps_per_launch=2, persistent=0, use_graph=1),
     dict(block=256, inst_per_warp=16, steps_per_launch=5, persistent=0, use_graph=1),
     dict(block=32, inst_per_warp=2, steps_per_launch=1, persistent=1, use_graph=0),
+    dict(block=128, inst_per_warp=16, steps_per_launch=4, persistent=0, use_graph=1, writer_warps=2),
+    dict(block=64, inst_per_warp=8, steps_per_launch=3, persistent=1, use_graph=1, writer_warps=2),
+    dict(block=256, inst_per_warp=4, steps_per_launch=8, persistent=1, use_graph=0, writer_warps=4),
+    dict(block=32, inst_per_warp=32, steps_per_launch=1, persistent=0, use_graph=1, writer_warps=1),
 ])
 def test_launch_configurations_agree(launch):
     w = W.cfg_small()
@@ -122,7 +126,9 @@ def test_ragged_instance_counts(n):
     full_compare(w.games, n, 40, seed=2, action_seed=2, launch=dict(block=64, inst_per_warp=32))
 
 
-def test_mixed_games_timing_and_stacks():
+@pytest.mark.parametrize("launch", [None, dict(block=128, inst_per_warp=8, steps_per_launch=4,
+                                                persistent=1, use_graph=1, writer_warps=1)])
+def test_mixed_games_timing_and_stacks(launch):
     """Different K and frame skip per game, stack_frames < frame skip,
     startup instructions that draw random numbers, shuffled instance order."""
     ts = [W.TemplateParams(seed=50 + i, size=300 + 100 * i, alu_ops=i, deco_pairs=i % 3,
@@ -137,7 +143,9 @@ def test_mixed_games_timing_and_stacks():
     ]
     n = 300
     goe = np.random.default_rng(0).integers(0, 4, n).astype(np.uint16)
-    full_compare(games, n, 120, seed=11, action_seed=12, game_of_env=goe)
+    env, _ = full_compare(games, n, 120, seed=11, action_seed=12, game_of_env=goe, launch=launch,
+                          use_step_n=launch is not None)
+    env.sync()
 
 
 def test_reward_descriptor_memory_and_transforms():
@@ -153,6 +161,9 @@ def test_reward_descriptor_memory_and_transforms():
                         Clause(Term("reg", 8, "nib_hi_minus_lo"), "<", -10)),
                   max_episode_steps=150)
     full_compare([g], 128, 200, seed=6, action_seed=6)
+    full_compare([g], 128, 200, seed=6, action_seed=6, use_step_n=True,
+                 launch=dict(block=64, inst_per_warp=16, steps_per_launch=5, persistent=0,
+                             use_graph=1, writer_warps=4))
 
 
 def test_out_of_range_actions():
@@ -356,6 +367,17 @@ def test_config_scale_sampled_persistent_graph():
     sampled_run(w, chunk=40, sample=sample,
                 launch=dict(block=128, inst_per_warp=8, steps_per_launch=4, persistent=1,
                             use_graph=1))
+
+
+def test_config_scale_sampled_writer_warps():
+    """The full 20,000-step workload through the warp-specialised kernel."""
+    w = W.cfg_scale()
+    sample = pick(w.n_envs, 16, 5, extra=(7, w.n_envs - 3))
+    env, n_done = sampled_run(w, chunk=64, sample=sample,
+                              launch=dict(block=256, inst_per_warp=16, steps_per_launch=8,
+                                          persistent=0, use_graph=1, writer_warps=4))
+    env.sync()
+    assert n_done > 0
 
 
 def test_config_batch_sampled():
