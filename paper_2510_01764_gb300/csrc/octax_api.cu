@@ -176,7 +176,8 @@ const char *launch_problem(const octax_launch &c) {
     if (!(W == 1 || W == 2 || W == 4 || W == 8)) return "writer_warps in {0,1,2,4,8}";
     if (J % W != 0 || !(J / W == 8 || J / W == 16 || J / W == 32))
       return "block/32*inst_per_warp/writer_warps must be 8, 16 or 32";
-    if (step_ws_smem_bytes(c.block, c.inst_per_warp) > 227 * 1024) return "too many instances per CTA for the writer ring";
+    if (step_ws_smem_bytes(c.block, c.inst_per_warp) > max_dynamic_smem())
+      return "too many instances per CTA for the writer ring";
   }
   return nullptr;
 }
@@ -766,42 +767,37 @@ int octax_autotune(octax_env *e, int n_steps, const uint8_t *actions_dev, float 
   octax_launch best = saved;
   float best_ms = 1e30f;
   int rc = OCTAX_OK;
-  const int blocks[] = {32, 64, 128, 256};
-  const int ipws[] = {32, 16, 8, 4};
-  const int spls[] = {1, 2, 4, 8};
-  const int writers[] = {0, 1, 2, 4};
-  for (int b : blocks) {
-    for (int ipw : ipws) {
-      const int J = b / 32 * ipw;
-      if (J < 8 || J > 256) continue;
-      for (int W : writers) {
-        for (int pers = 0; pers < 2 && rc == OCTAX_OK; ++pers) {
-          for (int spl : spls) {
-            if (spl > n_steps) continue;
-            octax_launch c{b, ipw, spl, pers, 1, W};
-            if (launch_problem(c)) continue;
-            e->cfg = c;
-            rc = enqueue_steps(e, c, n_steps, io);  // warm-up (graph build)
-            if (rc) break;
-            float ms_min = 1e30f;
-            for (int rep = 0; rep < 3 && rc == OCTAX_OK; ++rep) {
-              cudaEventRecord(t0, e->stream);
-              rc = enqueue_steps(e, c, n_steps, io);
-              cudaEventRecord(t1, e->stream);
-              cudaEventSynchronize(t1);
-              float ms = 0;
-              cudaEventElapsedTime(&ms, t0, t1);
-              ms_min = std::min(ms_min, ms);
-            }
-            if (rc == OCTAX_OK && ms_min < best_ms) {
-              best_ms = ms_min;
-              best = c;
-            }
-          }
-        }
-      }
+  auto trial = [&](const octax_launch &c) {
+    if (rc != OCTAX_OK || launch_problem(c) || c.steps_per_launch > n_steps) return;
+    e->cfg = c;
+    rc = enqueue_steps(e, c, n_steps, io);  // warm-up (graph build)
+    float ms_min = 1e30f;
+    for (int rep = 0; rep < 3 && rc == OCTAX_OK; ++rep) {
+      cudaEventRecord(t0, e->stream);
+      rc = enqueue_steps(e, c, n_steps, io);
+      cudaEventRecord(t1, e->stream);
+      cudaEventSynchronize(t1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, t0, t1);
+      ms_min = std::min(ms_min, ms);
     }
-  }
+    if (rc == OCTAX_OK && ms_min < best_ms) {
+      best_ms = ms_min;
+      best = c;
+    }
+  };
+  // stage 1: CTA shape (threads x instances per warp), plain kernel, 4 steps per launch
+  for (int b : {32, 64, 128, 256})
+    for (int ipw : {32, 16, 8, 4}) {
+      const int J = b / 32 * ipw;
+      if (J >= 8 && J <= 256) trial(octax_launch{b, ipw, std::min(4, n_steps), 0, 1, 0});
+    }
+  // stage 2: writer warps, persistence and steps per launch around the best shape
+  const octax_launch shape = best;
+  for (int W : {0, 1, 2, 4})
+    for (int pers : {0, 1})
+      for (int spl : {1, 2, 4, 8})
+        trial(octax_launch{shape.block, shape.inst_per_warp, spl, pers, 1, W});
   off = 0;
   for (const Piece &pc : pieces) {
     cudaMemcpyAsync(pc.p, backup + off, pc.bytes, cudaMemcpyDeviceToDevice, e->stream);

@@ -113,6 +113,7 @@ struct ResetLaunch {
 size_t step_smem_bytes(int block, int ipw);
 // Warp-specialised kernel: `block` emulator threads plus 32 * writers writer threads.
 size_t step_ws_smem_bytes(int block, int ipw);
+size_t max_dynamic_smem();
 cudaError_t launch_step(const StepLaunch &p, int grid, int block, cudaStream_t s);
 cudaError_t launch_reset(const ResetLaunch &p, int block, cudaStream_t s);
 cudaError_t launch_hash(const DevState &st, const uint8_t *images, const uint32_t *slot_of_row,

@@ -1177,6 +1177,19 @@ size_t step_smem_bytes(int block, int ipw) {
   return (size_t)kRamBytes + kGameSmem + kUopSmem + J * (32 * sizeof(uint64_t) + 32 * sizeof(uint32_t));
 }
 
+// Dynamic shared memory a CTA may opt into, less room for static shared data.
+size_t max_dynamic_smem() {
+  static size_t v = 0;
+  if (!v) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || optin <= 0)
+      optin = 99 * 1024;
+    v = (size_t)optin - 1024;
+  }
+  return v;
+}
+
 size_t step_ws_smem_bytes(int block, int ipw) {
   const size_t J = (size_t)(block / 32) * ipw;
   return step_smem_bytes(block, ipw) + 2 * 32 * 8 * J + ((2 * J + 15) & ~(size_t)15) + 4 * 8;
@@ -1189,7 +1202,7 @@ static cudaError_t ensure_smem_attr() {
                                        (int)step_smem_bytes(kMaxBlock, 32));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(step_kernel_ws, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           227 * 1024);
+                           (int)max_dynamic_smem());
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(reset_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)step_smem_bytes(kMaxBlock, 32));
