@@ -152,9 +152,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(config: str, launch: dict) -> dict | None:
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source and the same launch shape."""
+def profiled_traffic(config: str) -> dict | None:
+    """Per-instance-step DRAM bytes and warp instructions of the step kernel
+    from the committed ncu summary, if it was taken on the current kernel
+    source (otherwise None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))
@@ -162,8 +163,6 @@ def profiled_traffic(config: str, launch: dict) -> dict | None:
         return None
     e = d.get(config)
     if not e or e.get("kernel_source") != kernel_source_hash():
-        return None
-    if e.get("steps_per_launch") != launch.get("steps_per_launch"):
         return None
     return e
 
@@ -272,7 +271,19 @@ def run_gpu(args) -> dict | None:
     alg_bytes = n * (STEP_IO_BYTES * (K / n_launch) + STATE_BYTES)
     peak, peak_src = measured_peaks()
     achieved = alg_bytes / (launch_ms / 1e3) / 1e9
-    prof = profiled_traffic(args.config, launch)
+    prof = profiled_traffic(args.config)
+    units_per_launch = n * K / n_launch
+    traffic = None if prof is None else round(prof["dram_bytes_per_instance_step"] * units_per_launch)
+    issue = None
+    if prof is not None and clocks.get("sm_mhz"):
+        import torch as _t
+        sms = _t.cuda.get_device_properties(dev).multi_processor_count
+        peak_issue = sms * 4 * clocks["sm_mhz"] * 1e6          # warp-instructions/s
+        got = prof["warp_inst_per_instance_step"] * units_per_launch / (launch_ms / 1e3)
+        issue = {"achieved": round(got / 1e9, 2), "peak": round(peak_issue / 1e9, 2),
+                 "unit": "G warp-instr/s", "frac": round(got / peak_issue, 4),
+                 "source": "ncu instruction count per instance-step (profiles/traffic.json) x "
+                           "instance-steps per launch / live launch time; peak = SMs x 4 x median SM clock"}
     line = {
         "metric": METRIC,
         "value": round(value, 1),
@@ -315,8 +326,11 @@ def run_gpu(args) -> dict | None:
             "kernel": "step_kernel",
             "bytes_per_launch": int(alg_bytes),
             "launch_ms": round(launch_ms, 5),
-            "traffic": None if prof is None else prof["traffic_per_launch"],
+            "traffic": traffic,
+            "traffic_source": None if prof is None else
+            "ncu dram__bytes_read+write per instance-step (profiles/traffic.json) scaled to this launch",
         },
+        "issue_roofline": issue,
         "e2e": {
             "value": round(world * n * Ke / e2e_s, 1),
             "unit": "env steps/s",
@@ -326,8 +340,6 @@ def run_gpu(args) -> dict | None:
         },
         "clocks": clocks,
     }
-    if prof and prof.get("issue"):
-        line["issue_roofline"] = prof["issue"]
     if not args.no_serve and world == 1:
         line["serving"] = run_serving(args, dev)
         line["serving_p50_ms"] = line["serving"]["poisson"]["p50_ms"]
