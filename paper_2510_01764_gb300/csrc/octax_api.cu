@@ -219,6 +219,13 @@ int get_groups(octax_env *e, int block, GroupTable **out) {
     gs.push_back(Group{(uint32_t)s, (uint16_t)(end - s), g, 0u, 0u});
     s = end;
   }
+  // Longest first (instructions per step): CTAs are dispatched, and the
+  // persistent queue hands out groups, in table order.
+  std::stable_sort(gs.begin(), gs.end(), [&](const Group &a, const Group &b) {
+    const uint32_t ca = e->games_h[a.game].K * e->games_h[a.game].frameskip;
+    const uint32_t cb = e->games_h[b.game].K * e->games_h[b.game].frameskip;
+    return ca > cb;
+  });
   GroupTable t;
   t.count = (int)gs.size();
   cudaError_t r = dalloc(e, &t.dev, gs.size());
