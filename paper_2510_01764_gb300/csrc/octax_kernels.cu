@@ -20,7 +20,8 @@
 //    micro-op (operand fields plus what the datapath must do), so the hot
 //    loop does one shared load and a few bit tests per instruction;
 //  - observation frames are expanded from the packed rows by the whole warp
-//    together: every store is a 16-byte streaming store and each store
+//    together (a byte of pixels becomes 8 bytes through a 256-entry table in
+//    shared memory): every store is a 16-byte streaming store and each store
 //    instruction writes eight complete 64-byte image rows.
 // Each instance runs exactly K instructions per frame, so all lanes of a warp
 // meet at every frame boundary.
@@ -467,21 +468,19 @@ __device__ __forceinline__ void reset_instance(Regs &R, const Ctx &C, const Game
 // 4 pixels (bits 0..3) -> 4 bytes of value 0/1 (byte j = bit j).
 __device__ __forceinline__ uint32_t spread4(uint32_t nib) { return (nib * 0x00204081u) & 0x01010101u; }
 
-__device__ __forceinline__ uint4 expand16(uint64_t row, uint32_t q) {
+// Pixels 16q..16q+15 of a packed row -> 16 bytes of 0/1, through a
+// per-CTA table that maps a byte of pixels to its 8 output bytes.
+__device__ __forceinline__ uint4 expand16(uint64_t row, uint32_t q, const uint2 *lut) {
   const uint32_t bits = (uint32_t)(row >> (16u * q)) & 0xFFFFu;
-  uint4 o;
-  o.x = spread4(bits & 15u);
-  o.y = spread4((bits >> 4) & 15u);
-  o.z = spread4((bits >> 8) & 15u);
-  o.w = spread4(bits >> 12);
-  return o;
+  const uint2 lo = lut[bits & 0xFFu], hi = lut[bits >> 8];
+  return make_uint4(lo.x, lo.y, hi.x, hi.y);
 }
 
 // Whole-warp frame write: lane -> instance 8m + lane/4 of the warp, quarter
 // lane%4 of every row, for the warp's `ipw` instances. frame (per lane, 0 =
 // skip) points at the 2 KB frame of that lane's own instance.
 __device__ __forceinline__ void capture_frame(const uint64_t *disp_warp, int J, uint8_t *frame,
-                                              int lane, int ipw) {
+                                              int lane, int ipw, const uint2 *lut) {
   const uint64_t mine = reinterpret_cast<uint64_t>(frame);
   const uint32_t q = lane & 3;
   const int passes = (ipw + 7) >> 3;
@@ -492,7 +491,7 @@ __device__ __forceinline__ void capture_frame(const uint64_t *disp_warp, int J, 
       const uint64_t *col = disp_warp + src;
       uint8_t *dst = reinterpret_cast<uint8_t *>(base) + q * 16u;
 #pragma unroll 8
-      for (int r = 0; r < 32; ++r) __stcs(reinterpret_cast<uint4 *>(dst + r * 64), expand16(col[r * J], q));
+      for (int r = 0; r < 32; ++r) __stcs(reinterpret_cast<uint4 *>(dst + r * 64), expand16(col[r * J], q, lut));
     }
   }
 }
@@ -500,7 +499,7 @@ __device__ __forceinline__ void capture_frame(const uint64_t *disp_warp, int J, 
 // Whole-warp write of the reset observation (display repeated S times) for
 // every lane whose bit is set in `which`. obs: that lane's S-frame block.
 __device__ __forceinline__ void write_reset_obs(const uint64_t *disp_warp, int J, uint8_t *obs, int S,
-                                                unsigned which, int lane) {
+                                                unsigned which, int lane, const uint2 *lut) {
   const uint64_t mine = reinterpret_cast<uint64_t>(obs);
   while (which) {
     const int src = __ffs(which) - 1;
@@ -510,7 +509,7 @@ __device__ __forceinline__ void write_reset_obs(const uint64_t *disp_warp, int J
 #pragma unroll
     for (int it = 0; it < 4; ++it) {
       const int c = it * 32 + lane;  // 16-byte chunk of the 2 KB frame
-      const uint4 o = expand16(col[(c >> 2) * J], c & 3);
+      const uint4 o = expand16(col[(c >> 2) * J], c & 3, lut);
       for (int s = 0; s < S; ++s)
         __stcs(reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(base) + s * kFrameBytes + c * 16), o);
     }
@@ -521,19 +520,21 @@ struct Smem {
   uint8_t *img;
   GameDev *game;
   uint32_t *uops;
+  uint2 *lut;       // byte of pixels -> 8 bytes of 0/1
   uint64_t *disp;
   uint32_t *stack;
   uint32_t *V;
 };
 
 // Shared memory of a CTA with J instances: image | game | decoded opcodes |
-// display [32][J] u64 | stack [16][J] u32 | V [16][J] u32.
+// expansion table | display [32][J] u64 | stack [16][J] u32 | V [16][J] u32.
 __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
   Smem s;
   s.img = smem;
   s.game = reinterpret_cast<GameDev *>(smem + kRamBytes);
   s.uops = reinterpret_cast<uint32_t *>(smem + kRamBytes + kGameSmem);
-  s.disp = reinterpret_cast<uint64_t *>(smem + kRamBytes + kGameSmem + kUopSmem);
+  s.lut = reinterpret_cast<uint2 *>(smem + kRamBytes + kGameSmem + kUopSmem);
+  s.disp = reinterpret_cast<uint64_t *>(smem + kRamBytes + kGameSmem + kUopSmem + kLutSmem);
   s.stack = reinterpret_cast<uint32_t *>(s.disp + 32 * J);
   s.V = s.stack + 16 * J;
   return s;
@@ -549,6 +550,7 @@ __device__ __forceinline__ void stage_game(const Smem &S, const GameDev *games, 
   uint4 *gd = reinterpret_cast<uint4 *>(S.game);
   for (int i = threadIdx.x; i < (int)(sizeof(GameDev) / 16); i += blockDim.x) gd[i] = gs[i];
   __syncthreads();
+  for (int b = threadIdx.x; b < 256; b += blockDim.x) S.lut[b] = make_uint2(spread4(b & 15u), spread4(b >> 4));
   // decode the opcode at every even address of the image once
   for (int w = threadIdx.x; w < kRamBytes / 2; w += blockDim.x) {
     const uint32_t op = ((uint32_t)S.img[2 * w] << 8) | S.img[2 * w + 1];
@@ -651,7 +653,8 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
       }
       if (f >= first_kept) {
         __syncwarp();
-        capture_frame(disp_warp, J, my_obs ? my_obs + (f - first_kept) * kFrameBytes : nullptr, lane, ipw);
+        capture_frame(disp_warp, J, my_obs ? my_obs + (f - first_kept) * kFrameBytes : nullptr, lane, ipw,
+                      S.lut);
         __syncwarp();
       }
     }
@@ -674,7 +677,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
     const unsigned which = __ballot_sync(kFull, done);
     if (which) {
       __syncwarp();
-      write_reset_obs(disp_warp, J, my_obs, p.S, which, lane);
+      write_reset_obs(disp_warp, J, my_obs, p.S, which, lane, S.lut);
       __syncwarp();
     }
   }
@@ -929,10 +932,11 @@ __device__ void run_group_writer(const StepLaunch &p, const Group &g, const WsSm
         if (f < FS) {
           uint8_t *dst = obs + (f - first_kept) * kFrameBytes;
 #pragma unroll 8
-          for (int r = 0; r < 32; ++r) __stcs(reinterpret_cast<uint4 *>(dst + r * 64), expand16(col[r * J], q));
+          for (int r = 0; r < 32; ++r)
+            __stcs(reinterpret_cast<uint4 *>(dst + r * 64), expand16(col[r * J], q, W.base.lut));
         } else if (W.done[b * J + jj[m]]) {
           for (int r = 0; r < 32; ++r) {
-            const uint4 o = expand16(col[r * J], q);
+            const uint4 o = expand16(col[r * J], q, W.base.lut);
             for (int k = 0; k < S_; ++k)
               __stcs(reinterpret_cast<uint4 *>(obs + k * kFrameBytes + r * 64), o);
           }
@@ -1019,7 +1023,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
   if (p.obs && which) {
     __syncwarp();
     write_reset_obs(S.disp + w * ipw, J, doit ? p.obs + row * (int64_t)p.S * kFrameBytes : nullptr, p.S,
-                    which, lane);
+                    which, lane, S.lut);
     __syncwarp();
   }
   if (doit) {
@@ -1174,7 +1178,7 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
 
 size_t step_smem_bytes(int block, int ipw) {
   const size_t J = (size_t)(block / 32) * ipw;
-  return (size_t)kRamBytes + kGameSmem + kUopSmem + J * (32 * sizeof(uint64_t) + 32 * sizeof(uint32_t));
+  return (size_t)kRamBytes + kGameSmem + kUopSmem + kLutSmem + J * (32 * sizeof(uint64_t) + 32 * sizeof(uint32_t));
 }
 
 // Dynamic shared memory a CTA may opt into, less room for static shared data.
