@@ -346,15 +346,16 @@ __device__ __forceinline__ void exec_slow(Regs &R, const Ctx &C, uint32_t op, ui
   }
 }
 
-// One fetch / decode / execute cycle. key: held CHIP-8 key or -1.
-__device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_t quirks) {
+// Micro-op of the instruction at pc: from the table, or (odd PC, written
+// page) the raw opcode, which takes the general path.
+__device__ __forceinline__ uint32_t fetch_uop(const Regs &R, const Ctx &C, uint32_t pc) {
+  if (!((pc & 1u) | dirty_bit(R.dirty, pc))) return C.uops[pc >> 1];
+  return (rd8(R, C, pc) << 8) | rd8(R, C, pc + 1u);
+}
+
+// Execute micro-op u, the instruction at R.pc. key: held CHIP-8 key or -1.
+__device__ __forceinline__ void execute(Regs &R, const Ctx &C, uint32_t u, int key, uint32_t quirks) {
   const uint32_t pc = R.pc;
-  uint32_t u;
-  if (!((pc & 1u) | dirty_bit(R.dirty, pc))) {
-    u = C.uops[pc >> 1];
-  } else {  // odd PC or a written page: decode here, general path
-    u = (rd8(R, C, pc) << 8) | rd8(R, C, pc + 1u);
-  }
   if (u & kUopFast) {
     const uint32_t nnn = u & 0xFFFu, nn = u & 0xFFu, n = u & 15u;
     uint32_t *const Vx = C.V + ((u >> 12) & 15u) * C.J;
@@ -397,6 +398,12 @@ __device__ __forceinline__ void exec_one(Regs &R, const Ctx &C, int key, uint32_
     R.pc = (pc + 2u) & 0xFFFu;
     exec_slow(R, C, u & 0xFFFFu, pc, key, quirks);
   }
+}
+
+// Run `count` instructions.
+__device__ __forceinline__ void run_instrs(Regs &R, const Ctx &C, int key, uint32_t quirks,
+                                           uint32_t count) {
+  for (uint32_t k = 0; k < count; ++k) execute(R, C, fetch_uop(R, C, R.pc), key, quirks);
 }
 
 __device__ __forceinline__ int32_t term_value(const Regs &R, const Ctx &C, const TermDev &t) {
@@ -453,13 +460,11 @@ __device__ __forceinline__ void reset_instance(Regs &R, const Ctx &C, const Game
   for (int r = 0; r < 32; ++r) C.disp[r * C.J] = 0ull;
   R.phase = 1;
   R.draws = 0;
-  uint32_t in_frame = 0;
-  for (uint32_t i = 0; i < G.startup; ++i) {
-    exec_one(R, C, -1, quirks);
-    if (++in_frame == G.K) {
-      tick(R);
-      in_frame = 0;
-    }
+  for (uint32_t left = G.startup; left > 0;) {  // timers tick after every K instructions
+    const uint32_t c = left < G.K ? left : G.K;
+    run_instrs(R, C, -1, quirks, c);
+    if (c == G.K) tick(R);
+    left -= c;
   }
   R.phase = 0;
   R.draws = 0;
@@ -648,7 +653,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
     R.phase = 0;
     for (uint32_t f = 0; f < FS; ++f) {
       if (active) {
-        for (uint32_t k = 0; k < K; ++k) exec_one(R, C, key, quirks);
+        run_instrs(R, C, key, quirks, K);
         tick(R);
       }
       if (f >= first_kept) {
@@ -828,7 +833,7 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
     R.phase = 0;
     for (uint32_t f = 0; f < FS && !failed; ++f) {
       if (active) {
-        for (uint32_t k = 0; k < K; ++k) exec_one(R, C, key, quirks);
+        run_instrs(R, C, key, quirks, K);
         tick(R);
       }
       if (f >= first_kept) {  // hand the frame to the writers
