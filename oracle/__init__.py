@@ -58,7 +58,8 @@ class Game(C.Structure):
                 ("stack_frames", C.c_uint32), ("n_actions", C.c_uint32),
                 ("action_set", C.c_uint8 * 16), ("n_score_terms", C.c_uint32),
                 ("score", Term * 4), ("n_term_clauses", C.c_uint32), ("term", Clause * 4),
-                ("max_episode_steps", C.c_uint32), ("startup_instrs", C.c_uint32)]
+                ("max_episode_steps", C.c_uint32), ("startup_instrs", C.c_uint32),
+                ("sticky_threshold", C.c_uint32), ("max_noops", C.c_uint32)]
 
 
 class Inst(C.Structure):
@@ -67,14 +68,16 @@ class Inst(C.Structure):
                 ("stack", C.c_uint16 * 16), ("pix", (C.c_uint8 * 64) * 32),
                 ("ram", C.c_uint8 * 4096), ("episode_steps", C.c_uint32),
                 ("env_steps", C.c_uint32), ("key", C.c_uint32 * 2), ("uid", C.c_uint32),
-                ("phase", C.c_uint32), ("draws", C.c_uint32), ("game", C.c_int32)]
+                ("phase", C.c_uint32), ("draws", C.c_uint32), ("game", C.c_int32),
+                ("last_action", C.c_uint8)]
 
 
 RECORD_DTYPE = np.dtype([("V", np.uint8, 16), ("I", "<u2"), ("PC", "<u2"), ("SP", np.uint8),
                          ("DT", np.uint8), ("ST", np.uint8), ("status", np.uint8),
                          ("stack", "<u2", 16), ("display", "<u8", 32), ("ram", np.uint8, 4096),
-                         ("episode_steps", "<u4"), ("env_steps", "<u4")])
-assert RECORD_DTYPE.itemsize == 4416
+                         ("episode_steps", "<u4"), ("env_steps", "<u4"), ("last_action", np.uint8),
+                         ("pad", np.uint8, 7)])
+assert RECORD_DTYPE.itemsize == 4424
 
 
 def lib():
@@ -141,7 +144,14 @@ def make_game(spec) -> tuple[Game, object]:
         g.term[i] = Clause(_term(c.lhs), _CMP[c.cmp], int(c.rhs))
     g.max_episode_steps = spec.max_episode_steps
     g.startup_instrs = spec.startup_instrs
+    g.sticky_threshold = sticky_threshold(getattr(spec, "sticky_prob", 0.0))
+    g.max_noops = getattr(spec, "max_noops", 0)
     return g, rom
+
+
+def sticky_threshold(p: float) -> int:
+    """Probability -> 32-bit threshold (repeat when a uniform draw is below it)."""
+    return min(int(round(float(p) * 2 ** 32)), 2 ** 32 - 1) if p > 0 else 0
 
 
 def philox4x32_10(ctr, key) -> tuple:

@@ -396,12 +396,24 @@ int orc_terminated(const orc_inst *m, const orc_game *g) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* A 32-bit draw for the environment wrappers (READING: Philox4x32-10, word
+ * 0, counter = (uid, env step index, 0, phase) with phase 2 for the sticky
+ * action test and 3 for the no-op count; phases 0/1 belong to CXNN). */
+static uint32_t wrapper_draw(const orc_inst *m, uint32_t phase) {
+  uint32_t ctr[4] = {m->uid, m->env_steps, 0u, phase}, out[4];
+  orc_philox4x32_10(ctr, m->key, out);
+  return out[0];
+}
+
 /* Reset (§3.2 "ROM loading and initialization", "Environment integration";
  * §3.3 "Initialization handling"): RAM cleared, font at 0x050, ROM at 0x200,
  * registers, timers, stack and display cleared, PC = 0x200, then the game's
  * startup instructions run with no key held. READING: timers tick after every
  * K startup instructions, as in normal frames. The env step counter, the
- * random identity and the sticky status bits are kept. */
+ * random identity and the sticky status bits are kept.
+ * No-op reset (§3.2, "wrappers for no-op reset"): READING: after the startup
+ * instructions, a drawn number of no-key env steps (frameskip frames of K
+ * instructions and a timer tick each, nothing observed) in 0..max_noops. */
 int orc_inst_reset(orc_inst *m, const orc_game *g, uint32_t quirks) {
   if (g->rom_len > 4096u - 0x200u) return -1;
   memset(m->V, 0, sizeof m->V);
@@ -422,6 +434,15 @@ int orc_inst_reset(orc_inst *m, const orc_game *g, uint32_t quirks) {
     orc_exec_one(m, quirks, -1);
     if ((i + 1) % g->instr_per_frame == 0) orc_tick_timers(m);
   }
+  if (g->max_noops > 0) {
+    uint32_t noops = wrapper_draw(m, 3) % (g->max_noops + 1u);
+    for (uint32_t s = 0; s < noops; s++)
+      for (uint32_t f = 0; f < g->frameskip; f++) {
+        for (uint32_t k = 0; k < g->instr_per_frame; k++) orc_exec_one(m, quirks, -1);
+        orc_tick_timers(m);
+      }
+  }
+  m->last_action = (uint8_t)g->n_actions;  /* the previous action of a new episode: no-op */
   m->phase = 0;
   m->draws = 0;
   return 0;
@@ -442,6 +463,11 @@ static void write_frame(const orc_inst *m, uint8_t *dst /* 32*64 */) {
  * repeated (READING: auto-reset, terminal reward/done, reset observation). */
 int orc_inst_step(orc_inst *m, const orc_game *g, uint32_t quirks, uint32_t action,
                   uint8_t *obs, float *reward, uint8_t *done) {
+  /* Sticky actions (§3.2, "wrappers for ... sticky actions"). READING: per
+   * env step, with probability sticky_threshold / 2^32 the previous step's
+   * action is applied instead of the agent's. */
+  if (g->sticky_threshold > 0 && wrapper_draw(m, 2) < g->sticky_threshold) action = m->last_action;
+  m->last_action = (uint8_t)(action > 255u ? 255u : action);
   int key = -1;
   if (action < g->n_actions)
     key = g->action_set[action] & 15;
@@ -491,13 +517,14 @@ void orc_inst_record(const orc_inst *m, orc_record *r) {
   memcpy(r->ram, m->ram, 4096);
   r->episode_steps = m->episode_steps;
   r->env_steps = m->env_steps;
+  r->last_action = m->last_action;
 }
 
 /* Serialise the record field by field, little-endian, then FNV-1a. */
 uint64_t orc_inst_hash(const orc_inst *m) {
   orc_record r;
   orc_inst_record(m, &r);
-  uint8_t buf[4416];
+  uint8_t buf[4417];
   size_t o = 0;
   memcpy(buf + o, r.V, 16); o += 16;
   buf[o++] = (uint8_t)(r.I & 0xFF); buf[o++] = (uint8_t)(r.I >> 8);
@@ -512,6 +539,7 @@ uint64_t orc_inst_hash(const orc_inst *m) {
   memcpy(buf + o, r.ram, 4096); o += 4096;
   for (int b = 0; b < 4; b++) buf[o++] = (uint8_t)(r.episode_steps >> (8 * b));
   for (int b = 0; b < 4; b++) buf[o++] = (uint8_t)(r.env_steps >> (8 * b));
+  buf[o++] = r.last_action;
   return orc_fnv1a64(buf, o);
 }
 

@@ -74,6 +74,10 @@ typedef struct {
   orc_clause term[4];
   uint32_t max_episode_steps; /* truncation; 0 = none */
   uint32_t startup_instrs;    /* instructions run at reset, no key held */
+  uint32_t sticky_threshold;  /* sticky actions: repeat the previous action when
+                                 a uniform 32-bit draw is below this; 0 = off */
+  uint32_t max_noops;         /* no-op reset: 0..max_noops no-key steps after
+                                 the startup instructions; 0 = off */
 } orc_game;
 
 /* ---- status bits (sticky since creation) --------------------------------- */
@@ -98,6 +102,7 @@ typedef struct {
   uint32_t phase;      /* counter word 3: 0 = env step, 1 = reset startup */
   uint32_t draws;      /* CXNN draws so far in this step / startup */
   int32_t game;        /* index of this instance's game */
+  uint8_t last_action; /* action index applied at the previous step (sticky) */
 } orc_inst;
 
 /* Canonical state record: the unit of comparison between implementations. */
@@ -109,7 +114,9 @@ typedef struct {
   uint64_t display[32]; /* bit x of word y = pixel (x, y) */
   uint8_t ram[4096];
   uint32_t episode_steps, env_steps;
-} orc_record;           /* 4416 bytes */
+  uint8_t last_action;
+  uint8_t pad[7];
+} orc_record;           /* 4424 bytes; the hash covers the first 4417 */
 
 /* Philox4x32-10 (Salmon et al., SC'11): out = bijection(counter; key). */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -59,6 +59,8 @@ class GameSpec:
     term: tuple = ()           # Clauses, OR-ed; empty = never terminates
     max_episode_steps: int = 0  # 0 = no truncation
     startup_instrs: int = 0
+    sticky_prob: float = 0.0    # sticky actions: repeat the previous action w.p. this
+    max_noops: int = 0          # no-op reset: 0..max_noops no-key steps per reset
     name: str = ""
 
     @property

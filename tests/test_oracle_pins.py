@@ -616,4 +616,82 @@ def test_state_hash_is_fnv_of_record(oracle_lib):
     recs = e.records()
     hs = e.hashes()
     for i in range(4):
-        assert oracle_lib.fnv1a64(recs[i].tobytes()) == int(hs[i])
+        assert oracle_lib.fnv1a64(recs[i].tobytes()[:4417]) == int(hs[i])  # padding excluded
+
+
+# ---------------------------------------------------------------- wrappers (§3.2)
+# Echo program: every frame V3 = 1..4 for held key 7/9/5/8 (EXA1 skips the
+# assignment when the key is up), 0 for none; then wait for the delay timer so
+# that one pass runs per frame.
+ECHO = [
+    0x6300,                   # 0x200 V3 = 0 (no key)
+    0x6507, 0xE5A1, 0x6301,   # 0x202 key 7 held -> V3 = 1
+    0x6509, 0xE5A1, 0x6302,   # key 9 -> 2
+    0x6505, 0xE5A1, 0x6303,   # key 5 -> 3
+    0x6508, 0xE5A1, 0x6304,   # key 8 -> 4
+    0x6401, 0xF415,           # 0x21A DT = 1
+    0xF407, 0x3400, 0x121E,   # 0x21E wait for DT == 0
+    0x1200,
+]
+
+
+def _echo(**kw):
+    g = prog(ECHO, instr_per_frame=40, frameskip=1, stack_frames=1, **kw)
+    return g
+
+
+def test_sticky_off_matches_agent_actions(oracle_lib):
+    g = _echo()
+    m = oracle_lib.Machine(g)
+    acts = [0, 1, 2, 3, 4, 2, 0]
+    for a in acts:
+        m.step(a)
+        assert m.m.V[3] == (0 if a == 4 else a + 1)
+        assert m.m.last_action == a
+
+
+def test_sticky_always_repeats_previous_action(oracle_lib):
+    """p -> 1: every step repeats the previous action, which at episode start
+    is the no-op, so the agent's keys never reach the program."""
+    g = _echo(sticky_prob=1.0 - 2.0 ** -33)
+    m = oracle_lib.Machine(g)
+    for a in (0, 1, 2, 3, 0, 1):
+        m.step(a)
+        assert m.m.V[3] == 0 and m.m.last_action == 4
+
+
+def test_sticky_frequency(oracle_lib):
+    """p = 0.25: about a quarter of the steps apply the previous action."""
+    g = _echo(sticky_prob=0.25)
+    rng = np.random.default_rng(0)
+    repeats, changes = 0, 0
+    for uid in range(40):
+        m = oracle_lib.Machine(g, seed=3, uid=uid)
+        prev = 4
+        for t in range(50):
+            a = int(rng.integers(0, 4))
+            m.step(a)
+            applied = m.m.last_action
+            assert applied in (a, prev)
+            if a != prev:
+                changes += 1
+                repeats += applied == prev
+            prev = applied
+    frac = repeats / changes
+    assert 0.20 < frac < 0.30, frac
+
+
+def test_noop_reset_counts(oracle_lib):
+    """No-op reset: 0..max no-key steps (frameskip frames each) before the
+    episode starts; every count occurs and the episode step count is 0."""
+    g = prog([0x7001, 0x6401, 0xF415, 0xF407, 0x3400, 0x1206, 0x1200],  # V0 += 1 per frame
+             instr_per_frame=10, frameskip=4, stack_frames=1, max_noops=5)
+    seen = set()
+    for uid in range(300):
+        m = oracle_lib.Machine(g, seed=11, uid=uid)
+        frames = m.m.V[0]
+        # one increment per frame; n no-op steps = 4n frames
+        assert frames % 4 == 0, frames
+        seen.add(frames)
+        assert m.m.episode_steps == 0 and m.m.last_action == len(g.action_set)
+    assert seen == {4 * k for k in range(6)}
