@@ -101,7 +101,18 @@ typedef struct {
   uint32_t max_episode_steps; /* truncation after this many steps; 0 = none           */
   uint32_t startup_instrs;    /* instructions run at every reset with no key held,
                                  0..2^20                                             */
-} octax_game;
+  uint32_t sticky_threshold;  /* sticky actions (§3.2 wrappers): at every env step the
+                                 previous step's action index is applied instead of
+                                 the caller's when Philox4x32-10 word 0 at counter
+                                 (uid, env_steps, 0, 2) is below this; probability
+                                 p -> round(p * 2^32); 0 = off. A new episode's
+                                 previous action is the no-op (index n_actions). */
+  uint32_t max_noops;         /* no-op reset (§3.2 wrappers): after the startup
+                                 instructions every reset runs (word 0 at counter
+                                 (uid, env_steps, 0, 3)) mod (max_noops + 1) env
+                                 steps with no key held and nothing observed;
+                                 0..255, 0 = off                                    */
+} octax_game;                 /* 152 bytes */
 
 /* Canonical state of one instance: the unit of comparison and checkpointing.
  * RAM is the full 4 KB as the program sees it (font, ROM and all writes). */
@@ -115,7 +126,10 @@ typedef struct {
   uint8_t ram[4096];
   uint32_t episode_steps;    /* steps since the last reset */
   uint32_t env_steps;        /* steps since creation (random-number counter) */
-} octax_state_record;        /* 4416 bytes */
+  uint8_t last_action;       /* action index applied at the previous step (sticky
+                                actions); n_actions after a reset */
+  uint8_t pad[7];
+} octax_state_record;        /* 4424 bytes; octax_state_hash covers the first 4417 */
 
 /* Launch configuration (chosen by octax_autotune or set by hand). A CTA of
  * `block` emulator threads runs block/32 * inst_per_warp instances of one

@@ -115,6 +115,10 @@ int validate_game(const octax_game &g, int S) {
     set_error("all games of one environment need the same stack_frames");
     return OCTAX_EINVAL;
   }
+  if (g.max_noops > 255u) {
+    set_error("max_noops must be <= 255");
+    return OCTAX_EINVAL;
+  }
   if (g.startup_instrs > (1u << 20)) {
     set_error("startup_instrs must be <= 2^20");
     return OCTAX_EINVAL;
@@ -153,6 +157,8 @@ GameDev to_dev(const octax_game &g) {
   d.n_term = g.n_term_clauses;
   d.max_steps = g.max_episode_steps;
   d.startup = g.startup_instrs;
+  d.sticky = g.sticky_threshold;
+  d.max_noops = g.max_noops;
   memcpy(d.action_set, g.action_set, 16);
   for (int i = 0; i < 4; ++i) {
     d.score[i] = TermDev{g.score[i].src, g.score[i].xform, g.score[i].idx, g.score[i].arg};
@@ -259,6 +265,7 @@ StepLaunch base_launch(octax_env *e, const GroupTable *gt) {
   p.quirks = e->quirks;
   p.ipw = e->cfg.inst_per_warp;
   p.err = e->err_d;
+  p.wrappers = uses_wrappers(e->games_h.data(), e->games_h.size());
   return p;
 }
 
@@ -285,7 +292,8 @@ int enqueue_steps(octax_env *e, const octax_launch &cfg, int n_steps, const IO &
   const int launches = (n_steps + spl - 1) / spl;
   const int grid =
       cfg.persistent
-          ? std::min(gt->count, std::max(1, max_resident_ctas(cfg.block, cfg.inst_per_warp, cfg.writer_warps)))
+          ? std::min(gt->count, std::max(1, max_resident_ctas(cfg.block, cfg.inst_per_warp, cfg.writer_warps,
+                                                      uses_wrappers(e->games_h.data(), e->games_h.size()))))
           : gt->count;
   if (cfg.persistent) {
     rc = ensure_counters(e, launches);
@@ -453,6 +461,7 @@ int octax_create(const octax_game *games, int n_games, const uint16_t *game_of_e
   ALLOC(st.uid, n);
   ALLOC(st.out_row, n);
   ALLOC(st.game, n);
+  ALLOC(st.last_act, n);
   ALLOC(e->slot_of_row_d, n);
   ALLOC(e->io_d, 1);
   ALLOC(e->err_d, 1);
@@ -726,7 +735,7 @@ int octax_autotune(octax_env *e, int n_steps, const uint8_t *actions_dev, float 
   const Piece pieces[] = {{st.v, 16 * n},     {st.pcI, 4 * n},    {st.misc, 4 * n},
                           {st.stack, 32 * n}, {st.disp, 256 * n}, {st.dirty, 8 * n},
                           {st.ram, 4096 * n}, {st.ep, 4 * n},     {st.env_steps, 4 * n},
-                          {st.prev_score, 4 * n}};
+                          {st.prev_score, 4 * n}, {st.last_act, n}};
   size_t total = 0;
   for (const Piece &pc : pieces) total += pc.bytes;
   uint8_t *backup = nullptr, *acts = nullptr, *obs = nullptr, *done = nullptr;

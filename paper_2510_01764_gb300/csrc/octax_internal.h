@@ -28,7 +28,8 @@ struct ClauseDev {
   int32_t rhs;
 };
 struct alignas(16) GameDev {
-  uint32_t K, frameskip, n_actions, n_score, n_term, max_steps, startup, pad;
+  uint32_t K, frameskip, n_actions, n_score, n_term, max_steps, startup, sticky;
+  uint32_t max_noops, pad[3];
   uint8_t action_set[16];
   TermDev score[4];
   ClauseDev term[4];
@@ -55,7 +56,14 @@ struct DevState {
   uint32_t *uid;          // [n]      Philox counter word 0
   uint32_t *out_row;      // [n]      row of this slot in its request's outputs
   uint16_t *game;         // [n]
+  uint8_t *last_act;      // [n]      action index applied at the previous step
 };
+
+// Every per-slot array is set (checked on the host before each launch).
+inline bool state_complete(const DevState &s) {
+  return s.n > 0 && s.v && s.pcI && s.misc && s.stack && s.disp && s.dirty && s.ram && s.ep && s.env_steps &&
+         s.prev_score && s.key && s.uid && s.out_row && s.game && s.last_act;
+}
 
 // A group: up to block/32*ipw consecutive slots that share one game (one CTA's work).
 struct Group {
@@ -91,6 +99,7 @@ struct StepLaunch {
   int writers;             // >0: warp-specialised kernel with this many writer warps
   unsigned int *work_counter;  // non-null: persistent CTAs pull groups from it
   unsigned int *err;       // set when a bounded barrier wait gives up (specialised kernel)
+  int wrappers;            // 1: some game uses sticky actions or no-op reset (kernel variant)
 };
 
 struct ResetLaunch {
@@ -124,9 +133,15 @@ cudaError_t launch_records(const DevState &st, const uint8_t *images, const uint
 cudaError_t launch_set_records(const DevState &st, const GameDev *games, const uint8_t *images,
                                const uint32_t *slot_of_row, int64_t first, int64_t count,
                                const octax_state_record *in, cudaStream_t s);
-int max_resident_ctas(int block, int ipw, int writers);
+int max_resident_ctas(int block, int ipw, int writers, int wrappers);
+// True when a game enables the sticky-action or no-op-reset wrapper.
+inline int uses_wrappers(const GameDev *games, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (games[i].sticky != 0u || games[i].max_noops != 0u) return 1;
+  return 0;
+}
 // Bytes of device state per slot (all DevState arrays).
-constexpr size_t kSlotStateBytes = 16 + 4 + 4 + 32 + 256 + 8 + 4096 + 4 + 4 + 4 + 8 + 4 + 4 + 2;
+constexpr size_t kSlotStateBytes = 16 + 4 + 4 + 32 + 256 + 8 + 4096 + 4 + 4 + 4 + 8 + 4 + 4 + 2 + 1;
 cudaError_t alloc_state(DevState &st, int64_t n, void **block_out, size_t *bytes_out);
 // Append one step launch to a graph (after `dep`, if non-null).
 cudaError_t add_step_node(cudaGraph_t g, cudaGraphNode_t *node, cudaGraphNode_t dep, const StepLaunch &p,

@@ -39,6 +39,7 @@ struct Regs {
   uint64_t dirty;
   uint32_t draws, phase, env_steps;
   uint32_t key0, key1, uid;
+  uint32_t last_act;  // action index applied at the previous step (sticky actions)
 };
 
 struct Ctx {
@@ -444,7 +445,11 @@ __device__ __forceinline__ bool terminated(const Regs &R, const Ctx &C, const Ga
   return hit;
 }
 
-// Power-on state + the game's startup instructions (no key, timers tick every K).
+// Power-on state + the game's startup instructions (no key, timers tick every
+// K), then the no-op reset wrapper (§3.2): a drawn number of no-key env steps
+// of frameskip frames each, unobserved. The previous action becomes the no-op.
+// kWrap = false compiles the wrapper out (no game of the launch uses it).
+template <bool kWrap>
 __device__ __forceinline__ void reset_instance(Regs &R, const Ctx &C, const GameDev &G, uint32_t quirks) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) C.V[i * C.J] = 0;
@@ -458,14 +463,22 @@ __device__ __forceinline__ void reset_instance(Regs &R, const Ctx &C, const Game
   for (int i = 0; i < 16; ++i) C.stack[i * C.J] = 0;
 #pragma unroll 8
   for (int r = 0; r < 32; ++r) C.disp[r * C.J] = 0ull;
+  // Startup: full chunks of K (each followed by a tick), then the remainder
+  // (no tick); after it, the no-op frames (K instructions and a tick each).
+  // One loop, so that the interpreter is inlined here only once.
+  const uint32_t noop_frames =
+      !kWrap || G.max_noops == 0u ? 0u
+                        : philox_w0(R.uid, R.env_steps, 0u, 3u, R.key0, R.key1) % (G.max_noops + 1u) * G.frameskip;
+  const uint32_t full = G.startup / G.K, rem = G.startup - full * G.K;
+  const uint32_t chunks = full + (rem != 0u) + noop_frames;
   R.phase = 1;
   R.draws = 0;
-  for (uint32_t left = G.startup; left > 0;) {  // timers tick after every K instructions
-    const uint32_t c = left < G.K ? left : G.K;
-    run_instrs(R, C, -1, quirks, c);
-    if (c == G.K) tick(R);
-    left -= c;
+  for (uint32_t i = 0; i < chunks; ++i) {
+    const bool partial = i == full && rem != 0u;
+    run_instrs(R, C, -1, quirks, partial ? rem : G.K);
+    if (!partial) tick(R);
   }
+  R.last_act = G.n_actions;
   R.phase = 0;
   R.draws = 0;
 }
@@ -577,6 +590,7 @@ __device__ __forceinline__ void load_regs(Regs &R, const DevState &st, int64_t s
   R.key0 = st.key[slot];
   R.key1 = st.key[n + slot];
   R.uid = st.uid[slot];
+  R.last_act = st.last_act[slot];
   R.draws = 0;
   R.phase = 0;
 }
@@ -586,6 +600,7 @@ __device__ __forceinline__ void store_regs(const Regs &R, const DevState &st, in
   st.misc[slot] = R.sp | (R.dt << 8) | (R.st << 16) | (R.status << 24);
   st.dirty[slot] = R.dirty;
   st.env_steps[slot] = R.env_steps;
+  st.last_act[slot] = (uint8_t)R.last_act;
 }
 
 // V0-VF: packed 4 per u32 in global memory, one per u32 in shared memory.
@@ -608,6 +623,7 @@ __device__ __forceinline__ void store_V(const Ctx &C, const DevState &st, int64_
   }
 }
 
+template <bool kWrap>
 __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
   const int t = threadIdx.x, lane = t & 31, w = t >> 5, ipw = p.ipw;
   const int J = (blockDim.x >> 5) * ipw;  // instances per CTA
@@ -644,7 +660,10 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
     int key = -1;
     uint8_t *my_obs = nullptr;
     if (active) {
-      const uint32_t a = io.actions[io_row];
+      uint32_t a = io.actions[io_row];
+      // sticky actions (§3.2): repeat the previous step's action with probability sticky / 2^32
+      if (kWrap && G.sticky != 0u && philox_w0(R.uid, R.env_steps, 0u, 2u, R.key0, R.key1) < G.sticky) a = R.last_act;
+      R.last_act = a;
       if (a < G.n_actions) key = G.action_set[a] & 15;
       else if (a > G.n_actions) R.status |= OCTAX_STATUS_BAD_ACTION;
       my_obs = io.obs + io_row * (int64_t)p.S * kFrameBytes;
@@ -672,7 +691,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
       io.reward[io_row] = (float)(sc - prev);
       io.done[io_row] = done ? 1 : 0;
       if (done) {
-        reset_instance(R, C, G, quirks);
+        reset_instance<kWrap>(R, C, G, quirks);
         ep = 0;
         prev = score(R, C, G);
       } else {
@@ -701,6 +720,9 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
 
 // No __launch_bounds__: with it ptxas caps registers at 128 and may spill;
 // without it the register count still admits a 256-thread CTA.
+// kWrap: the sticky-action / no-op-reset variant (its draws cost registers,
+// so games without the wrappers run the variant without them).
+template <bool kWrap>
 __global__ void step_kernel(const StepLaunch p) {
   extern __shared__ __align__(16) uint8_t smem[];
   const Smem S = carve(smem, (blockDim.x >> 5) * p.ipw);
@@ -720,7 +742,7 @@ __global__ void step_kernel(const StepLaunch p) {
       cur_game = g.game;
     }
     __syncthreads();
-    run_group(p, g, S);
+    run_group<kWrap>(p, g, S);
     __syncthreads();  // shared memory is reused by the next group
     if (!p.work_counter) break;
   }
@@ -825,7 +847,10 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
     const int64_t io_row = (int64_t)(p.step0 + s) * io.rows + row;
     int key = -1;
     if (active) {
-      const uint32_t a = io.actions[io_row];
+      uint32_t a = io.actions[io_row];
+      // sticky actions (§3.2): repeat the previous step's action with probability sticky / 2^32
+      if (G.sticky != 0u && philox_w0(R.uid, R.env_steps, 0u, 2u, R.key0, R.key1) < G.sticky) a = R.last_act;
+      R.last_act = a;
       if (a < G.n_actions) key = G.action_set[a] & 15;
       else if (a > G.n_actions) R.status |= OCTAX_STATUS_BAD_ACTION;
     }
@@ -861,7 +886,7 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
       io.reward[io_row] = (float)(sc - prev);
       io.done[io_row] = done ? 1 : 0;
       if (done) {
-        reset_instance(R, C, G, quirks);
+        reset_instance<true>(R, C, G, quirks);
         ep = 0;
         prev = score(R, C, G);
       } else {
@@ -1023,7 +1048,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
   }
   const Ctx C{S.img, S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
               st.ram + slot * (int64_t)kRamBytes, J, S.uops};
-  if (doit) reset_instance(R, C, G, p.quirks);
+  if (doit) reset_instance<true>(R, C, G, p.quirks);
   const unsigned which = __ballot_sync(kFull, doit);
   if (p.obs && which) {
     __syncwarp();
@@ -1095,6 +1120,7 @@ __global__ void hash_kernel(const DevState st, const uint8_t *images, const uint
   const uint32_t ep = st.ep[slot], es = st.env_steps[slot];
   for (int b = 0; b < 4; ++b) h = fnv_byte(h, ep >> (8 * b));
   for (int b = 0; b < 4; ++b) h = fnv_byte(h, es >> (8 * b));
+  h = fnv_byte(h, st.last_act[slot]);
   out[row] = h;
 }
 
@@ -1123,6 +1149,8 @@ __global__ void records_kernel(const DevState st, const uint8_t *images, const u
   for (uint32_t a = 0; a < (uint32_t)kRamBytes; ++a) rec.ram[a] = ram_byte(st, img, slot, dirty, a);
   rec.episode_steps = st.ep[slot];
   rec.env_steps = st.env_steps[slot];
+  rec.last_action = st.last_act[slot];
+  for (int k = 0; k < 7; ++k) rec.pad[k] = 0;
 }
 
 __global__ void set_records_kernel(const DevState st, const GameDev *games, const uint8_t *images,
@@ -1159,6 +1187,7 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
   st.dirty[slot] = dirty;
   st.ep[slot] = rec.episode_steps;
   st.env_steps[slot] = rec.env_steps;
+  st.last_act[slot] = rec.last_action;
   // score of the restored state (the next step's reward baseline)
   const GameDev &G = games[game];
   int32_t s = 0;
@@ -1207,8 +1236,11 @@ size_t step_ws_smem_bytes(int block, int ipw) {
 static cudaError_t ensure_smem_attr() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)step_smem_bytes(kMaxBlock, 32));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)step_smem_bytes(kMaxBlock, 32));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(step_kernel_ws, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)max_dynamic_smem());
@@ -1220,17 +1252,21 @@ static cudaError_t ensure_smem_attr() {
 }
 
 cudaError_t launch_step(const StepLaunch &p, int grid, int block, cudaStream_t s) {
+  if (!state_complete(p.st)) return cudaErrorInvalidValue;
   cudaError_t e = ensure_smem_attr();
   if (e != cudaSuccess) return e;
   if (grid <= 0) return cudaSuccess;
   if (p.writers > 0)
     step_kernel_ws<<<grid, block + 32 * p.writers, step_ws_smem_bytes(block, p.ipw), s>>>(p);
+  else if (p.wrappers)
+    step_kernel<true><<<grid, block, step_smem_bytes(block, p.ipw), s>>>(p);
   else
-    step_kernel<<<grid, block, step_smem_bytes(block, p.ipw), s>>>(p);
+    step_kernel<false><<<grid, block, step_smem_bytes(block, p.ipw), s>>>(p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_reset(const ResetLaunch &p, int block, cudaStream_t s) {
+  if (!state_complete(p.st)) return cudaErrorInvalidValue;
   cudaError_t e = ensure_smem_attr();
   if (e != cudaSuccess) return e;
   if (p.n_groups <= 0) return cudaSuccess;
@@ -1241,6 +1277,7 @@ cudaError_t launch_reset(const ResetLaunch &p, int block, cudaStream_t s) {
 cudaError_t launch_hash(const DevState &st, const uint8_t *images, const uint32_t *slot_of_row,
                         int64_t rows, uint64_t *out, cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;
+  if (!state_complete(st)) return cudaErrorInvalidValue;
   const int tb = 128;
   hash_kernel<<<(unsigned)((rows + tb - 1) / tb), tb, 0, s>>>(st, images, slot_of_row, rows, out);
   return cudaGetLastError();
@@ -1249,6 +1286,7 @@ cudaError_t launch_hash(const DevState &st, const uint8_t *images, const uint32_
 cudaError_t launch_records(const DevState &st, const uint8_t *images, const uint32_t *slot_of_row,
                            int64_t first, int64_t count, octax_state_record *out, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
+  if (!state_complete(st)) return cudaErrorInvalidValue;
   const int tb = 128;
   records_kernel<<<(unsigned)((count + tb - 1) / tb), tb, 0, s>>>(st, images, slot_of_row, first, count,
                                                                    out);
@@ -1259,6 +1297,7 @@ cudaError_t launch_set_records(const DevState &st, const GameDev *games, const u
                                const uint32_t *slot_of_row, int64_t first, int64_t count,
                                const octax_state_record *in, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
+  if (!state_complete(st)) return cudaErrorInvalidValue;
   const int tb = 128;
   set_records_kernel<<<(unsigned)((count + tb - 1) / tb), tb, 0, s>>>(st, games, images, slot_of_row,
                                                                        first, count, in);
@@ -1267,6 +1306,7 @@ cudaError_t launch_set_records(const DevState &st, const GameDev *games, const u
 
 cudaError_t add_step_node(cudaGraph_t g, cudaGraphNode_t *node, cudaGraphNode_t dep, const StepLaunch &p,
                           int grid, int block) {
+  if (!state_complete(p.st)) return cudaErrorInvalidValue;
   cudaError_t e = ensure_smem_attr();
   if (e != cudaSuccess) return e;
   StepLaunch copy = p;
@@ -1274,7 +1314,9 @@ cudaError_t add_step_node(cudaGraph_t g, cudaGraphNode_t *node, cudaGraphNode_t 
   cudaKernelNodeParams kp;
   memset(&kp, 0, sizeof kp);
   const bool ws = p.writers > 0;
-  kp.func = ws ? reinterpret_cast<void *>(step_kernel_ws) : reinterpret_cast<void *>(step_kernel);
+  kp.func = ws ? reinterpret_cast<void *>(step_kernel_ws)
+               : p.wrappers ? reinterpret_cast<void *>(step_kernel<true>)
+                            : reinterpret_cast<void *>(step_kernel<false>);
   kp.gridDim = dim3((unsigned)grid);
   kp.blockDim = dim3((unsigned)(ws ? block + 32 * p.writers : block));
   kp.sharedMemBytes = (unsigned)(ws ? step_ws_smem_bytes(block, p.ipw) : step_smem_bytes(block, p.ipw));
@@ -1287,7 +1329,7 @@ cudaError_t alloc_state(DevState &st, int64_t n, void **block_out, size_t *bytes
   // every array starts on a 256-byte boundary
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t sizes[] = {16 * N, 4 * N, 4 * N, 32 * N, 256 * N, 8 * N, 4096 * N,
-                          4 * N,  4 * N, 4 * N, 8 * N,  4 * N,   4 * N, 2 * N};
+                          4 * N,  4 * N, 4 * N, 8 * N,  4 * N,   4 * N, 2 * N, N};
   size_t total = 0;
   for (size_t b : sizes) total += up(b);
   uint8_t *base = nullptr;
@@ -1297,8 +1339,8 @@ cudaError_t alloc_state(DevState &st, int64_t n, void **block_out, size_t *bytes
   void **dst[] = {(void **)&st.v,   (void **)&st.pcI,        (void **)&st.misc,      (void **)&st.stack,
                   (void **)&st.disp, (void **)&st.dirty,     (void **)&st.ram,       (void **)&st.ep,
                   (void **)&st.env_steps, (void **)&st.prev_score, (void **)&st.key, (void **)&st.uid,
-                  (void **)&st.out_row, (void **)&st.game};
-  for (int i = 0; i < 14; ++i) {
+                  (void **)&st.out_row, (void **)&st.game, (void **)&st.last_act};
+  for (int i = 0; i < 15; ++i) {
     *dst[i] = base + off;
     off += up(sizes[i]);
   }
@@ -1308,7 +1350,7 @@ cudaError_t alloc_state(DevState &st, int64_t n, void **block_out, size_t *bytes
   return cudaSuccess;
 }
 
-int max_resident_ctas(int block, int ipw, int writers) {
+int max_resident_ctas(int block, int ipw, int writers, int wrappers) {
   if (ensure_smem_attr() != cudaSuccess) return 0;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
@@ -1316,8 +1358,10 @@ int max_resident_ctas(int block, int ipw, int writers) {
   if (writers > 0)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel_ws, block + 32 * writers,
                                                   step_ws_smem_bytes(block, ipw));
+  else if (wrappers)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<true>, block, step_smem_bytes(block, ipw));
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel, block, step_smem_bytes(block, ipw));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<false>, block, step_smem_bytes(block, ipw));
   return sms * per_sm;
 }
 

@@ -270,6 +270,7 @@ bool tick(octax_server *s) {
   p.quirks = s->quirks;
   p.ipw = s->ipw;
   p.err = s->err_d;
+  p.wrappers = uses_wrappers(s->games_h.data(), s->games_h.size());
   if (r == cudaSuccess) r = launch_step(p, (int)g, s->block, s->stream);
   if (r == cudaSuccess) r = cudaEventRecord(t.ev, s->stream);
   if (r != cudaSuccess) {

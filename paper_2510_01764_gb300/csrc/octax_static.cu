@@ -32,8 +32,8 @@ constexpr int kStaticMaxGroups = (int)((kStaticMaxEnvs + kStaticPerCta - 1) / kS
 constexpr size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t N = (size_t)kStaticMaxEnvs;
 // per-slot arrays, in DevState order
-constexpr size_t kArr[14] = {16 * N, 4 * N, 4 * N, 32 * N, 256 * N, 8 * N, 4096 * N,
-                             4 * N,  4 * N, 4 * N, 8 * N,  4 * N,   4 * N, 2 * N};
+constexpr size_t kArr[15] = {16 * N, 4 * N, 4 * N, 32 * N, 256 * N, 8 * N, 4096 * N,
+                             4 * N,  4 * N, 4 * N, 8 * N,  4 * N,   4 * N, 2 * N, N};
 constexpr size_t state_bytes() {
   size_t t = 0;
   for (size_t b : kArr) t += up256(b);
@@ -128,8 +128,8 @@ extern "C" int octax_rollout_static(const octax_game *game, int64_t n_envs, uint
   void **dst[] = {(void **)&st.v,        (void **)&st.pcI,        (void **)&st.misc, (void **)&st.stack,
                   (void **)&st.disp,     (void **)&st.dirty,      (void **)&st.ram,  (void **)&st.ep,
                   (void **)&st.env_steps, (void **)&st.prev_score, (void **)&st.key,  (void **)&st.uid,
-                  (void **)&st.out_row,  (void **)&st.game};
-  for (int i = 0; i < 14; ++i) {
+                  (void **)&st.out_row,  (void **)&st.game,   (void **)&st.last_act};
+  for (int i = 0; i < 15; ++i) {
     *dst[i] = base + off;
     off += up256(kArr[i]);
   }
@@ -185,6 +185,7 @@ extern "C" int octax_rollout_static(const octax_game *game, int64_t n_envs, uint
     p.S = game->stack_frames;
     p.quirks = quirks;
     p.ipw = kStaticIpw;
+    p.wrappers = uses_wrappers(dev_games.data(), 1);
     r = launch_step(p, n_groups, kStaticBlock, s);
     if (r != cudaSuccess) return cuda_fail(r, "octax_rollout_static: step launch");
   }

@@ -48,7 +48,8 @@ class CGame(C.Structure):
                 ("action_set", C.c_uint8 * 16), ("n_score_terms", C.c_uint8),
                 ("n_term_clauses", C.c_uint8), ("pad", C.c_uint8 * 2), ("score", CTerm * 4),
                 ("term", CClause * 4), ("max_episode_steps", C.c_uint32),
-                ("startup_instrs", C.c_uint32)]
+                ("startup_instrs", C.c_uint32), ("sticky_threshold", C.c_uint32),
+                ("max_noops", C.c_uint32)]
 
 
 class CLaunch(C.Structure):
@@ -60,8 +61,9 @@ class CLaunch(C.Structure):
 RECORD_DTYPE = np.dtype([("V", np.uint8, 16), ("I", "<u2"), ("PC", "<u2"), ("SP", np.uint8),
                          ("DT", np.uint8), ("ST", np.uint8), ("status", np.uint8),
                          ("stack", "<u2", 16), ("display", "<u8", 32), ("ram", np.uint8, 4096),
-                         ("episode_steps", "<u4"), ("env_steps", "<u4")])
-assert RECORD_DTYPE.itemsize == 4416
+                         ("episode_steps", "<u4"), ("env_steps", "<u4"),
+                         ("last_action", np.uint8), ("pad", np.uint8, 7)])
+assert RECORD_DTYPE.itemsize == 4424
 
 class CServerConfig(C.Structure):
     _fields_ = [("memory_budget_bytes", C.c_int64), ("block", C.c_int32),
@@ -177,7 +179,14 @@ def make_game(spec) -> tuple[CGame, object]:
         g.term[i] = CClause(_term(c.lhs), _CMP[c.cmp], (C.c_uint8 * 3)(), int(c.rhs))
     g.max_episode_steps = spec.max_episode_steps
     g.startup_instrs = spec.startup_instrs
+    g.sticky_threshold = sticky_threshold(getattr(spec, "sticky_prob", 0.0))
+    g.max_noops = getattr(spec, "max_noops", 0)
     return g, rom
+
+
+def sticky_threshold(p: float) -> int:
+    """Sticky-action probability -> the descriptor's 32-bit threshold."""
+    return min(int(round(float(p) * 2 ** 32)), 2 ** 32 - 1) if p > 0 else 0
 
 
 def _ptr(t) -> C.c_void_p | None:

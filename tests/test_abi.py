@@ -98,7 +98,8 @@ def test_descriptor_validation_without_gpu(lib):
     L = o.load_library()
     bad = [GameSpec(rom=b""), GameSpec(rom=b"\x00" * 3585), GameSpec(rom=b"\x12\x00", frameskip=2),
            GameSpec(rom=b"\x12\x00", instr_per_frame=0), GameSpec(rom=b"\x12\x00", action_set=(16,)),
-           GameSpec(rom=b"\x12\x00", startup_instrs=(1 << 20) + 1)]
+           GameSpec(rom=b"\x12\x00", startup_instrs=(1 << 20) + 1),
+           GameSpec(rom=b"\x12\x00", max_noops=256)]
     for g in bad:
         cg, keep = o.make_game(g) if len(g.rom) else (o.CGame(), None)
         arr = (o.CGame * 1)(cg)

@@ -148,6 +148,31 @@ def test_mixed_games_timing_and_stacks(launch):
     env.sync()
 
 
+@pytest.mark.parametrize("launch", [
+    None,
+    dict(block=64, inst_per_warp=16, steps_per_launch=4, persistent=1, use_graph=1),
+    dict(block=128, inst_per_warp=8, steps_per_launch=3, persistent=0, use_graph=1, writer_warps=2),
+])
+def test_sticky_actions_and_noop_reset(launch):
+    """§3.2 wrappers: sticky actions (p = 0.25) and no-op reset (0..30 no-op
+    steps) on games with frequent episode ends, next to a game without
+    either in the same launch; the previous action is compared in the state."""
+    ts = [W.TemplateParams(seed=60 + i, size=400, wait_frames=i % 2) for i in range(3)]
+    games = [
+        W.replace(W.template_game(ts[0], score_limit=2, max_episode_steps=17), sticky_prob=0.25,
+                  max_noops=30),
+        W.replace(W.template_game(ts[1], max_episode_steps=9), max_noops=5, startup_instrs=23),
+        W.template_game(ts[2], score_limit=3),
+        W.replace(W.random_game(91), sticky_prob=0.9),
+    ]
+    n = 260
+    goe = np.random.default_rng(3).integers(0, 4, n).astype(np.uint16)
+    env, ref = full_compare(games, n, 90, seed=21, action_seed=22, game_of_env=goe, launch=launch,
+                            use_step_n=launch is not None)
+    la = env.get_state()["last_action"]
+    assert (la == 4).any() and (la < 4).any()
+
+
 def test_reward_descriptor_memory_and_transforms():
     """Score from memory bytes written by FX33, several transforms, compound
     termination, truncation."""

@@ -13,7 +13,7 @@ from paper_2510_01764_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-SLOT_BYTES = 4454 + 8
+SLOT_BYTES = 4455 + 8
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -98,6 +98,26 @@ def test_requests_match_oracle():
     srv.close()
     for r, got in zip(reqs, outs):
         T, n = r["actions"].shape
+        ref = oracle.OracleEnv(gs, n, seed=r["seed"], game_of_env=np.full(n, r["game"], np.uint16))
+        ref.reset()
+        ob, rw, dn, _ = ref.rollout(r["actions"], obs=True)
+        assert np.array_equal(got[0].numpy(), ob)
+        assert np.array_equal(got[1].numpy(), rw)
+        assert np.array_equal(got[2].numpy(), dn)
+
+
+def test_requests_with_wrappers_match_oracle():
+    """Sticky actions and no-op reset (§3.2) through the serving path."""
+    o = octax()
+    gs = games()
+    gs[1] = W.replace(gs[1], sticky_prob=0.3, max_noops=9)
+    gs[4] = W.replace(gs[4], max_noops=3)
+    reqs = make_requests(6, 5, max_envs=64)
+    srv = o.Server(gs, memory_budget_bytes=10000 * SLOT_BYTES)
+    _, _, outs = run_all(srv, reqs, stagger_s=0.0005)
+    srv.close()
+    for r, got in zip(reqs, outs):
+        n = r["actions"].shape[1]
         ref = oracle.OracleEnv(gs, n, seed=r["seed"], game_of_env=np.full(n, r["game"], np.uint16))
         ref.reset()
         ob, rw, dn, _ = ref.rollout(r["actions"], obs=True)

@@ -61,6 +61,8 @@ def test_static_rollout_matches_step_n_twice_in_a_row():
     cases = [
         (W.template_game(W.TemplateParams(seed=2), score_limit=3, max_episode_steps=40), 1000, 11, 90),
         (W.random_game(5), 77, 12, 33),        # fewer instances: stale state must not leak
+        (W.replace(W.template_game(W.TemplateParams(seed=4), max_episode_steps=12), sticky_prob=0.25,
+                   max_noops=6), 300, 13, 40),  # sticky actions + no-op reset
     ]
     for game, n, seed, T in cases:
         acts = torch.from_numpy(W.actions(seed, 0, T, n, game.n_actions + 1)).cuda()
