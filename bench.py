@@ -167,6 +167,51 @@ def profiled_traffic(config: str) -> dict | None:
     return e
 
 
+_NCU_SCALE = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1e-9, "ns": 1e-9,
+              "usecond": 1e-6, "us": 1e-6, "msecond": 1e-3, "ms": 1e-3, "second": 1.0, "s": 1.0}
+
+
+def record_traffic(csv_path: str, config: str, launch: str, units: int) -> dict:
+    """Store the step kernel's DRAM bytes and warp instructions per instance
+    step, averaged over the launches of an `ncu --page raw --csv` export, in
+    profiles/traffic.json under `config` (tagged with the kernel source hash)."""
+    import csv
+
+    rows = list(csv.reader(open(csv_path)))
+    hdr, unit_row, data = rows[0], rows[1], [r for r in rows[2:] if r and "step_kernel" in ",".join(r)]
+    if not data:
+        raise SystemExit(f"no step_kernel launch in {csv_path}")
+
+    def mean(name: str) -> float:
+        i = hdr.index(name)
+        scale = _NCU_SCALE.get(unit_row[i], 1.0)
+        return sum(float(r[i].replace(",", "")) for r in data) / len(data) * scale
+
+    traffic = mean("dram__bytes_read.sum") + mean("dram__bytes_write.sum")
+    entry = {
+        "kernel_source": kernel_source_hash(),
+        "captured_launch": launch,
+        "captured_launches": len(data),
+        "captured_instance_steps_per_launch": units,
+        "dram_bytes_per_launch": traffic,
+        "dram_bytes_per_instance_step": traffic / units,
+        "warp_inst_per_instance_step": mean("smsp__inst_executed.sum") / units,
+        "captured_duration_s": mean("gpu__time_duration.sum"),
+        "note": "ncu --set full --clock-control none; DRAM write bytes exclude observation "
+                "lines still in L2 at kernel exit",
+    }
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        d = {}
+    d[config] = entry
+    with open(path, "w") as f:
+        json.dump(d, f, indent=1)
+        f.write("\n")
+    return entry
+
+
 # --------------------------------------------------------------------------- GPU arm
 def run_gpu(args) -> dict | None:
     import torch
@@ -196,9 +241,9 @@ def run_gpu(args) -> dict | None:
 
         # ---- launch configuration: autotuned for T-step calls
         if args.launch:
-            f = [int(x) for x in args.launch.split(",")] + [0]
+            f = [int(x) for x in args.launch.split(",")] + [0, 0]
             env.set_launch(block=f[0], inst_per_warp=f[1], steps_per_launch=f[2], persistent=f[3],
-                           use_graph=f[4], writer_warps=f[5])
+                           use_graph=f[4], writer_warps=f[5], balance=f[6])
         else:
             env.autotune(T, acts[:T])
         launch = env.launch
@@ -237,7 +282,7 @@ def run_gpu(args) -> dict | None:
             ms_best, _ = timed(launch)
         clocks = clk.summary()
         plain_cfg = dict(block=launch["block"], inst_per_warp=launch["inst_per_warp"],
-                         steps_per_launch=1, persistent=0, use_graph=0, writer_warps=0)
+                         steps_per_launch=1, persistent=0, use_graph=0, writer_warps=0, balance=0)
         ms_plain, _ = timed(plain_cfg)
         env.set_launch(**launch)
 
@@ -305,8 +350,9 @@ def run_gpu(args) -> dict | None:
             "rollout_buffer_steps": T,
             "launch": launch,
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-            "l2": "no flush: each step writes 134 MB of observations into a 32-step rollout ring "
-                  "and touches 72 MB of emulator state, more than the 126 MB L2",
+            "l2": (f"no flush: each step writes {n * 4 * 2048 / 1e6:.0f} MB of observations into a "
+                   f"{T}-step rollout ring ({T * n * 4 * 2048 / 1e6:.0f} MB); emulator state "
+                   f"{n * 4455 / 1e6:.0f} MB; L2 126 MB"),
         },
         "plain_kernel": {
             "value": round(whole_job_rate(world, n, K, ms_plain), 1),
@@ -507,7 +553,7 @@ def main():
     ap.add_argument("--config", default="scale", choices=["scale", "small", "batch", "divergence"])
     ap.add_argument("--rollout", type=int, default=32, help="steps per octax_step_n call")
     ap.add_argument("--launch", default="",
-                    help="block,inst_per_warp,steps_per_launch,persistent,graph[,writer_warps] "
+                    help="block,inst_per_warp,steps_per_launch,persistent,graph[,writer_warps[,balance]] "
                          "(default: autotune)")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -516,7 +562,17 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-steps", type=int, default=1_000_000)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
+    ap.add_argument("--record-traffic", default="", metavar="CSV",
+                    help="no GPU: read an `ncu -i <rep> --page raw --csv` export of step_kernel "
+                         "launches into profiles/traffic.json for --config")
+    ap.add_argument("--traffic-launch", default="", help="launch string of the captured run")
+    ap.add_argument("--traffic-units", type=int, default=0,
+                    help="instance steps per captured launch (instances x steps per launch)")
     args = ap.parse_args()
+    if args.record_traffic:
+        print(json.dumps(record_traffic(args.record_traffic, args.config, args.traffic_launch,
+                                        args.traffic_units), indent=1))
+        return
     if args.impl == "reference":
         line = run_reference(args)
         if line:

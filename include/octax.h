@@ -142,6 +142,9 @@ typedef struct {
   int32_t persistent;        /* 1: resident CTAs pull instance groups off a queue */
   int32_t use_graph;         /* 1: octax_step_n replays a captured CUDA graph     */
   int32_t writer_warps;      /* 0, 1, 2, 4 or 8 observation-writer warps         */
+  int32_t balance;           /* 1: spread the instances evenly over a whole number
+                                of waves of resident CTAs (every SM gets the same
+                                number of CTAs); 0: full CTAs, ragged last one   */
 } octax_launch;
 
 typedef struct octax_env octax_env;

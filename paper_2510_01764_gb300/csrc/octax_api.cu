@@ -50,10 +50,10 @@ struct GroupTable {
 };
 
 struct GraphKey {
-  int n_steps, block, ipw, spl, persistent, writers;
+  int n_steps, block, ipw, spl, persistent, writers, balance;
   bool operator<(const GraphKey &o) const {
-    return std::tie(n_steps, block, ipw, spl, persistent, writers) <
-           std::tie(o.n_steps, o.block, o.ipw, o.spl, o.persistent, o.writers);
+    return std::tie(n_steps, block, ipw, spl, persistent, writers, balance) <
+           std::tie(o.n_steps, o.block, o.ipw, o.spl, o.persistent, o.writers, o.balance);
   }
 };
 
@@ -74,8 +74,8 @@ struct octax_env {
   uint32_t *slot_of_row_d = nullptr;
   std::vector<void *> allocs;
   size_t bytes = 0;
-  octax_launch cfg{64, 8, 4, 0, 1, 0};
-  std::map<int, GroupTable> groups;
+  octax_launch cfg{64, 8, 4, 0, 1, 0, 0};
+  std::map<std::pair<int, int>, GroupTable> groups;  // by (instances per CTA, wave)
   unsigned int *counters_d = nullptr;
   int counters_cap = 0;
   IO *io_d = nullptr;
@@ -173,10 +173,19 @@ int block_ok(int b) { return b == 32 || b == 64 || b == 128 || b == 256; }
 int ipw_ok(int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32; }
 int per_cta(const octax_launch &c) { return c.block / 32 * c.inst_per_warp; }
 
+// Resident CTAs of one wave for a balanced launch (0 = not balanced).
+int wave_of(const octax_env *e, const octax_launch &c) {
+  if (!c.balance) return 0;
+  return max_resident_ctas(c.block, c.inst_per_warp, c.writer_warps,
+                           uses_wrappers(e->games_h.data(), e->games_h.size()));
+}
+
 const char *launch_problem(const octax_launch &c) {
   if (!block_ok(c.block) || !ipw_ok(c.inst_per_warp)) return "block in {32,64,128,256}, inst_per_warp in {1,...,32}";
   if (c.steps_per_launch < 1 || c.steps_per_launch > 64) return "steps_per_launch 1..64";
-  if ((c.persistent != 0 && c.persistent != 1) || (c.use_graph != 0 && c.use_graph != 1)) return "flags 0/1";
+  if ((c.persistent != 0 && c.persistent != 1) || (c.use_graph != 0 && c.use_graph != 1) ||
+      (c.balance != 0 && c.balance != 1))
+    return "flags 0/1";
   if (c.writer_warps != 0) {
     const int W = c.writer_warps, J = per_cta(c);
     if (!(W == 1 || W == 2 || W == 4 || W == 8)) return "writer_warps in {0,1,2,4,8}";
@@ -209,21 +218,42 @@ int octax::build_games(const octax_game *games, int n_games, std::vector<GameDev
 
 namespace {
 
-// Groups of up to `block` (instances per CTA) consecutive same-game slots.
-int get_groups(octax_env *e, int block, GroupTable **out) {
-  auto it = e->groups.find(block);
+// Groups of up to `cap` (instances per CTA) consecutive same-game slots.
+// wave > 0 (balanced): the group count is rounded up to a whole number of
+// waves of `wave` resident CTAs and every run of same-game slots is cut into
+// groups of near-equal size, so that every SM receives the same number of
+// CTAs of about the same size. wave = 0: full groups, a ragged last one.
+int get_groups(octax_env *e, int cap, int wave, GroupTable **out) {
+  const std::pair<int, int> gkey(cap, wave);
+  auto it = e->groups.find(gkey);
   if (it != e->groups.end()) {
     *out = &it->second;
     return OCTAX_OK;
   }
-  std::vector<Group> gs;
-  int64_t s = 0;
-  while (s < e->n) {
+  std::vector<std::pair<int64_t, int64_t>> runs;  // [first, end) of same-game slots
+  for (int64_t s = 0; s < e->n;) {
     int64_t end = s;
-    const uint16_t g = e->game_of_slot[s];
-    while (end < e->n && e->game_of_slot[end] == g && end - s < block) ++end;
-    gs.push_back(Group{(uint32_t)s, (uint16_t)(end - s), g, 0u, 0u});
+    while (end < e->n && e->game_of_slot[end] == e->game_of_slot[s]) ++end;
+    runs.emplace_back(s, end);
     s = end;
+  }
+  int64_t size = cap;  // target instances per group
+  if (wave > 0) {
+    int64_t g0 = 0;
+    for (const auto &r : runs) g0 += (r.second - r.first + cap - 1) / cap;
+    const int64_t g = (g0 + wave - 1) / wave * wave;
+    size = std::max<int64_t>(1, (e->n + g - 1) / g);  // <= cap because g >= g0
+  }
+  std::vector<Group> gs;
+  for (const auto &r : runs) {
+    const int64_t len = r.second - r.first, k = (len + size - 1) / size;
+    const uint16_t game = e->game_of_slot[r.first];
+    int64_t s = r.first;
+    for (int64_t q = 0; q < k; ++q) {
+      const int64_t cnt = len / k + (q < len % k ? 1 : 0);
+      gs.push_back(Group{(uint32_t)s, (uint16_t)cnt, game, 0u, 0u});
+      s += cnt;
+    }
   }
   // Longest first (instructions per step): CTAs are dispatched, and the
   // persistent queue hands out groups, in table order.
@@ -238,8 +268,8 @@ int get_groups(octax_env *e, int block, GroupTable **out) {
   if (r != cudaSuccess) return cuda_fail(r, "group table");
   r = cudaMemcpy(t.dev, gs.data(), gs.size() * sizeof(Group), cudaMemcpyHostToDevice);
   if (r != cudaSuccess) return cuda_fail(r, "group table upload");
-  e->groups[block] = t;
-  *out = &e->groups[block];
+  e->groups[gkey] = t;
+  *out = &e->groups[gkey];
   return OCTAX_OK;
 }
 
@@ -286,7 +316,7 @@ int check_io(const uint8_t *actions, const uint8_t *obs, const float *reward, co
 // Enqueue n_steps steps as a chain of launches of `spl` steps each.
 int enqueue_steps(octax_env *e, const octax_launch &cfg, int n_steps, const IO &io) {
   GroupTable *gt = nullptr;
-  int rc = get_groups(e, per_cta(cfg), &gt);
+  int rc = get_groups(e, per_cta(cfg), wave_of(e, cfg), &gt);
   if (rc) return rc;
   const int spl = cfg.steps_per_launch;
   const int launches = (n_steps + spl - 1) / spl;
@@ -318,7 +348,7 @@ int enqueue_steps(octax_env *e, const octax_launch &cfg, int n_steps, const IO &
     return OCTAX_OK;
   }
   // CUDA graph: the kernels read their IO from io_d, refreshed before replay.
-  const GraphKey key{n_steps, cfg.block, cfg.inst_per_warp, spl, cfg.persistent, cfg.writer_warps};
+  const GraphKey key{n_steps, cfg.block, cfg.inst_per_warp, spl, cfg.persistent, cfg.writer_warps, cfg.balance};
   auto it = e->graphs.find(key);
   if (it == e->graphs.end()) {
     cudaGraph_t g;
@@ -486,7 +516,7 @@ int octax_create(const octax_game *games, int n_games, const uint16_t *game_of_e
     return rc;
   }
   GroupTable *gt = nullptr;
-  int rc = get_groups(e, per_cta(e->cfg), &gt);
+  int rc = get_groups(e, per_cta(e->cfg), wave_of(e, e->cfg), &gt);
   if (rc) {
     free_env(e);
     return rc;
@@ -525,7 +555,7 @@ int octax_reset(octax_env *e, const uint8_t *mask_dev, uint8_t *obs_dev) {
     return OCTAX_EINVAL;
   }
   GroupTable *gt = nullptr;
-  int rc = get_groups(e, per_cta(e->cfg), &gt);
+  int rc = get_groups(e, per_cta(e->cfg), wave_of(e, e->cfg), &gt);
   if (rc) return rc;
   ResetLaunch p;
   memset(&p, 0, sizeof p);
@@ -802,18 +832,20 @@ int octax_autotune(octax_env *e, int n_steps, const uint8_t *actions_dev, float 
       best = c;
     }
   };
-  // stage 1: CTA shape (threads x instances per warp), plain kernel, 4 steps per launch
+  // stage 1: CTA shape (threads x instances per warp) and balanced waves,
+  // plain kernel, 4 steps per launch
   for (int b : {32, 64, 128, 256})
-    for (int ipw : {32, 16, 8, 4}) {
-      const int J = b / 32 * ipw;
-      if (J >= 8 && J <= 256) trial(octax_launch{b, ipw, std::min(4, n_steps), 0, 1, 0});
-    }
+    for (int ipw : {32, 16, 8, 4})
+      for (int bal : {0, 1}) {
+        const int J = b / 32 * ipw;
+        if (J >= 8 && J <= 256) trial(octax_launch{b, ipw, std::min(4, n_steps), 0, 1, 0, bal});
+      }
   // stage 2: writer warps, persistence and steps per launch around the best shape
   const octax_launch shape = best;
   for (int W : {0, 1, 2, 4})
     for (int pers : {0, 1})
       for (int spl : {1, 2, 4, 8})
-        trial(octax_launch{shape.block, shape.inst_per_warp, spl, pers, 1, W});
+        trial(octax_launch{shape.block, shape.inst_per_warp, spl, pers, 1, W, shape.balance});
   off = 0;
   for (const Piece &pc : pieces) {
     cudaMemcpyAsync(pc.p, backup + off, pc.bytes, cudaMemcpyDeviceToDevice, e->stream);

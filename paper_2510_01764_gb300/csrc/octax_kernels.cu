@@ -34,6 +34,13 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+// The CTA's dynamic shared memory. Every kernel lays it out with carve(), so
+// the game's 4 KB RAM image is its first 4 KB. Reading the image through this
+// array (not through a pointer) keeps those loads in the shared state space.
+extern __shared__ __align__(16) uint8_t g_smem[];
+
+__device__ __forceinline__ uint32_t img_byte(uint32_t a) { return g_smem[a]; }
+
 struct Regs {
   uint32_t pc, I, sp, dt, st, status;
   uint64_t dirty;
@@ -43,7 +50,6 @@ struct Regs {
 };
 
 struct Ctx {
-  const uint8_t *img;  // shared: initial RAM image of this CTA's game
   uint64_t *disp;      // shared: this instance's row 0; row r at disp[r * J]
   uint32_t *stack;     // shared: this instance's entry 0; entry i at stack[i * J]
   uint32_t *V;         // shared: this instance's V0; Vx at V[x * J]
@@ -62,14 +68,14 @@ __device__ __forceinline__ uint32_t dirty_bit(uint64_t dirty, uint32_t a) {
 
 __device__ __forceinline__ uint32_t rd8(const Regs &R, const Ctx &C, uint32_t a) {
   a &= 0xFFFu;
-  return dirty_bit(R.dirty, a) ? (uint32_t)C.ram[a] : (uint32_t)C.img[a];
+  return dirty_bit(R.dirty, a) ? (uint32_t)C.ram[a] : img_byte(a);
 }
 
 __device__ __forceinline__ void wr8(Regs &R, const Ctx &C, uint32_t a, uint32_t val) {
   a &= 0xFFFu;
   const uint32_t page = a >> kPageShift;
   if (!((R.dirty >> page) & 1u)) {  // first write to this page: copy it from the image
-    const uint4 *src = reinterpret_cast<const uint4 *>(C.img + (page << kPageShift));
+    const uint4 *src = reinterpret_cast<const uint4 *>(g_smem + (page << kPageShift));
     uint4 *dst = reinterpret_cast<uint4 *>(C.ram + (page << kPageShift));
     dst[0] = src[0];
     dst[1] = src[1];
@@ -112,6 +118,22 @@ __device__ __forceinline__ void draw(Regs &R, const Ctx &C, uint32_t vx, uint32_
   const bool wrap = quirks & OCTAX_QUIRK_WRAP_SPRITES;
   // the sprite spans at most two pages: read it from the image unless one is dirty
   const bool clean = n == 0 || !(dirty_bit(R.dirty, I) | dirty_bit(R.dirty, I + n - 1u));
+  if (clean && !wrap && I + n <= (uint32_t)kRamBytes) {
+    // Common case: sprite in the shared image, rows below the screen clipped,
+    // no per-row checks; collision bits are OR-ed over the rows.
+    const uint32_t rows = n < 32u - y0 ? n : 32u - y0;
+    uint64_t *row = C.disp + y0 * C.J;
+    uint64_t hit = 0;
+    for (uint32_t r = 0; r < rows; ++r) {
+      const uint64_t s = (uint64_t)(__brev(img_byte(I + r)) >> 24) << x0;  // pixel j -> bit x0 + j, right edge clips
+      const uint64_t old = *row;
+      hit |= old & s;
+      *row = old ^ s;
+      row += C.J;
+    }
+    setVF(C, hit != 0ull);
+    return;
+  }
   uint32_t coll = 0;
   for (uint32_t r = 0; r < n; ++r) {
     uint32_t py = y0 + r;
@@ -120,7 +142,7 @@ __device__ __forceinline__ void draw(Regs &R, const Ctx &C, uint32_t vx, uint32_
       py &= 31u;
     }
     const uint32_t a = (I + r) & 0xFFFu;
-    const uint32_t b = clean ? (uint32_t)C.img[a] : rd8(R, C, a);
+    const uint32_t b = clean ? img_byte(a) : rd8(R, C, a);
     const uint32_t rev = __brev(b) >> 24;  // pixel j of the sprite -> bit j
     uint64_t s = (uint64_t)rev << x0;       // right edge clips
     if (wrap && x0 > 56u) s |= (uint64_t)rev >> (64u - x0);
@@ -395,6 +417,9 @@ __device__ __forceinline__ void execute(Regs &R, const Ctx &C, uint32_t u, int k
     R.I = I;
     R.dt = (tk == 1u) ? vx : R.dt;
     R.st = (tk == 2u) ? vx : R.st;
+  } else if ((u >> 12) == 0xDu) {  // DXYN, the most frequent slow opcode: its own branch
+    R.pc = (pc + 2u) & 0xFFFu;
+    draw(R, C, getV(C, (u >> 8) & 15u), getV(C, (u >> 4) & 15u), u & 15u, quirks);
   } else {
     R.pc = (pc + 2u) & 0xFFFu;
     exec_slow(R, C, u & 0xFFFFu, pc, key, quirks);
@@ -649,7 +674,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
 #pragma unroll 8
     for (int r = 0; r < 32; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
   }
-  const Ctx C{S.img, S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
+  const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
               st.ram + slot * (int64_t)kRamBytes, J, S.uops};
   if (mine) load_V(C, st, slot);
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
@@ -724,7 +749,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
 // so games without the wrappers run the variant without them).
 template <bool kWrap>
 __global__ void step_kernel(const StepLaunch p) {
-  extern __shared__ __align__(16) uint8_t smem[];
+  uint8_t *const smem = g_smem;
   const Smem S = carve(smem, (blockDim.x >> 5) * p.ipw);
   __shared__ int s_group;
   int cur_game = -1;
@@ -838,7 +863,7 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
 #pragma unroll 8
     for (int r = 0; r < 32; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
   }
-  const Ctx C{S.img, S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
+  const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
               st.ram + slot * (int64_t)kRamBytes, J, S.uops};
   if (mine) load_V(C, st, slot);
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
@@ -979,7 +1004,7 @@ __device__ void run_group_writer(const StepLaunch &p, const Group &g, const WsSm
 }
 
 __global__ void step_kernel_ws(const StepLaunch p) {
-  extern __shared__ __align__(16) uint8_t smem[];
+  uint8_t *const smem = g_smem;
   const int E = (int)(blockDim.x >> 5) - p.writers;
   const int J = E * p.ipw;
   const WsSmem W = carve_ws(smem, J);
@@ -1019,7 +1044,7 @@ __global__ void step_kernel_ws(const StepLaunch p) {
 }
 
 __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
-  extern __shared__ __align__(16) uint8_t smem[];
+  uint8_t *const smem = g_smem;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5, ipw = p.ipw;
   const int J = (blockDim.x >> 5) * ipw;
   const int j = w * ipw + lane;
@@ -1046,7 +1071,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
   } else {
     load_regs(R, st, slot);
   }
-  const Ctx C{S.img, S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
+  const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
               st.ram + slot * (int64_t)kRamBytes, J, S.uops};
   if (doit) reset_instance<true>(R, C, G, p.quirks);
   const unsigned which = __ballot_sync(kFull, doit);

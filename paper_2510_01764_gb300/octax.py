@@ -55,7 +55,7 @@ class CGame(C.Structure):
 class CLaunch(C.Structure):
     _fields_ = [("block", C.c_int32), ("inst_per_warp", C.c_int32),
                 ("steps_per_launch", C.c_int32), ("persistent", C.c_int32),
-                ("use_graph", C.c_int32), ("writer_warps", C.c_int32)]
+                ("use_graph", C.c_int32), ("writer_warps", C.c_int32), ("balance", C.c_int32)]
 
 
 RECORD_DTYPE = np.dtype([("V", np.uint8, 16), ("I", "<u2"), ("PC", "<u2"), ("SP", np.uint8),
@@ -326,13 +326,13 @@ class Env:
         check(load_library().octax_get_launch(self._h, C.byref(c)))
         return {"block": c.block, "inst_per_warp": c.inst_per_warp,
                 "steps_per_launch": c.steps_per_launch, "persistent": c.persistent,
-                "use_graph": c.use_graph, "writer_warps": c.writer_warps}
+                "use_graph": c.use_graph, "writer_warps": c.writer_warps, "balance": c.balance}
 
     def set_launch(self, **kw) -> None:
         cur = self.launch
         cur.update(kw)
         c = CLaunch(cur["block"], cur["inst_per_warp"], cur["steps_per_launch"], cur["persistent"],
-                    cur["use_graph"], cur["writer_warps"])
+                    cur["use_graph"], cur["writer_warps"], cur["balance"])
         check(load_library().octax_set_launch(self._h, C.byref(c)))
 
     def autotune(self, n_steps: int = 8, actions=None) -> float:

@@ -97,6 +97,10 @@ def test_config_small_full_parity():
     dict(block=64, inst_per_warp=8, steps_per_launch=3, persistent=1, use_graph=1, writer_warps=2),
     dict(block=256, inst_per_warp=4, steps_per_launch=8, persistent=1, use_graph=0, writer_warps=4),
     dict(block=32, inst_per_warp=32, steps_per_launch=1, persistent=0, use_graph=1, writer_warps=1),
+    dict(block=64, inst_per_warp=8, steps_per_launch=4, persistent=0, use_graph=1, balance=1),
+    dict(block=256, inst_per_warp=8, steps_per_launch=3, persistent=1, use_graph=0, balance=1),
+    dict(block=128, inst_per_warp=16, steps_per_launch=2, persistent=0, use_graph=1, writer_warps=2,
+         balance=1),
 ])
 def test_launch_configurations_agree(launch):
     w = W.cfg_small()
@@ -127,7 +131,9 @@ def test_ragged_instance_counts(n):
 
 
 @pytest.mark.parametrize("launch", [None, dict(block=128, inst_per_warp=8, steps_per_launch=4,
-                                                persistent=1, use_graph=1, writer_warps=1)])
+                                                persistent=1, use_graph=1, writer_warps=1),
+                                    dict(block=64, inst_per_warp=4, steps_per_launch=2,
+                                         persistent=0, use_graph=1, balance=1)])
 def test_mixed_games_timing_and_stacks(launch):
     """Different K and frame skip per game, stack_frames < frame skip,
     startup instructions that draw random numbers, shuffled instance order."""
@@ -405,7 +411,19 @@ def test_config_scale_sampled_writer_warps():
     assert n_done > 0
 
 
-def test_config_batch_sampled():
+def test_config_scale_sampled_balanced():
+    """The full workload with instances spread evenly over whole waves of
+    resident CTAs (the benchmark's CTA shape)."""
+    w = W.cfg_scale()
+    sample = pick(w.n_envs, 16, 6, extra=(53, 54, 107, 108, w.n_envs - 1))
+    env, n_done = sampled_run(w, chunk=64, sample=sample,
+                              launch=dict(block=256, inst_per_warp=8, steps_per_launch=8,
+                                          persistent=0, use_graph=1, balance=1))
+    assert n_done > 0
+
+
+@pytest.mark.parametrize("balance", [0, 1])
+def test_config_batch_sampled(balance):
     """65,536 instances over 16 ROMs (K from {5,8,10,15,20}, uneven episodes),
     16 frames per persistent graph-captured launch."""
     w = W.cfg_batch()
@@ -414,7 +432,7 @@ def test_config_batch_sampled():
     sample = np.unique(np.concatenate(per_game + [pick(w.n_envs, 16, 3)]))
     sampled_run(w, chunk=32, sample=sample,
                 launch=dict(block=64, inst_per_warp=16, steps_per_launch=4, persistent=1,
-                            use_graph=1))
+                            use_graph=1, balance=balance))
 
 
 def test_config_divergence_sampled():
