@@ -137,7 +137,7 @@ typedef struct {
  * observations (block/32 * inst_per_warp / writer_warps must be 8, 16 or 32). */
 typedef struct {
   int32_t block;             /* emulator threads per CTA: 32, 64, 128 or 256    */
-  int32_t inst_per_warp;     /* instances emulated per warp: 1, 2, 4, 8, 16, 32 */
+  int32_t inst_per_warp;     /* instances emulated per warp: 1..32                */
   int32_t steps_per_launch;  /* octax_step_n: env steps per kernel launch 1..64  */
   int32_t persistent;        /* 1: resident CTAs pull instance groups off a queue */
   int32_t use_graph;         /* 1: octax_step_n replays a captured CUDA graph     */

@@ -170,7 +170,7 @@ GameDev to_dev(const octax_game &g) {
 }
 
 int block_ok(int b) { return b == 32 || b == 64 || b == 128 || b == 256; }
-int ipw_ok(int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32; }
+int ipw_ok(int v) { return v >= 1 && v <= 32; }
 int per_cta(const octax_launch &c) { return c.block / 32 * c.inst_per_warp; }
 
 // Resident CTAs of one wave for a balanced launch (0 = not balanced).
@@ -835,7 +835,7 @@ int octax_autotune(octax_env *e, int n_steps, const uint8_t *actions_dev, float 
   // stage 1: CTA shape (threads x instances per warp) and balanced waves,
   // plain kernel, 4 steps per launch
   for (int b : {32, 64, 128, 256})
-    for (int ipw : {32, 16, 8, 4})
+    for (int ipw : {32, 16, 8, 7, 6, 4})
       for (int bal : {0, 1}) {
         const int J = b / 32 * ipw;
         if (J >= 8 && J <= 256) trial(octax_launch{b, ipw, std::min(4, n_steps), 0, 1, 0, bal});

@@ -98,6 +98,9 @@ def test_config_small_full_parity():
     dict(block=256, inst_per_warp=4, steps_per_launch=8, persistent=1, use_graph=0, writer_warps=4),
     dict(block=32, inst_per_warp=32, steps_per_launch=1, persistent=0, use_graph=1, writer_warps=1),
     dict(block=64, inst_per_warp=8, steps_per_launch=4, persistent=0, use_graph=1, balance=1),
+    dict(block=256, inst_per_warp=7, steps_per_launch=4, persistent=0, use_graph=1, balance=1),
+    dict(block=128, inst_per_warp=5, steps_per_launch=3, persistent=1, use_graph=1),
+    dict(block=64, inst_per_warp=12, steps_per_launch=2, persistent=0, use_graph=0),
     dict(block=256, inst_per_warp=8, steps_per_launch=3, persistent=1, use_graph=0, balance=1),
     dict(block=128, inst_per_warp=16, steps_per_launch=2, persistent=0, use_graph=1, writer_warps=2,
          balance=1),
