@@ -23,7 +23,13 @@ _lib = None
 
 QUIRKS = {"shift_uses_vy": 0x01, "loadstore_inc_i": 0x02, "logic_resets_vf": 0x04,
           "jump_vx": 0x08, "wrap_sprites": 0x10, "fx1e_vf": 0x20}
-ST_BAD_OP, ST_STACK_FAULT, ST_BAD_ACTION = 1, 2, 4
+ST_BAD_OP, ST_STACK_FAULT, ST_BAD_ACTION, ST_EXIT = 1, 2, 4, 8
+VARIANTS = {"chip8": 0, "schip": 1}
+
+
+def frame_shape(variant: str) -> tuple:
+    """(rows, columns) of one observation frame."""
+    return (64, 128) if variant == "schip" else (32, 64)
 
 _XFORM = {"raw": 0, "neg": 1, "dec_tens": 2, "dec_ones": 3, "dec_tens_minus_ones": 4,
           "nib_hi_minus_lo": 5, "zero_if_gt": 6}
@@ -59,25 +65,27 @@ class Game(C.Structure):
                 ("action_set", C.c_uint8 * 16), ("n_score_terms", C.c_uint32),
                 ("score", Term * 4), ("n_term_clauses", C.c_uint32), ("term", Clause * 4),
                 ("max_episode_steps", C.c_uint32), ("startup_instrs", C.c_uint32),
-                ("sticky_threshold", C.c_uint32), ("max_noops", C.c_uint32)]
+                ("sticky_threshold", C.c_uint32), ("max_noops", C.c_uint32),
+                ("variant", C.c_uint32)]
 
 
 class Inst(C.Structure):
     _fields_ = [("V", C.c_uint8 * 16), ("I", C.c_uint16), ("PC", C.c_uint16), ("SP", C.c_uint8),
                 ("DT", C.c_uint8), ("ST", C.c_uint8), ("status", C.c_uint8),
-                ("stack", C.c_uint16 * 16), ("pix", (C.c_uint8 * 64) * 32),
+                ("stack", C.c_uint16 * 16), ("pix", (C.c_uint8 * 128) * 64),
                 ("ram", C.c_uint8 * 4096), ("episode_steps", C.c_uint32),
                 ("env_steps", C.c_uint32), ("key", C.c_uint32 * 2), ("uid", C.c_uint32),
                 ("phase", C.c_uint32), ("draws", C.c_uint32), ("game", C.c_int32),
-                ("last_action", C.c_uint8)]
+                ("last_action", C.c_uint8), ("variant", C.c_uint8), ("hires", C.c_uint8),
+                ("rpl", C.c_uint8 * 16)]
 
 
 RECORD_DTYPE = np.dtype([("V", np.uint8, 16), ("I", "<u2"), ("PC", "<u2"), ("SP", np.uint8),
                          ("DT", np.uint8), ("ST", np.uint8), ("status", np.uint8),
-                         ("stack", "<u2", 16), ("display", "<u8", 32), ("ram", np.uint8, 4096),
+                         ("stack", "<u2", 16), ("display", "<u8", (64, 2)), ("ram", np.uint8, 4096),
                          ("episode_steps", "<u4"), ("env_steps", "<u4"), ("last_action", np.uint8),
-                         ("pad", np.uint8, 7)])
-assert RECORD_DTYPE.itemsize == 4424
+                         ("hires", np.uint8), ("pad", np.uint8, 6), ("rpl", np.uint8, 16)])
+assert RECORD_DTYPE.itemsize == 5208
 
 
 def lib():
@@ -146,6 +154,7 @@ def make_game(spec) -> tuple[Game, object]:
     g.startup_instrs = spec.startup_instrs
     g.sticky_threshold = sticky_threshold(getattr(spec, "sticky_prob", 0.0))
     g.max_noops = getattr(spec, "max_noops", 0)
+    g.variant = VARIANTS[getattr(spec, "variant", "chip8")]
     return g, rom
 
 
@@ -172,6 +181,7 @@ class Machine:
 
     def __init__(self, spec, quirks: int = 0, seed: int = 0, uid: int = 0):
         self._g, self._rom = make_game(spec)
+        self._variant = getattr(spec, "variant", "chip8")
         self.quirks = quirks
         self.m = Inst()
         self.m.key[0] = seed & 0xFFFFFFFF
@@ -188,7 +198,7 @@ class Machine:
         lib().orc_tick_timers(C.byref(self.m))
 
     def step(self, action: int, obs: bool = True):
-        o = np.zeros((self._g.stack_frames, 32, 64), dtype=np.uint8) if obs else None
+        o = np.zeros((self._g.stack_frames,) + frame_shape(self._variant), dtype=np.uint8) if obs else None
         r = C.c_float()
         d = C.c_uint8()
         lib().orc_inst_step(C.byref(self.m), C.byref(self._g), self.quirks, action, _ptr(o),
@@ -210,7 +220,9 @@ class Machine:
 
     @property
     def pixels(self) -> np.ndarray:
-        return np.ctypeslib.as_array(self.m.pix).copy()
+        """The screen: 32x64 (CHIP-8) or the 64x128 buffer (SCHIP)."""
+        h, w = frame_shape(self._variant)
+        return np.ctypeslib.as_array(self.m.pix)[:h, :w].copy()
 
     @property
     def ram(self) -> np.ndarray:
@@ -235,6 +247,7 @@ class OracleEnv:
         self._games_arr = arr
         self.n = int(n_envs)
         self.stack_frames = games[0].stack_frames
+        self.frame = frame_shape(getattr(games[0], "variant", "chip8"))
         self._goe = None if game_of_env is None else np.ascontiguousarray(game_of_env, dtype=np.uint16)
         self._uoe = None if uid_of_env is None else np.ascontiguousarray(uid_of_env, dtype=np.uint32)
         self.h = lib().orc_env_create(arr, len(games), _ptr(self._goe), _ptr(self._uoe), self.n,
@@ -251,7 +264,7 @@ class OracleEnv:
         self.close()
 
     def reset(self, mask=None) -> np.ndarray:
-        obs = np.zeros((self.n, self.stack_frames, 32, 64), dtype=np.uint8)
+        obs = np.zeros((self.n, self.stack_frames) + self.frame, dtype=np.uint8)
         m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
         lib().orc_env_reset(self.h, _ptr(m), _ptr(obs))
         return obs
@@ -259,7 +272,7 @@ class OracleEnv:
     def step(self, actions, *, obs: bool = True, threads: int = 1):
         a = np.ascontiguousarray(actions, dtype=np.uint8)
         assert a.shape == (self.n,)
-        o = np.zeros((self.n, self.stack_frames, 32, 64), dtype=np.uint8) if obs else None
+        o = np.zeros((self.n, self.stack_frames) + self.frame, dtype=np.uint8) if obs else None
         r = np.zeros(self.n, dtype=np.float32)
         d = np.zeros(self.n, dtype=np.uint8)
         lib().orc_env_step(self.h, _ptr(a), _ptr(o), _ptr(r), _ptr(d), threads)
@@ -269,7 +282,7 @@ class OracleEnv:
         a = np.ascontiguousarray(actions, dtype=np.uint8)
         steps = a.shape[0]
         assert a.shape[1] == self.n
-        o = np.zeros((steps, self.n, self.stack_frames, 32, 64), dtype=np.uint8) if obs else None
+        o = np.zeros((steps, self.n, self.stack_frames) + self.frame, dtype=np.uint8) if obs else None
         r = np.zeros((steps, self.n), dtype=np.float32)
         d = np.zeros((steps, self.n), dtype=np.uint8)
         h = np.zeros((steps, self.n), dtype=np.uint64) if hashes else None

@@ -43,6 +43,21 @@ static const uint8_t ORC_FONT[80] = {
     0xF0, 0x80, 0xF0, 0x80, 0x80  /* F */
 };
 
+/* SCHIP 8x10 glyphs at 0x0A0 (FX30). READING: no source fixes their shapes;
+ * each is the 4x5 glyph above with every pixel drawn as a 2x2 block (row r
+ * of the big glyph is row r/2 of the small one, each of its 4 pixels
+ * doubled). Written into RAM at reset of SCHIP games only. */
+#define ORC_BIG_FONT_ADDR 0x0A0u
+static uint8_t big_glyph_row(uint32_t digit, uint32_t row) {
+  uint32_t small = ORC_FONT[5u * digit + row / 2u] >> 4; /* 4 pixels, MSB leftmost */
+  uint8_t out = 0;
+  for (uint32_t i = 0; i < 4; i++)
+    if ((small >> i) & 1u) out = (uint8_t)(out | (3u << (2u * i)));
+  return out;
+}
+
+size_t orc_frame_bytes(uint32_t variant) { return variant == ORC_SCHIP ? 64u * 128u : 32u * 64u; }
+
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
  * easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies with the
@@ -138,6 +153,65 @@ static void draw_sprite(orc_inst *m, uint32_t x, uint32_t y, uint32_t n, uint32_
   m->V[15] = collision;
 }
 
+/* SCHIP DXYN / DXY0 (Super-CHIP 1.1). The screen is a 128x64 buffer. In
+ * hires mode sprites use its pixels; in lores mode coordinates are on a 64x32
+ * grid and every lit sprite pixel toggles a 2x2 block of the buffer. N = 0
+ * draws a 16x16 sprite from 32 bytes at I (two bytes per row, MSB leftmost);
+ * READING: 16x16 in both modes. VF = 1 if any toggled buffer pixel was lit
+ * (READING: a flag, not the per-row count of the HP48 interpreter). Clipping
+ * and the wrap quirk as in CHIP-8, on the grid of the current mode. */
+static void draw_sprite_schip(orc_inst *m, uint32_t x, uint32_t y, uint32_t n, uint32_t quirks) {
+  uint32_t W = m->hires ? 128u : 64u, H = m->hires ? 64u : 32u;
+  uint32_t x0 = m->V[x] % W, y0 = m->V[y] % H;
+  uint32_t rows = n == 0 ? 16u : n, cols = n == 0 ? 16u : 8u;
+  uint8_t collision = 0;
+  for (uint32_t row = 0; row < rows; row++) {
+    uint32_t bits = n == 0 ? ((uint32_t)mem_read(m, (uint32_t)m->I + 2u * row) << 8) |
+                                 mem_read(m, (uint32_t)m->I + 2u * row + 1u)
+                           : mem_read(m, (uint32_t)m->I + row);
+    uint32_t py = y0 + row;
+    if (py >= H) {
+      if (quirks & QUIRK_WRAP_SPRITES)
+        py %= H;
+      else
+        continue;
+    }
+    for (uint32_t col = 0; col < cols; col++) {
+      if (!((bits >> (cols - 1u - col)) & 1u)) continue;
+      uint32_t px = x0 + col;
+      if (px >= W) {
+        if (quirks & QUIRK_WRAP_SPRITES)
+          px %= W;
+        else
+          continue;
+      }
+      uint32_t s = m->hires ? 1u : 2u; /* buffer pixels per grid pixel */
+      for (uint32_t dy = 0; dy < s; dy++)
+        for (uint32_t dx = 0; dx < s; dx++) {
+          uint8_t *p = &m->pix[py * s + dy][px * s + dx];
+          if (*p) collision = 1;
+          *p ^= 1u;
+        }
+    }
+  }
+  m->V[15] = collision;
+}
+
+/* SCHIP scrolls of the 128x64 buffer; vacated pixels are cleared. READING:
+ * distances count pixels of the current mode (doubled in lores). */
+static void scroll_down(orc_inst *m, uint32_t rows) {
+  for (int y = 63; y >= 0; y--)
+    for (int x = 0; x < 128; x++) m->pix[y][x] = (uint32_t)y >= rows ? m->pix[y - (int)rows][x] : 0;
+}
+static void scroll_right(orc_inst *m, uint32_t cols) {
+  for (int y = 0; y < 64; y++)
+    for (int x = 127; x >= 0; x--) m->pix[y][x] = (uint32_t)x >= cols ? m->pix[y][x - (int)cols] : 0;
+}
+static void scroll_left(orc_inst *m, uint32_t cols) {
+  for (int y = 0; y < 64; y++)
+    for (int x = 0; x < 128; x++) m->pix[y][x] = (uint32_t)x + cols < 128u ? m->pix[y][x + (int)cols] : 0;
+}
+
 static void set_status(orc_inst *m, uint8_t bit) { m->status |= bit; }
 
 /* One fetch/decode/execute cycle (§3.2 "Fetch-decode-execute cycle"; App. B
@@ -155,10 +229,27 @@ void orc_exec_one(orc_inst *m, uint32_t quirks, int key_held) {
   uint32_t nn = op & 0xFFu;
   uint32_t nnn = op & 0xFFFu;
 
+  const int schip = m->variant == ORC_SCHIP;
+  const uint32_t unit = m->hires ? 1u : 2u; /* SCHIP buffer pixels per grid pixel */
+
   switch (op >> 12) {
     case 0x0:
       if (op == 0x00E0) { /* CLS */
         memset(m->pix, 0, sizeof m->pix);
+      } else if (schip && (op & 0xFFF0u) == 0x00C0u) { /* SCHIP 00CN: scroll down N */
+        scroll_down(m, n * unit);
+      } else if (schip && op == 0x00FB) { /* scroll right 4 */
+        scroll_right(m, 4u * unit);
+      } else if (schip && op == 0x00FC) { /* scroll left 4 */
+        scroll_left(m, 4u * unit);
+      } else if (schip && op == 0x00FD) { /* exit. READING: the program stops
+                                             here (re-executes) and EXIT is set */
+        set_status(m, ORC_ST_EXIT);
+        m->PC = (uint16_t)pc;
+      } else if (schip && op == 0x00FE) { /* lores. READING: no clear */
+        m->hires = 0;
+      } else if (schip && op == 0x00FF) { /* hires. READING: no clear */
+        m->hires = 1;
       } else if (op == 0x00EE) { /* RET. READING: popping an empty stack faults
                                     and wraps to the top entry. */
         if (m->SP == 0) {
@@ -277,7 +368,10 @@ void orc_exec_one(orc_inst *m, uint32_t quirks, int key_held) {
       m->V[x] = (uint8_t)(random_byte(m, pc) & nn);
       break;
     case 0xD: /* DRW VX, VY, N */
-      draw_sprite(m, x, y, n, quirks);
+      if (schip)
+        draw_sprite_schip(m, x, y, n, quirks);
+      else
+        draw_sprite(m, x, y, n, quirks);
       break;
     case 0xE: {
       int pressed = (key_held >= 0) && ((uint32_t)key_held == (m->V[x] & 0xFu));
@@ -320,6 +414,27 @@ void orc_exec_one(orc_inst *m, uint32_t quirks, int key_held) {
         }
         case 0x29: /* LD F, VX: glyph of the low digit of VX */
           m->I = (uint16_t)(0x50u + 5u * (m->V[x] % 16u));
+          break;
+        case 0x30: /* SCHIP LD HF, VX: 8x10 glyph of the low digit of VX */
+          if (!schip) {
+            set_status(m, ORC_ST_BAD_OP);
+            break;
+          }
+          m->I = (uint16_t)(ORC_BIG_FONT_ADDR + 10u * (m->V[x] % 16u));
+          break;
+        case 0x75: /* SCHIP: flags[0..X] = V0..VX. READING: 16 flag bytes */
+          if (!schip) {
+            set_status(m, ORC_ST_BAD_OP);
+            break;
+          }
+          for (uint32_t i = 0; i <= x; i++) m->rpl[i] = m->V[i];
+          break;
+        case 0x85: /* SCHIP: V0..VX = flags[0..X] */
+          if (!schip) {
+            set_status(m, ORC_ST_BAD_OP);
+            break;
+          }
+          for (uint32_t i = 0; i <= x; i++) m->V[i] = m->rpl[i];
           break;
         case 0x33: { /* BCD */
           uint32_t v = m->V[x];
@@ -426,6 +541,12 @@ int orc_inst_reset(orc_inst *m, const orc_game *g, uint32_t quirks) {
   memset(m->pix, 0, sizeof m->pix);
   memset(m->ram, 0, sizeof m->ram);
   memcpy(m->ram + 0x50, ORC_FONT, sizeof ORC_FONT);
+  m->variant = (uint8_t)g->variant;
+  m->hires = 0;                       /* READING: every episode starts in lores */
+  memset(m->rpl, 0, sizeof m->rpl);   /* READING: flags do not outlive an episode */
+  if (g->variant == ORC_SCHIP)
+    for (uint32_t d = 0; d < 16; d++)
+      for (uint32_t r = 0; r < 10; r++) m->ram[ORC_BIG_FONT_ADDR + 10u * d + r] = big_glyph_row(d, r);
   memcpy(m->ram + 0x200, g->rom, g->rom_len);
   m->episode_steps = 0;
   m->phase = 1;
@@ -448,9 +569,11 @@ int orc_inst_reset(orc_inst *m, const orc_game *g, uint32_t quirks) {
   return 0;
 }
 
-static void write_frame(const orc_inst *m, uint8_t *dst /* 32*64 */) {
-  for (int y = 0; y < 32; y++)
-    for (int x = 0; x < 64; x++) dst[y * 64 + x] = m->pix[y][x];
+/* One observation frame: the 64x32 screen (CHIP-8) or the 128x64 buffer (SCHIP). */
+static void write_frame(const orc_inst *m, uint8_t *dst) {
+  int W = m->variant == ORC_SCHIP ? 128 : 64, H = m->variant == ORC_SCHIP ? 64 : 32;
+  for (int y = 0; y < H; y++)
+    for (int x = 0; x < W; x++) dst[y * W + x] = m->pix[y][x];
 }
 
 /* One environment step (§3.2 "Environment integration", §4.2): the action's
@@ -481,7 +604,7 @@ int orc_inst_step(orc_inst *m, const orc_game *g, uint32_t quirks, uint32_t acti
     for (uint32_t k = 0; k < g->instr_per_frame; k++) orc_exec_one(m, quirks, key);
     orc_tick_timers(m);
     uint32_t first_kept = g->frameskip - g->stack_frames;
-    if (obs && f >= first_kept) write_frame(m, obs + (size_t)(f - first_kept) * 2048u);
+    if (obs && f >= first_kept) write_frame(m, obs + (size_t)(f - first_kept) * orc_frame_bytes(g->variant));
   }
   int32_t score_after = orc_score(m, g);
   m->episode_steps++;
@@ -493,7 +616,7 @@ int orc_inst_step(orc_inst *m, const orc_game *g, uint32_t quirks, uint32_t acti
   if (*done) {
     orc_inst_reset(m, g, quirks);
     if (obs)
-      for (uint32_t s = 0; s < g->stack_frames; s++) write_frame(m, obs + (size_t)s * 2048u);
+      for (uint32_t s = 0; s < g->stack_frames; s++) write_frame(m, obs + (size_t)s * orc_frame_bytes(g->variant));
   }
   return 0;
 }
@@ -508,23 +631,29 @@ void orc_inst_record(const orc_inst *m, orc_record *r) {
   r->ST = m->ST;
   r->status = m->status;
   memcpy(r->stack, m->stack, sizeof r->stack);
-  for (int y = 0; y < 32; y++) {
-    uint64_t w = 0;
-    for (int x = 0; x < 64; x++)
-      if (m->pix[y][x]) w |= (uint64_t)1 << x;
-    r->display[y] = w;
-  }
+  for (int y = 0; y < 64; y++)
+    for (int h = 0; h < 2; h++) {
+      uint64_t w = 0;
+      for (int x = 0; x < 64; x++)
+        if (m->pix[y][64 * h + x]) w |= (uint64_t)1 << x;
+      r->display[y][h] = w;
+    }
   memcpy(r->ram, m->ram, 4096);
   r->episode_steps = m->episode_steps;
   r->env_steps = m->env_steps;
   r->last_action = m->last_action;
+  r->hires = m->hires;
+  memcpy(r->rpl, m->rpl, 16);
 }
 
-/* Serialise the record field by field, little-endian, then FNV-1a. */
+/* Serialise the record field by field, little-endian, then FNV-1a. CHIP-8:
+ * the display is rows 0-31, word 0. SCHIP: all 64 x 2 words (row-major),
+ * followed after last_action by hires and the 16 flag bytes. */
 uint64_t orc_inst_hash(const orc_inst *m) {
   orc_record r;
   orc_inst_record(m, &r);
-  uint8_t buf[4417];
+  const int schip = m->variant == ORC_SCHIP;
+  uint8_t buf[5300];
   size_t o = 0;
   memcpy(buf + o, r.V, 16); o += 16;
   buf[o++] = (uint8_t)(r.I & 0xFF); buf[o++] = (uint8_t)(r.I >> 8);
@@ -534,12 +663,17 @@ uint64_t orc_inst_hash(const orc_inst *m) {
     buf[o++] = (uint8_t)(r.stack[i] & 0xFF);
     buf[o++] = (uint8_t)(r.stack[i] >> 8);
   }
-  for (int y = 0; y < 32; y++)
-    for (int b = 0; b < 8; b++) buf[o++] = (uint8_t)(r.display[y] >> (8 * b));
+  for (int y = 0; y < (schip ? 64 : 32); y++)
+    for (int h = 0; h < (schip ? 2 : 1); h++)
+      for (int b = 0; b < 8; b++) buf[o++] = (uint8_t)(r.display[y][h] >> (8 * b));
   memcpy(buf + o, r.ram, 4096); o += 4096;
   for (int b = 0; b < 4; b++) buf[o++] = (uint8_t)(r.episode_steps >> (8 * b));
   for (int b = 0; b < 4; b++) buf[o++] = (uint8_t)(r.env_steps >> (8 * b));
   buf[o++] = r.last_action;
+  if (schip) {
+    buf[o++] = r.hires;
+    memcpy(buf + o, r.rpl, 16); o += 16;
+  }
   return orc_fnv1a64(buf, o);
 }
 
@@ -565,8 +699,8 @@ orc_env *orc_env_create(const orc_game *games, int n_games, const uint16_t *game
     const orc_game *g = &games[gi];
     if (g->rom_len == 0 || g->rom_len > 3584u || g->instr_per_frame == 0 || g->frameskip == 0 ||
         g->stack_frames == 0 || g->stack_frames > g->frameskip || g->n_actions > 16 ||
-        g->n_score_terms > 4 || g->n_term_clauses > 4 ||
-        g->stack_frames != games[0].stack_frames)
+        g->n_score_terms > 4 || g->n_term_clauses > 4 || g->variant > ORC_SCHIP ||
+        g->stack_frames != games[0].stack_frames || g->variant != games[0].variant)
       return NULL;
   }
   orc_env *e = (orc_env *)calloc(1, sizeof *e);
@@ -602,13 +736,14 @@ orc_env *orc_env_create(const orc_game *games, int n_games, const uint16_t *game
 }
 
 int orc_env_reset(orc_env *e, const uint8_t *mask, uint8_t *obs) {
-  size_t per = (size_t)e->stack_frames * 2048u;
+  const size_t fb = orc_frame_bytes(e->games[0].variant);
+  size_t per = (size_t)e->stack_frames * fb;
   for (int64_t i = 0; i < e->n; i++) {
     if (mask && !mask[i]) continue;
     orc_inst *m = &e->inst[i];
     orc_inst_reset(m, &e->games[m->game], e->quirks);
     if (obs)
-      for (int s = 0; s < e->stack_frames; s++) write_frame(m, obs + per * (size_t)i + (size_t)s * 2048u);
+      for (int s = 0; s < e->stack_frames; s++) write_frame(m, obs + per * (size_t)i + (size_t)s * fb);
   }
   return 0;
 }
@@ -625,7 +760,7 @@ typedef struct {
 static void *step_range(void *arg) {
   step_job *j = (step_job *)arg;
   orc_env *e = j->e;
-  size_t per = (size_t)e->stack_frames * 2048u;
+  size_t per = (size_t)e->stack_frames * orc_frame_bytes(e->games[0].variant);
   for (int64_t i = j->lo; i < j->hi; i++) {
     orc_inst *m = &e->inst[i];
     float r;
@@ -686,7 +821,7 @@ void orc_env_destroy(orc_env *e) {
 
 int orc_env_rollout(orc_env *e, int n_steps, const uint8_t *actions, uint8_t *obs, float *reward,
                     uint8_t *done, uint64_t *hashes, int n_threads) {
-  size_t per = (size_t)e->stack_frames * 2048u;
+  size_t per = (size_t)e->stack_frames * orc_frame_bytes(e->games[0].variant);
   for (int s = 0; s < n_steps; s++) {
     orc_env_step(e, actions + (size_t)s * (size_t)e->n, obs ? obs + (size_t)s * (size_t)e->n * per : NULL,
                  reward ? reward + (size_t)s * (size_t)e->n : NULL, done ? done + (size_t)s * (size_t)e->n : NULL,

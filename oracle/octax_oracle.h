@@ -21,8 +21,14 @@
  * semantics here are the classic CHIP-8 definition. Every point the paper leaves
  * open is marked READING in octax_oracle.c.
  *
+ * §5 (future work) names the Super-CHIP8 extension: a 128x64 display and the
+ * instruction set extended for HP48 calculators. The paper defines neither, so
+ * the SCHIP variant here follows the published Super-CHIP 1.1 instruction
+ * list; every point where interpreters differ is marked READING.
+ *
  * Parity unpinned: the 4x5 font glyph bytes (the paper fixes only their address
- * range 0x050-0x09F, App. B "Font System").
+ * range 0x050-0x09F, App. B "Font System") and the 8x10 SCHIP glyphs (not in
+ * the paper at all).
  */
 #ifndef OCTAX_ORACLE_H
 #define OCTAX_ORACLE_H
@@ -78,10 +84,13 @@ typedef struct {
                                  a uniform 32-bit draw is below this; 0 = off */
   uint32_t max_noops;         /* no-op reset: 0..max_noops no-key steps after
                                  the startup instructions; 0 = off */
+  uint32_t variant;           /* ORC_CHIP8 or ORC_SCHIP; one per environment */
 } orc_game;
 
+enum { ORC_CHIP8 = 0, ORC_SCHIP = 1 };
+
 /* ---- status bits (sticky since creation) --------------------------------- */
-enum { ORC_ST_BAD_OP = 1, ORC_ST_STACK_FAULT = 2, ORC_ST_BAD_ACTION = 4 };
+enum { ORC_ST_BAD_OP = 1, ORC_ST_STACK_FAULT = 2, ORC_ST_BAD_ACTION = 4, ORC_ST_EXIT = 8 };
 
 /* ---- one emulator instance ----------------------------------------------- */
 typedef struct {
@@ -92,7 +101,8 @@ typedef struct {
   uint8_t DT, ST;
   uint8_t status;
   uint16_t stack[16];
-  uint8_t pix[32][64]; /* one byte per pixel, 0 or 1, [y][x] */
+  uint8_t pix[64][128]; /* one byte per pixel, 0 or 1, [y][x]; CHIP-8 uses
+                           rows 0-31, columns 0-63 */
   uint8_t ram[4096];
   uint32_t episode_steps;
   uint32_t env_steps;
@@ -103,6 +113,9 @@ typedef struct {
   uint32_t draws;      /* CXNN draws so far in this step / startup */
   int32_t game;        /* index of this instance's game */
   uint8_t last_action; /* action index applied at the previous step (sticky) */
+  uint8_t variant;     /* ORC_CHIP8 / ORC_SCHIP (copied from the game at reset) */
+  uint8_t hires;       /* SCHIP: 1 = 128x64 mode, 0 = 64x32 mode (2x2 pixels) */
+  uint8_t rpl[16];     /* SCHIP FX75/FX85 flag registers */
 } orc_inst;
 
 /* Canonical state record: the unit of comparison between implementations. */
@@ -111,12 +124,18 @@ typedef struct {
   uint16_t I, PC;
   uint8_t SP, DT, ST, status;
   uint16_t stack[16];
-  uint64_t display[32]; /* bit x of word y = pixel (x, y) */
+  uint64_t display[64][2]; /* bit (x mod 64) of display[y][x / 64] = pixel (x, y);
+                              CHIP-8 fills rows 0-31, word 0 */
   uint8_t ram[4096];
   uint32_t episode_steps, env_steps;
   uint8_t last_action;
-  uint8_t pad[7];
-} orc_record;           /* 4424 bytes; the hash covers the first 4417 */
+  uint8_t hires;
+  uint8_t pad[6];
+  uint8_t rpl[16];
+} orc_record;           /* 5208 bytes */
+
+/* Bytes of one observation frame: 32*64 (CHIP-8) or 64*128 (SCHIP). */
+size_t orc_frame_bytes(uint32_t variant);
 
 /* Philox4x32-10 (Salmon et al., SC'11): out = bijection(counter; key). */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

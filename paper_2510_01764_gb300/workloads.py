@@ -61,6 +61,7 @@ class GameSpec:
     startup_instrs: int = 0
     sticky_prob: float = 0.0    # sticky actions: repeat the previous action w.p. this
     max_noops: int = 0          # no-op reset: 0..max_noops no-key steps per reset
+    variant: str = "chip8"      # "chip8" (64x32 screen) or "schip" (128x64 buffer, Super-CHIP)
     name: str = ""
 
     @property

@@ -616,7 +616,20 @@ def test_state_hash_is_fnv_of_record(oracle_lib):
     recs = e.records()
     hs = e.hashes()
     for i in range(4):
-        assert oracle_lib.fnv1a64(recs[i].tobytes()[:4417]) == int(hs[i])  # padding excluded
+        assert oracle_lib.fnv1a64(canonical_bytes(recs[i], "chip8")) == int(hs[i])
+
+
+def canonical_bytes(r, variant: str) -> bytes:
+    """The hashed serialisation of a record, field by field, little-endian:
+    CHIP-8 hashes display rows 0-31 (word 0); SCHIP all 64 x 2 words, then
+    hires and the 16 flag bytes after last_action."""
+    head = (r["V"].tobytes() + r["I"].tobytes() + r["PC"].tobytes() +
+            bytes([r["SP"], r["DT"], r["ST"], r["status"]]) + r["stack"].tobytes())
+    disp = r["display"].tobytes() if variant == "schip" else r["display"][:32, 0].tobytes()
+    tail = r["episode_steps"].tobytes() + r["env_steps"].tobytes() + bytes([r["last_action"]])
+    if variant == "schip":
+        tail += bytes([r["hires"]]) + r["rpl"].tobytes()
+    return head + disp + r["ram"].tobytes() + tail
 
 
 # ---------------------------------------------------------------- wrappers (§3.2)
