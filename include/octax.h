@@ -8,7 +8,10 @@
  * into a 64x32 1-bit display (App. B "Sprite Drawing"), 60 Hz delay/sound
  * timers, K instructions per frame with frame skip and a stacked observation
  * (§3.2 "Environment integration", §4.2), and reward/termination read from
- * game registers or memory with automatic reset (§3.3).
+ * game registers or memory with automatic reset (§3.3). Games may instead be
+ * Super-CHIP programs, the 128x64 extension named in §5 (OCTAX_VARIANT_SCHIP,
+ * one variant per environment): lores/hires modes, 16x16 sprites, scrolls,
+ * 8x10 glyphs and flag registers, with uint8 [S][64][128] observations.
  *
  * Conventions (every entry point):
  *  - Plain pointers and sizes only. "_dev" pointers are CUDA device memory
@@ -55,6 +58,17 @@ extern "C" {
 #define OCTAX_STATUS_BAD_OP 0x01u      /* an undefined opcode was executed (no-op) */
 #define OCTAX_STATUS_STACK_FAULT 0x02u /* CALL on a full / RET on an empty stack   */
 #define OCTAX_STATUS_BAD_ACTION 0x04u  /* action index > n_actions (no key held)   */
+#define OCTAX_STATUS_EXIT 0x08u        /* SCHIP 00FD executed (the program halts)  */
+
+/* ---- instruction-set variant (octax_game.variant) --------------------------- */
+#define OCTAX_VARIANT_CHIP8 0u /* 64x32 display, observation frames of 32 x 64 bytes       */
+#define OCTAX_VARIANT_SCHIP 1u /* 128x64 buffer (lores: 64x32 grid of 2x2 blocks), frames of
+                                  64 x 128 bytes; adds 00CN 00FB 00FC 00FD 00FE 00FF, DXY0
+                                  (16x16), FX30 (8x10 glyphs at 0x0A0), FX75 / FX85 (16
+                                  flag bytes, cleared at reset). Every episode starts in
+                                  lores; scroll distances count pixels of the current
+                                  mode; mode switches keep the buffer; 00FD re-executes
+                                  itself and sets OCTAX_STATUS_EXIT; VF = any collision. */
 
 /* ---- reward / termination descriptor (§3.3 score_fn / terminated_fn) ----- */
 enum { OCTAX_SRC_REG = 0, OCTAX_SRC_MEM = 1 };
@@ -95,7 +109,9 @@ typedef struct {
   uint8_t action_set[16];    /* action index -> CHIP-8 key (0..15)                    */
   uint8_t n_score_terms;     /* 0..4: score = sum of terms                            */
   uint8_t n_term_clauses;    /* 0..4: terminated = OR of clauses (0 = never)          */
-  uint8_t pad[2];
+  uint8_t variant;           /* OCTAX_VARIANT_*; the same for all games of one
+                                environment (or server)                              */
+  uint8_t pad;
   octax_term score[4];
   octax_clause term[4];
   uint32_t max_episode_steps; /* truncation after this many steps; 0 = none           */
@@ -122,19 +138,27 @@ typedef struct {
   uint8_t SP;                /* occupied call-stack entries, 0..16 */
   uint8_t DT, ST, status;
   uint16_t stack[16];
-  uint64_t display[32];      /* bit x of word y = pixel (x, y) */
+  uint64_t display[64][2];   /* bit (x mod 64) of display[y][x / 64] = pixel (x, y);
+                                CHIP-8 uses rows 0-31, word 0 (other words are 0) */
   uint8_t ram[4096];
   uint32_t episode_steps;    /* steps since the last reset */
   uint32_t env_steps;        /* steps since creation (random-number counter) */
   uint8_t last_action;       /* action index applied at the previous step (sticky
                                 actions); n_actions after a reset */
-  uint8_t pad[7];
-} octax_state_record;        /* 4424 bytes; octax_state_hash covers the first 4417 */
+  uint8_t hires;             /* SCHIP: 1 in 128x64 mode */
+  uint8_t pad[6];
+  uint8_t rpl[16];           /* SCHIP flag registers (FX75 / FX85) */
+} octax_state_record;        /* 5208 bytes. octax_state_hash is FNV-1a 64 over, in
+                                order and little-endian: V, I, PC, SP, DT, ST, status,
+                                stack, the display (CHIP-8: display[0..31][0]; SCHIP:
+                                all [64][2] row-major), ram, episode_steps, env_steps,
+                                last_action, and for SCHIP hires and rpl            */
 
 /* Launch configuration (chosen by octax_autotune or set by hand). A CTA of
  * `block` emulator threads runs block/32 * inst_per_warp instances of one
  * game; with writer_warps > 0 it also has that many warps that only write
- * observations (block/32 * inst_per_warp / writer_warps must be 8, 16 or 32). */
+ * observations (block/32 * inst_per_warp / writer_warps must be 8, 16 or 32;
+ * CHIP-8 environments only). */
 typedef struct {
   int32_t block;             /* emulator threads per CTA: 32, 64, 128 or 256    */
   int32_t inst_per_warp;     /* instances emulated per warp: 1..32                */
@@ -162,12 +186,13 @@ int octax_create(const octax_game *games, int n_games, const uint16_t *game_of_e
 
 /* Reset the instances with mask_dev[i] != 0 (mask_dev NULL = all) and write
  * their observation (the reset display in every stack slot) to
- * obs_dev[i][stack_frames][32][64] (uint8 0/1; NULL = no write). */
+ * obs_dev[i][stack_frames][H][W] (uint8 0/1; NULL = no write). H x W is 32 x 64
+ * for CHIP-8 and 64 x 128 for SCHIP environments. */
 int octax_reset(octax_env *env, const uint8_t *mask_dev, uint8_t *obs_dev);
 
 /* One environment step for every instance (§3.2, §4.2).
  * actions_dev: uint8 [n_envs], index into the game's action_set.
- * obs_dev: uint8 [n_envs][stack_frames][32][64], the last stack_frames frames
+ * obs_dev: uint8 [n_envs][stack_frames][H][W], the last stack_frames frames
  *   of the step, oldest first; for a done instance the reset display.
  * reward_dev: float32 [n_envs], score after minus score before the step.
  * done_dev: uint8 [n_envs], terminated or truncated; done instances are reset. */
@@ -176,7 +201,7 @@ int octax_step(octax_env *env, const uint8_t *actions_dev, uint8_t *obs_dev,
 
 /* n_steps steps in as few launches as the launch configuration allows
  * (steps_per_launch per launch, CUDA-graph replay, persistent scheduling).
- * actions_dev [n_steps][n_envs]; obs_dev [n_steps][n_envs][S][32][64];
+ * actions_dev [n_steps][n_envs]; obs_dev [n_steps][n_envs][S][H][W];
  * reward_dev, done_dev [n_steps][n_envs]. Same results as n_steps octax_step. */
 int octax_step_n(octax_env *env, int n_steps, const uint8_t *actions_dev, uint8_t *obs_dev,
                  float *reward_dev, uint8_t *done_dev);
@@ -219,6 +244,8 @@ int octax_autotune(octax_env *env, int n_steps, const uint8_t *actions_dev, floa
 
 int64_t octax_num_envs(const octax_env *env);
 int octax_stack_frames(const octax_env *env);
+/* OCTAX_VARIANT_CHIP8 or OCTAX_VARIANT_SCHIP. */
+int octax_variant(const octax_env *env);
 /* Device bytes owned by the environment. */
 size_t octax_device_bytes(const octax_env *env);
 void octax_destroy(octax_env *env);
@@ -252,7 +279,7 @@ typedef struct {
   uint32_t pad2;
   uint64_t seed;               /* Philox key of this request's instances     */
   const uint8_t *actions_host; /* [n_steps][n_envs] action indices, copied    */
-  uint8_t *obs_dev;            /* [n_steps][n_envs][S][32][64], 16-byte aligned */
+  uint8_t *obs_dev;            /* [n_steps][n_envs][S][H][W], 16-byte aligned */
   float *reward_dev;           /* [n_steps][n_envs]                           */
   uint8_t *done_dev;           /* [n_steps][n_envs]                           */
 } octax_request;               /* the caller keeps the device buffers alive until done */
@@ -301,7 +328,8 @@ void octax_server_destroy(octax_server *s);
  * [n_steps][n_envs][stack_frames][32][64] (16-byte aligned); reward_dev and
  * done_dev [n_steps][n_envs]. Asynchronous on cuda_stream (NULL = legacy
  * default stream).
- * Limits: 1 <= n_envs <= 1024 (EINVAL beyond); every device that loads the
+ * Limits: 1 <= n_envs <= 1024 (EINVAL beyond); CHIP-8 games only (EINVAL
+ * for OCTAX_VARIANT_SCHIP); every device that loads the
  * library holds the array (about 4.6 MB) until the process exits.
  * The first call on a device looks up the array's device address, so make it
  * before any stream capture. Every call reuses the same array: calls whose

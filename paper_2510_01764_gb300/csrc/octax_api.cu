@@ -64,6 +64,7 @@ struct octax_env {
   int64_t n = 0;
   int n_games = 0;
   int S = 4;
+  int schip = 0;  // OCTAX_VARIANT_SCHIP environment
   uint32_t quirks = 0;
   uint64_t seed = 0;
   std::vector<GameDev> games_h;
@@ -101,7 +102,7 @@ cudaError_t dalloc(octax_env *e, T **p, size_t count) {
   return cudaSuccess;
 }
 
-int validate_game(const octax_game &g, int S) {
+int validate_game(const octax_game &g, int S, int variant) {
   char buf[160];
   if (!g.rom || g.rom_len < 1 || g.rom_len > 3584) {
     set_error("game rom must be 1..3584 bytes");
@@ -113,6 +114,10 @@ int validate_game(const octax_game &g, int S) {
   }
   if (g.stack_frames != S) {
     set_error("all games of one environment need the same stack_frames");
+    return OCTAX_EINVAL;
+  }
+  if (g.variant > OCTAX_VARIANT_SCHIP || g.variant != variant) {
+    set_error("variant must be OCTAX_VARIANT_CHIP8 or OCTAX_VARIANT_SCHIP, the same for all games");
     return OCTAX_EINVAL;
   }
   if (g.max_noops > 255u) {
@@ -159,6 +164,7 @@ GameDev to_dev(const octax_game &g) {
   d.startup = g.startup_instrs;
   d.sticky = g.sticky_threshold;
   d.max_noops = g.max_noops;
+  d.variant = g.variant;
   memcpy(d.action_set, g.action_set, 16);
   for (int i = 0; i < 4; ++i) {
     d.score[i] = TermDev{g.score[i].src, g.score[i].xform, g.score[i].idx, g.score[i].arg};
@@ -177,10 +183,10 @@ int per_cta(const octax_launch &c) { return c.block / 32 * c.inst_per_warp; }
 int wave_of(const octax_env *e, const octax_launch &c) {
   if (!c.balance) return 0;
   return max_resident_ctas(c.block, c.inst_per_warp, c.writer_warps,
-                           uses_wrappers(e->games_h.data(), e->games_h.size()));
+                           uses_wrappers(e->games_h.data(), e->games_h.size()), e->schip);
 }
 
-const char *launch_problem(const octax_launch &c) {
+const char *launch_problem(const octax_launch &c, int schip) {
   if (!block_ok(c.block) || !ipw_ok(c.inst_per_warp)) return "block in {32,64,128,256}, inst_per_warp in {1,...,32}";
   if (c.steps_per_launch < 1 || c.steps_per_launch > 64) return "steps_per_launch 1..64";
   if ((c.persistent != 0 && c.persistent != 1) || (c.use_graph != 0 && c.use_graph != 1) ||
@@ -191,9 +197,12 @@ const char *launch_problem(const octax_launch &c) {
     if (!(W == 1 || W == 2 || W == 4 || W == 8)) return "writer_warps in {0,1,2,4,8}";
     if (J % W != 0 || !(J / W == 8 || J / W == 16 || J / W == 32))
       return "block/32*inst_per_warp/writer_warps must be 8, 16 or 32";
+    if (schip) return "writer warps serve CHIP-8 environments only";
     if (step_ws_smem_bytes(c.block, c.inst_per_warp) > max_dynamic_smem())
       return "too many instances per CTA for the writer ring";
   }
+  if (step_smem_bytes(c.block, c.inst_per_warp, schip) > max_dynamic_smem())
+    return "too many instances per CTA for shared memory";
   return nullptr;
 }
 
@@ -203,15 +212,26 @@ const char *launch_problem(const octax_launch &c) {
 int octax::build_games(const octax_game *games, int n_games, std::vector<GameDev> &dev,
                        std::vector<uint8_t> &images) {
   for (int g = 0; g < n_games; ++g) {
-    int rc = validate_game(games[g], games[0].stack_frames);
+    int rc = validate_game(games[g], games[0].stack_frames, games[0].variant);
     if (rc) return rc;
   }
   dev.clear();
   images.assign((size_t)n_games * kRamBytes, 0);
   for (int g = 0; g < n_games; ++g) {
     dev.push_back(to_dev(games[g]));
-    memcpy(&images[(size_t)g * kRamBytes + 0x50], kFont, sizeof kFont);
-    memcpy(&images[(size_t)g * kRamBytes + 0x200], games[g].rom, games[g].rom_len);
+    uint8_t *img = &images[(size_t)g * kRamBytes];
+    memcpy(img + 0x50, kFont, sizeof kFont);
+    if (games[g].variant == OCTAX_VARIANT_SCHIP)
+      // 8x10 glyphs: glyph pixel (c, r) of the 4x5 font drawn as the 2x2 block
+      // at columns 2c, 2c+1 of rows 2r, 2r+1 (MSB = leftmost pixel).
+      for (int d = 0; d < 16; ++d)
+        for (int r = 0; r < 10; ++r) {
+          uint8_t out = 0;
+          for (int c = 0; c < 4; ++c)
+            if (kFont[5 * d + r / 2] & (0x80 >> c)) out |= (uint8_t)(0xC0 >> (2 * c));
+          img[kBigFontAddr + 10 * d + r] = out;
+        }
+    memcpy(img + 0x200, games[g].rom, games[g].rom_len);
   }
   return OCTAX_OK;
 }
@@ -323,7 +343,8 @@ int enqueue_steps(octax_env *e, const octax_launch &cfg, int n_steps, const IO &
   const int grid =
       cfg.persistent
           ? std::min(gt->count, std::max(1, max_resident_ctas(cfg.block, cfg.inst_per_warp, cfg.writer_warps,
-                                                      uses_wrappers(e->games_h.data(), e->games_h.size()))))
+                                                      uses_wrappers(e->games_h.data(), e->games_h.size()),
+                                                      e->schip)))
           : gt->count;
   if (cfg.persistent) {
     rc = ensure_counters(e, launches);
@@ -441,6 +462,7 @@ int octax_create(const octax_game *games, int n_games, const uint16_t *game_of_e
   e->n = n_envs;
   e->n_games = n_games;
   e->S = games[0].stack_frames;
+  e->schip = games[0].variant == OCTAX_VARIANT_SCHIP;
   e->quirks = quirks;
   e->seed = seed;
   if (cuda_stream) {
@@ -481,7 +503,7 @@ int octax_create(const octax_game *games, int n_games, const uint16_t *game_of_e
   ALLOC(st.pcI, n);
   ALLOC(st.misc, n);
   ALLOC(st.stack, 16 * n);
-  ALLOC(st.disp, 32 * n);
+  ALLOC(st.disp, (size_t)disp_words(e->schip) * n);
   ALLOC(st.dirty, n);
   ALLOC(st.ram, n * kRamBytes);
   ALLOC(st.ep, n);
@@ -492,6 +514,9 @@ int octax_create(const octax_game *games, int n_games, const uint16_t *game_of_e
   ALLOC(st.out_row, n);
   ALLOC(st.game, n);
   ALLOC(st.last_act, n);
+  ALLOC(st.mode, n);
+  ALLOC(st.rpl, 16 * n);
+  st.schip = e->schip;
   ALLOC(e->slot_of_row_d, n);
   ALLOC(e->io_d, 1);
   ALLOC(e->err_d, 1);
@@ -628,7 +653,7 @@ int octax_step_host(octax_env *e, const uint8_t *actions_host, uint8_t *obs_host
     cudaError_t r = cudaStreamSynchronize(e->stream);
     return r == cudaSuccess ? OCTAX_OK : cuda_fail(r, "octax_step_host");
   }
-  const size_t n = (size_t)e->n, obs_bytes = n * (size_t)e->S * kFrameBytes;
+  const size_t n = (size_t)e->n, obs_bytes = n * (size_t)e->S * frame_bytes(e->schip);
   if (!e->hs_act) {
     cudaError_t r = dalloc(e, &e->hs_act, n);
     if (r == cudaSuccess) r = dalloc(e, &e->hs_obs, obs_bytes);
@@ -742,7 +767,7 @@ int octax_set_launch(octax_env *e, const octax_launch *cfg) {
     set_error("octax_set_launch: null argument");
     return OCTAX_EINVAL;
   }
-  if (const char *why = launch_problem(*cfg)) {
+  if (const char *why = launch_problem(*cfg, e->schip)) {
     set_error(std::string("octax_set_launch: ") + why);
     return OCTAX_EINVAL;
   }
@@ -763,14 +788,14 @@ int octax_autotune(octax_env *e, int n_steps, const uint8_t *actions_dev, float 
     size_t bytes;
   };
   const Piece pieces[] = {{st.v, 16 * n},     {st.pcI, 4 * n},    {st.misc, 4 * n},
-                          {st.stack, 32 * n}, {st.disp, 256 * n}, {st.dirty, 8 * n},
+                          {st.stack, 32 * n}, {st.disp, 8 * (size_t)disp_words(e->schip) * n}, {st.dirty, 8 * n},
                           {st.ram, 4096 * n}, {st.ep, 4 * n},     {st.env_steps, 4 * n},
-                          {st.prev_score, 4 * n}, {st.last_act, n}};
+                          {st.prev_score, 4 * n}, {st.last_act, n}, {st.mode, n}, {st.rpl, 16 * n}};
   size_t total = 0;
   for (const Piece &pc : pieces) total += pc.bytes;
   uint8_t *backup = nullptr, *acts = nullptr, *obs = nullptr, *done = nullptr;
   float *rew = nullptr;
-  const size_t obs_bytes = (size_t)n_steps * n * e->S * kFrameBytes;
+  const size_t obs_bytes = (size_t)n_steps * n * e->S * frame_bytes(e->schip);
   cudaError_t r = cudaMalloc(&backup, total);
   if (r == cudaSuccess) r = cudaMalloc(&acts, (size_t)n_steps * n);
   if (r == cudaSuccess) r = cudaMalloc(&obs, obs_bytes);
@@ -814,7 +839,7 @@ int octax_autotune(octax_env *e, int n_steps, const uint8_t *actions_dev, float 
   float best_ms = 1e30f;
   int rc = OCTAX_OK;
   auto trial = [&](const octax_launch &c) {
-    if (rc != OCTAX_OK || launch_problem(c) || c.steps_per_launch > n_steps) return;
+    if (rc != OCTAX_OK || launch_problem(c, e->schip) || c.steps_per_launch > n_steps) return;
     e->cfg = c;
     rc = enqueue_steps(e, c, n_steps, io);  // warm-up (graph build)
     float ms_min = 1e30f;
@@ -868,6 +893,9 @@ int octax_autotune(octax_env *e, int n_steps, const uint8_t *actions_dev, float 
 
 int64_t octax_num_envs(const octax_env *e) { return e ? e->n : -1; }
 int octax_stack_frames(const octax_env *e) { return e ? e->S : -1; }
+int octax_variant(const octax_env *e) {
+  return e ? (e->schip ? (int)OCTAX_VARIANT_SCHIP : (int)OCTAX_VARIANT_CHIP8) : -1;
+}
 size_t octax_device_bytes(const octax_env *e) { return e ? e->bytes : 0; }
 
 void octax_destroy(octax_env *e) { free_env(e); }

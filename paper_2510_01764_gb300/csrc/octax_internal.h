@@ -13,7 +13,14 @@ namespace octax {
 
 constexpr int kRamBytes = 4096;
 constexpr int kPageShift = 6;               // 64-byte RAM pages: 64 pages -> one u64 mask
-constexpr int kFrameBytes = 32 * 64;        // one uint8 observation frame
+constexpr int kFrameBytes = 32 * 64;        // one uint8 CHIP-8 observation frame
+constexpr int kSchipFrameBytes = 64 * 128;  // one uint8 SCHIP observation frame (the 128x64 buffer)
+constexpr uint32_t kBigFontAddr = 0x0A0;    // SCHIP 8x10 glyphs, 10 bytes each
+// Packed display words (u64) per instance: 32 rows x 1 (CHIP-8), 64 rows x 2 (SCHIP).
+constexpr int kDispWords = 32;
+constexpr int kSchipDispWords = 128;
+__host__ __device__ inline int frame_bytes(int schip) { return schip ? kSchipFrameBytes : kFrameBytes; }
+__host__ __device__ inline int disp_words(int schip) { return schip ? kSchipDispWords : kDispWords; }
 constexpr int kMaxBlock = 256;
 
 // Game descriptor as the kernels read it (one per game, device memory).
@@ -29,7 +36,7 @@ struct ClauseDev {
 };
 struct alignas(16) GameDev {
   uint32_t K, frameskip, n_actions, n_score, n_term, max_steps, startup, sticky;
-  uint32_t max_noops, pad[3];
+  uint32_t max_noops, variant, pad[2];
   uint8_t action_set[16];
   TermDev score[4];
   ClauseDev term[4];
@@ -46,7 +53,8 @@ struct DevState {
   uint32_t *pcI;          // [n]      PC | I << 16
   uint32_t *misc;         // [n]      SP | DT << 8 | ST << 16 | status << 24
   uint16_t *stack;        // [16][n]
-  uint64_t *disp;         // [32][n]  bit x of word y = pixel (x, y)
+  uint64_t *disp;         // [W][n]   CHIP-8 (W = 32): bit x of word y = pixel (x, y);
+                          //          SCHIP (W = 128): bit x of word 2y + h = pixel (64h + x, y)
   uint64_t *dirty;        // [n]      RAM pages that differ from the ROM image
   uint8_t *ram;           // [n][4096] per-instance RAM (valid on dirty pages only)
   uint32_t *ep;           // [n]      steps since reset
@@ -57,12 +65,15 @@ struct DevState {
   uint32_t *out_row;      // [n]      row of this slot in its request's outputs
   uint16_t *game;         // [n]
   uint8_t *last_act;      // [n]      action index applied at the previous step
+  uint8_t *mode;          // [n]      SCHIP: 1 = hires
+  uint8_t *rpl;           // [n][16]  SCHIP flag registers
+  int schip;              // 1: SCHIP layout (disp has 128 words per slot)
 };
 
 // Every per-slot array is set (checked on the host before each launch).
 inline bool state_complete(const DevState &s) {
   return s.n > 0 && s.v && s.pcI && s.misc && s.stack && s.disp && s.dirty && s.ram && s.ep && s.env_steps &&
-         s.prev_score && s.key && s.uid && s.out_row && s.game && s.last_act;
+         s.prev_score && s.key && s.uid && s.out_row && s.game && s.last_act && s.mode && s.rpl;
 }
 
 // A group: up to block/32*ipw consecutive slots that share one game (one CTA's work).
@@ -77,7 +88,7 @@ struct Group {
 // Where one request's per-step inputs and outputs live.
 struct IO {
   const uint8_t *actions;  // [steps][rows]
-  uint8_t *obs;            // [steps][rows][S][32][64]
+  uint8_t *obs;            // [steps][rows][S][H][W]
   float *reward;           // [steps][rows]
   uint8_t *done;           // [steps][rows]
   int64_t rows;            // rows per step
@@ -120,7 +131,7 @@ struct ResetLaunch {
   int set_rows;            // init: out_row = group.row0 + lane, game = group.game
 };
 
-size_t step_smem_bytes(int block, int ipw);
+size_t step_smem_bytes(int block, int ipw, int schip);
 // Warp-specialised kernel: `block` emulator threads plus 32 * writers writer threads.
 size_t step_ws_smem_bytes(int block, int ipw);
 size_t max_dynamic_smem();
@@ -133,7 +144,7 @@ cudaError_t launch_records(const DevState &st, const uint8_t *images, const uint
 cudaError_t launch_set_records(const DevState &st, const GameDev *games, const uint8_t *images,
                                const uint32_t *slot_of_row, int64_t first, int64_t count,
                                const octax_state_record *in, cudaStream_t s);
-int max_resident_ctas(int block, int ipw, int writers, int wrappers);
+int max_resident_ctas(int block, int ipw, int writers, int wrappers, int schip);
 // True when a game enables the sticky-action or no-op-reset wrapper.
 inline int uses_wrappers(const GameDev *games, size_t n) {
   for (size_t i = 0; i < n; ++i)
@@ -141,8 +152,11 @@ inline int uses_wrappers(const GameDev *games, size_t n) {
   return 0;
 }
 // Bytes of device state per slot (all DevState arrays).
-constexpr size_t kSlotStateBytes = 16 + 4 + 4 + 32 + 256 + 8 + 4096 + 4 + 4 + 4 + 8 + 4 + 4 + 2 + 1;
-cudaError_t alloc_state(DevState &st, int64_t n, void **block_out, size_t *bytes_out);
+constexpr size_t kSlotStateBytes = 16 + 4 + 4 + 32 + 256 + 8 + 4096 + 4 + 4 + 4 + 8 + 4 + 4 + 2 + 1 + 1 + 16;
+inline size_t slot_state_bytes(int schip) {
+  return kSlotStateBytes + (schip ? 8 * (kSchipDispWords - kDispWords) : 0);
+}
+cudaError_t alloc_state(DevState &st, int64_t n, int schip, void **block_out, size_t *bytes_out);
 // Append one step launch to a graph (after `dep`, if non-null).
 cudaError_t add_step_node(cudaGraph_t g, cudaGraphNode_t *node, cudaGraphNode_t dep, const StepLaunch &p,
                           int grid, int block);

@@ -25,6 +25,7 @@
 //    instruction writes eight complete 64-byte image rows.
 // Each instance runs exactly K instructions per frame, so all lanes of a warp
 // meet at every frame boundary.
+#include <algorithm>
 #include <cstring>
 
 #include "octax_internal.h"
@@ -47,6 +48,7 @@ struct Regs {
   uint32_t draws, phase, env_steps;
   uint32_t key0, key1, uid;
   uint32_t last_act;  // action index applied at the previous step (sticky actions)
+  uint32_t hires;     // SCHIP: 1 in 128x64 mode
 };
 
 struct Ctx {
@@ -56,6 +58,14 @@ struct Ctx {
   uint8_t *ram;        // global: this instance's 4 KB RAM (dirty pages)
   int J;
   const uint32_t *uops;  // shared: decoded opcode at every even image address (make_uop)
+  uint8_t *rpl;          // global: this instance's 16 SCHIP flag bytes
+};
+
+// Packed display words per instance and bytes per observation frame.
+template <bool kS>
+struct Disp {
+  static constexpr int kWords = kS ? kSchipDispWords : kDispWords;
+  static constexpr int kFrame = kS ? kSchipFrameBytes : kFrameBytes;
 };
 
 __device__ __forceinline__ uint32_t getV(const Ctx &C, uint32_t x) { return C.V[x * C.J]; }
@@ -154,6 +164,74 @@ __device__ __forceinline__ void draw(Regs &R, const Ctx &C, uint32_t vx, uint32_
   setVF(C, coll);
 }
 
+// Each of the low 16 bits of v doubled (bit j -> bits 2j and 2j + 1).
+__device__ __forceinline__ uint32_t double_bits(uint32_t v) {
+  v = (v | (v << 8)) & 0x00FF00FFu;
+  v = (v | (v << 4)) & 0x0F0F0F0Fu;
+  v = (v | (v << 2)) & 0x33333333u;
+  v = (v | (v << 1)) & 0x55555555u;
+  return v | (v << 1);
+}
+
+// SCHIP DXYN / DXY0 on the 128x64 buffer (word 2y + h of an instance holds
+// pixels 64h..64h+63 of row y, bit x = pixel 64h + x). In hires mode sprite
+// pixels are buffer pixels; in lores mode the grid is 64x32 and each sprite
+// pixel covers a 2x2 block. N = 0: 16x16 sprite, two bytes per row. VF = any
+// lit buffer pixel turned off. Clipping (or the wrap quirk) on the grid.
+__device__ __forceinline__ void draw_schip(Regs &R, const Ctx &C, uint32_t vx, uint32_t vy, uint32_t n,
+                                           uint32_t quirks) {
+  const bool wrap = quirks & OCTAX_QUIRK_WRAP_SPRITES;
+  const uint32_t unit = R.hires ? 1u : 2u;               // buffer pixels per grid pixel
+  const uint32_t gw = 128u / unit, gh = 64u / unit;      // grid
+  const uint32_t x0 = vx & (gw - 1u), y0 = vy & (gh - 1u);
+  const uint32_t rows = n ? n : 16u, width = n ? 8u : 16u;
+  const uint32_t bx = x0 * unit, bits_w = width * unit;  // buffer column, pattern width (<= 32)
+  uint32_t coll = 0;
+  for (uint32_t r = 0; r < rows; ++r) {
+    uint32_t gy = y0 + r;
+    if (gy >= gh) {
+      if (!wrap) break;
+      gy -= gh;
+    }
+    const uint32_t bits = n ? rd8(R, C, R.I + r) : ((rd8(R, C, R.I + 2u * r) << 8) | rd8(R, C, R.I + 2u * r + 1u));
+    const uint32_t rev = __brev(bits) >> (32u - width);   // sprite pixel j -> bit j
+    const uint64_t pat = unit == 1u ? (uint64_t)rev : (uint64_t)double_bits(rev);
+    // pat << bx as a 128-bit value (lo, hi); bits past column 127 drop
+    uint64_t lo = bx < 64u ? pat << bx : 0ull;
+    uint64_t hi = bx == 0u ? 0ull : bx < 64u ? pat >> (64u - bx) : pat << (bx - 64u);
+    if (wrap && bx + bits_w > 128u) lo |= pat >> (128u - bx);  // wrapped part re-enters at column 0
+    for (uint32_t d = 0; d < unit; ++d) {
+      uint64_t *row = C.disp + 2u * (gy * unit + d) * C.J;
+      const uint64_t o0 = row[0], o1 = row[C.J];
+      coll |= ((o0 & lo) | (o1 & hi)) != 0ull;
+      row[0] = o0 ^ lo;
+      row[C.J] = o1 ^ hi;
+    }
+  }
+  setVF(C, coll);
+}
+
+// SCHIP scrolls of the 128x64 buffer by buffer pixels; vacated pixels clear.
+__device__ __forceinline__ void scroll_down(const Ctx &C, uint32_t k) {
+  for (int y = 63; y >= 0; --y)
+    for (int h = 0; h < 2; ++h)
+      C.disp[(2 * y + h) * C.J] = (uint32_t)y >= k ? C.disp[(2 * (y - (int)k) + h) * C.J] : 0ull;
+}
+__device__ __forceinline__ void scroll_right(const Ctx &C, uint32_t c) {  // 0 < c < 64
+  for (int y = 0; y < 64; ++y) {
+    const uint64_t lo = C.disp[2 * y * C.J], hi = C.disp[(2 * y + 1) * C.J];
+    C.disp[2 * y * C.J] = lo << c;
+    C.disp[(2 * y + 1) * C.J] = (hi << c) | (lo >> (64u - c));
+  }
+}
+__device__ __forceinline__ void scroll_left(const Ctx &C, uint32_t c) {  // 0 < c < 64
+  for (int y = 0; y < 64; ++y) {
+    const uint64_t lo = C.disp[2 * y * C.J], hi = C.disp[(2 * y + 1) * C.J];
+    C.disp[2 * y * C.J] = (lo >> c) | (hi << (64u - c));
+    C.disp[(2 * y + 1) * C.J] = hi >> c;
+  }
+}
+
 // Opcodes the predicated datapath covers: classes 1 3 4 6 7 A always; 5 9
 // with N = 0; 8 with N in 0-7,E (classic shifts and logic); E with 9E/A1;
 // F with 07 0A 15 18 29, and 1E without its quirk.
@@ -208,6 +286,8 @@ __device__ __forceinline__ uint32_t make_uop(uint32_t op, uint32_t quirks) {
 
 // The rare / heavy instructions and every variant the fast datapath leaves
 // out (quirk bits, undefined encodings). PC has already been advanced.
+// kS: the SCHIP variant (128x64 buffer, extra 00xx and FXxx forms).
+template <bool kS>
 __device__ __forceinline__ void exec_slow(Regs &R, const Ctx &C, uint32_t op, uint32_t pc, int key,
                                        uint32_t quirks) {
   const uint32_t x = (op >> 8) & 15u, y = (op >> 4) & 15u, n = op & 15u, nn = op & 0xFFu;
@@ -217,7 +297,18 @@ __device__ __forceinline__ void exec_slow(Regs &R, const Ctx &C, uint32_t op, ui
     case 0x0:
       if (op == 0x00E0u) {
 #pragma unroll 8
-        for (int r = 0; r < 32; ++r) C.disp[r * C.J] = 0ull;
+        for (int r = 0; r < Disp<kS>::kWords; ++r) C.disp[r * C.J] = 0ull;
+      } else if (kS && (op & 0xFFF0u) == 0x00C0u) {  // scroll down N
+        scroll_down(C, n * (R.hires ? 1u : 2u));
+      } else if (kS && op == 0x00FBu) {  // scroll right 4
+        scroll_right(C, R.hires ? 4u : 8u);
+      } else if (kS && op == 0x00FCu) {  // scroll left 4
+        scroll_left(C, R.hires ? 4u : 8u);
+      } else if (kS && op == 0x00FDu) {  // exit: stay here
+        R.status |= OCTAX_STATUS_EXIT;
+        R.pc = pc;
+      } else if (kS && (op == 0x00FEu || op == 0x00FFu)) {  // lores / hires, buffer kept
+        R.hires = op & 1u;
       } else if (op == 0x00EEu) {
         if (R.sp == 0) {
           R.status |= OCTAX_STATUS_STACK_FAULT;
@@ -319,7 +410,8 @@ __device__ __forceinline__ void exec_slow(Regs &R, const Ctx &C, uint32_t op, ui
       break;
     }
     case 0xD:
-      draw(R, C, vx, vy, n, quirks);
+      if (kS) draw_schip(R, C, vx, vy, n, quirks);
+      else draw(R, C, vx, vy, n, quirks);
       break;
     case 0xE: {
       const bool pressed = key >= 0 && (uint32_t)key == (vx & 15u);
@@ -348,6 +440,24 @@ __device__ __forceinline__ void exec_slow(Regs &R, const Ctx &C, uint32_t op, ui
           break;
         }
         case 0x29: R.I = 0x50u + 5u * (vx & 15u); break;
+        case 0x30:
+          if (kS) R.I = kBigFontAddr + 10u * (vx & 15u);
+          else R.status |= OCTAX_STATUS_BAD_OP;
+          break;
+        case 0x75:
+          if (kS) {
+            for (uint32_t i = 0; i <= x; ++i) C.rpl[i] = (uint8_t)getV(C, i);
+          } else {
+            R.status |= OCTAX_STATUS_BAD_OP;
+          }
+          break;
+        case 0x85:
+          if (kS) {
+            for (uint32_t i = 0; i <= x; ++i) setV(C, i, C.rpl[i]);
+          } else {
+            R.status |= OCTAX_STATUS_BAD_OP;
+          }
+          break;
         case 0x33:
           wr8(R, C, R.I, vx / 100u);
           wr8(R, C, R.I + 1u, (vx / 10u) % 10u);
@@ -377,6 +487,7 @@ __device__ __forceinline__ uint32_t fetch_uop(const Regs &R, const Ctx &C, uint3
 }
 
 // Execute micro-op u, the instruction at R.pc. key: held CHIP-8 key or -1.
+template <bool kS>
 __device__ __forceinline__ void execute(Regs &R, const Ctx &C, uint32_t u, int key, uint32_t quirks) {
   const uint32_t pc = R.pc;
   if (u & kUopFast) {
@@ -419,17 +530,19 @@ __device__ __forceinline__ void execute(Regs &R, const Ctx &C, uint32_t u, int k
     R.st = (tk == 2u) ? vx : R.st;
   } else if ((u >> 12) == 0xDu) {  // DXYN, the most frequent slow opcode: its own branch
     R.pc = (pc + 2u) & 0xFFFu;
-    draw(R, C, getV(C, (u >> 8) & 15u), getV(C, (u >> 4) & 15u), u & 15u, quirks);
+    if (kS) draw_schip(R, C, getV(C, (u >> 8) & 15u), getV(C, (u >> 4) & 15u), u & 15u, quirks);
+    else draw(R, C, getV(C, (u >> 8) & 15u), getV(C, (u >> 4) & 15u), u & 15u, quirks);
   } else {
     R.pc = (pc + 2u) & 0xFFFu;
-    exec_slow(R, C, u & 0xFFFFu, pc, key, quirks);
+    exec_slow<kS>(R, C, u & 0xFFFFu, pc, key, quirks);
   }
 }
 
 // Run `count` instructions.
+template <bool kS>
 __device__ __forceinline__ void run_instrs(Regs &R, const Ctx &C, int key, uint32_t quirks,
                                            uint32_t count) {
-  for (uint32_t k = 0; k < count; ++k) execute(R, C, fetch_uop(R, C, R.pc), key, quirks);
+  for (uint32_t k = 0; k < count; ++k) execute<kS>(R, C, fetch_uop(R, C, R.pc), key, quirks);
 }
 
 __device__ __forceinline__ int32_t term_value(const Regs &R, const Ctx &C, const TermDev &t) {
@@ -474,7 +587,7 @@ __device__ __forceinline__ bool terminated(const Regs &R, const Ctx &C, const Ga
 // K), then the no-op reset wrapper (§3.2): a drawn number of no-key env steps
 // of frameskip frames each, unobserved. The previous action becomes the no-op.
 // kWrap = false compiles the wrapper out (no game of the launch uses it).
-template <bool kWrap>
+template <bool kWrap, bool kS>
 __device__ __forceinline__ void reset_instance(Regs &R, const Ctx &C, const GameDev &G, uint32_t quirks) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) C.V[i * C.J] = 0;
@@ -487,7 +600,10 @@ __device__ __forceinline__ void reset_instance(Regs &R, const Ctx &C, const Game
 #pragma unroll
   for (int i = 0; i < 16; ++i) C.stack[i * C.J] = 0;
 #pragma unroll 8
-  for (int r = 0; r < 32; ++r) C.disp[r * C.J] = 0ull;
+  for (int r = 0; r < Disp<kS>::kWords; ++r) C.disp[r * C.J] = 0ull;
+  R.hires = 0;  // SCHIP: every episode starts in lores with clear flag registers
+  if (kS)
+    for (int i = 0; i < 16; ++i) C.rpl[i] = 0;
   // Startup: full chunks of K (each followed by a tick), then the remainder
   // (no tick); after it, the no-op frames (K instructions and a tick each).
   // One loop, so that the interpreter is inlined here only once.
@@ -500,7 +616,7 @@ __device__ __forceinline__ void reset_instance(Regs &R, const Ctx &C, const Game
   R.draws = 0;
   for (uint32_t i = 0; i < chunks; ++i) {
     const bool partial = i == full && rem != 0u;
-    run_instrs(R, C, -1, quirks, partial ? rem : G.K);
+    run_instrs<kS>(R, C, -1, quirks, partial ? rem : G.K);
     if (!partial) tick(R);
   }
   R.last_act = G.n_actions;
@@ -522,8 +638,15 @@ __device__ __forceinline__ uint4 expand16(uint64_t row, uint32_t q, const uint2 
 // Whole-warp frame write: lane -> instance 8m + lane/4 of the warp, quarter
 // lane%4 of every row, for the warp's `ipw` instances. frame (per lane, 0 =
 // skip) points at the 2 KB frame of that lane's own instance.
+template <bool kS>
 __device__ __forceinline__ void capture_frame(const uint64_t *disp_warp, int J, uint8_t *frame,
-                                              int lane, int ipw, const uint2 *lut) {
+                                              int lane, int ipw, const uint2 *lut);
+
+// CHIP-8 frame (32 rows x 64 bytes): lanes 4i..4i+3 write the four 16-pixel
+// quarters of one row of instance i (8 instances per pass).
+template <>
+__device__ __forceinline__ void capture_frame<false>(const uint64_t *disp_warp, int J, uint8_t *frame,
+                                                     int lane, int ipw, const uint2 *lut) {
   const uint64_t mine = reinterpret_cast<uint64_t>(frame);
   const uint32_t q = lane & 3;
   const int passes = (ipw + 7) >> 3;
@@ -539,22 +662,46 @@ __device__ __forceinline__ void capture_frame(const uint64_t *disp_warp, int J, 
   }
 }
 
-// Whole-warp write of the reset observation (display repeated S times) for
-// every lane whose bit is set in `which`. obs: that lane's S-frame block.
+// SCHIP frame (64 rows x 128 bytes): lanes 8i..8i+7 write the eight 16-pixel
+// chunks of one row of instance i (4 instances per pass).
+template <>
+__device__ __forceinline__ void capture_frame<true>(const uint64_t *disp_warp, int J, uint8_t *frame,
+                                                    int lane, int ipw, const uint2 *lut) {
+  const uint64_t mine = reinterpret_cast<uint64_t>(frame);
+  const uint32_t q = lane & 7, h = q >> 2;
+  const int passes = (ipw + 3) >> 2;
+  for (int m = 0; m < passes; ++m) {
+    const int src = 4 * m + (lane >> 3);
+    const uint64_t base = __shfl_sync(kFull, mine, src);
+    if (base) {
+      const uint64_t *col = disp_warp + src;
+      uint8_t *dst = reinterpret_cast<uint8_t *>(base) + q * 16u;
+#pragma unroll 8
+      for (int r = 0; r < 64; ++r)
+        __stcs(reinterpret_cast<uint4 *>(dst + r * 128), expand16(col[(2 * r + h) * J], q & 3u, lut));
+    }
+  }
+}
+
+// Reset observation of the instances in `which`: the display in every stack slot.
+template <bool kS>
 __device__ __forceinline__ void write_reset_obs(const uint64_t *disp_warp, int J, uint8_t *obs, int S,
                                                 unsigned which, int lane, const uint2 *lut) {
   const uint64_t mine = reinterpret_cast<uint64_t>(obs);
+  constexpr int kChunks = Disp<kS>::kFrame / 16;  // 16-byte chunks per frame
   while (which) {
     const int src = __ffs(which) - 1;
     which &= which - 1;
     const uint64_t base = __shfl_sync(kFull, mine, src);
     const uint64_t *col = disp_warp + src;
 #pragma unroll
-    for (int it = 0; it < 4; ++it) {
-      const int c = it * 32 + lane;  // 16-byte chunk of the 2 KB frame
-      const uint4 o = expand16(col[(c >> 2) * J], c & 3, lut);
+    for (int it = 0; it < kChunks / 32; ++it) {
+      const int c = it * 32 + lane;  // 16-byte chunk of the frame
+      uint4 o;
+      if (kS) o = expand16(col[(2 * (c >> 3) + ((c >> 2) & 1)) * J], c & 3, lut);
+      else o = expand16(col[(c >> 2) * J], c & 3, lut);
       for (int s = 0; s < S; ++s)
-        __stcs(reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(base) + s * kFrameBytes + c * 16), o);
+        __stcs(reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(base) + s * Disp<kS>::kFrame + c * 16), o);
     }
   }
 }
@@ -570,7 +717,9 @@ struct Smem {
 };
 
 // Shared memory of a CTA with J instances: image | game | decoded opcodes |
-// expansion table | display [32][J] u64 | stack [16][J] u32 | V [16][J] u32.
+// expansion table | display [W][J] u64 | stack [16][J] u32 | V [16][J] u32,
+// W = 32 (CHIP-8) or 128 (SCHIP).
+template <bool kS>
 __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
   Smem s;
   s.img = smem;
@@ -578,7 +727,7 @@ __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
   s.uops = reinterpret_cast<uint32_t *>(smem + kRamBytes + kGameSmem);
   s.lut = reinterpret_cast<uint2 *>(smem + kRamBytes + kGameSmem + kUopSmem);
   s.disp = reinterpret_cast<uint64_t *>(smem + kRamBytes + kGameSmem + kUopSmem + kLutSmem);
-  s.stack = reinterpret_cast<uint32_t *>(s.disp + 32 * J);
+  s.stack = reinterpret_cast<uint32_t *>(s.disp + Disp<kS>::kWords * J);
   s.V = s.stack + 16 * J;
   return s;
 }
@@ -601,6 +750,7 @@ __device__ __forceinline__ void stage_game(const Smem &S, const GameDev *games, 
   }
 }
 
+template <bool kS>
 __device__ __forceinline__ void load_regs(Regs &R, const DevState &st, int64_t slot) {
   const uint32_t pcI = st.pcI[slot], misc = st.misc[slot];
   const int64_t n = st.n;
@@ -616,16 +766,19 @@ __device__ __forceinline__ void load_regs(Regs &R, const DevState &st, int64_t s
   R.key1 = st.key[n + slot];
   R.uid = st.uid[slot];
   R.last_act = st.last_act[slot];
+  R.hires = kS ? st.mode[slot] : 0u;
   R.draws = 0;
   R.phase = 0;
 }
 
+template <bool kS>
 __device__ __forceinline__ void store_regs(const Regs &R, const DevState &st, int64_t slot) {
   st.pcI[slot] = R.pc | (R.I << 16);
   st.misc[slot] = R.sp | (R.dt << 8) | (R.st << 16) | (R.status << 24);
   st.dirty[slot] = R.dirty;
   st.env_steps[slot] = R.env_steps;
   st.last_act[slot] = (uint8_t)R.last_act;
+  if (kS) st.mode[slot] = (uint8_t)R.hires;
 }
 
 // V0-VF: packed 4 per u32 in global memory, one per u32 in shared memory.
@@ -648,7 +801,7 @@ __device__ __forceinline__ void store_V(const Ctx &C, const DevState &st, int64_
   }
 }
 
-template <bool kWrap>
+template <bool kWrap, bool kS>
 __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
   const int t = threadIdx.x, lane = t & 31, w = t >> 5, ipw = p.ipw;
   const int J = (blockDim.x >> 5) * ipw;  // instances per CTA
@@ -664,7 +817,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
   uint64_t *disp_warp = S.disp + w * ipw;
 
   Regs R;
-  load_regs(R, st, slot);
+  load_regs<kS>(R, st, slot);
   const int64_t row = active ? (int64_t)st.out_row[slot] : 0;
   uint32_t ep = st.ep[slot];
   int32_t prev = st.prev_score[slot];
@@ -672,10 +825,10 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) S.stack[i * J + j] = st.stack[i * n + slot];
 #pragma unroll 8
-    for (int r = 0; r < 32; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
+    for (int r = 0; r < Disp<kS>::kWords; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, J, S.uops};
+              st.ram + slot * (int64_t)kRamBytes, J, S.uops, st.rpl + slot * 16};
   if (mine) load_V(C, st, slot);
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
   __syncwarp();
@@ -691,19 +844,19 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
       R.last_act = a;
       if (a < G.n_actions) key = G.action_set[a] & 15;
       else if (a > G.n_actions) R.status |= OCTAX_STATUS_BAD_ACTION;
-      my_obs = io.obs + io_row * (int64_t)p.S * kFrameBytes;
+      my_obs = io.obs + io_row * (int64_t)p.S * Disp<kS>::kFrame;
     }
     R.draws = 0;
     R.phase = 0;
     for (uint32_t f = 0; f < FS; ++f) {
       if (active) {
-        run_instrs(R, C, key, quirks, K);
+        run_instrs<kS>(R, C, key, quirks, K);
         tick(R);
       }
       if (f >= first_kept) {
         __syncwarp();
-        capture_frame(disp_warp, J, my_obs ? my_obs + (f - first_kept) * kFrameBytes : nullptr, lane, ipw,
-                      S.lut);
+        capture_frame<kS>(disp_warp, J, my_obs ? my_obs + (f - first_kept) * Disp<kS>::kFrame : nullptr, lane,
+                          ipw, S.lut);
         __syncwarp();
       }
     }
@@ -716,7 +869,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
       io.reward[io_row] = (float)(sc - prev);
       io.done[io_row] = done ? 1 : 0;
       if (done) {
-        reset_instance<kWrap>(R, C, G, quirks);
+        reset_instance<kWrap, kS>(R, C, G, quirks);
         ep = 0;
         prev = score(R, C, G);
       } else {
@@ -726,20 +879,20 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
     const unsigned which = __ballot_sync(kFull, done);
     if (which) {
       __syncwarp();
-      write_reset_obs(disp_warp, J, my_obs, p.S, which, lane, S.lut);
+      write_reset_obs<kS>(disp_warp, J, my_obs, p.S, which, lane, S.lut);
       __syncwarp();
     }
   }
 
   if (active) {
-    store_regs(R, st, slot);
+    store_regs<kS>(R, st, slot);
     store_V(C, st, slot);
     st.ep[slot] = ep;
     st.prev_score[slot] = prev;
 #pragma unroll
     for (int i = 0; i < 16; ++i) st.stack[i * n + slot] = (uint16_t)S.stack[i * J + j];
 #pragma unroll 8
-    for (int r = 0; r < 32; ++r) st.disp[r * n + slot] = S.disp[r * J + j];
+    for (int r = 0; r < Disp<kS>::kWords; ++r) st.disp[r * n + slot] = S.disp[r * J + j];
   }
 }
 
@@ -747,10 +900,10 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
 // without it the register count still admits a 256-thread CTA.
 // kWrap: the sticky-action / no-op-reset variant (its draws cost registers,
 // so games without the wrappers run the variant without them).
-template <bool kWrap>
+template <bool kWrap, bool kS>
 __global__ void step_kernel(const StepLaunch p) {
   uint8_t *const smem = g_smem;
-  const Smem S = carve(smem, (blockDim.x >> 5) * p.ipw);
+  const Smem S = carve<kS>(smem, (blockDim.x >> 5) * p.ipw);
   __shared__ int s_group;
   int cur_game = -1;
   int gi = blockIdx.x;
@@ -767,7 +920,7 @@ __global__ void step_kernel(const StepLaunch p) {
       cur_game = g.game;
     }
     __syncthreads();
-    run_group<kWrap>(p, g, S);
+    run_group<kWrap, kS>(p, g, S);
     __syncthreads();  // shared memory is reused by the next group
     if (!p.work_counter) break;
   }
@@ -827,7 +980,7 @@ struct WsSmem {
 // base layout | ring | done flags | barriers
 __device__ __forceinline__ WsSmem carve_ws(uint8_t *smem, int J) {
   WsSmem w;
-  w.base = carve(smem, J);
+  w.base = carve<false>(smem, J);
   w.ring = reinterpret_cast<uint64_t *>(w.base.V + 16 * J);
   w.done = reinterpret_cast<uint8_t *>(w.ring + 2 * 32 * J);
   w.full = reinterpret_cast<uint64_t *>(w.done + ((2 * J + 15) & ~15));
@@ -853,7 +1006,7 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
   const uint32_t quirks = p.quirks;
 
   Regs R;
-  load_regs(R, st, slot);
+  load_regs<false>(R, st, slot);
   const int64_t row = active ? (int64_t)st.out_row[slot] : 0;
   uint32_t ep = st.ep[slot];
   int32_t prev = st.prev_score[slot];
@@ -864,7 +1017,7 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
     for (int r = 0; r < 32; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, J, S.uops};
+              st.ram + slot * (int64_t)kRamBytes, J, S.uops, st.rpl + slot * 16};
   if (mine) load_V(C, st, slot);
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
 
@@ -883,7 +1036,7 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
     R.phase = 0;
     for (uint32_t f = 0; f < FS && !failed; ++f) {
       if (active) {
-        run_instrs(R, C, key, quirks, K);
+        run_instrs<false>(R, C, key, quirks, K);
         tick(R);
       }
       if (f >= first_kept) {  // hand the frame to the writers
@@ -911,7 +1064,7 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
       io.reward[io_row] = (float)(sc - prev);
       io.done[io_row] = done ? 1 : 0;
       if (done) {
-        reset_instance<true>(R, C, G, quirks);
+        reset_instance<true, false>(R, C, G, quirks);
         ep = 0;
         prev = score(R, C, G);
       } else {
@@ -937,7 +1090,7 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
   }
 
   if (active && !failed) {
-    store_regs(R, st, slot);
+    store_regs<false>(R, st, slot);
     store_V(C, st, slot);
     st.ep[slot] = ep;
     st.prev_score[slot] = prev;
@@ -1043,12 +1196,13 @@ __global__ void step_kernel_ws(const StepLaunch p) {
   }
 }
 
+template <bool kS>
 __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
   uint8_t *const smem = g_smem;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5, ipw = p.ipw;
   const int J = (blockDim.x >> 5) * ipw;
   const int j = w * ipw + lane;
-  const Smem S = carve(smem, J);
+  const Smem S = carve<kS>(smem, J);
   const Group g = p.groups[blockIdx.x];
   stage_game(S, p.games, p.images, g.game, p.quirks);
   __syncthreads();
@@ -1069,20 +1223,20 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
     R.key1 = (uint32_t)(seed >> 32);
     R.uid = p.uid_of_slot ? p.uid_of_slot[slot] : (uint32_t)row;
   } else {
-    load_regs(R, st, slot);
+    load_regs<kS>(R, st, slot);
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, J, S.uops};
-  if (doit) reset_instance<true>(R, C, G, p.quirks);
+              st.ram + slot * (int64_t)kRamBytes, J, S.uops, st.rpl + slot * 16};
+  if (doit) reset_instance<true, kS>(R, C, G, p.quirks);
   const unsigned which = __ballot_sync(kFull, doit);
   if (p.obs && which) {
     __syncwarp();
-    write_reset_obs(S.disp + w * ipw, J, doit ? p.obs + row * (int64_t)p.S * kFrameBytes : nullptr, p.S,
-                    which, lane, S.lut);
+    write_reset_obs<kS>(S.disp + w * ipw, J, doit ? p.obs + row * (int64_t)p.S * Disp<kS>::kFrame : nullptr,
+                        p.S, which, lane, S.lut);
     __syncwarp();
   }
   if (doit) {
-    store_regs(R, st, slot);
+    store_regs<kS>(R, st, slot);
     store_V(C, st, slot);
     st.ep[slot] = 0;
     st.prev_score[slot] = score(R, C, G);
@@ -1098,7 +1252,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) st.stack[i * n + slot] = (uint16_t)S.stack[i * J + j];
 #pragma unroll 8
-    for (int r = 0; r < 32; ++r) st.disp[r * n + slot] = S.disp[r * J + j];
+    for (int r = 0; r < Disp<kS>::kWords; ++r) st.disp[r * n + slot] = S.disp[r * J + j];
   }
 }
 
@@ -1136,7 +1290,7 @@ __global__ void hash_kernel(const DevState st, const uint8_t *images, const uint
     h = fnv_byte(h, e);
     h = fnv_byte(h, e >> 8);
   }
-  for (int r = 0; r < 32; ++r) {
+  for (int r = 0; r < disp_words(st.schip); ++r) {  // SCHIP words run [y][h], as in the record
     const uint64_t w = st.disp[r * n + slot];
     for (int b = 0; b < 8; ++b) h = fnv_byte(h, (uint32_t)(w >> (8 * b)));
   }
@@ -1146,6 +1300,10 @@ __global__ void hash_kernel(const DevState st, const uint8_t *images, const uint
   for (int b = 0; b < 4; ++b) h = fnv_byte(h, ep >> (8 * b));
   for (int b = 0; b < 4; ++b) h = fnv_byte(h, es >> (8 * b));
   h = fnv_byte(h, st.last_act[slot]);
+  if (st.schip) {
+    h = fnv_byte(h, st.mode[slot]);
+    for (int i = 0; i < 16; ++i) h = fnv_byte(h, st.rpl[slot * 16 + i]);
+  }
   out[row] = h;
 }
 
@@ -1168,14 +1326,19 @@ __global__ void records_kernel(const DevState st, const uint8_t *images, const u
   rec.ST = (uint8_t)(misc >> 16);
   rec.status = (uint8_t)(misc >> 24);
   for (int k = 0; k < 16; ++k) rec.stack[k] = st.stack[k * n + slot];
-  for (int r = 0; r < 32; ++r) rec.display[r] = st.disp[r * n + slot];
+  for (int y = 0; y < 64; ++y)
+    for (int hw = 0; hw < 2; ++hw)
+      rec.display[y][hw] = st.schip ? st.disp[(2 * y + hw) * n + slot]
+                                    : (y < 32 && hw == 0 ? st.disp[y * n + slot] : 0ull);
   const uint8_t *img = images + (size_t)st.game[slot] * kRamBytes;
   const uint64_t dirty = st.dirty[slot];
   for (uint32_t a = 0; a < (uint32_t)kRamBytes; ++a) rec.ram[a] = ram_byte(st, img, slot, dirty, a);
   rec.episode_steps = st.ep[slot];
   rec.env_steps = st.env_steps[slot];
   rec.last_action = st.last_act[slot];
-  for (int k = 0; k < 7; ++k) rec.pad[k] = 0;
+  rec.hires = st.schip ? st.mode[slot] : 0;
+  for (int k = 0; k < 6; ++k) rec.pad[k] = 0;
+  for (int k = 0; k < 16; ++k) rec.rpl[k] = st.schip ? st.rpl[slot * 16 + k] : 0;
 }
 
 __global__ void set_records_kernel(const DevState st, const GameDev *games, const uint8_t *images,
@@ -1195,7 +1358,10 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
   st.misc[slot] = (uint32_t)rec.SP | ((uint32_t)rec.DT << 8) | ((uint32_t)rec.ST << 16) |
                   ((uint32_t)rec.status << 24);
   for (int k = 0; k < 16; ++k) st.stack[k * n + slot] = rec.stack[k];
-  for (int r = 0; r < 32; ++r) st.disp[r * n + slot] = rec.display[r];
+  for (int r = 0; r < disp_words(st.schip); ++r)
+    st.disp[r * n + slot] = st.schip ? rec.display[r >> 1][r & 1] : rec.display[r][0];
+  st.mode[slot] = st.schip ? rec.hires : 0;
+  for (int k = 0; k < 16; ++k) st.rpl[slot * 16 + k] = st.schip ? rec.rpl[k] : 0;
   const int game = st.game[slot];
   const uint8_t *img = images + (size_t)game * kRamBytes;
   uint64_t dirty = 0;
@@ -1235,9 +1401,10 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
 
 }  // namespace
 
-size_t step_smem_bytes(int block, int ipw) {
+size_t step_smem_bytes(int block, int ipw, int schip) {
   const size_t J = (size_t)(block / 32) * ipw;
-  return (size_t)kRamBytes + kGameSmem + kUopSmem + kLutSmem + J * (32 * sizeof(uint64_t) + 32 * sizeof(uint32_t));
+  return (size_t)kRamBytes + kGameSmem + kUopSmem + kLutSmem +
+         J * (disp_words(schip) * sizeof(uint64_t) + 32 * sizeof(uint32_t));
 }
 
 // Dynamic shared memory a CTA may opt into, less room for static shared data.
@@ -1255,25 +1422,36 @@ size_t max_dynamic_smem() {
 
 size_t step_ws_smem_bytes(int block, int ipw) {
   const size_t J = (size_t)(block / 32) * ipw;
-  return step_smem_bytes(block, ipw) + 2 * 32 * 8 * J + ((2 * J + 15) & ~(size_t)15) + 4 * 8;
+  return step_smem_bytes(block, ipw, 0) + 2 * 32 * 8 * J + ((2 * J + 15) & ~(size_t)15) + 4 * 8;
 }
 
 static cudaError_t ensure_smem_attr() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)step_smem_bytes(kMaxBlock, 32));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)step_smem_bytes(kMaxBlock, 32));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(step_kernel_ws, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)max_dynamic_smem());
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(reset_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)step_smem_bytes(kMaxBlock, 32));
+  const int chip8 = (int)std::min(step_smem_bytes(kMaxBlock, 32, 0), max_dynamic_smem());
+  const int schip = (int)std::min(step_smem_bytes(kMaxBlock, 32, 1), max_dynamic_smem());
+  const void *fns[] = {(const void *)step_kernel<false, false>, (const void *)step_kernel<true, false>,
+                       (const void *)reset_kernel<false>,       (const void *)step_kernel<false, true>,
+                       (const void *)step_kernel<true, true>,   (const void *)reset_kernel<true>};
+  for (int i = 0; i < 6; ++i) {
+    cudaError_t e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, i < 3 ? chip8 : schip);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaFuncSetAttribute(step_kernel_ws, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)max_dynamic_smem());
   if (e == cudaSuccess) done = true;
   return e;
+}
+
+// The step kernel instantiation for a launch (null: writer warps on SCHIP).
+static const void *step_fn(const StepLaunch &p) {
+  if (p.writers > 0) return p.st.schip ? nullptr : (const void *)step_kernel_ws;
+  if (p.st.schip) return p.wrappers ? (const void *)step_kernel<true, true> : (const void *)step_kernel<false, true>;
+  return p.wrappers ? (const void *)step_kernel<true, false> : (const void *)step_kernel<false, false>;
+}
+
+static size_t step_fn_smem(const StepLaunch &p, int block) {
+  return p.writers > 0 ? step_ws_smem_bytes(block, p.ipw) : step_smem_bytes(block, p.ipw, p.st.schip);
 }
 
 cudaError_t launch_step(const StepLaunch &p, int grid, int block, cudaStream_t s) {
@@ -1281,13 +1459,12 @@ cudaError_t launch_step(const StepLaunch &p, int grid, int block, cudaStream_t s
   cudaError_t e = ensure_smem_attr();
   if (e != cudaSuccess) return e;
   if (grid <= 0) return cudaSuccess;
-  if (p.writers > 0)
-    step_kernel_ws<<<grid, block + 32 * p.writers, step_ws_smem_bytes(block, p.ipw), s>>>(p);
-  else if (p.wrappers)
-    step_kernel<true><<<grid, block, step_smem_bytes(block, p.ipw), s>>>(p);
-  else
-    step_kernel<false><<<grid, block, step_smem_bytes(block, p.ipw), s>>>(p);
-  return cudaGetLastError();
+  const void *fn = step_fn(p);
+  if (!fn) return cudaErrorInvalidValue;
+  StepLaunch copy = p;
+  void *args[] = {&copy};
+  const int threads = p.writers > 0 ? block + 32 * p.writers : block;
+  return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3((unsigned)threads), args, step_fn_smem(p, block), s);
 }
 
 cudaError_t launch_reset(const ResetLaunch &p, int block, cudaStream_t s) {
@@ -1295,7 +1472,10 @@ cudaError_t launch_reset(const ResetLaunch &p, int block, cudaStream_t s) {
   cudaError_t e = ensure_smem_attr();
   if (e != cudaSuccess) return e;
   if (p.n_groups <= 0) return cudaSuccess;
-  reset_kernel<<<p.n_groups, block, step_smem_bytes(block, p.ipw), s>>>(p);
+  if (p.st.schip)
+    reset_kernel<true><<<p.n_groups, block, step_smem_bytes(block, p.ipw, 1), s>>>(p);
+  else
+    reset_kernel<false><<<p.n_groups, block, step_smem_bytes(block, p.ipw, 0), s>>>(p);
   return cudaGetLastError();
 }
 
@@ -1334,27 +1514,26 @@ cudaError_t add_step_node(cudaGraph_t g, cudaGraphNode_t *node, cudaGraphNode_t 
   if (!state_complete(p.st)) return cudaErrorInvalidValue;
   cudaError_t e = ensure_smem_attr();
   if (e != cudaSuccess) return e;
+  const void *fn = step_fn(p);
+  if (!fn) return cudaErrorInvalidValue;
   StepLaunch copy = p;
   void *args[] = {&copy};
   cudaKernelNodeParams kp;
   memset(&kp, 0, sizeof kp);
-  const bool ws = p.writers > 0;
-  kp.func = ws ? reinterpret_cast<void *>(step_kernel_ws)
-               : p.wrappers ? reinterpret_cast<void *>(step_kernel<true>)
-                            : reinterpret_cast<void *>(step_kernel<false>);
+  kp.func = const_cast<void *>(fn);
   kp.gridDim = dim3((unsigned)grid);
-  kp.blockDim = dim3((unsigned)(ws ? block + 32 * p.writers : block));
-  kp.sharedMemBytes = (unsigned)(ws ? step_ws_smem_bytes(block, p.ipw) : step_smem_bytes(block, p.ipw));
+  kp.blockDim = dim3((unsigned)(p.writers > 0 ? block + 32 * p.writers : block));
+  kp.sharedMemBytes = (unsigned)step_fn_smem(p, block);
   kp.kernelParams = args;
   return cudaGraphAddKernelNode(node, g, dep ? &dep : nullptr, dep ? 1 : 0, &kp);
 }
 
-cudaError_t alloc_state(DevState &st, int64_t n, void **block_out, size_t *bytes_out) {
+cudaError_t alloc_state(DevState &st, int64_t n, int schip, void **block_out, size_t *bytes_out) {
   const size_t N = (size_t)n;
   // every array starts on a 256-byte boundary
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t sizes[] = {16 * N, 4 * N, 4 * N, 32 * N, 256 * N, 8 * N, 4096 * N,
-                          4 * N,  4 * N, 4 * N, 8 * N,  4 * N,   4 * N, 2 * N, N};
+  const size_t sizes[] = {16 * N, 4 * N, 4 * N, 32 * N, 8 * (size_t)disp_words(schip) * N, 8 * N, 4096 * N,
+                          4 * N,  4 * N, 4 * N, 8 * N,  4 * N,   4 * N, 2 * N, N, N, 16 * N};
   size_t total = 0;
   for (size_t b : sizes) total += up(b);
   uint8_t *base = nullptr;
@@ -1364,18 +1543,20 @@ cudaError_t alloc_state(DevState &st, int64_t n, void **block_out, size_t *bytes
   void **dst[] = {(void **)&st.v,   (void **)&st.pcI,        (void **)&st.misc,      (void **)&st.stack,
                   (void **)&st.disp, (void **)&st.dirty,     (void **)&st.ram,       (void **)&st.ep,
                   (void **)&st.env_steps, (void **)&st.prev_score, (void **)&st.key, (void **)&st.uid,
-                  (void **)&st.out_row, (void **)&st.game, (void **)&st.last_act};
-  for (int i = 0; i < 15; ++i) {
+                  (void **)&st.out_row, (void **)&st.game, (void **)&st.last_act, (void **)&st.mode,
+                  (void **)&st.rpl};
+  for (int i = 0; i < 17; ++i) {
     *dst[i] = base + off;
     off += up(sizes[i]);
   }
   st.n = n;
+  st.schip = schip;
   *block_out = base;
   *bytes_out = total;
   return cudaSuccess;
 }
 
-int max_resident_ctas(int block, int ipw, int writers, int wrappers) {
+int max_resident_ctas(int block, int ipw, int writers, int wrappers, int schip) {
   if (ensure_smem_attr() != cudaSuccess) return 0;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
@@ -1383,10 +1564,12 @@ int max_resident_ctas(int block, int ipw, int writers, int wrappers) {
   if (writers > 0)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel_ws, block + 32 * writers,
                                                   step_ws_smem_bytes(block, ipw));
-  else if (wrappers)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<true>, block, step_smem_bytes(block, ipw));
+  else if (schip)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wrappers ? step_kernel<true, true> : step_kernel<false, true>,
+                                                  block, step_smem_bytes(block, ipw, 1));
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<false>, block, step_smem_bytes(block, ipw));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wrappers ? step_kernel<true, false> : step_kernel<false, false>,
+                                                  block, step_smem_bytes(block, ipw, 0));
   return sms * per_sm;
 }
 

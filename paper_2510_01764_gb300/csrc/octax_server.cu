@@ -107,6 +107,7 @@ struct octax_server {
   int J = 16;       // instances per CTA
   int depth = 2;
   int n_games = 0, S = 4;
+  int schip = 0;  // OCTAX_VARIANT_SCHIP games
   uint32_t quirks = 0;
   uint32_t capacity = 0;
   std::vector<GameDev> games_h;
@@ -248,7 +249,7 @@ bool tick(octax_server *s) {
     Req *q = run[i];
     const size_t n = q->r.n_envs, st = q->steps_done;
     t.h_io[i] = IO{s->act_arena + (size_t)q->slot0 * kMaxSteps + st * n,
-                   q->r.obs_dev + st * n * (size_t)s->S * kFrameBytes, q->r.reward_dev + st * n,
+                   q->r.obs_dev + st * n * (size_t)s->S * frame_bytes(s->schip), q->r.reward_dev + st * n,
                    q->r.done_dev + st * n, (int64_t)n};
     for (uint32_t c = 0; c < q->r.n_envs; c += B)
       t.h_groups[g++] = Group{q->slot0 + c, (uint16_t)std::min<uint32_t>(B, q->r.n_envs - c), q->r.game,
@@ -355,7 +356,12 @@ int octax_server_create(const octax_game *games, int n_games, uint32_t quirks,
               "max_inflight_ticks 1..8");
     return OCTAX_EINVAL;
   }
-  const int64_t per_slot = (int64_t)(kSlotStateBytes + kMaxSteps);
+  const int schip = games[0].variant == OCTAX_VARIANT_SCHIP;
+  if (step_smem_bytes(B, ipw, schip) > max_dynamic_smem()) {
+    set_error("octax_server_create: too many instances per CTA for shared memory");
+    return OCTAX_EINVAL;
+  }
+  const int64_t per_slot = (int64_t)(slot_state_bytes(schip) + kMaxSteps);
   const int64_t cap64 = cfg->memory_budget_bytes / per_slot;
   if (cap64 < 1 || cap64 > ((int64_t)1 << 31)) {
     set_error("octax_server_create: memory budget must hold 1 .. 2^31 instances");
@@ -375,13 +381,14 @@ int octax_server_create(const octax_game *games, int n_games, uint32_t quirks,
   s->depth = depth;
   s->n_games = n_games;
   s->S = games[0].stack_frames;
+  s->schip = schip;
   s->quirks = quirks;
   s->capacity = (uint32_t)cap64;
   s->slots = RangeAlloc(s->capacity);
   s->games_h = games_dev;
   size_t bytes = 0;
   cudaError_t r = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-  if (r == cudaSuccess) r = alloc_state(s->st, s->capacity, &s->state_block, &bytes);
+  if (r == cudaSuccess) r = alloc_state(s->st, s->capacity, s->schip, &s->state_block, &bytes);
   if (r == cudaSuccess) r = cudaMalloc(&s->act_arena, (size_t)s->capacity * kMaxSteps);
   if (r == cudaSuccess) r = cudaMalloc(&s->err_d, sizeof(unsigned int));
   if (r == cudaSuccess) r = cudaMemset(s->err_d, 0, sizeof(unsigned int));

@@ -32,8 +32,8 @@ constexpr int kStaticMaxGroups = (int)((kStaticMaxEnvs + kStaticPerCta - 1) / kS
 constexpr size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t N = (size_t)kStaticMaxEnvs;
 // per-slot arrays, in DevState order
-constexpr size_t kArr[15] = {16 * N, 4 * N, 4 * N, 32 * N, 256 * N, 8 * N, 4096 * N,
-                             4 * N,  4 * N, 4 * N, 8 * N,  4 * N,   4 * N, 2 * N, N};
+constexpr size_t kArr[17] = {16 * N, 4 * N, 4 * N, 32 * N, 256 * N, 8 * N, 4096 * N,
+                             4 * N,  4 * N, 4 * N, 8 * N,  4 * N,   4 * N, 2 * N, N, N, 16 * N};
 constexpr size_t state_bytes() {
   size_t t = 0;
   for (size_t b : kArr) t += up256(b);
@@ -105,6 +105,10 @@ extern "C" int octax_rollout_static(const octax_game *game, int64_t n_envs, uint
     set_error("octax_rollout_static: need a game, n_envs >= 1, n_steps >= 1, known quirk bits");
     return OCTAX_EINVAL;
   }
+  if (game->variant != OCTAX_VARIANT_CHIP8) {
+    set_error("octax_rollout_static: CHIP-8 games only");
+    return OCTAX_EINVAL;
+  }
   if (n_envs > kStaticMaxEnvs) {
     set_error("octax_rollout_static: n_envs exceeds the static capacity of 1024 instances");
     return OCTAX_EINVAL;
@@ -128,8 +132,9 @@ extern "C" int octax_rollout_static(const octax_game *game, int64_t n_envs, uint
   void **dst[] = {(void **)&st.v,        (void **)&st.pcI,        (void **)&st.misc, (void **)&st.stack,
                   (void **)&st.disp,     (void **)&st.dirty,      (void **)&st.ram,  (void **)&st.ep,
                   (void **)&st.env_steps, (void **)&st.prev_score, (void **)&st.key,  (void **)&st.uid,
-                  (void **)&st.out_row,  (void **)&st.game,   (void **)&st.last_act};
-  for (int i = 0; i < 15; ++i) {
+                  (void **)&st.out_row,  (void **)&st.game,   (void **)&st.last_act,
+                  (void **)&st.mode,     (void **)&st.rpl};
+  for (int i = 0; i < 17; ++i) {
     *dst[i] = base + off;
     off += up256(kArr[i]);
   }

@@ -46,7 +46,8 @@ class CGame(C.Structure):
                 ("instr_per_frame", C.c_uint8), ("frameskip", C.c_uint8),
                 ("stack_frames", C.c_uint8), ("n_actions", C.c_uint8),
                 ("action_set", C.c_uint8 * 16), ("n_score_terms", C.c_uint8),
-                ("n_term_clauses", C.c_uint8), ("pad", C.c_uint8 * 2), ("score", CTerm * 4),
+                ("n_term_clauses", C.c_uint8), ("variant", C.c_uint8), ("pad", C.c_uint8),
+                ("score", CTerm * 4),
                 ("term", CClause * 4), ("max_episode_steps", C.c_uint32),
                 ("startup_instrs", C.c_uint32), ("sticky_threshold", C.c_uint32),
                 ("max_noops", C.c_uint32)]
@@ -60,10 +61,18 @@ class CLaunch(C.Structure):
 
 RECORD_DTYPE = np.dtype([("V", np.uint8, 16), ("I", "<u2"), ("PC", "<u2"), ("SP", np.uint8),
                          ("DT", np.uint8), ("ST", np.uint8), ("status", np.uint8),
-                         ("stack", "<u2", 16), ("display", "<u8", 32), ("ram", np.uint8, 4096),
+                         ("stack", "<u2", 16), ("display", "<u8", (64, 2)), ("ram", np.uint8, 4096),
                          ("episode_steps", "<u4"), ("env_steps", "<u4"),
-                         ("last_action", np.uint8), ("pad", np.uint8, 7)])
-assert RECORD_DTYPE.itemsize == 4424
+                         ("last_action", np.uint8), ("hires", np.uint8), ("pad", np.uint8, 6),
+                         ("rpl", np.uint8, 16)])
+assert RECORD_DTYPE.itemsize == 5208
+VARIANT_CHIP8, VARIANT_SCHIP = 0, 1
+STATUS_EXIT = 0x08
+
+
+def frame_shape(variant) -> tuple:
+    """(rows, columns) of one observation frame of a variant ("chip8"/"schip" or 0/1)."""
+    return (64, 128) if variant in ("schip", VARIANT_SCHIP) else (32, 64)
 
 class CServerConfig(C.Structure):
     _fields_ = [("memory_budget_bytes", C.c_int64), ("block", C.c_int32),
@@ -92,7 +101,7 @@ class CServerStats(C.Structure):
 EXPORTS = ("octax_create", "octax_reset", "octax_step", "octax_step_n", "octax_step_host",
            "octax_state_hash", "octax_get_state", "octax_set_state", "octax_sync",
            "octax_get_launch", "octax_set_launch", "octax_autotune", "octax_num_envs",
-           "octax_stack_frames", "octax_device_bytes", "octax_destroy", "octax_last_error",
+           "octax_stack_frames", "octax_variant", "octax_device_bytes", "octax_destroy", "octax_last_error",
            "octax_server_create", "octax_server_submit", "octax_server_wait",
            "octax_server_query", "octax_server_release", "octax_server_get_stats",
            "octax_server_destroy", "octax_rollout_static")
@@ -128,6 +137,7 @@ def load_library(path: str = LIB_PATH):
             "octax_autotune": (I32, [P, I32, P, C.POINTER(C.c_float)]),
             "octax_num_envs": (I64, [P]),
             "octax_stack_frames": (I32, [P]),
+            "octax_variant": (I32, [P]),
             "octax_device_bytes": (C.c_size_t, [P]),
             "octax_destroy": (None, [P]),
             "octax_last_error": (C.c_char_p, []),
@@ -181,6 +191,7 @@ def make_game(spec) -> tuple[CGame, object]:
     g.startup_instrs = spec.startup_instrs
     g.sticky_threshold = sticky_threshold(getattr(spec, "sticky_prob", 0.0))
     g.max_noops = getattr(spec, "max_noops", 0)
+    g.variant = VARIANT_SCHIP if getattr(spec, "variant", "chip8") == "schip" else VARIANT_CHIP8
     return g, rom
 
 
@@ -196,7 +207,7 @@ def _ptr(t) -> C.c_void_p | None:
 
 
 class Env:
-    """n_envs CHIP-8 environments stepped by the CUDA kernels on one GPU."""
+    """n_envs CHIP-8 (or Super-CHIP) environments stepped by the CUDA kernels on one GPU."""
 
     def __init__(self, games, n_envs: int, *, game_of_env=None, uid_of_env=None,
                  quirks: int = 0, seed: int = 0, device=None, stream=None):
@@ -212,6 +223,7 @@ class Env:
         self.games = list(games)
         self.n = int(n_envs)
         self.S = int(self.games[0].stack_frames)
+        self.frame = frame_shape(getattr(self.games[0], "variant", "chip8"))
         keep = [make_game(g) for g in self.games]
         arr = (CGame * len(keep))(*[k[0] for k in keep])
         goe = None if game_of_env is None else np.ascontiguousarray(game_of_env, dtype=np.uint16)
@@ -240,7 +252,7 @@ class Env:
 
     @property
     def obs_shape(self):
-        return (self.n, self.S, 32, 64)
+        return (self.n, self.S) + self.frame
 
     # ------------------------------------------------------------------ API
     def reset(self, mask=None, out=None):
@@ -379,6 +391,7 @@ class Server:
         torch.cuda.set_device(self.device)
         self.games = list(games)
         self.S = int(self.games[0].stack_frames)
+        self.frame = frame_shape(getattr(self.games[0], "variant", "chip8"))
         keep = [make_game(g) for g in self.games]
         arr = (CGame * len(keep))(*[k[0] for k in keep])
         cfg = CServerConfig(int(memory_budget_bytes), block, inst_per_warp, max_inflight_ticks, 0)
@@ -393,7 +406,7 @@ class Server:
         a = np.ascontiguousarray(actions, dtype=np.uint8)
         T, n = a.shape
         if out is None:
-            out = (torch.empty((T, n, self.S, 32, 64), dtype=torch.uint8, device=self.device),
+            out = (torch.empty((T, n, self.S) + self.frame, dtype=torch.uint8, device=self.device),
                    torch.empty((T, n), dtype=torch.float32, device=self.device),
                    torch.empty((T, n), dtype=torch.uint8, device=self.device))
         obs, rew, done = out

@@ -341,6 +341,183 @@ def random_game(seed: int, *, instr_per_frame: int = 10, frameskip: int = 4) -> 
 
 
 # --------------------------------------------------------------------------
+# Super-CHIP workloads (the 128x64 variant): a hires template game and
+# random-opcode programs over the CHIP-8 kinds plus the SCHIP forms.
+
+PLAYER16_SPRITE = (0x07, 0xE0, 0x1F, 0xF8, 0x3F, 0xFC, 0x7F, 0xFE, 0x7F, 0xFE, 0xFF, 0xFF,
+                   0xFF, 0xFF, 0xFF, 0xFF, 0xFF, 0xFF, 0xFF, 0xFF, 0x7F, 0xFE, 0x7F, 0xFE,
+                   0x3F, 0xFC, 0x1F, 0xF8, 0x07, 0xE0, 0x00, 0x00)   # 16x16 disc
+
+
+def schip_template_rom(p: TemplateParams) -> bytes:
+    """Hires (128x64) variant of the template game: 16x16 player (DXY0) moved
+    by 4 keys, an 8x4 object falling at a CXNN column, 8x3 decorative
+    draw/erase pairs, the score drawn in 8x10 glyphs (FX33, FX65, FX30), and on
+    every hit the score copied through the flag registers (FX75/FX85) and a
+    left-then-right scroll (00FC, 00FB)."""
+    rng = np.random.Generator(np.random.Philox(key=p.seed + 0x5C41))
+    a = Asm()
+    a.op(0x00FF)               # hires
+    a.op(0x6800 | 56)          # V8 = player x
+    a.op(0x6900 | 44)          # V9 = player y
+    a.op(0x6600)               # V6 = score
+    a.ref(0x2, "draw_score")
+    a.op(0x6B00 | 8)           # VB = object y
+    a.op(0xCA7F)               # VA = rnd & 127
+    a.ref(0xA, "object")
+    a.op(0xDAB4)
+    a.ref(0xA, "player")
+    a.op(0xD890)               # 16x16 player
+    a.label("loop")
+    a.ref(0xA, "player")
+    a.op(0xD890)               # erase
+    for key, upd in ((7, 0x78FE), (9, 0x7802), (5, 0x79FE), (8, 0x7902)):
+        a.op(0x6500 | key)
+        a.op(0xE5A1)
+        a.op(upd)
+    a.op(0x6E7F)
+    a.op(0x88E2)               # V8 &= 127
+    a.op(0x6E3F)
+    a.op(0x89E2)               # V9 &= 63
+    a.ref(0xA, "player")
+    a.op(0xD890)
+    scratch = (0x3, 0x7, 0xE)
+    readable = (0x3, 0x7, 0xE, 0x6, 0x8, 0x9, 0xA, 0xB)
+    for _ in range(p.alu_ops):
+        kind = int(rng.integers(0, 13))
+        x = int(scratch[rng.integers(0, 3)])
+        y = int(readable[rng.integers(0, len(readable))])
+        nn = int(rng.integers(0, 256))
+        if kind == 0:
+            a.op(0x6000 | x << 8 | nn)
+        elif kind == 1:
+            a.op(0x7000 | x << 8 | nn)
+        elif kind in (2, 3):
+            a.op((0x3000 if kind == 2 else 0x4000) | x << 8 | nn)
+        else:
+            sub = (0x0, 0x1, 0x2, 0x3, 0x4, 0x5, 0x6, 0x7, 0xE)[kind - 4]
+            a.op(0x8000 | x << 8 | y << 4 | sub)
+    if p.deco_pairs:
+        a.ref(0xA, "deco")
+        a.op(0x6300 | int(rng.integers(0, 120)))
+        a.op(0x6700 | int(rng.integers(12, 50)))
+        for _ in range(p.deco_pairs):
+            a.op(0xD373)
+            a.op(0xD373)
+    a.ref(0xA, "object")
+    a.op(0xDAB4)               # erase object
+    a.op(0x7B00 | 2 * p.fall)  # fall
+    a.op(0x6E3B)               # VE = 59
+    a.op(0x8EB5)               # VE = 59 - VB, VF = (59 >= VB)
+    a.op(0x3F00)
+    a.ref(0x1, "no_respawn")
+    a.op(0x6B00 | 8)
+    a.op(0xCA7F)
+    a.label("no_respawn")
+    a.ref(0xA, "object")
+    a.op(0xDAB4)
+    a.op(0x3F00)
+    a.ref(0x2, "hit")
+    a.op(0x6400 | p.wait_frames)
+    a.op(0xF415)
+    a.label("wait")
+    a.op(0xF407)
+    a.op(0x3400)
+    a.ref(0x1, "wait")
+    a.ref(0x1, "loop")
+    a.label("hit")
+    a.ref(0xA, "object")
+    a.op(0xDAB4)
+    a.ref(0x2, "draw_score")   # erase
+    a.op(0x7601)
+    a.op(0xF675)               # flags[0..6] = V0..V6
+    a.op(0x6600)
+    a.op(0xF685)               # V0..V6 = flags[0..6] (score back)
+    a.ref(0x2, "draw_score")
+    a.op(0x00FC)               # scroll left 4 ...
+    a.op(0x00FB)               # ... and back (edge columns lost)
+    a.op(0x6B00 | 8)
+    a.op(0xCA7F)
+    a.ref(0xA, "object")
+    a.op(0xDAB4)
+    a.op(0x00EE)
+    a.label("draw_score")
+    a.ref(0xA, "scratch")
+    a.op(0xF633)
+    a.op(0xF265)
+    a.op(0x6C00 | 98)
+    a.op(0x6D00 | 1)
+    for d in range(3):
+        a.op(0xF030 | d << 8)  # I = 8x10 glyph of Vd
+        a.op(0xDCDA)
+        a.op(0x7C09)
+    a.op(0x00EE)
+    a.label("player")
+    a.data(PLAYER16_SPRITE)
+    a.label("object")
+    a.data(OBJECT_SPRITE)
+    a.label("deco")
+    a.data(DECO_SPRITE)
+    a.label("scratch")
+    a.data((0, 0, 0, 0))
+    rom = bytearray(a.assemble())
+    if len(rom) < p.size:
+        rom += rng.integers(0, 256, size=p.size - len(rom), dtype=np.uint8).tobytes()
+    return bytes(rom)
+
+
+def schip_template_game(p: TemplateParams, *, instr_per_frame: int = 20, frameskip: int = 4,
+                        score_limit: int = 0, max_episode_steps: int = 0) -> GameSpec:
+    """SCHIP template ROM + descriptor: reward = V6 increase, done at V6 >= limit."""
+    term = (Clause(Term("reg", 6), ">=", score_limit),) if score_limit > 0 else ()
+    return GameSpec(rom=schip_template_rom(p), instr_per_frame=instr_per_frame,
+                    frameskip=frameskip, stack_frames=4, action_set=(7, 9, 5, 8),
+                    score=(Term("reg", 6),), term=term,
+                    max_episode_steps=max_episode_steps, startup_instrs=0, variant="schip",
+                    name=f"schip-template-{p.seed}")
+
+
+SCHIP_KINDS = ("00CN", "00FB", "00FC", "00FD", "00FE", "00FF", "DXY0", "FX30", "FX75", "FX85")
+
+
+def random_schip_rom(seed: int, n_bytes: int = 3584, schip_weight: float = 0.15,
+                     exit_weight: float = 0.002) -> bytes:
+    """Random program over the 35 CHIP-8 kinds and the SCHIP forms: each
+    opcode is a SCHIP form with probability ``schip_weight`` (00FD at
+    ``exit_weight``, the rest uniform), otherwise a CHIP-8 opcode as in
+    ``random_opcode_rom``."""
+    base = bytearray(random_opcode_rom(seed, n_bytes))
+    rng = np.random.Generator(np.random.Philox(key=seed + 0x5C42))
+    n_ops = n_bytes // 2
+    others = [k for k in SCHIP_KINDS if k != "00FD"]
+    for i in range(n_ops):
+        u = rng.random()
+        if u < exit_weight:
+            k = "00FD"
+        elif u < schip_weight:
+            k = others[int(rng.integers(0, len(others)))]
+        else:
+            continue
+        x, y, n = int(rng.integers(0, 16)), int(rng.integers(0, 16)), int(rng.integers(0, 16))
+        if k == "00CN":
+            w = 0x00C0 | n
+        elif k == "DXY0":
+            w = 0xD000 | x << 8 | y << 4
+        elif k[0] == "F":
+            w = 0xF000 | x << 8 | int(k[2:], 16)
+        else:
+            w = int(k, 16)
+        base[2 * i:2 * i + 2] = bytes((w >> 8, w & 0xFF))
+    return bytes(base)
+
+
+def random_schip_game(seed: int, *, instr_per_frame: int = 10, frameskip: int = 4) -> GameSpec:
+    return GameSpec(rom=random_schip_rom(seed), instr_per_frame=instr_per_frame,
+                    frameskip=frameskip, stack_frames=4, action_set=(1, 2, 3, 4),
+                    score=(Term("reg", 6),), term=(), variant="schip", name=f"random-schip-{seed}")
+
+
+# --------------------------------------------------------------------------
 # Action streams: uniform over the action set, counter-based per step so that
 # any window of steps can be regenerated independently.
 
@@ -385,6 +562,15 @@ def cfg_scale(n_envs: int = 16384, n_steps: int = 20000) -> Workload:
     g = template_game(TemplateParams(seed=2, size=600), score_limit=20, max_episode_steps=5000)
     return Workload(f"plain-scale-{n_envs}x{n_steps}", [g], None, n_envs, n_steps, seed=2,
                     action_seed=2)
+
+
+def cfg_schip(n_envs: int = 16384, n_steps: int = 4000) -> Workload:
+    """16,384 instances of the hires SCHIP template ROM (seed 3), K = 20, frame
+    skip 4, observations uint8 [4, 64, 128], done on score >= 20 or 2,000 steps."""
+    g = schip_template_game(TemplateParams(seed=3, size=700, deco_pairs=1), score_limit=20,
+                            max_episode_steps=2000)
+    return Workload(f"schip-scale-{n_envs}x{n_steps}", [g], None, n_envs, n_steps, seed=3,
+                    action_seed=3)
 
 
 BATCH_K = (5, 8, 10, 15, 20)

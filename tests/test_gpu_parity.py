@@ -353,7 +353,7 @@ def sampled_run(w, *, chunk, sample, launch=None, use_step_n=True):
     assert np.array_equal(env.reset()[idx].cpu().numpy(), ref.reset())
     n_actions = w.games[0].n_actions
     T = chunk
-    obs_buf = torch.empty((T, w.n_envs, 4, 32, 64), dtype=torch.uint8, device="cuda")
+    obs_buf = torch.empty((T, w.n_envs, 4) + env.frame, dtype=torch.uint8, device="cuda")
     rew_buf = torch.empty((T, w.n_envs), dtype=torch.float32, device="cuda")
     done_buf = torch.empty((T, w.n_envs), dtype=torch.uint8, device="cuda")
     n_done = 0
