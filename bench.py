@@ -34,10 +34,27 @@ sys.path.insert(0, ROOT)
 from paper_2510_01764_gb300 import workloads as W  # noqa: E402
 
 METRIC = "env steps/s on 1 GB300 (bit-exact vs oracle) vs plain kernel; serving p50/p99 ms"
-OBS_BYTES = 4 * 32 * 64
-# algorithmic HBM bytes of the step kernel ("roofline"):
-STEP_IO_BYTES = OBS_BYTES + 1 + 4 + 1            # obs + action + reward + done, per env step
-STATE_BYTES = 348 + 332                          # per instance per launch: state read + write
+
+# Algorithmic HBM bytes of the step kernel. Per env step and instance: the
+# observation (4 frames) + action + reward + done. Per launch and instance:
+# the emulator state read at the start and written at the end (V 16, PC|I 4,
+# SP|timers|status 4, stack 32, display, dirty mask 8, counters 8, previous
+# score 4, previous action 1; read only: Philox key 8, uid 4, output row 4;
+# SCHIP adds the mode byte).
+def frame_shape(w: W.Workload) -> tuple:
+    return (64, 128) if w.games[0].variant == "schip" else (32, 64)
+
+
+def step_io_bytes(w: W.Workload) -> int:
+    r, c = frame_shape(w)
+    return 4 * r * c + 1 + 4 + 1
+
+
+def state_bytes(w: W.Workload) -> int:
+    schip = w.games[0].variant == "schip"
+    disp = 1024 if schip else 256
+    written = 16 + 4 + 4 + 32 + disp + 8 + 8 + 4 + 1 + (1 if schip else 0)
+    return written + (written + 16)  # written, and read back with the 16 read-only bytes
 
 
 def dist_env():
@@ -65,7 +82,7 @@ def whole_job_rate(world: int, n_envs: int, steps: int, ms: float) -> float:
 
 def workload(name: str) -> W.Workload:
     return {"scale": W.cfg_scale, "small": W.cfg_small, "batch": W.cfg_batch,
-            "divergence": W.cfg_divergence}[name]()
+            "divergence": W.cfg_divergence, "schip": W.cfg_schip}[name]()
 
 
 def describe(config: str, w: W.Workload) -> str:
@@ -77,6 +94,9 @@ def describe(config: str, w: W.Workload) -> str:
         "batch": f"batch: {w.n_envs} instances over 16 template ROMs (200-3,000 B), K per ROM in "
                  "{5,8,10,15,20}, uneven episodes, 16 frames per persistent graph launch",
         "divergence": f"divergence: {w.n_envs} instances of 64 random-opcode ROMs (3,584 B), K=10",
+        "schip": f"schip-scale: {w.n_envs} instances of the hires Super-CHIP template ROM (seed 3, "
+                 f"{len(g.rom)} B), K=20, frameskip 4, obs uint8 [4,64,128], auto-reset at score>=20 "
+                 "or 2,000 steps",
     }[config]
 
 
@@ -234,7 +254,7 @@ def run_gpu(args) -> dict | None:
         T = args.rollout
         acts_h = W.actions(w.action_seed, 0, K, n, w.games[0].n_actions)
         acts = torch.from_numpy(acts_h).to(dev)
-        obs = torch.empty((T, n, 4, 32, 64), dtype=torch.uint8, device=dev)
+        obs = torch.empty((T, n, 4) + frame_shape(w), dtype=torch.uint8, device=dev)
         rew = torch.empty((T, n), dtype=torch.float32, device=dev)
         done = torch.empty((T, n), dtype=torch.uint8, device=dev)
         init_state = env.get_state()
@@ -289,7 +309,7 @@ def run_gpu(args) -> dict | None:
         # ---- end to end through the host-buffer entry point
         Ke = min(K, args.e2e_steps)
         a_h = torch.from_numpy(acts_h[:Ke].copy()).pin_memory()
-        o_h = torch.empty((n, 4, 32, 64), dtype=torch.uint8, pin_memory=True)
+        o_h = torch.empty((n, 4) + frame_shape(w), dtype=torch.uint8, pin_memory=True)
         r_h = torch.empty(n, dtype=torch.float32, pin_memory=True)
         d_h = torch.empty(n, dtype=torch.uint8, pin_memory=True)
         env.set_launch(**plain_cfg)
@@ -313,7 +333,7 @@ def run_gpu(args) -> dict | None:
     spl = launch["steps_per_launch"]
     n_launch = sum((hi - lo + spl - 1) // spl for lo, hi in calls)
     launch_ms = ms_best / n_launch
-    alg_bytes = n * (STEP_IO_BYTES * (K / n_launch) + STATE_BYTES)
+    alg_bytes = n * (step_io_bytes(w) * (K / n_launch) + state_bytes(w))
     peak, peak_src = measured_peaks()
     achieved = alg_bytes / (launch_ms / 1e3) / 1e9
     prof = profiled_traffic(args.config)
@@ -350,9 +370,9 @@ def run_gpu(args) -> dict | None:
             "rollout_buffer_steps": T,
             "launch": launch,
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-            "l2": (f"no flush: each step writes {n * 4 * 2048 / 1e6:.0f} MB of observations into a "
-                   f"{T}-step rollout ring ({T * n * 4 * 2048 / 1e6:.0f} MB); emulator state "
-                   f"{n * 4455 / 1e6:.0f} MB; L2 126 MB"),
+            "l2": (f"no flush: each step writes {n * (step_io_bytes(w) - 6) / 1e6:.0f} MB of observations "
+                   f"into a {T}-step rollout ring ({T * n * (step_io_bytes(w) - 6) / 1e6:.0f} MB); "
+                   f"emulator state {n * (state_bytes(w) / 2 + 4096) / 1e6:.0f} MB; L2 126 MB"),
         },
         "plain_kernel": {
             "value": round(whole_job_rate(world, n, K, ms_plain), 1),
@@ -382,7 +402,7 @@ def run_gpu(args) -> dict | None:
             "unit": "env steps/s",
             "steps": Ke,
             "h2d_bytes_per_step": n,
-            "d2h_bytes_per_step": n * (OBS_BYTES + 4 + 1),
+            "d2h_bytes_per_step": n * (step_io_bytes(w) - 1),
         },
         "clocks": clocks,
     }
@@ -550,7 +570,7 @@ def main():
     ap.add_argument("--steps", type=int, default=0, help="timed env steps (0 = the workload's)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="octax", choices=["octax", "reference"])
-    ap.add_argument("--config", default="scale", choices=["scale", "small", "batch", "divergence"])
+    ap.add_argument("--config", default="scale", choices=["scale", "small", "batch", "divergence", "schip"])
     ap.add_argument("--rollout", type=int, default=32, help="steps per octax_step_n call")
     ap.add_argument("--launch", default="",
                     help="block,inst_per_warp,steps_per_launch,persistent,graph[,writer_warps[,balance]] "
