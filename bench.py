@@ -216,6 +216,7 @@ def record_traffic(csv_path: str, config: str, launch: str, units: int) -> dict:
         "dram_bytes_per_launch": traffic,
         "dram_bytes_per_instance_step": traffic / units,
         "warp_inst_per_instance_step": mean("smsp__inst_executed.sum") / units,
+        "active_threads_per_warp_inst": mean("smsp__thread_inst_executed_per_inst_executed.ratio"),
         "captured_duration_s": mean("gpu__time_duration.sum"),
         "note": "ncu --set full --clock-control none; DRAM write bytes exclude observation "
                 "lines still in L2 at kernel exit",
@@ -347,6 +348,8 @@ def run_gpu(args) -> dict | None:
         got = prof["warp_inst_per_instance_step"] * units_per_launch / (launch_ms / 1e3)
         issue = {"achieved": round(got / 1e9, 2), "peak": round(peak_issue / 1e9, 2),
                  "unit": "G warp-instr/s", "frac": round(got / peak_issue, 4),
+                 "divergence_efficiency": (round(prof["active_threads_per_warp_inst"] / 32, 4)
+                                           if "active_threads_per_warp_inst" in prof else None),
                  "source": "ncu instruction count per instance-step (profiles/traffic.json) x "
                            "instance-steps per launch / live launch time; peak = SMs x 4 x median SM clock"}
     line = {
