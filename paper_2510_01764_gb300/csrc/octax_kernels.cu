@@ -234,7 +234,8 @@ __device__ __forceinline__ void scroll_left(const Ctx &C, uint32_t c) {  // 0 < 
 
 // Opcodes the predicated datapath covers: classes 1 3 4 6 7 A always; 5 9
 // with N = 0; 8 with N in 0-7,E (classic shifts and logic); E with 9E/A1;
-// F with 07 0A 15 18 29, and 1E without its quirk.
+// F with 07 and 15. The rarer FX forms (0A 18 1E 29 ...) take the slow path,
+// which keeps their selects out of every instruction slot.
 __device__ __forceinline__ bool is_fast_op(uint32_t op, uint32_t quirks) {
   const uint32_t cls = op >> 12, n = op & 15u, nn = op & 0xFFu;
   const uint32_t cbit = 1u << cls;
@@ -243,8 +244,7 @@ __device__ __forceinline__ bool is_fast_op(uint32_t op, uint32_t quirks) {
   fast |= (cls == 8) & ((n <= 7) | (n == 14)) &
           ((quirks & (OCTAX_QUIRK_SHIFT_USES_VY | OCTAX_QUIRK_LOGIC_RESETS_VF)) == 0);
   fast |= (cls == 14) & ((nn == 0x9Eu) | (nn == 0xA1u));
-  fast |= (cls == 15) & ((nn == 0x07u) | (nn == 0x0Au) | (nn == 0x15u) | (nn == 0x18u) | (nn == 0x29u) |
-                         ((nn == 0x1Eu) & ((quirks & OCTAX_QUIRK_FX1E_VF) == 0)));
+  fast |= (cls == 15) & ((nn == 0x07u) | (nn == 0x15u));
   return fast;
 }
 
@@ -252,8 +252,8 @@ __device__ __forceinline__ bool is_fast_op(uint32_t op, uint32_t quirks) {
 // A slow opcode is stored raw (bit 20 clear). A fast one is
 //   bits 0-11 NNN (NN, N in its low bits) | 12-15 X | 16-19 Y | 20 fast |
 //   21 skip negated | 22-23 skip source (1: VX vs NN, 2: VX vs VY, 3: key) |
-//   24 jump | 25-27 VX write (1 NN, 2 VX+NN, 3 8XYN, 4 DT, 5 key) |
-//   28-29 I write (1 NNN, 2 I+VX, 3 glyph) | 30-31 timer (1 DT, 2 ST) from VX.
+//   24 jump | 25-27 VX write (1 NN, 2 VX+NN, 3 8XYN, 4 DT) |
+//   28-29 I write (1 NNN) | 30-31 timer (1 DT) from VX.
 constexpr uint32_t kUopFast = 1u << 20;
 
 __device__ __forceinline__ uint32_t make_uop(uint32_t op, uint32_t quirks) {
@@ -274,11 +274,7 @@ __device__ __forceinline__ uint32_t make_uop(uint32_t op, uint32_t quirks) {
     case 0xE: u |= skip(3, nn == 0xA1u ? 1u : 0u); break;
     default:  // 0xF
       if (nn == 0x07u) u |= 4u << 25;
-      else if (nn == 0x0Au) u |= 5u << 25;
-      else if (nn == 0x15u) u |= 1u << 30;
-      else if (nn == 0x18u) u |= 2u << 30;
-      else if (nn == 0x1Eu) u |= 2u << 28;
-      else u |= 3u << 28;  // 0x29
+      else u |= 1u << 30;  // 0x15
       break;
   }
   return u;
@@ -501,7 +497,6 @@ __device__ __forceinline__ void execute(Regs &R, const Ctx &C, uint32_t u, int k
     const bool skip = (src != 0u) & (cond != (((u >> 21) & 1u) != 0u));
     uint32_t npc = (pc + (skip ? 4u : 2u)) & 0xFFFu;
     npc = (u & (1u << 24)) ? nnn : npc;
-    npc = ((wk == 5u) & (key < 0)) ? pc : npc;
     R.pc = npc;
     // 8XYN result and flag (N in 0-7, E)
     const uint32_t sum = vx + vy;
@@ -517,17 +512,12 @@ __device__ __forceinline__ void execute(Regs &R, const Ctx &C, uint32_t u, int k
     uint32_t val = (wk == 2u) ? (vx + nn) : nn;
     val = (wk == 3u) ? alu : val;
     val = (wk == 4u) ? R.dt : val;
-    val = (wk == 5u) ? (uint32_t)key : val;
-    if ((wk != 0u) & !((wk == 5u) & (key < 0))) *Vx = val & 0xFFu;
+    if (wk != 0u) *Vx = val & 0xFFu;
     if ((wk == 3u) & (n >= 4u)) C.V[15 * C.J] = flag;  // after VX: with X = F the flag wins
     // index register and timers
     const uint32_t ik = (u >> 28) & 3u, tk = u >> 30;
-    uint32_t I = (ik == 1u) ? nnn : R.I;
-    I = (ik == 2u) ? ((I + vx) & 0xFFFFu) : I;
-    I = (ik == 3u) ? (0x50u + 5u * (vx & 15u)) : I;
-    R.I = I;
+    R.I = (ik == 1u) ? nnn : R.I;
     R.dt = (tk == 1u) ? vx : R.dt;
-    R.st = (tk == 2u) ? vx : R.st;
   } else if ((u >> 12) == 0xDu) {  // DXYN, the most frequent slow opcode: its own branch
     R.pc = (pc + 2u) & 0xFFFu;
     if (kS) draw_schip(R, C, getV(C, (u >> 8) & 15u), getV(C, (u >> 4) & 15u), u & 15u, quirks);
@@ -542,6 +532,7 @@ __device__ __forceinline__ void execute(Regs &R, const Ctx &C, uint32_t u, int k
 template <bool kS>
 __device__ __forceinline__ void run_instrs(Regs &R, const Ctx &C, int key, uint32_t quirks,
                                            uint32_t count) {
+#pragma unroll 2
   for (uint32_t k = 0; k < count; ++k) execute<kS>(R, C, fetch_uop(R, C, R.pc), key, quirks);
 }
 
@@ -896,12 +887,9 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
   }
 }
 
-// No __launch_bounds__: with it ptxas caps registers at 128 and may spill;
-// without it the register count still admits a 256-thread CTA.
-// kWrap: the sticky-action / no-op-reset variant (its draws cost registers,
-// so games without the wrappers run the variant without them).
+// One CTA's loop over groups (a persistent CTA pulls them off the queue).
 template <bool kWrap, bool kS>
-__global__ void step_kernel(const StepLaunch p) {
+__device__ __forceinline__ void step_body(const StepLaunch &p) {
   uint8_t *const smem = g_smem;
   const Smem S = carve<kS>(smem, (blockDim.x >> 5) * p.ipw);
   __shared__ int s_group;
@@ -924,6 +912,18 @@ __global__ void step_kernel(const StepLaunch p) {
     __syncthreads();  // shared memory is reused by the next group
     if (!p.work_counter) break;
   }
+}
+
+// The plain CHIP-8 kernel is held to 128 registers so that two 256-thread
+// CTAs fit on an SM. kWrap: the sticky-action / no-op-reset variant (its draws
+// cost registers, so games without the wrappers run the variant without
+// them); kS: the Super-CHIP display layout. Those instantiations need more
+// registers and carry no bound.
+__global__ void __launch_bounds__(kMaxBlock, 2) step_kernel_chip8(const StepLaunch p) { step_body<false, false>(p); }
+
+template <bool kWrap, bool kS>
+__global__ void step_kernel(const StepLaunch p) {
+  step_body<kWrap, kS>(p);
 }
 
 
@@ -1430,7 +1430,7 @@ static cudaError_t ensure_smem_attr() {
   if (done) return cudaSuccess;
   const int chip8 = (int)std::min(step_smem_bytes(kMaxBlock, 32, 0), max_dynamic_smem());
   const int schip = (int)std::min(step_smem_bytes(kMaxBlock, 32, 1), max_dynamic_smem());
-  const void *fns[] = {(const void *)step_kernel<false, false>, (const void *)step_kernel<true, false>,
+  const void *fns[] = {(const void *)step_kernel_chip8,        (const void *)step_kernel<true, false>,
                        (const void *)reset_kernel<false>,       (const void *)step_kernel<false, true>,
                        (const void *)step_kernel<true, true>,   (const void *)reset_kernel<true>};
   for (int i = 0; i < 6; ++i) {
@@ -1447,7 +1447,7 @@ static cudaError_t ensure_smem_attr() {
 static const void *step_fn(const StepLaunch &p) {
   if (p.writers > 0) return p.st.schip ? nullptr : (const void *)step_kernel_ws;
   if (p.st.schip) return p.wrappers ? (const void *)step_kernel<true, true> : (const void *)step_kernel<false, true>;
-  return p.wrappers ? (const void *)step_kernel<true, false> : (const void *)step_kernel<false, false>;
+  return p.wrappers ? (const void *)step_kernel<true, false> : (const void *)step_kernel_chip8;
 }
 
 static size_t step_fn_smem(const StepLaunch &p, int block) {
@@ -1568,7 +1568,8 @@ int max_resident_ctas(int block, int ipw, int writers, int wrappers, int schip) 
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wrappers ? step_kernel<true, true> : step_kernel<false, true>,
                                                   block, step_smem_bytes(block, ipw, 1));
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wrappers ? step_kernel<true, false> : step_kernel<false, false>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wrappers ? (const void *)step_kernel<true, false>
+                                                           : (const void *)step_kernel_chip8,
                                                   block, step_smem_bytes(block, ipw, 0));
   return sms * per_sm;
 }
