@@ -43,7 +43,7 @@ struct alignas(16) GameDev {
 };
 static_assert(sizeof(GameDev) <= 192, "GameDev must fit its shared-memory slot");
 constexpr int kGameSmem = 192;
-constexpr int kUopSmem = kRamBytes / 2 * 4;  // one decoded u32 per even address
+constexpr int kUopSmem = kRamBytes / 2 * 16;  // one 16-byte micro-op per even address
 constexpr int kLutSmem = 256 * 8;            // byte of pixels -> 8 output bytes
 
 // Emulator state, structure-of-arrays over slots (slot = index in these arrays).

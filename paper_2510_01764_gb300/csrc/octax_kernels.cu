@@ -57,7 +57,7 @@ struct Ctx {
   uint32_t *V;         // shared: this instance's V0; Vx at V[x * J]
   uint8_t *ram;        // global: this instance's 4 KB RAM (dirty pages)
   int J;
-  const uint32_t *uops;  // shared: decoded opcode at every even image address (make_uop)
+  const uint4 *uops;     // shared: micro-op at every even image address (stage_game)
   uint8_t *rpl;          // global: this instance's 16 SCHIP flag bytes
 };
 
@@ -476,20 +476,22 @@ __device__ __forceinline__ void exec_slow(Regs &R, const Ctx &C, uint32_t op, ui
 }
 
 // Micro-op of the instruction at pc: from the table, or (odd PC, written
-// page) the raw opcode, which takes the general path.
-__device__ __forceinline__ uint32_t fetch_uop(const Regs &R, const Ctx &C, uint32_t pc) {
+// page) the raw opcode, which takes the general path. Table entries are
+// {make_uop word, X * J, Y * J, NNN}: the shared-memory offsets of VX and VY
+// come pre-multiplied, so one 16-byte load feeds the datapath.
+__device__ __forceinline__ uint4 fetch_uop(const Regs &R, const Ctx &C, uint32_t pc) {
   if (!((pc & 1u) | dirty_bit(R.dirty, pc))) return C.uops[pc >> 1];
-  return (rd8(R, C, pc) << 8) | rd8(R, C, pc + 1u);
+  return make_uint4((rd8(R, C, pc) << 8) | rd8(R, C, pc + 1u), 0u, 0u, 0u);
 }
 
 // Execute micro-op u, the instruction at R.pc. key: held CHIP-8 key or -1.
 template <bool kS>
-__device__ __forceinline__ void execute(Regs &R, const Ctx &C, uint32_t u, int key, uint32_t quirks) {
-  const uint32_t pc = R.pc;
+__device__ __forceinline__ void execute(Regs &R, const Ctx &C, const uint4 u4, int key, uint32_t quirks) {
+  const uint32_t pc = R.pc, u = u4.x;
   if (u & kUopFast) {
-    const uint32_t nnn = u & 0xFFFu, nn = u & 0xFFu, n = u & 15u;
-    uint32_t *const Vx = C.V + ((u >> 12) & 15u) * C.J;
-    const uint32_t vx = *Vx, vy = C.V[((u >> 16) & 15u) * C.J];
+    const uint32_t nnn = u4.w, nn = u & 0xFFu, n = u & 15u;
+    uint32_t *const Vx = C.V + u4.y;
+    const uint32_t vx = *Vx, vy = C.V[u4.z];
     // next PC: skips, jump, wait-for-key
     const uint32_t src = (u >> 22) & 3u, wk = (u >> 25) & 7u;
     const bool pressed = key >= 0 && (uint32_t)key == (vx & 15u);
@@ -700,7 +702,7 @@ __device__ __forceinline__ void write_reset_obs(const uint64_t *disp_warp, int J
 struct Smem {
   uint8_t *img;
   GameDev *game;
-  uint32_t *uops;
+  uint4 *uops;      // micro-op table (fetch_uop)
   uint2 *lut;       // byte of pixels -> 8 bytes of 0/1
   uint64_t *disp;
   uint32_t *stack;
@@ -715,7 +717,7 @@ __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
   Smem s;
   s.img = smem;
   s.game = reinterpret_cast<GameDev *>(smem + kRamBytes);
-  s.uops = reinterpret_cast<uint32_t *>(smem + kRamBytes + kGameSmem);
+  s.uops = reinterpret_cast<uint4 *>(smem + kRamBytes + kGameSmem);
   s.lut = reinterpret_cast<uint2 *>(smem + kRamBytes + kGameSmem + kUopSmem);
   s.disp = reinterpret_cast<uint64_t *>(smem + kRamBytes + kGameSmem + kUopSmem + kLutSmem);
   s.stack = reinterpret_cast<uint32_t *>(s.disp + Disp<kS>::kWords * J);
@@ -725,7 +727,7 @@ __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
 
 // Every thread of the CTA calls this (it contains a barrier).
 __device__ __forceinline__ void stage_game(const Smem &S, const GameDev *games, const uint8_t *images,
-                                           int game, uint32_t quirks) {
+                                           int game, uint32_t quirks, int J) {
   const uint4 *src = reinterpret_cast<const uint4 *>(images + (size_t)game * kRamBytes);
   uint4 *dst = reinterpret_cast<uint4 *>(S.img);
   for (int i = threadIdx.x; i < kRamBytes / 16; i += blockDim.x) dst[i] = src[i];
@@ -737,7 +739,8 @@ __device__ __forceinline__ void stage_game(const Smem &S, const GameDev *games, 
   // decode the opcode at every even address of the image once
   for (int w = threadIdx.x; w < kRamBytes / 2; w += blockDim.x) {
     const uint32_t op = ((uint32_t)S.img[2 * w] << 8) | S.img[2 * w + 1];
-    S.uops[w] = make_uop(op, quirks);
+    S.uops[w] = make_uint4(make_uop(op, quirks), ((op >> 8) & 15u) * (uint32_t)J, ((op >> 4) & 15u) * (uint32_t)J,
+                           op & 0xFFFu);
   }
 }
 
@@ -904,7 +907,7 @@ __device__ __forceinline__ void step_body(const StepLaunch &p) {
     if (gi >= p.n_groups) break;
     const Group g = p.groups[gi];
     if ((int)g.game != cur_game) {
-      stage_game(S, p.games, p.images, g.game, p.quirks);
+      stage_game(S, p.games, p.images, g.game, p.quirks, (blockDim.x >> 5) * p.ipw);
       cur_game = g.game;
     }
     __syncthreads();
@@ -1183,7 +1186,7 @@ __global__ void step_kernel_ws(const StepLaunch p) {
     if (gi >= p.n_groups) break;
     const Group g = p.groups[gi];
     if ((int)g.game != cur_game) {
-      stage_game(W.base, p.games, p.images, g.game, p.quirks);
+      stage_game(W.base, p.games, p.images, g.game, p.quirks, J);
       cur_game = g.game;
     }
     __syncthreads();
@@ -1204,7 +1207,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
   const int j = w * ipw + lane;
   const Smem S = carve<kS>(smem, J);
   const Group g = p.groups[blockIdx.x];
-  stage_game(S, p.games, p.images, g.game, p.quirks);
+  stage_game(S, p.games, p.images, g.game, p.quirks, J);
   __syncthreads();
   const DevState &st = p.st;
   const int64_t n = st.n;
