@@ -45,6 +45,7 @@ static_assert(sizeof(GameDev) <= 192, "GameDev must fit its shared-memory slot")
 constexpr int kGameSmem = 192;
 constexpr int kUopSmem = kRamBytes / 2 * 16;  // one 16-byte micro-op per even address
 constexpr int kLutSmem = 256 * 8;            // byte of pixels -> 8 output bytes
+constexpr int kAluSmem = 16 * 2 * 16;        // 8XYN coefficients per N (two int4)
 
 // Emulator state, structure-of-arrays over slots (slot = index in these arrays).
 struct DevState {

@@ -58,6 +58,7 @@ struct Ctx {
   uint8_t *ram;        // global: this instance's 4 KB RAM (dirty pages)
   int J;
   const uint4 *uops;     // shared: micro-op at every even image address (stage_game)
+  const int4 *alu;       // shared: 8XYN coefficients, two int4 per N (stage_game)
   uint8_t *rpl;          // global: this instance's 16 SCHIP flag bytes
 };
 
@@ -255,9 +256,17 @@ __device__ __forceinline__ bool is_fast_op(uint32_t op, uint32_t quirks) {
 //   24 jump | 25-27 VX write (1 NN, 2 VX+NN, 3 8XYN, 4 DT) |
 //   28-29 I write (1 NNN) | 30-31 timer (1 DT) from VX.
 constexpr uint32_t kUopFast = 1u << 20;
+// A slow opcode tagged for the short FX branch of execute (FX0A, FX18, FX29 and
+// FX1E without its quirk): bit 21 set on the raw opcode (bit 20 clear).
+constexpr uint32_t kUopFx = 1u << 21;
 
 __device__ __forceinline__ uint32_t make_uop(uint32_t op, uint32_t quirks) {
-  if (!is_fast_op(op, quirks)) return op;
+  if (!is_fast_op(op, quirks)) {
+    const uint32_t nn = op & 0xFFu;
+    const bool fx = (op >> 12) == 0xFu &&
+                    (nn == 0x0Au || nn == 0x18u || nn == 0x29u || (nn == 0x1Eu && !(quirks & OCTAX_QUIRK_FX1E_VF)));
+    return fx ? (op | kUopFx) : op;
+  }
   const uint32_t cls = op >> 12, nn = op & 0xFFu;
   uint32_t u = (op & 0xFFFu) | (((op >> 8) & 15u) << 12) | (((op >> 4) & 15u) << 16) | kUopFast;
   auto skip = [](uint32_t src, uint32_t neg) { return (src << 22) | (neg << 21); };
@@ -500,16 +509,15 @@ __device__ __forceinline__ void execute(Regs &R, const Ctx &C, const uint4 u4, i
     uint32_t npc = (pc + (skip ? 4u : 2u)) & 0xFFFu;
     npc = (u & (1u << 24)) ? nnn : npc;
     R.pc = npc;
-    // 8XYN result and flag (N in 0-7, E)
-    const uint32_t sum = vx + vy;
-    const uint32_t a0 = (n & 1u) ? (vx | vy) : vy, a1 = (n & 1u) ? (vx ^ vy) : (vx & vy);
-    const uint32_t b0 = (n & 1u) ? (vx - vy) : sum, b1 = (n & 1u) ? (vy - vx) : (vx >> 1);
-    uint32_t alu = (n & 4u) ? ((n & 2u) ? b1 : b0) : ((n & 2u) ? a1 : a0);
-    alu = (n == 14) ? (vx << 1) : alu;
-    const uint32_t f0 = (n & 1u) ? (uint32_t)(vx >= vy) : (sum >> 8);
-    const uint32_t f1 = (n & 1u) ? (uint32_t)(vy >= vx) : (vx & 1u);
-    uint32_t flag = (n & 2u) ? f1 : f0;
-    flag = (n == 14) ? (vx >> 7) : flag;
+    // 8XYN result and flag (N in 0-7, E) as integer linear combinations, so
+    // the work runs as multiply-adds (stage_game lists the coefficients):
+    // result = c0 vx + c1 vy + c2 (vx & vy) + c3 (vx >> 1), whose low byte is
+    // VX; the carry / NOT-borrow / shifted-out bit is bit 8 of a result + b vx + k.
+    const int4 cr = C.alu[2 * n], cf = C.alu[2 * n + 1];
+    const int32_t ix = (int32_t)vx, iy = (int32_t)vy;
+    const int32_t res = cr.x * ix + cr.y * iy + cr.z * (ix & iy) + cr.w * (ix >> 1);
+    const uint32_t alu = (uint32_t)res;
+    const uint32_t flag = ((uint32_t)(cf.x * res + cf.y * ix + cf.z) >> 8) & 1u;
     // VX write: 6XNN, 7XNN, 8XYN, FX07, FX0A (with a key held)
     uint32_t val = (wk == 2u) ? (vx + nn) : nn;
     val = (wk == 3u) ? alu : val;
@@ -520,6 +528,20 @@ __device__ __forceinline__ void execute(Regs &R, const Ctx &C, const uint4 u4, i
     const uint32_t ik = (u >> 28) & 3u, tk = u >> 30;
     R.I = (ik == 1u) ? nnn : R.I;
     R.dt = (tk == 1u) ? vx : R.dt;
+  } else if (u & kUopFx) {  // FX0A / FX18 / FX1E / FX29: a short branch, not the general switch
+    R.pc = (pc + 2u) & 0xFFFu;
+    uint32_t *const Vx = C.V + u4.y;
+    const uint32_t vx = *Vx, nn = u & 0xFFu;
+    if (nn == 0x0Au) {
+      if (key >= 0) *Vx = (uint32_t)key;
+      else R.pc = pc;
+    } else if (nn == 0x18u) {
+      R.st = vx;
+    } else if (nn == 0x1Eu) {
+      R.I = (R.I + vx) & 0xFFFFu;
+    } else {
+      R.I = 0x50u + 5u * (vx & 15u);
+    }
   } else if ((u >> 12) == 0xDu) {  // DXYN, the most frequent slow opcode: its own branch
     R.pc = (pc + 2u) & 0xFFFu;
     if (kS) draw_schip(R, C, getV(C, (u >> 8) & 15u), getV(C, (u >> 4) & 15u), u & 15u, quirks);
@@ -703,6 +725,7 @@ struct Smem {
   uint8_t *img;
   GameDev *game;
   uint4 *uops;      // micro-op table (fetch_uop)
+  int4 *alu;        // 8XYN coefficients (execute)
   uint2 *lut;       // byte of pixels -> 8 bytes of 0/1
   uint64_t *disp;
   uint32_t *stack;
@@ -710,7 +733,7 @@ struct Smem {
 };
 
 // Shared memory of a CTA with J instances: image | game | decoded opcodes |
-// expansion table | display [W][J] u64 | stack [16][J] u32 | V [16][J] u32,
+// expansion table | 8XYN coefficients | display [W][J] u64 | stack [16][J] u32 | V [16][J] u32,
 // W = 32 (CHIP-8) or 128 (SCHIP).
 template <bool kS>
 __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
@@ -719,7 +742,8 @@ __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
   s.game = reinterpret_cast<GameDev *>(smem + kRamBytes);
   s.uops = reinterpret_cast<uint4 *>(smem + kRamBytes + kGameSmem);
   s.lut = reinterpret_cast<uint2 *>(smem + kRamBytes + kGameSmem + kUopSmem);
-  s.disp = reinterpret_cast<uint64_t *>(smem + kRamBytes + kGameSmem + kUopSmem + kLutSmem);
+  s.alu = reinterpret_cast<int4 *>(smem + kRamBytes + kGameSmem + kUopSmem + kLutSmem);
+  s.disp = reinterpret_cast<uint64_t *>(smem + kRamBytes + kGameSmem + kUopSmem + kLutSmem + kAluSmem);
   s.stack = reinterpret_cast<uint32_t *>(s.disp + Disp<kS>::kWords * J);
   s.V = s.stack + 16 * J;
   return s;
@@ -736,6 +760,24 @@ __device__ __forceinline__ void stage_game(const Smem &S, const GameDev *games, 
   for (int i = threadIdx.x; i < (int)(sizeof(GameDev) / 16); i += blockDim.x) gd[i] = gs[i];
   __syncthreads();
   for (int b = threadIdx.x; b < 256; b += blockDim.x) S.lut[b] = make_uint2(spread4(b & 15u), spread4(b >> 4));
+  if (threadIdx.x < 16) {
+    // per N: {c0, c1, c2, c3} {a, b, k, 0} (see execute); other N are never fast
+    int4 r = make_int4(0, 0, 0, 0), f = make_int4(0, 0, 0, 0);
+    switch (threadIdx.x) {
+      case 0x0: r = make_int4(0, 1, 0, 0); break;                                    // VY
+      case 0x1: r = make_int4(1, 1, -1, 0); break;                                   // x + y - (x & y) = x | y
+      case 0x2: r = make_int4(0, 0, 1, 0); break;                                    // x & y
+      case 0x3: r = make_int4(1, 1, -2, 0); break;                                   // x + y - 2 (x & y) = x ^ y
+      case 0x4: r = make_int4(1, 1, 0, 0); f = make_int4(1, 0, 0, 0); break;         // carry = bit 8 of the sum
+      case 0x5: r = make_int4(1, -1, 0, 0); f = make_int4(1, 0, 256, 0); break;      // NOT borrow: x - y + 256 >= 256
+      case 0x6: r = make_int4(0, 0, 0, 1); f = make_int4(-512, 256, 0, 0); break;    // bit 0: 256 (x - 2 (x >> 1))
+      case 0x7: r = make_int4(-1, 1, 0, 0); f = make_int4(1, 0, 256, 0); break;      // NOT borrow: y - x + 256 >= 256
+      case 0xE: r = make_int4(2, 0, 0, 0); f = make_int4(1, 0, 0, 0); break;         // bit 7 shifted out = bit 8 of 2x
+      default: break;
+    }
+    S.alu[2 * threadIdx.x] = r;
+    S.alu[2 * threadIdx.x + 1] = f;
+  }
   // decode the opcode at every even address of the image once
   for (int w = threadIdx.x; w < kRamBytes / 2; w += blockDim.x) {
     const uint32_t op = ((uint32_t)S.img[2 * w] << 8) | S.img[2 * w + 1];
@@ -822,7 +864,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
     for (int r = 0; r < Disp<kS>::kWords; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, J, S.uops, st.rpl + slot * 16};
+              st.ram + slot * (int64_t)kRamBytes, J, S.uops, S.alu, st.rpl + slot * 16};
   if (mine) load_V(C, st, slot);
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
   __syncwarp();
@@ -1020,7 +1062,7 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
     for (int r = 0; r < 32; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, J, S.uops, st.rpl + slot * 16};
+              st.ram + slot * (int64_t)kRamBytes, J, S.uops, S.alu, st.rpl + slot * 16};
   if (mine) load_V(C, st, slot);
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
 
@@ -1229,7 +1271,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
     load_regs<kS>(R, st, slot);
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, J, S.uops, st.rpl + slot * 16};
+              st.ram + slot * (int64_t)kRamBytes, J, S.uops, S.alu, st.rpl + slot * 16};
   if (doit) reset_instance<true, kS>(R, C, G, p.quirks);
   const unsigned which = __ballot_sync(kFull, doit);
   if (p.obs && which) {
@@ -1406,7 +1448,7 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
 
 size_t step_smem_bytes(int block, int ipw, int schip) {
   const size_t J = (size_t)(block / 32) * ipw;
-  return (size_t)kRamBytes + kGameSmem + kUopSmem + kLutSmem +
+  return (size_t)kRamBytes + kGameSmem + kUopSmem + kLutSmem + kAluSmem +
          J * (disp_words(schip) * sizeof(uint64_t) + 32 * sizeof(uint32_t));
 }
 
