@@ -249,12 +249,14 @@ __device__ __forceinline__ bool is_fast_op(uint32_t op, uint32_t quirks) {
   return fast;
 }
 
-// Decoded form of the opcode at an even image address, built once per CTA.
-// A slow opcode is stored raw (bit 20 clear). A fast one is
-//   bits 0-11 NNN (NN, N in its low bits) | 12-15 X | 16-19 Y | 20 fast |
-//   21 skip negated | 22-23 skip source (1: VX vs NN, 2: VX vs VY, 3: key) |
-//   24 jump | 25-27 VX write (1 NN, 2 VX+NN, 3 8XYN, 4 DT) |
-//   28-29 I write (1 NNN) | 30-31 timer (1 DT) from VX.
+// Decoded form of the opcode at an even image address, built once per CTA
+// (the operands travel beside it: see fetch_uop). A slow opcode is stored raw
+// (bit 20 clear). A fast one has one bit per datapath decision, so that each
+// select tests a single bit:
+//   bits 0-7 NN (N in its low bits) | 19 write VF (8XYN, N >= 4) | 20 fast |
+//   21 skip negated | 22 skip | 23 skip compares VY (else NN) | 24 jump |
+//   25 skip tests the held key | 26 VX = NN | 27 VX += NN | 28 VX = 8XYN |
+//   29 VX = DT | 30 I = NNN | 31 DT = VX.
 constexpr uint32_t kUopFast = 1u << 20;
 // A slow opcode tagged for the short FX branch of execute (FX0A, FX18, FX29 and
 // FX1E without its quirk): bit 21 set on the raw opcode (bit 20 clear).
@@ -268,22 +270,21 @@ __device__ __forceinline__ uint32_t make_uop(uint32_t op, uint32_t quirks) {
     return fx ? (op | kUopFx) : op;
   }
   const uint32_t cls = op >> 12, nn = op & 0xFFu;
-  uint32_t u = (op & 0xFFFu) | (((op >> 8) & 15u) << 12) | (((op >> 4) & 15u) << 16) | kUopFast;
-  auto skip = [](uint32_t src, uint32_t neg) { return (src << 22) | (neg << 21); };
+  uint32_t u = (op & 0xFFu) | kUopFast;
   switch (cls) {
     case 0x1: u |= 1u << 24; break;
-    case 0x3: u |= skip(1, 0); break;
-    case 0x4: u |= skip(1, 1); break;
-    case 0x5: u |= skip(2, 0); break;
-    case 0x9: u |= skip(2, 1); break;
-    case 0x6: u |= 1u << 25; break;
-    case 0x7: u |= 2u << 25; break;
-    case 0x8: u |= 3u << 25; break;
-    case 0xA: u |= 1u << 28; break;
-    case 0xE: u |= skip(3, nn == 0xA1u ? 1u : 0u); break;
+    case 0x3: u |= 1u << 22; break;
+    case 0x4: u |= (1u << 22) | (1u << 21); break;
+    case 0x5: u |= (1u << 22) | (1u << 23); break;
+    case 0x9: u |= (1u << 22) | (1u << 23) | (1u << 21); break;
+    case 0x6: u |= 1u << 26; break;
+    case 0x7: u |= 1u << 27; break;
+    case 0x8: u |= (1u << 28) | ((op & 15u) >= 4u ? (1u << 19) : 0u); break;
+    case 0xA: u |= 1u << 30; break;
+    case 0xE: u |= (1u << 22) | (1u << 25) | (nn == 0xA1u ? (1u << 21) : 0u); break;
     default:  // 0xF
-      if (nn == 0x07u) u |= 4u << 25;
-      else u |= 1u << 30;  // 0x15
+      if (nn == 0x07u) u |= 1u << 29;
+      else u |= 1u << 31;  // 0x15
       break;
   }
   return u;
@@ -501,11 +502,10 @@ __device__ __forceinline__ void execute(Regs &R, const Ctx &C, const uint4 u4, i
     const uint32_t nnn = u4.w, nn = u & 0xFFu, n = u & 15u;
     uint32_t *const Vx = C.V + u4.y;
     const uint32_t vx = *Vx, vy = C.V[u4.z];
-    // next PC: skips, jump, wait-for-key
-    const uint32_t src = (u >> 22) & 3u, wk = (u >> 25) & 7u;
-    const bool pressed = key >= 0 && (uint32_t)key == (vx & 15u);
-    const bool cond = (src == 3u) ? pressed : (vx == ((src == 2u) ? vy : nn));
-    const bool skip = (src != 0u) & (cond != (((u >> 21) & 1u) != 0u));
+    // next PC: skips (bit 22; 23: against VY, 25: against the held key; 21: negated), jump (24)
+    const uint32_t lhs = (u & (1u << 25)) ? (vx & 15u) : vx;
+    const uint32_t rhs = (u & (1u << 25)) ? (uint32_t)key : ((u & (1u << 23)) ? vy : nn);
+    const bool skip = (u & (1u << 22)) && ((lhs == rhs) != ((u & (1u << 21)) != 0u));
     uint32_t npc = (pc + (skip ? 4u : 2u)) & 0xFFFu;
     npc = (u & (1u << 24)) ? nnn : npc;
     R.pc = npc;
@@ -518,16 +518,14 @@ __device__ __forceinline__ void execute(Regs &R, const Ctx &C, const uint4 u4, i
     const int32_t res = cr.x * ix + cr.y * iy + cr.z * (ix & iy) + cr.w * (ix >> 1);
     const uint32_t alu = (uint32_t)res;
     const uint32_t flag = ((uint32_t)(cf.x * res + cf.y * ix + cf.z) >> 8) & 1u;
-    // VX write: 6XNN, 7XNN, 8XYN, FX07, FX0A (with a key held)
-    uint32_t val = (wk == 2u) ? (vx + nn) : nn;
-    val = (wk == 3u) ? alu : val;
-    val = (wk == 4u) ? R.dt : val;
-    if (wk != 0u) *Vx = val & 0xFFu;
-    if ((wk == 3u) & (n >= 4u)) C.V[15 * C.J] = flag;  // after VX: with X = F the flag wins
-    // index register and timers
-    const uint32_t ik = (u >> 28) & 3u, tk = u >> 30;
-    R.I = (ik == 1u) ? nnn : R.I;
-    R.dt = (tk == 1u) ? vx : R.dt;
+    // VX write (26: NN, 27: VX + NN, 28: 8XYN, 29: DT), VF (19), I = NNN (30), DT = VX (31)
+    uint32_t val = (u & (1u << 27)) ? (vx + nn) : nn;
+    val = (u & (1u << 28)) ? alu : val;
+    val = (u & (1u << 29)) ? R.dt : val;
+    if (u & (15u << 26)) *Vx = val & 0xFFu;
+    if (u & (1u << 19)) C.V[15 * C.J] = flag;  // after VX: with X = F the flag wins
+    R.I = (u & (1u << 30)) ? nnn : R.I;
+    R.dt = (u & (1u << 31)) ? vx : R.dt;
   } else if (u & kUopFx) {  // FX0A / FX18 / FX1E / FX29: a short branch, not the general switch
     R.pc = (pc + 2u) & 0xFFFu;
     uint32_t *const Vx = C.V + u4.y;
