@@ -43,7 +43,10 @@ struct alignas(16) GameDev {
 };
 static_assert(sizeof(GameDev) <= 192, "GameDev must fit its shared-memory slot");
 constexpr int kGameSmem = 192;
-constexpr int kUopSmem = kRamBytes / 2 * 16;  // one 16-byte micro-op per even address
+// Micro-op table: one entry per even address, 16 bytes (wide: operand offsets
+// and NNN ready to use) or 8 bytes (narrow: packed; half the shared memory).
+constexpr int kUopSmemWide = kRamBytes / 2 * 16;
+constexpr int kUopSmemNarrow = kRamBytes / 2 * 8;
 constexpr int kLutSmem = 256 * 8;            // byte of pixels -> 8 output bytes
 constexpr int kAluSmem = 16 * 2 * 16;        // 8XYN coefficients per N (two int4)
 
@@ -132,7 +135,9 @@ struct ResetLaunch {
   int set_rows;            // init: out_row = group.row0 + lane, game = group.game
 };
 
-size_t step_smem_bytes(int block, int ipw, int schip);
+// Dynamic shared memory of a step CTA; wide = 16-byte micro-op table (the
+// narrow size is the minimum a launch shape needs).
+size_t step_smem_bytes(int block, int ipw, int schip, int wide = 0);
 // Warp-specialised kernel: `block` emulator threads plus 32 * writers writer threads.
 size_t step_ws_smem_bytes(int block, int ipw);
 size_t max_dynamic_smem();

@@ -26,6 +26,9 @@
 // Each instance runs exactly K instructions per frame, so all lanes of a warp
 // meet at every frame boundary.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstring>
 
 #include "octax_internal.h"
@@ -57,7 +60,7 @@ struct Ctx {
   uint32_t *V;         // shared: this instance's V0; Vx at V[x * J]
   uint8_t *ram;        // global: this instance's 4 KB RAM (dirty pages)
   int J;
-  const uint4 *uops;     // shared: micro-op at every even image address (stage_game)
+  const void *uops;      // shared: micro-op table, uint4 or uint2 entries (stage_game)
   const int4 *alu;       // shared: 8XYN coefficients, two int4 per N (stage_game)
   uint8_t *rpl;          // global: this instance's 16 SCHIP flag bytes
 };
@@ -253,7 +256,7 @@ __device__ __forceinline__ bool is_fast_op(uint32_t op, uint32_t quirks) {
 // (the operands travel beside it: see fetch_uop). A slow opcode is stored raw
 // (bit 20 clear). A fast one has one bit per datapath decision, so that each
 // select tests a single bit:
-//   bits 0-7 NN (N in its low bits) | 19 write VF (8XYN, N >= 4) | 20 fast |
+//   bits 0-11 NNN (NN, N in its low bits) | 19 write VF (8XYN, N >= 4) | 20 fast |
 //   21 skip negated | 22 skip | 23 skip compares VY (else NN) | 24 jump |
 //   25 skip tests the held key | 26 VX = NN | 27 VX += NN | 28 VX = 8XYN |
 //   29 VX = DT | 30 I = NNN | 31 DT = VX.
@@ -270,7 +273,7 @@ __device__ __forceinline__ uint32_t make_uop(uint32_t op, uint32_t quirks) {
     return fx ? (op | kUopFx) : op;
   }
   const uint32_t cls = op >> 12, nn = op & 0xFFu;
-  uint32_t u = (op & 0xFFu) | kUopFast;
+  uint32_t u = (op & 0xFFFu) | kUopFast;
   switch (cls) {
     case 0x1: u |= 1u << 24; break;
     case 0x3: u |= 1u << 22; break;
@@ -485,12 +488,18 @@ __device__ __forceinline__ void exec_slow(Regs &R, const Ctx &C, uint32_t op, ui
   }
 }
 
-// Micro-op of the instruction at pc: from the table, or (odd PC, written
-// page) the raw opcode, which takes the general path. Table entries are
-// {make_uop word, X * J, Y * J, NNN}: the shared-memory offsets of VX and VY
-// come pre-multiplied, so one 16-byte load feeds the datapath.
+// Micro-op of the instruction at pc as {make_uop word, X * J, Y * J, NNN}:
+// the shared-memory offsets of VX and VY come pre-multiplied. kW: the table
+// holds those four words (one 16-byte load); otherwise it holds {word,
+// X * J | Y * J << 16} (half the shared memory, two more extracts). Odd PCs
+// and written pages give the raw opcode, which takes the general path.
+template <bool kW>
 __device__ __forceinline__ uint4 fetch_uop(const Regs &R, const Ctx &C, uint32_t pc) {
-  if (!((pc & 1u) | dirty_bit(R.dirty, pc))) return C.uops[pc >> 1];
+  if (!((pc & 1u) | dirty_bit(R.dirty, pc))) {
+    if (kW) return static_cast<const uint4 *>(C.uops)[pc >> 1];
+    const uint2 e = static_cast<const uint2 *>(C.uops)[pc >> 1];
+    return make_uint4(e.x, e.y & 0xFFFFu, e.y >> 16, e.x & 0xFFFu);
+  }
   return make_uint4((rd8(R, C, pc) << 8) | rd8(R, C, pc + 1u), 0u, 0u, 0u);
 }
 
@@ -551,11 +560,12 @@ __device__ __forceinline__ void execute(Regs &R, const Ctx &C, const uint4 u4, i
 }
 
 // Run `count` instructions.
-template <bool kS>
+template <bool kS, bool kW>
 __device__ __forceinline__ void run_instrs(Regs &R, const Ctx &C, int key, uint32_t quirks,
                                            uint32_t count) {
-#pragma unroll 2
-  for (uint32_t k = 0; k < count; ++k) execute<kS>(R, C, fetch_uop(R, C, R.pc), key, quirks);
+  // Not unrolled: on divergent programs a second copy of the datapath costs
+  // more in instruction fetch than the loop overhead it saves.
+  for (uint32_t k = 0; k < count; ++k) execute<kS>(R, C, fetch_uop<kW>(R, C, R.pc), key, quirks);
 }
 
 __device__ __forceinline__ int32_t term_value(const Regs &R, const Ctx &C, const TermDev &t) {
@@ -600,7 +610,7 @@ __device__ __forceinline__ bool terminated(const Regs &R, const Ctx &C, const Ga
 // K), then the no-op reset wrapper (§3.2): a drawn number of no-key env steps
 // of frameskip frames each, unobserved. The previous action becomes the no-op.
 // kWrap = false compiles the wrapper out (no game of the launch uses it).
-template <bool kWrap, bool kS>
+template <bool kWrap, bool kS, bool kW>
 __device__ __forceinline__ void reset_instance(Regs &R, const Ctx &C, const GameDev &G, uint32_t quirks) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) C.V[i * C.J] = 0;
@@ -629,7 +639,7 @@ __device__ __forceinline__ void reset_instance(Regs &R, const Ctx &C, const Game
   R.draws = 0;
   for (uint32_t i = 0; i < chunks; ++i) {
     const bool partial = i == full && rem != 0u;
-    run_instrs<kS>(R, C, -1, quirks, partial ? rem : G.K);
+    run_instrs<kS, kW>(R, C, -1, quirks, partial ? rem : G.K);
     if (!partial) tick(R);
   }
   R.last_act = G.n_actions;
@@ -722,7 +732,7 @@ __device__ __forceinline__ void write_reset_obs(const uint64_t *disp_warp, int J
 struct Smem {
   uint8_t *img;
   GameDev *game;
-  uint4 *uops;      // micro-op table (fetch_uop)
+  void *uops;       // micro-op table (fetch_uop)
   int4 *alu;        // 8XYN coefficients (execute)
   uint2 *lut;       // byte of pixels -> 8 bytes of 0/1
   uint64_t *disp;
@@ -733,12 +743,13 @@ struct Smem {
 // Shared memory of a CTA with J instances: image | game | decoded opcodes |
 // expansion table | 8XYN coefficients | display [W][J] u64 | stack [16][J] u32 | V [16][J] u32,
 // W = 32 (CHIP-8) or 128 (SCHIP).
-template <bool kS>
+template <bool kS, bool kW>
 __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
+  constexpr int kUopSmem = kW ? kUopSmemWide : kUopSmemNarrow;
   Smem s;
   s.img = smem;
   s.game = reinterpret_cast<GameDev *>(smem + kRamBytes);
-  s.uops = reinterpret_cast<uint4 *>(smem + kRamBytes + kGameSmem);
+  s.uops = smem + kRamBytes + kGameSmem;
   s.lut = reinterpret_cast<uint2 *>(smem + kRamBytes + kGameSmem + kUopSmem);
   s.alu = reinterpret_cast<int4 *>(smem + kRamBytes + kGameSmem + kUopSmem + kLutSmem);
   s.disp = reinterpret_cast<uint64_t *>(smem + kRamBytes + kGameSmem + kUopSmem + kLutSmem + kAluSmem);
@@ -748,6 +759,7 @@ __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
 }
 
 // Every thread of the CTA calls this (it contains a barrier).
+template <bool kW>
 __device__ __forceinline__ void stage_game(const Smem &S, const GameDev *games, const uint8_t *images,
                                            int game, uint32_t quirks, int J) {
   const uint4 *src = reinterpret_cast<const uint4 *>(images + (size_t)game * kRamBytes);
@@ -779,8 +791,9 @@ __device__ __forceinline__ void stage_game(const Smem &S, const GameDev *games, 
   // decode the opcode at every even address of the image once
   for (int w = threadIdx.x; w < kRamBytes / 2; w += blockDim.x) {
     const uint32_t op = ((uint32_t)S.img[2 * w] << 8) | S.img[2 * w + 1];
-    S.uops[w] = make_uint4(make_uop(op, quirks), ((op >> 8) & 15u) * (uint32_t)J, ((op >> 4) & 15u) * (uint32_t)J,
-                           op & 0xFFFu);
+    const uint32_t xo = ((op >> 8) & 15u) * (uint32_t)J, yo = ((op >> 4) & 15u) * (uint32_t)J;
+    if (kW) static_cast<uint4 *>(S.uops)[w] = make_uint4(make_uop(op, quirks), xo, yo, op & 0xFFFu);
+    else static_cast<uint2 *>(S.uops)[w] = make_uint2(make_uop(op, quirks), xo | (yo << 16));
   }
 }
 
@@ -835,7 +848,7 @@ __device__ __forceinline__ void store_V(const Ctx &C, const DevState &st, int64_
   }
 }
 
-template <bool kWrap, bool kS>
+template <bool kWrap, bool kS, bool kW>
 __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
   const int t = threadIdx.x, lane = t & 31, w = t >> 5, ipw = p.ipw;
   const int J = (blockDim.x >> 5) * ipw;  // instances per CTA
@@ -884,7 +897,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
     R.phase = 0;
     for (uint32_t f = 0; f < FS; ++f) {
       if (active) {
-        run_instrs<kS>(R, C, key, quirks, K);
+        run_instrs<kS, kW>(R, C, key, quirks, K);
         tick(R);
       }
       if (f >= first_kept) {
@@ -903,7 +916,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
       io.reward[io_row] = (float)(sc - prev);
       io.done[io_row] = done ? 1 : 0;
       if (done) {
-        reset_instance<kWrap, kS>(R, C, G, quirks);
+        reset_instance<kWrap, kS, kW>(R, C, G, quirks);
         ep = 0;
         prev = score(R, C, G);
       } else {
@@ -931,10 +944,10 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
 }
 
 // One CTA's loop over groups (a persistent CTA pulls them off the queue).
-template <bool kWrap, bool kS>
+template <bool kWrap, bool kS, bool kW>
 __device__ __forceinline__ void step_body(const StepLaunch &p) {
   uint8_t *const smem = g_smem;
-  const Smem S = carve<kS>(smem, (blockDim.x >> 5) * p.ipw);
+  const Smem S = carve<kS, kW>(smem, (blockDim.x >> 5) * p.ipw);
   __shared__ int s_group;
   int cur_game = -1;
   int gi = blockIdx.x;
@@ -947,11 +960,11 @@ __device__ __forceinline__ void step_body(const StepLaunch &p) {
     if (gi >= p.n_groups) break;
     const Group g = p.groups[gi];
     if ((int)g.game != cur_game) {
-      stage_game(S, p.games, p.images, g.game, p.quirks, (blockDim.x >> 5) * p.ipw);
+      stage_game<kW>(S, p.games, p.images, g.game, p.quirks, (blockDim.x >> 5) * p.ipw);
       cur_game = g.game;
     }
     __syncthreads();
-    run_group<kWrap, kS>(p, g, S);
+    run_group<kWrap, kS, kW>(p, g, S);
     __syncthreads();  // shared memory is reused by the next group
     if (!p.work_counter) break;
   }
@@ -962,11 +975,17 @@ __device__ __forceinline__ void step_body(const StepLaunch &p) {
 // cost registers, so games without the wrappers run the variant without
 // them); kS: the Super-CHIP display layout. Those instantiations need more
 // registers and carry no bound.
-__global__ void __launch_bounds__(kMaxBlock, 2) step_kernel_chip8(const StepLaunch p) { step_body<false, false>(p); }
+// kW: 16-byte micro-op table (the launcher picks it where it costs no
+// occupancy; Super-CHIP kernels, whose displays dominate shared memory, use
+// the 8-byte table).
+template <bool kW>
+__global__ void __launch_bounds__(kMaxBlock, 2) step_kernel_chip8(const StepLaunch p) {
+  step_body<false, false, kW>(p);
+}
 
-template <bool kWrap, bool kS>
+template <bool kWrap, bool kS, bool kW>
 __global__ void step_kernel(const StepLaunch p) {
-  step_body<kWrap, kS>(p);
+  step_body<kWrap, kS, kW>(p);
 }
 
 
@@ -1023,7 +1042,7 @@ struct WsSmem {
 // base layout | ring | done flags | barriers
 __device__ __forceinline__ WsSmem carve_ws(uint8_t *smem, int J) {
   WsSmem w;
-  w.base = carve<false>(smem, J);
+  w.base = carve<false, false>(smem, J);
   w.ring = reinterpret_cast<uint64_t *>(w.base.V + 16 * J);
   w.done = reinterpret_cast<uint8_t *>(w.ring + 2 * 32 * J);
   w.full = reinterpret_cast<uint64_t *>(w.done + ((2 * J + 15) & ~15));
@@ -1079,7 +1098,7 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
     R.phase = 0;
     for (uint32_t f = 0; f < FS && !failed; ++f) {
       if (active) {
-        run_instrs<false>(R, C, key, quirks, K);
+        run_instrs<false, false>(R, C, key, quirks, K);
         tick(R);
       }
       if (f >= first_kept) {  // hand the frame to the writers
@@ -1107,7 +1126,7 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
       io.reward[io_row] = (float)(sc - prev);
       io.done[io_row] = done ? 1 : 0;
       if (done) {
-        reset_instance<true, false>(R, C, G, quirks);
+        reset_instance<true, false, false>(R, C, G, quirks);
         ep = 0;
         prev = score(R, C, G);
       } else {
@@ -1226,7 +1245,7 @@ __global__ void step_kernel_ws(const StepLaunch p) {
     if (gi >= p.n_groups) break;
     const Group g = p.groups[gi];
     if ((int)g.game != cur_game) {
-      stage_game(W.base, p.games, p.images, g.game, p.quirks, J);
+      stage_game<false>(W.base, p.games, p.images, g.game, p.quirks, J);
       cur_game = g.game;
     }
     __syncthreads();
@@ -1245,9 +1264,9 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
   const int t = threadIdx.x, lane = t & 31, w = t >> 5, ipw = p.ipw;
   const int J = (blockDim.x >> 5) * ipw;
   const int j = w * ipw + lane;
-  const Smem S = carve<kS>(smem, J);
+  const Smem S = carve<kS, false>(smem, J);
   const Group g = p.groups[blockIdx.x];
-  stage_game(S, p.games, p.images, g.game, p.quirks, J);
+  stage_game<false>(S, p.games, p.images, g.game, p.quirks, J);
   __syncthreads();
   const DevState &st = p.st;
   const int64_t n = st.n;
@@ -1270,7 +1289,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
               st.ram + slot * (int64_t)kRamBytes, J, S.uops, S.alu, st.rpl + slot * 16};
-  if (doit) reset_instance<true, kS>(R, C, G, p.quirks);
+  if (doit) reset_instance<true, kS, false>(R, C, G, p.quirks);
   const unsigned which = __ballot_sync(kFull, doit);
   if (p.obs && which) {
     __syncwarp();
@@ -1444,9 +1463,9 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
 
 }  // namespace
 
-size_t step_smem_bytes(int block, int ipw, int schip) {
+size_t step_smem_bytes(int block, int ipw, int schip, int wide) {
   const size_t J = (size_t)(block / 32) * ipw;
-  return (size_t)kRamBytes + kGameSmem + kUopSmem + kLutSmem + kAluSmem +
+  return (size_t)kRamBytes + kGameSmem + (wide ? kUopSmemWide : kUopSmemNarrow) + kLutSmem + kAluSmem +
          J * (disp_words(schip) * sizeof(uint64_t) + 32 * sizeof(uint32_t));
 }
 
@@ -1471,30 +1490,62 @@ size_t step_ws_smem_bytes(int block, int ipw) {
 static cudaError_t ensure_smem_attr() {
   static bool done = false;
   if (done) return cudaSuccess;
-  const int chip8 = (int)std::min(step_smem_bytes(kMaxBlock, 32, 0), max_dynamic_smem());
-  const int schip = (int)std::min(step_smem_bytes(kMaxBlock, 32, 1), max_dynamic_smem());
-  const void *fns[] = {(const void *)step_kernel_chip8,        (const void *)step_kernel<true, false>,
-                       (const void *)reset_kernel<false>,       (const void *)step_kernel<false, true>,
-                       (const void *)step_kernel<true, true>,   (const void *)reset_kernel<true>};
-  for (int i = 0; i < 6; ++i) {
-    cudaError_t e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, i < 3 ? chip8 : schip);
+  const size_t cap = max_dynamic_smem();
+  auto lim = [&](int schip, int wide) { return (int)std::min(step_smem_bytes(kMaxBlock, 32, schip, wide), cap); };
+  const struct {
+    const void *fn;
+    int smem;
+  } fns[] = {
+      {(const void *)step_kernel_chip8<true>, lim(0, 1)},       {(const void *)step_kernel_chip8<false>, lim(0, 0)},
+      {(const void *)step_kernel<true, false, true>, lim(0, 1)}, {(const void *)step_kernel<true, false, false>, lim(0, 0)},
+      {(const void *)step_kernel<false, true, false>, lim(1, 0)}, {(const void *)step_kernel<true, true, false>, lim(1, 0)},
+      {(const void *)reset_kernel<false>, lim(0, 0)},            {(const void *)reset_kernel<true>, lim(1, 0)},
+      {(const void *)step_kernel_ws, (int)cap}};
+  for (const auto &f : fns) {
+    cudaError_t e = cudaFuncSetAttribute(f.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, f.smem);
     if (e != cudaSuccess) return e;
   }
-  cudaError_t e = cudaFuncSetAttribute(step_kernel_ws, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)max_dynamic_smem());
-  if (e == cudaSuccess) done = true;
-  return e;
+  done = true;
+  return cudaSuccess;
+}
+
+// CHIP-8 step kernel (no writer warps) for a shape: the 16-byte micro-op
+// table when it fits and keeps the narrow table's resident CTAs per SM.
+static bool use_wide(int block, int ipw, int wrappers) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int>, bool> memo;
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_tuple(block, ipw, wrappers);
+  auto it = memo.find(key);
+  if (it != memo.end()) return it->second;
+  const size_t sw = step_smem_bytes(block, ipw, 0, 1), sn = step_smem_bytes(block, ipw, 0, 0);
+  bool wide = false;
+  if (sw <= max_dynamic_smem()) {
+    int ow = 0, on = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &ow, wrappers ? (const void *)step_kernel<true, false, true> : (const void *)step_kernel_chip8<true>, block, sw);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &on, wrappers ? (const void *)step_kernel<true, false, false> : (const void *)step_kernel_chip8<false>, block, sn);
+    wide = ow >= on && ow > 0;
+  }
+  memo[key] = wide;
+  return wide;
 }
 
 // The step kernel instantiation for a launch (null: writer warps on SCHIP).
-static const void *step_fn(const StepLaunch &p) {
+static const void *step_fn(const StepLaunch &p, int block) {
   if (p.writers > 0) return p.st.schip ? nullptr : (const void *)step_kernel_ws;
-  if (p.st.schip) return p.wrappers ? (const void *)step_kernel<true, true> : (const void *)step_kernel<false, true>;
-  return p.wrappers ? (const void *)step_kernel<true, false> : (const void *)step_kernel_chip8;
+  if (p.st.schip)
+    return p.wrappers ? (const void *)step_kernel<true, true, false> : (const void *)step_kernel<false, true, false>;
+  if (use_wide(block, p.ipw, p.wrappers))
+    return p.wrappers ? (const void *)step_kernel<true, false, true> : (const void *)step_kernel_chip8<true>;
+  return p.wrappers ? (const void *)step_kernel<true, false, false> : (const void *)step_kernel_chip8<false>;
 }
 
 static size_t step_fn_smem(const StepLaunch &p, int block) {
-  return p.writers > 0 ? step_ws_smem_bytes(block, p.ipw) : step_smem_bytes(block, p.ipw, p.st.schip);
+  if (p.writers > 0) return step_ws_smem_bytes(block, p.ipw);
+  const int wide = !p.st.schip && use_wide(block, p.ipw, p.wrappers);
+  return step_smem_bytes(block, p.ipw, p.st.schip, wide);
 }
 
 cudaError_t launch_step(const StepLaunch &p, int grid, int block, cudaStream_t s) {
@@ -1502,7 +1553,7 @@ cudaError_t launch_step(const StepLaunch &p, int grid, int block, cudaStream_t s
   cudaError_t e = ensure_smem_attr();
   if (e != cudaSuccess) return e;
   if (grid <= 0) return cudaSuccess;
-  const void *fn = step_fn(p);
+  const void *fn = step_fn(p, block);
   if (!fn) return cudaErrorInvalidValue;
   StepLaunch copy = p;
   void *args[] = {&copy};
@@ -1557,7 +1608,7 @@ cudaError_t add_step_node(cudaGraph_t g, cudaGraphNode_t *node, cudaGraphNode_t 
   if (!state_complete(p.st)) return cudaErrorInvalidValue;
   cudaError_t e = ensure_smem_attr();
   if (e != cudaSuccess) return e;
-  const void *fn = step_fn(p);
+  const void *fn = step_fn(p, block);
   if (!fn) return cudaErrorInvalidValue;
   StepLaunch copy = p;
   void *args[] = {&copy};
@@ -1607,13 +1658,14 @@ int max_resident_ctas(int block, int ipw, int writers, int wrappers, int schip) 
   if (writers > 0)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel_ws, block + 32 * writers,
                                                   step_ws_smem_bytes(block, ipw));
-  else if (schip)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wrappers ? step_kernel<true, true> : step_kernel<false, true>,
-                                                  block, step_smem_bytes(block, ipw, 1));
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wrappers ? (const void *)step_kernel<true, false>
-                                                           : (const void *)step_kernel_chip8,
-                                                  block, step_smem_bytes(block, ipw, 0));
+  else {
+    StepLaunch p;
+    memset(&p, 0, sizeof p);
+    p.st.schip = schip;
+    p.wrappers = wrappers;
+    p.ipw = ipw;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_fn(p, block), block, step_fn_smem(p, block));
+  }
   return sms * per_sm;
 }
 
