@@ -182,6 +182,22 @@ def test_sticky_actions_and_noop_reset(launch):
     assert (la == 4).any() and (la < 4).any()
 
 
+def test_degenerate_games():
+    """Edge cases of the descriptor: no actions (index 0 is the no-op), K = 1
+    with one-frame observations, an episode limit of one step (a reset after
+    every step), and 100,000 startup instructions drawing random numbers."""
+    tp = W.TemplateParams(seed=21)
+    games = [
+        W.replace(W.template_game(tp), action_set=(), instr_per_frame=1, frameskip=1, stack_frames=1),
+        W.replace(W.template_game(tp), instr_per_frame=3, frameskip=1, stack_frames=1, max_episode_steps=1),
+        W.replace(W.random_game(44, frameskip=1), stack_frames=1, startup_instrs=100_000),
+    ]
+    n = 96
+    goe = (np.arange(n) % 3).astype(np.uint16)
+    env, _ = full_compare(games, n, 25, seed=8, action_seed=8, game_of_env=goe, n_actions=3)
+    assert env.get_state()["episode_steps"][goe == 1].max() == 0
+
+
 def test_reward_descriptor_memory_and_transforms():
     """Score from memory bytes written by FX33, several transforms, compound
     termination, truncation."""

@@ -708,3 +708,34 @@ def test_noop_reset_counts(oracle_lib):
         seen.add(frames)
         assert m.m.episode_steps == 0 and m.m.last_action == len(g.action_set)
     assert seen == {4 * k for k in range(6)}
+
+
+def _chi2_uniform(counts) -> float:
+    counts = np.asarray(counts, dtype=np.float64)
+    e = counts.sum() / len(counts)
+    return float(((counts - e) ** 2 / e).sum())
+
+
+def test_rnd_bytes_are_uniform(oracle_lib):
+    """CXNN with NN = FF over 40,000 draws (many instances and steps): the
+    byte histogram passes a chi-square test (255 dof; 99.9 % point ~ 330)."""
+    g = prog([0xC0FF, 0x8104, 0x1200], instr_per_frame=3, frameskip=1, stack_frames=1)  # one draw a step
+    e = oracle_lib.OracleEnv([g], 400, seed=77)
+    e.reset()
+    seen = []
+    for _ in range(100):
+        e.step(np.zeros(400, np.uint8))
+        seen.append(e.records()["V"][:, 0].copy())
+    counts = np.bincount(np.concatenate(seen), minlength=256)
+    assert _chi2_uniform(counts) < 330, counts
+
+
+def test_noop_count_is_uniform(oracle_lib):
+    """No-op reset with max 7: the number of no-op frames over 4,000
+    identities is uniform over 0..7 (7 dof; 99.9 % point ~ 24.3)."""
+    g = prog([0x7001, 0x6401, 0xF415, 0xF407, 0x3400, 0x1206, 0x1200],
+             instr_per_frame=10, frameskip=1, stack_frames=1, max_noops=7)
+    e = oracle_lib.OracleEnv([g], 4000, seed=5)
+    counts = np.bincount(e.records()["V"][:, 0], minlength=8)
+    assert counts.sum() == 4000 and len(counts) == 8
+    assert _chi2_uniform(counts) < 24.3, counts
