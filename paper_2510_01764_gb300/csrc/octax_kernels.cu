@@ -970,21 +970,20 @@ __device__ __forceinline__ void step_body(const StepLaunch &p) {
   }
 }
 
-// The plain CHIP-8 kernel is held to 128 registers so that two 256-thread
-// CTAs fit on an SM. kWrap: the sticky-action / no-op-reset variant (its draws
-// cost registers, so games without the wrappers run the variant without
-// them); kS: the Super-CHIP display layout. Those instantiations need more
-// registers and carry no bound.
+// kWrap: the sticky-action / no-op-reset variant (games without the wrappers
+// run the kernel without them); kS: the Super-CHIP display layout.
 // kW: 16-byte micro-op table (the launcher picks it where it costs no
 // occupancy; Super-CHIP kernels, whose displays dominate shared memory, use
-// the 8-byte table).
+// the 8-byte table). Every step kernel is held to 128 registers (two
+// 256-thread CTAs per SM): unbounded, the wrapper and Super-CHIP
+// instantiations took 157-210 and ran 12-16 % slower.
 template <bool kW>
 __global__ void __launch_bounds__(kMaxBlock, 2) step_kernel_chip8(const StepLaunch p) {
   step_body<false, false, kW>(p);
 }
 
 template <bool kWrap, bool kS, bool kW>
-__global__ void step_kernel(const StepLaunch p) {
+__global__ void __launch_bounds__(kMaxBlock, 2) step_kernel(const StepLaunch p) {
   step_body<kWrap, kS, kW>(p);
 }
 
