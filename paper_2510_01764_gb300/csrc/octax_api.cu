@@ -869,7 +869,7 @@ int octax_autotune(octax_env *e, int n_steps, const uint8_t *actions_dev, float 
   const octax_launch shape = best;
   for (int W : {0, 1, 2, 4})
     for (int pers : {0, 1})
-      for (int spl : {1, 2, 4, 8})
+      for (int spl : {1, 2, 4, 8, 16, 32})
         trial(octax_launch{shape.block, shape.inst_per_warp, spl, pers, 1, W, shape.balance});
   off = 0;
   for (const Piece &pc : pieces) {

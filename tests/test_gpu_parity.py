@@ -431,12 +431,13 @@ def test_config_scale_sampled_writer_warps():
 
 
 def test_config_scale_sampled_balanced():
-    """The full workload with instances spread evenly over whole waves of
-    resident CTAs (the benchmark's CTA shape)."""
+    """The full workload in the launch configuration the benchmark times:
+    256 threads x 7 instances per warp, balanced waves, 32 steps per
+    graph-replayed launch."""
     w = W.cfg_scale()
     sample = pick(w.n_envs, 16, 6, extra=(53, 54, 107, 108, w.n_envs - 1))
     env, n_done = sampled_run(w, chunk=64, sample=sample,
-                              launch=dict(block=256, inst_per_warp=8, steps_per_launch=8,
+                              launch=dict(block=256, inst_per_warp=7, steps_per_launch=32,
                                           persistent=0, use_graph=1, balance=1))
     assert n_done > 0
 
