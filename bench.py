@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -165,10 +166,20 @@ def measured_peaks() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
+def strip_comments(src: str) -> str:
+    """C/C++ source without comments and with whitespace collapsed (string
+    literals in the kernel sources hold no comment markers)."""
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
 def kernel_source_hash() -> str:
+    """Hash of the step kernel's code (comments and layout ignored), which ties
+    a recorded ncu traffic figure to the code it was measured on."""
     h = hashlib.sha256()
     for f in ("octax_kernels.cu", "octax_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_2510_01764_gb300", "csrc", f), "rb").read())
+        h.update(strip_comments(open(os.path.join(ROOT, "paper_2510_01764_gb300", "csrc", f)).read()).encode())
     return h.hexdigest()[:16]
 
 

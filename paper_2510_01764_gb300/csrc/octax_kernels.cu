@@ -4,7 +4,8 @@
 //  - each warp emulates `ipw` instances, one per lane; PC/I/SP/timers/status
 //    and the 64-bit dirty-page mask live in registers; V0-VF (one u32 each),
 //    the call stack and the bit-packed 64x32 display (one u64 per row, bit x =
-//    pixel x) live in shared memory laid out [register|entry|row][instance],
+//    pixel x; Super-CHIP: two u64 per row of the 128x64 buffer) live in
+//    shared memory laid out [register|entry|row][instance],
 //    so lanes touching their own instance never bank-conflict;
 //  - the game's initial 4 KB RAM image (font + ROM) is staged once per CTA in
 //    shared memory and is read-only; an instance's writes go to 64-byte pages
@@ -12,17 +13,21 @@
 //    loads read the shared image unless the page is dirty, and a reset only
 //    clears the mask;
 //  - dispatch limits divergence: the common opcodes (jumps, skips, loads,
-//    adds, ALU, key tests, timer and index ops) run through one branch-free
-//    predicated datapath that every lane executes together; only the rare or
-//    heavy ones (DXYN, CXNN, calls/returns, 00E0, BCD and bulk memory ops,
-//    quirk variants, undefined encodings) take a divergent switch. Every
-//    even address of the image is decoded once per CTA into a 32-bit
-//    micro-op (operand fields plus what the datapath must do), so the hot
-//    loop does one shared load and a few bit tests per instruction;
+//    adds, 8XYN ALU, key tests, FX07/FX15) run through one branch-free
+//    predicated datapath that every lane executes together, with 8XYN as
+//    integer multiply-adds from a per-N coefficient table; DXYN and four FX
+//    forms take short branches, and the rest (CXNN, calls/returns, 00E0, BCD
+//    and bulk memory ops, quirk variants, undefined encodings, the
+//    Super-CHIP forms) a divergent switch. Every even address of the image
+//    is decoded once per CTA into a micro-op (one bit per datapath decision,
+//    NNN, and the pre-multiplied shared-memory offsets of VX and VY), so the
+//    hot loop does one or two shared loads and single-bit tests per
+//    instruction;
 //  - observation frames are expanded from the packed rows by the whole warp
 //    together (a byte of pixels becomes 8 bytes through a 256-entry table in
 //    shared memory): every store is a 16-byte streaming store and each store
-//    instruction writes eight complete 64-byte image rows.
+//    instruction writes eight complete 64-byte image rows (CHIP-8) or four
+//    128-byte rows (Super-CHIP).
 // Each instance runs exactly K instructions per frame, so all lanes of a warp
 // meet at every frame boundary.
 #include <algorithm>
