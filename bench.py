@@ -228,6 +228,7 @@ def record_traffic(csv_path: str, config: str, launch: str, units: int) -> dict:
         "dram_bytes_per_instance_step": traffic / units,
         "warp_inst_per_instance_step": mean("smsp__inst_executed.sum") / units,
         "active_threads_per_warp_inst": mean("smsp__thread_inst_executed_per_inst_executed.ratio"),
+        "branch_uniform_pct": mean("smsp__sass_average_branch_targets_threads_uniform.pct"),
         "captured_duration_s": mean("gpu__time_duration.sum"),
         "note": "ncu --set full --clock-control none; DRAM write bytes exclude observation "
                 "lines still in L2 at kernel exit",
@@ -361,6 +362,8 @@ def run_gpu(args) -> dict | None:
                  "unit": "G warp-instr/s", "frac": round(got / peak_issue, 4),
                  "divergence_efficiency": (round(prof["active_threads_per_warp_inst"] / 32, 4)
                                            if "active_threads_per_warp_inst" in prof else None),
+                 "branch_efficiency": (round(prof["branch_uniform_pct"] / 100, 4)
+                                       if "branch_uniform_pct" in prof else None),
                  "source": "ncu instruction count per instance-step (profiles/traffic.json) x "
                            "instance-steps per launch / live launch time; peak = SMs x 4 x median SM clock"}
     line = {
