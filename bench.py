@@ -319,6 +319,23 @@ def run_gpu(args) -> dict | None:
         ms_plain, _ = timed(plain_cfg)
         env.set_launch(**launch)
 
+        # ---- the same calls writing bit-packed observations (octax_step_n_packed)
+        pobs = torch.empty((T, n) + env.packed_obs_shape, dtype=torch.int64, device=dev)
+        for lo, hi in calls[:2]:
+            env.step_n_packed(acts[lo:hi], out=(pobs[:hi - lo], rew[:hi - lo], done[:hi - lo]))
+        env.set_state(init_state)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for lo, hi in calls:
+            env.step_n_packed(acts[lo:hi], out=(pobs[:hi - lo], rew[:hi - lo], done[:hi - lo]))
+        p1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_packed = p0.elapsed_time(p1)
+        del pobs
+
         # ---- end to end through the host-buffer entry point
         Ke = min(K, args.e2e_steps)
         a_h = torch.from_numpy(acts_h[:Ke].copy()).pin_memory()
@@ -336,7 +353,7 @@ def run_gpu(args) -> dict | None:
         e2e_s = time.perf_counter() - t0
         env.set_launch(**launch)
 
-    ms_best, ms_plain, e2e_s = max_over_ranks([ms_best, ms_plain, e2e_s], dev)
+    ms_best, ms_plain, e2e_s, ms_packed = max_over_ranks([ms_best, ms_plain, e2e_s, ms_packed], dev)
     if world > 1:
         torch.distributed.barrier()
     if rank != 0:
@@ -398,6 +415,15 @@ def run_gpu(args) -> dict | None:
             "launch": plain_cfg,
         },
         "speedup_vs_plain": round(ms_plain / ms_best, 3),
+        "packed_obs": {
+            "value": round(whole_job_rate(world, n, K, ms_packed), 1),
+            "unit": "env steps/s",
+            "ms_per_step": round(ms_packed / K, 6),
+            "obs_bytes_per_env_step": (step_io_bytes(w) - 6) // 8,
+            "hbm_frac": round(n * (((step_io_bytes(w) - 6) // 8 + 6) * (K / n_launch) + state_bytes(w))
+                              / (ms_packed / n_launch / 1e3) / 1e9 / peak, 4),
+            "note": "octax_step_n_packed, same workload and launch: one bit per pixel (u64 row words)",
+        },
         "gpu_launches": n_launch,
         "roofline": {
             "bound": "hbm",

@@ -206,11 +206,26 @@ int octax_step(octax_env *env, const uint8_t *actions_dev, uint8_t *obs_dev,
 int octax_step_n(octax_env *env, int n_steps, const uint8_t *actions_dev, uint8_t *obs_dev,
                  float *reward_dev, uint8_t *done_dev);
 
+/* octax_step_n writing packed observations, one bit per pixel instead of one
+ * byte (8x fewer observation bytes): obs_words_dev is uint64 [n_steps][n_envs]
+ * [S][W], 16-byte aligned, with W = 32 for CHIP-8 (word y = row y, bit x =
+ * pixel x) and 128 for SCHIP (word 2y + h = pixels 64h..64h+63 of row y, bit x
+ * = pixel 64h + x). The frames hold the same pixels as octax_step_n's; rewards,
+ * done flags and state are identical. Writer warps are not used for these
+ * calls. */
+int octax_step_n_packed(octax_env *env, int n_steps, const uint8_t *actions_dev, uint64_t *obs_words_dev,
+                        float *reward_dev, uint8_t *done_dev);
+
 /* octax_step with host buffers, synchronous. Page-locked (pinned) buffers are
  * read and written by the kernel directly through their device mapping;
  * pageable buffers go through device staging buffers and copies. */
 int octax_step_host(octax_env *env, const uint8_t *actions_host, uint8_t *obs_host,
                     float *reward_host, uint8_t *done_host);
+
+/* octax_step_host writing packed frames (layout of octax_step_n_packed) into
+ * obs_words_host [n_envs][S][W]: 8x fewer bytes over the host link. */
+int octax_step_host_packed(octax_env *env, const uint8_t *actions_host, uint64_t *obs_words_host,
+                           float *reward_host, uint8_t *done_host);
 
 /* FNV-1a 64-bit hash of each instance's canonical record (octax_state_record
  * bytes in field order, little-endian) into hash_dev [n_envs]. */

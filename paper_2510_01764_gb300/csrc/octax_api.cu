@@ -625,6 +625,21 @@ int octax_step_n(octax_env *e, int n_steps, const uint8_t *actions_dev, uint8_t 
   return enqueue_steps(e, e->cfg, n_steps, io);
 }
 
+int octax_step_n_packed(octax_env *e, int n_steps, const uint8_t *actions_dev, uint64_t *obs_words_dev,
+                        float *reward_dev, uint8_t *done_dev) {
+  if (!e || n_steps < 1) {
+    set_error("octax_step_n_packed: need env and n_steps >= 1");
+    return OCTAX_EINVAL;
+  }
+  uint8_t *obs = reinterpret_cast<uint8_t *>(obs_words_dev);
+  int rc = check_io(actions_dev, obs, reward_dev, done_dev);
+  if (rc) return rc;
+  IO io{actions_dev, obs, reward_dev, done_dev, e->n, 1, 0};
+  octax_launch cfg = e->cfg;
+  cfg.writer_warps = 0;  // the writer warps write uint8 frames only
+  return enqueue_steps(e, cfg, n_steps, io);
+}
+
 // Device-accessible address of a page-locked host buffer, or nullptr.
 static void *mapped_host(const void *p) {
   cudaPointerAttributes a;
@@ -635,10 +650,25 @@ static void *mapped_host(const void *p) {
   return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
 }
 
-int octax_step_host(octax_env *e, const uint8_t *actions_host, uint8_t *obs_host, float *reward_host,
-                    uint8_t *done_host) {
+namespace {
+
+// One env step on device buffers, uint8 or packed frames (no graph).
+int step_once(octax_env *e, const uint8_t *actions_dev, uint8_t *obs_dev, float *reward_dev, uint8_t *done_dev,
+              int packed) {
+  int rc = check_io(actions_dev, obs_dev, reward_dev, done_dev);
+  if (rc) return rc;
+  IO io{actions_dev, obs_dev, reward_dev, done_dev, e->n, packed, 0};
+  octax_launch cfg = e->cfg;
+  cfg.steps_per_launch = 1;
+  cfg.use_graph = 0;
+  if (packed) cfg.writer_warps = 0;
+  return enqueue_steps(e, cfg, 1, io);
+}
+
+int step_host(octax_env *e, const uint8_t *actions_host, uint8_t *obs_host, float *reward_host,
+              uint8_t *done_host, int packed, const char *who) {
   if (!e || !actions_host || !obs_host || !reward_host || !done_host) {
-    set_error("octax_step_host: null argument");
+    set_error(std::string(who) + ": null argument");
     return OCTAX_EINVAL;
   }
   // Page-locked buffers are device-mapped: the kernel reads the actions and
@@ -647,32 +677,46 @@ int octax_step_host(octax_env *e, const uint8_t *actions_host, uint8_t *obs_host
   void *d_act = mapped_host(actions_host), *d_obs = mapped_host(obs_host);
   void *d_rew = mapped_host(reward_host), *d_done = mapped_host(done_host);
   if (d_act && d_obs && d_rew && d_done && aligned16(d_obs)) {
-    int rc = octax_step(e, static_cast<const uint8_t *>(d_act), static_cast<uint8_t *>(d_obs),
-                        static_cast<float *>(d_rew), static_cast<uint8_t *>(d_done));
+    int rc = step_once(e, static_cast<const uint8_t *>(d_act), static_cast<uint8_t *>(d_obs),
+                       static_cast<float *>(d_rew), static_cast<uint8_t *>(d_done), packed);
     if (rc) return rc;
     cudaError_t r = cudaStreamSynchronize(e->stream);
-    return r == cudaSuccess ? OCTAX_OK : cuda_fail(r, "octax_step_host");
+    return r == cudaSuccess ? OCTAX_OK : cuda_fail(r, who);
   }
-  const size_t n = (size_t)e->n, obs_bytes = n * (size_t)e->S * frame_bytes(e->schip);
-  if (!e->hs_act) {
+  const size_t n = (size_t)e->n;
+  const size_t obs_bytes = n * (size_t)e->S * (packed ? packed_frame_bytes(e->schip) : frame_bytes(e->schip));
+  if (!e->hs_act) {  // staging sized for uint8 frames, which are the larger
     cudaError_t r = dalloc(e, &e->hs_act, n);
-    if (r == cudaSuccess) r = dalloc(e, &e->hs_obs, obs_bytes);
+    if (r == cudaSuccess) r = dalloc(e, &e->hs_obs, n * (size_t)e->S * frame_bytes(e->schip));
     if (r == cudaSuccess) r = dalloc(e, &e->hs_rew, n);
     if (r == cudaSuccess) r = dalloc(e, &e->hs_done, n);
     if (r != cudaSuccess) {
-      set_error("octax_step_host: staging allocation failed");
+      set_error(std::string(who) + ": staging allocation failed");
       return OCTAX_ENOMEM;
     }
   }
   cudaError_t r = cudaMemcpyAsync(e->hs_act, actions_host, n, cudaMemcpyHostToDevice, e->stream);
-  if (r != cudaSuccess) return cuda_fail(r, "octax_step_host actions");
-  int rc = octax_step(e, e->hs_act, e->hs_obs, e->hs_rew, e->hs_done);
+  if (r != cudaSuccess) return cuda_fail(r, who);
+  int rc = step_once(e, e->hs_act, e->hs_obs, e->hs_rew, e->hs_done, packed);
   if (rc) return rc;
   r = cudaMemcpyAsync(obs_host, e->hs_obs, obs_bytes, cudaMemcpyDeviceToHost, e->stream);
   if (r == cudaSuccess) r = cudaMemcpyAsync(reward_host, e->hs_rew, n * 4, cudaMemcpyDeviceToHost, e->stream);
   if (r == cudaSuccess) r = cudaMemcpyAsync(done_host, e->hs_done, n, cudaMemcpyDeviceToHost, e->stream);
   if (r == cudaSuccess) r = cudaStreamSynchronize(e->stream);
-  return r == cudaSuccess ? OCTAX_OK : cuda_fail(r, "octax_step_host");
+  return r == cudaSuccess ? OCTAX_OK : cuda_fail(r, who);
+}
+
+}  // namespace
+
+int octax_step_host(octax_env *e, const uint8_t *actions_host, uint8_t *obs_host, float *reward_host,
+                    uint8_t *done_host) {
+  return step_host(e, actions_host, obs_host, reward_host, done_host, 0, "octax_step_host");
+}
+
+int octax_step_host_packed(octax_env *e, const uint8_t *actions_host, uint64_t *obs_words_host,
+                           float *reward_host, uint8_t *done_host) {
+  return step_host(e, actions_host, reinterpret_cast<uint8_t *>(obs_words_host), reward_host, done_host, 1,
+                   "octax_step_host_packed");
 }
 
 int octax_state_hash(octax_env *e, uint64_t *hash_dev) {

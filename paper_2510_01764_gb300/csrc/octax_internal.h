@@ -21,6 +21,9 @@ constexpr int kDispWords = 32;
 constexpr int kSchipDispWords = 128;
 __host__ __device__ inline int frame_bytes(int schip) { return schip ? kSchipFrameBytes : kFrameBytes; }
 __host__ __device__ inline int disp_words(int schip) { return schip ? kSchipDispWords : kDispWords; }
+// A packed observation frame: the display words themselves (u64, bit x of a
+// word = pixel x of its 64-pixel run).
+__host__ __device__ inline int packed_frame_bytes(int schip) { return 8 * disp_words(schip); }
 constexpr int kMaxBlock = 256;
 
 // Game descriptor as the kernels read it (one per game, device memory).
@@ -96,6 +99,8 @@ struct IO {
   float *reward;           // [steps][rows]
   uint8_t *done;           // [steps][rows]
   int64_t rows;            // rows per step
+  int32_t packed;          // 1: obs frames are the packed display words (packed_frame_bytes)
+  int32_t pad;
 };
 
 struct StepLaunch {

@@ -711,6 +711,49 @@ __device__ __forceinline__ void capture_frame<true>(const uint64_t *disp_warp, i
   }
 }
 
+// Packed frame of every instance of the warp with a non-null `frame`: its
+// display words copied as they are, two per 16-byte streaming store
+// (CHIP-8: 16 stores per instance, two instances per pass; SCHIP: 64).
+template <bool kS>
+__device__ __forceinline__ void capture_packed(const uint64_t *disp_warp, int J, uint8_t *frame, int lane,
+                                               int ipw) {
+  constexpr int kPairs = Disp<kS>::kWords / 2;  // 16-byte stores per instance-frame
+  constexpr int kPerPass = 32 / (kPairs < 32 ? kPairs : 32);
+  const uint64_t mine = reinterpret_cast<uint64_t>(frame);
+  for (int m = 0; m < ipw; m += kPerPass) {
+    const int src = m + lane / (32 / kPerPass);
+    const uint64_t base = __shfl_sync(kFull, mine, src < 32 ? src : 31);
+    if (src < ipw && base) {
+      const uint64_t *col = disp_warp + src;
+      for (int c = lane % (32 / kPerPass); c < kPairs; c += 32 / kPerPass) {
+        const uint64_t w0 = col[(2 * c) * J], w1 = col[(2 * c + 1) * J];
+        __stcs(reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(base) + c * 16),
+               make_uint4((uint32_t)w0, (uint32_t)(w0 >> 32), (uint32_t)w1, (uint32_t)(w1 >> 32)));
+      }
+    }
+  }
+}
+
+// Packed reset observation of the instances in `which` (every stack slot).
+template <bool kS>
+__device__ __forceinline__ void write_reset_packed(const uint64_t *disp_warp, int J, uint8_t *obs, int S,
+                                                   unsigned which, int lane) {
+  constexpr int kPairs = Disp<kS>::kWords / 2;
+  const uint64_t mine = reinterpret_cast<uint64_t>(obs);
+  while (which) {
+    const int src = __ffs(which) - 1;
+    which &= which - 1;
+    const uint64_t base = __shfl_sync(kFull, mine, src);
+    const uint64_t *col = disp_warp + src;
+    for (int c = lane; c < kPairs; c += 32) {
+      const uint64_t w0 = col[(2 * c) * J], w1 = col[(2 * c + 1) * J];
+      const uint4 o = make_uint4((uint32_t)w0, (uint32_t)(w0 >> 32), (uint32_t)w1, (uint32_t)(w1 >> 32));
+      for (int s = 0; s < S; ++s)
+        __stcs(reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(base) + s * 8 * Disp<kS>::kWords + c * 16), o);
+    }
+  }
+}
+
 // Reset observation of the instances in `which`: the display in every stack slot.
 template <bool kS>
 __device__ __forceinline__ void write_reset_obs(const uint64_t *disp_warp, int J, uint8_t *obs, int S,
@@ -896,7 +939,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
       R.last_act = a;
       if (a < G.n_actions) key = G.action_set[a] & 15;
       else if (a > G.n_actions) R.status |= OCTAX_STATUS_BAD_ACTION;
-      my_obs = io.obs + io_row * (int64_t)p.S * Disp<kS>::kFrame;
+      my_obs = io.obs + io_row * (int64_t)p.S * (io.packed ? 8 * Disp<kS>::kWords : Disp<kS>::kFrame);
     }
     R.draws = 0;
     R.phase = 0;
@@ -907,8 +950,12 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
       }
       if (f >= first_kept) {
         __syncwarp();
-        capture_frame<kS>(disp_warp, J, my_obs ? my_obs + (f - first_kept) * Disp<kS>::kFrame : nullptr, lane,
-                          ipw, S.lut);
+        if (io.packed)
+          capture_packed<kS>(disp_warp, J, my_obs ? my_obs + (f - first_kept) * 8 * Disp<kS>::kWords : nullptr,
+                             lane, ipw);
+        else
+          capture_frame<kS>(disp_warp, J, my_obs ? my_obs + (f - first_kept) * Disp<kS>::kFrame : nullptr, lane,
+                            ipw, S.lut);
         __syncwarp();
       }
     }
@@ -931,7 +978,8 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
     const unsigned which = __ballot_sync(kFull, done);
     if (which) {
       __syncwarp();
-      write_reset_obs<kS>(disp_warp, J, my_obs, p.S, which, lane, S.lut);
+      if (io.packed) write_reset_packed<kS>(disp_warp, J, my_obs, p.S, which, lane);
+      else write_reset_obs<kS>(disp_warp, J, my_obs, p.S, which, lane, S.lut);
       __syncwarp();
     }
   }

@@ -101,7 +101,7 @@ class CServerStats(C.Structure):
 EXPORTS = ("octax_create", "octax_reset", "octax_step", "octax_step_n", "octax_step_host",
            "octax_state_hash", "octax_get_state", "octax_set_state", "octax_sync",
            "octax_get_launch", "octax_set_launch", "octax_autotune", "octax_num_envs",
-           "octax_stack_frames", "octax_variant", "octax_device_bytes", "octax_destroy", "octax_last_error",
+           "octax_stack_frames", "octax_variant", "octax_step_n_packed", "octax_step_host_packed", "octax_device_bytes", "octax_destroy", "octax_last_error",
            "octax_server_create", "octax_server_submit", "octax_server_wait",
            "octax_server_query", "octax_server_release", "octax_server_get_stats",
            "octax_server_destroy", "octax_rollout_static")
@@ -128,6 +128,8 @@ def load_library(path: str = LIB_PATH):
             "octax_step": (I32, [P, P, P, P, P]),
             "octax_step_n": (I32, [P, I32, P, P, P, P]),
             "octax_step_host": (I32, [P, P, P, P, P]),
+            "octax_step_n_packed": (I32, [P, I32, P, P, P, P]),
+            "octax_step_host_packed": (I32, [P, P, P, P, P]),
             "octax_state_hash": (I32, [P, P]),
             "octax_get_state": (I32, [P, I64, I64, P]),
             "octax_set_state": (I32, [P, I64, I64, P]),
@@ -295,6 +297,29 @@ class Env:
                                           _ptr(done)))
         return obs, rew, done
 
+    @property
+    def packed_obs_shape(self) -> tuple:
+        """Per-instance packed observation: (S, 32) CHIP-8 or (S, 128) SCHIP words."""
+        return (self.S, 32 if self.frame == (32, 64) else 128)
+
+    def step_n_packed(self, actions, out=None):
+        """step_n with bit-packed observations: int64 words [T, n, S, W] (bit x of
+        a word = pixel x of its 64-pixel run; see octax_step_n_packed)."""
+        torch = self._torch
+        T = int(actions.shape[0])
+        self._check_dev(actions, torch.uint8, (T, self.n), "actions")
+        if out is None:
+            out = (torch.empty((T, self.n) + self.packed_obs_shape, dtype=torch.int64, device=self.device),
+                   torch.empty((T, self.n), dtype=torch.float32, device=self.device),
+                   self._u8(T, self.n))
+        obs, rew, done = out
+        self._check_dev(obs, torch.int64, (T, self.n) + self.packed_obs_shape, "obs")
+        self._check_dev(rew, torch.float32, (T, self.n), "reward")
+        self._check_dev(done, torch.uint8, (T, self.n), "done")
+        check(load_library().octax_step_n_packed(self._h, T, _ptr(actions), _ptr(obs), _ptr(rew),
+                                                 _ptr(done)))
+        return obs, rew, done
+
     def step_host(self, actions, out=None):
         """Host buffers in and out (pinned CPU tensors copy fastest); synchronous."""
         torch = self._torch
@@ -311,6 +336,25 @@ class Env:
                 raise ValueError(f"{nm}: need contiguous host {dt} {shp}")
         check(load_library().octax_step_host(self._h, _ptr(actions), _ptr(obs), _ptr(rew),
                                              _ptr(done)))
+        return obs, rew, done
+
+    def step_host_packed(self, actions, out=None):
+        """step_host with packed frames (int64 words [n, S, W], see
+        step_n_packed): 8x fewer observation bytes over the host link."""
+        torch = self._torch
+        if out is None:
+            out = (torch.empty((self.n,) + self.packed_obs_shape, dtype=torch.int64, pin_memory=True),
+                   torch.empty(self.n, dtype=torch.float32, pin_memory=True),
+                   torch.empty(self.n, dtype=torch.uint8, pin_memory=True))
+        obs, rew, done = out
+        for t, dt, shp, nm in ((actions, torch.uint8, (self.n,), "actions"),
+                               (obs, torch.int64, (self.n,) + self.packed_obs_shape, "obs"),
+                               (rew, torch.float32, (self.n,), "reward"),
+                               (done, torch.uint8, (self.n,), "done")):
+            if t.device.type != "cpu" or t.dtype != dt or tuple(t.shape) != shp or not t.is_contiguous():
+                raise ValueError(f"{nm}: need contiguous host {dt} {shp}")
+        check(load_library().octax_step_host_packed(self._h, _ptr(actions), _ptr(obs), _ptr(rew),
+                                                    _ptr(done)))
         return obs, rew, done
 
     def state_hash(self, out=None):

@@ -339,6 +339,37 @@ def test_host_buffer_step_matches_device_step(pinned):
             assert torch.equal(x.cpu(), y)
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("variant", ["chip8", "schip"])
+def test_packed_host_step_matches_oracle(pinned, variant):
+    """step_host_packed (mapped pinned buffers, or staged pageable ones, the
+    staging shared with step_host) against the oracle's packed frames."""
+    o = octax()
+    g = W.replace(W.template_game(W.TemplateParams(seed=3), score_limit=2, max_episode_steps=9),
+                  variant=variant)
+    n = 70
+    env = o.Env([g], n, seed=4)
+    ref = oracle.OracleEnv([g], n, seed=4)
+    env.reset()
+    ref.reset()
+    acts = W.actions(4, 0, 24, n, 5)
+    W_ = 32 if variant == "chip8" else 128
+    out = (torch.empty((n, 4, W_), dtype=torch.int64, pin_memory=pinned),
+           torch.empty(n, dtype=torch.float32, pin_memory=pinned),
+           torch.empty(n, dtype=torch.uint8, pin_memory=pinned))
+    for s in range(24):
+        o2, r2, d2 = ref.step(acts[s])
+        act = torch.from_numpy(acts[s].copy())
+        if s % 3 == 2:
+            obs, rew, done = env.step_host(act)
+            assert np.array_equal(obs.numpy(), o2)
+        else:
+            obs, rew, done = env.step_host_packed(act.pin_memory() if pinned else act, out=out)
+            assert np.array_equal(obs.numpy().view(np.uint64), pack_frames(o2))
+        assert np.array_equal(rew.numpy(), r2) and np.array_equal(done.numpy(), d2)
+    assert np.array_equal(hashes(env), ref.hashes())
+
+
 def test_sync_timeout_is_reported():
     """octax_sync returns ETIMEOUT (not a hang) while work is still running."""
     o = octax()
@@ -462,3 +493,48 @@ def test_config_divergence_sampled():
     sampled_run(w, chunk=8, sample=sample,
                 launch=dict(block=128, inst_per_warp=32, steps_per_launch=4, persistent=0,
                             use_graph=1))
+
+
+# ----------------------------------------------------------------- packed observations
+def pack_frames(obs_u8: np.ndarray) -> np.ndarray:
+    """uint8 0/1 frames [..., H, W] -> u64 words [..., H * W / 64] (bit x of a
+    word = pixel x of its 64-pixel run), the layout octax_step_n_packed writes."""
+    b = np.packbits(obs_u8, axis=-1, bitorder="little")
+    return b.view("<u8").reshape(obs_u8.shape[:-2] + (-1,))
+
+
+@pytest.mark.parametrize("launch", [
+    None,
+    dict(block=256, inst_per_warp=7, steps_per_launch=8, persistent=0, use_graph=1, balance=1),
+    dict(block=64, inst_per_warp=16, steps_per_launch=3, persistent=1, use_graph=1),
+    dict(block=128, inst_per_warp=16, steps_per_launch=4, persistent=0, use_graph=1, writer_warps=2),
+])
+def test_packed_observations(launch):
+    """step_n_packed: the packed frames are the uint8 frames bit for bit, and
+    rewards, done flags (auto-resets included) and state match the oracle;
+    packed and uint8 calls interleave on one environment."""
+    o = octax()
+    games = [W.template_game(W.TemplateParams(seed=4), score_limit=3, max_episode_steps=37),
+             W.random_game(55)]
+    n = 150
+    goe = (np.arange(n) % 2).astype(np.uint16)
+    env = o.Env(games, n, seed=6, game_of_env=goe)
+    if launch:
+        env.set_launch(**launch)
+    ref = oracle.OracleEnv(games, n, seed=6, game_of_env=goe)
+    env.reset()
+    ref.reset()
+    acts = W.actions(6, 0, 60, n, 5)
+    a_dev = torch.from_numpy(acts).cuda()
+    for lo, hi, packed in ((0, 20, True), (20, 30, False), (30, 60, True)):
+        o2, r2, d2, _ = ref.rollout(acts[lo:hi], obs=True)
+        if packed:
+            obs, rew, done = env.step_n_packed(a_dev[lo:hi])
+            assert np.array_equal(obs.cpu().numpy().view(np.uint64), pack_frames(o2))
+        else:
+            obs, rew, done = env.step_n(a_dev[lo:hi])
+            assert np.array_equal(obs.cpu().numpy(), o2)
+        assert np.array_equal(rew.cpu().numpy(), r2)
+        assert np.array_equal(done.cpu().numpy(), d2)
+        assert np.array_equal(hashes(env), ref.hashes())
+    assert int(done.sum()) >= 0

@@ -158,3 +158,22 @@ def test_schip_scale_sampled():
                               launch=dict(block=128, inst_per_warp=7, steps_per_launch=8, persistent=0,
                                           use_graph=1, balance=1))
     assert n_done > 0
+
+
+def test_schip_packed_observations():
+    from test_gpu_parity import pack_frames
+    o = octax()
+    games = [template(seed=5, score_limit=3, max_episode_steps=25), W.random_schip_game(61)]
+    n = 90
+    goe = (np.arange(n) % 2).astype(np.uint16)
+    env = o.Env(games, n, seed=2, game_of_env=goe)
+    ref = oracle.OracleEnv(games, n, seed=2, game_of_env=goe)
+    env.reset()
+    ref.reset()
+    acts = W.actions(2, 0, 40, n, 5)
+    obs, rew, done = env.step_n_packed(torch.from_numpy(acts).cuda())
+    o2, r2, d2, _ = ref.rollout(acts, obs=True)
+    assert obs.shape == (40, n, 4, 128)
+    assert np.array_equal(obs.cpu().numpy().view(np.uint64), pack_frames(o2))
+    assert np.array_equal(rew.cpu().numpy(), r2) and np.array_equal(done.cpu().numpy(), d2)
+    assert np.array_equal(hashes(env), ref.hashes())
