@@ -351,9 +351,21 @@ def run_gpu(args) -> dict | None:
         for s in range(Ke):
             env.step_host(a_h[s], out=(o_h, r_h, d_h))
         e2e_s = time.perf_counter() - t0
+        # the same through the packed host-buffer entry point
+        po_h = torch.empty((n,) + env.packed_obs_shape, dtype=torch.int64, pin_memory=True)
+        env.set_state(init_state)
+        for s in range(min(3, Ke)):
+            env.step_host_packed(a_h[s], out=(po_h, r_h, d_h))
+        env.set_state(init_state)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for s in range(Ke):
+            env.step_host_packed(a_h[s], out=(po_h, r_h, d_h))
+        e2e_packed_s = time.perf_counter() - t0
         env.set_launch(**launch)
 
-    ms_best, ms_plain, e2e_s, ms_packed = max_over_ranks([ms_best, ms_plain, e2e_s, ms_packed], dev)
+    ms_best, ms_plain, e2e_s, ms_packed, e2e_packed_s = max_over_ranks(
+        [ms_best, ms_plain, e2e_s, ms_packed, e2e_packed_s], dev)
     if world > 1:
         torch.distributed.barrier()
     if rank != 0:
@@ -422,6 +434,10 @@ def run_gpu(args) -> dict | None:
             "obs_bytes_per_env_step": (step_io_bytes(w) - 6) // 8,
             "hbm_frac": round(n * (((step_io_bytes(w) - 6) // 8 + 6) * (K / n_launch) + state_bytes(w))
                               / (ms_packed / n_launch / 1e3) / 1e9 / peak, 4),
+            "e2e": {"value": round(world * n * Ke / e2e_packed_s, 1), "unit": "env steps/s", "steps": Ke,
+                    "h2d_bytes_per_step": n,
+                    "d2h_bytes_per_step": n * ((step_io_bytes(w) - 6) // 8 + 5),
+                    "entry": "octax_step_host_packed"},
             "note": "octax_step_n_packed, same workload and launch: one bit per pixel (u64 row words)",
         },
         "gpu_launches": n_launch,
