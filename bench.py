@@ -83,7 +83,7 @@ def whole_job_rate(world: int, n_envs: int, steps: int, ms: float) -> float:
 
 def workload(name: str) -> W.Workload:
     return {"scale": W.cfg_scale, "small": W.cfg_small, "batch": W.cfg_batch,
-            "divergence": W.cfg_divergence, "schip": W.cfg_schip}[name]()
+            "divergence": W.cfg_divergence, "schip": W.cfg_schip, "shooter": W.cfg_shooter}[name]()
 
 
 def describe(config: str, w: W.Workload) -> str:
@@ -98,7 +98,16 @@ def describe(config: str, w: W.Workload) -> str:
         "schip": f"schip-scale: {w.n_envs} instances of the hires Super-CHIP template ROM (seed 3, "
                  f"{len(g.rom)} B), K=20, frameskip 4, obs uint8 [4,64,128], auto-reset at score>=20 "
                  "or 2,000 steps",
+        "shooter": f"target-shooter: {w.n_envs} instances of the Target Shooter levels 1-3 (one third each, "
+                   f"{'/'.join(str(len(x.rom)) for x in w.games)} B), K=10, frameskip 4, uniform random "
+                   "actions over 5, auto-reset after 10 targets or 5,000 steps",
     }[config]
+
+
+def data_kind(config: str) -> str:
+    return {"divergence": "synthetic (seeded random-opcode ROMs, Philox actions)",
+            "shooter": "Target Shooter ROMs (written from the paper's description), Philox actions",
+            }.get(config, "synthetic (seeded template ROMs, Philox actions)")
 
 
 class Clocks:
@@ -407,7 +416,7 @@ def run_gpu(args) -> dict | None:
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "u8",
-        "data": "synthetic (seeded template ROM, Philox actions)",
+        "data": data_kind(args.config),
         "frames_per_s": round(value * w.games[0].frameskip, 1),
         "config": {
             "workload": describe(args.config, w),
@@ -614,7 +623,7 @@ def run_reference(args) -> dict | None:
     return {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "env steps/s",
             "n_gpus": world, "steps": K, "warmup": Wm, "ms_per_step": round(dt * 1e3 / K, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-            "data": "synthetic (seeded template ROM, Philox actions)",
+            "data": data_kind(args.config),
             "config": {"workload": describe(args.config, w), "n_envs_sampled": m},
             "cpu_baseline": {"value": round(value, 1), "unit": "env steps/s", "cores": threads,
                              "kind": "oracle",
@@ -629,7 +638,8 @@ def main():
     ap.add_argument("--steps", type=int, default=0, help="timed env steps (0 = the workload's)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="octax", choices=["octax", "reference"])
-    ap.add_argument("--config", default="scale", choices=["scale", "small", "batch", "divergence", "schip"])
+    ap.add_argument("--config", default="scale",
+                    choices=["scale", "small", "batch", "divergence", "schip", "shooter"])
     ap.add_argument("--rollout", type=int, default=32, help="steps per octax_step_n call")
     ap.add_argument("--launch", default="",
                     help="block,inst_per_warp,steps_per_launch,persistent,graph[,writer_warps[,balance]] "

@@ -522,6 +522,172 @@ def random_schip_game(seed: int, *, instr_per_frame: int = 10, frameskip: int = 
 # any window of steps can be regenerated independently.
 
 
+# --------------------------------------------------------------------------
+# Target Shooter, levels 1-3 (App. D): targets appear at random places, the
+# player moves a crosshair onto them and shoots; each hit adds one to V2, and
+# after ten targets V3 becomes 1. Level 1 targets stay until hit; level 2
+# targets expire after a delay-timer timeout (a miss, which still counts
+# towards the ten); level 3 targets also move, bouncing off the edges. Keys:
+# 5 up, 8 down, 7 left, 9 right, 6 shoot. These programs are written here
+# from that description and register mapping, not from the paper's listings.
+
+CROSSHAIR_SPRITE = (0x20, 0x20, 0xF8, 0x20, 0x20)  # 5x5 plus, centre at (+2, +2)
+TARGET_SPRITE = (0x70, 0xD8, 0xA8, 0xD8, 0x70)     # 5x5 ring with a centre dot
+SHOOTER_TARGETS = 10
+SHOOTER_KEYS = (5, 7, 8, 9, 6)                      # up, left, down, right, shoot
+
+
+def shooter_rom(level: int, timeout_frames: int = 0) -> bytes:
+    """Target Shooter ROM for level 1, 2 or 3 (see above)."""
+    return _shooter(level, timeout_frames)[0]
+
+
+def shooter_labels(level: int, timeout_frames: int = 0) -> dict:
+    """Addresses of the Target Shooter labels (``loop``, ``shoot``, ``end`` ...)."""
+    return _shooter(level, timeout_frames)[1]
+
+
+def _shooter(level: int, timeout_frames: int) -> tuple:
+    """Assemble one Target Shooter level.
+
+    Registers: V0/V1 crosshair x/y, V2 score, V3 game-over flag, V4/V5 target
+    x/y, V6 targets shown so far, V7/V8 target velocity (level 3), V9 key
+    scratch, VA move phase (level 3), VB timeout, VC-VE scratch.
+    timeout_frames: target lifetime in 60 Hz frames for levels 2 and 3
+    (default 90 and 120).
+    """
+    assert level in (1, 2, 3)
+    timeout = timeout_frames or (0, 0, 90, 120)[level]
+    a = Asm()
+    # ---- init
+    a.op(0x6200)               # V2 = 0 (score)
+    a.op(0x6300)               # V3 = 0
+    a.op(0x6600)               # V6 = 0 (targets shown)
+    a.op(0x6000 | 30)          # V0 = crosshair x
+    a.op(0x6100 | 14)          # V1 = crosshair y
+    a.op(0x6A00)               # VA = 0
+    a.op(0x6B00 | timeout)     # VB = timeout
+    a.ref(0x2, "draw_score")
+    a.ref(0xA, "cross")
+    a.op(0xD015)               # draw crosshair
+    a.ref(0x2, "spawn")
+    # ---- main loop
+    a.label("loop")
+    if level >= 2:             # expired target: a miss
+        a.op(0xF907)           # V9 = DT
+        a.op(0x3900)           # skip next if V9 == 0
+        a.ref(0x1, "alive")
+        a.ref(0x2, "miss")
+        a.label("alive")
+    if level == 3:             # move the target every second pass
+        a.op(0x7A01)           # VA += 1
+        a.op(0x6E01)
+        a.op(0x8EA2)           # VE = VA & 1
+        a.op(0x3E00)           # skip next if VE == 0
+        a.ref(0x2, "move")
+    a.ref(0xA, "cross")
+    a.op(0xD015)               # erase crosshair
+    for key, upd in ((5, 0x71FF), (8, 0x7101), (7, 0x70FF), (9, 0x7001)):
+        a.op(0x6900 | key)     # V9 = key
+        a.op(0xE9A1)           # skip next if key V9 is not held
+        a.op(upd)              # move
+    a.op(0x6E3F)
+    a.op(0x80E2)               # V0 &= 63
+    a.op(0x6E1F)
+    a.op(0x81E2)               # V1 &= 31
+    a.op(0xD015)               # redraw crosshair
+    a.op(0x6906)               # V9 = shoot key
+    a.op(0xE99E)               # skip next if held
+    a.ref(0x1, "loop")
+    a.ref(0x2, "shoot")
+    a.ref(0x1, "loop")
+    # ---- shoot: a hit when |V0 - V4| <= 2 and |V1 - V5| <= 2
+    a.label("shoot")
+    for p, t in ((0x0, 0x4), (0x1, 0x5)):
+        a.op(0x8C00 | p << 4)  # VC = crosshair coordinate
+        a.op(0x8C05 | t << 4)  # VC -= target coordinate
+        a.op(0x7C02)           # VC += 2: 0..4 on a hit
+        a.op(0x6D04)
+        a.op(0x8DC5)           # VD = 4 - VC, VF = (4 >= VC)
+        a.op(0x3F01)           # skip next if VF == 1
+        a.op(0x00EE)           # out of range: return
+    a.ref(0x2, "draw_score")   # erase old score
+    a.op(0x7201)               # V2 += 1
+    a.ref(0x2, "draw_score")   # draw new score
+    a.ref(0x1, "next")
+    # ---- miss: the target expired
+    a.label("miss")
+    # ---- next: erase the target, show the next one or end the game
+    a.label("next")
+    a.ref(0xA, "target")
+    a.op(0xD455)               # erase target
+    a.op(0x3600 | SHOOTER_TARGETS)  # skip next if V6 == 10
+    a.ref(0x1, "spawn")        # (tail call: spawn returns to the caller)
+    a.op(0x6301)               # V3 = 1: game over
+    a.label("end")
+    a.ref(0x1, "end")
+    # ---- spawn: random place, reset the timer (and velocity), draw
+    a.label("spawn")
+    a.op(0xC437)               # V4 = rnd & 0x37
+    a.op(0xC517)               # V5 = rnd & 0x17
+    a.op(0x7402)               # V4 in 2..57
+    a.op(0x7502)               # V5 in 2..25
+    a.op(0x7601)               # V6 += 1
+    if level >= 2:
+        a.op(0xFB15)           # DT = VB
+    if level == 3:
+        for r in (0x7, 0x8):
+            a.op(0xC002 | r << 8)  # Vr = rnd & 2
+            a.op(0x70FF | r << 8)  # Vr -= 1: +1 or -1
+    a.ref(0xA, "target")
+    a.op(0xD455)               # draw target
+    a.op(0x00EE)
+    if level == 3:
+        # ---- move: erase, step with bounces at x 1/58 and y 1/26, draw
+        a.label("move")
+        a.ref(0xA, "target")
+        a.op(0xD455)
+        for c, v, hi in ((0x4, 0x7, 58), (0x5, 0x8, 26)):
+            a.op(0x8E00 | c << 4)      # VE = coordinate
+            a.op(0x8E04 | v << 4)      # VE += velocity
+            for edge in (1, hi):
+                a.op(0x4E00 | edge)    # skip next if VE != edge
+                a.ref(0x2, f"flip{v}")  # reverse the velocity
+            a.op(0x8004 | c << 8 | v << 4)  # coordinate += velocity
+        a.op(0xD455)
+        a.op(0x00EE)
+        for v in (0x7, 0x8):
+            a.label(f"flip{v}")
+            a.op(0x6D00)
+            a.op(0x8D05 | v << 4)      # VD = 0 - velocity
+            a.op(0x80D0 | v << 8)      # velocity = VD
+            a.op(0x00EE)
+    # ---- draw_score: hex digit of V2 at (59, 1)
+    a.label("draw_score")
+    a.op(0x6C00 | 59)
+    a.op(0x6D01)
+    a.op(0xF229)               # I = glyph(V2)
+    a.op(0xDCD5)
+    a.op(0x00EE)
+    # ---- data
+    a.label("cross")
+    a.data(CROSSHAIR_SPRITE)
+    a.label("target")
+    a.data(TARGET_SPRITE)
+    return a.assemble(), dict(a.labels)
+
+
+def shooter_game(level: int, *, instr_per_frame: int = 10, frameskip: int = 4, timeout_frames: int = 0,
+                 max_episode_steps: int = 0, sticky_prob: float = 0.0, max_noops: int = 0) -> GameSpec:
+    """Target Shooter descriptor: reward = V2 increase (one per hit), done
+    when V3 == 1, actions (up, left, down, right, shoot) = keys 5, 7, 8, 9, 6."""
+    return GameSpec(rom=shooter_rom(level, timeout_frames), instr_per_frame=instr_per_frame,
+                    frameskip=frameskip, stack_frames=4, action_set=SHOOTER_KEYS,
+                    score=(Term("reg", 2),), term=(Clause(Term("reg", 3), "==", 1),),
+                    max_episode_steps=max_episode_steps, sticky_prob=sticky_prob,
+                    max_noops=max_noops, name=f"target-shooter-{level}")
+
+
 def actions(seed: int, step_lo: int, step_hi: int, n_envs: int, n_actions: int = 4) -> np.ndarray:
     """uint8 [step_hi - step_lo, n_envs] drawn from Philox(seed, counter=step)."""
     out = np.empty((step_hi - step_lo, n_envs), dtype=np.uint8)
@@ -571,6 +737,16 @@ def cfg_schip(n_envs: int = 16384, n_steps: int = 4000) -> Workload:
                             max_episode_steps=2000)
     return Workload(f"schip-scale-{n_envs}x{n_steps}", [g], None, n_envs, n_steps, seed=3,
                     action_seed=3)
+
+
+def cfg_shooter(n_envs: int = 16384, n_steps: int = 20000) -> Workload:
+    """16,384 instances of the three Target Shooter levels (instance i plays
+    level 1 + i mod 3), K = 10, frame skip 4, uniform random actions over the
+    five actions, done after ten targets or 5,000 steps (auto-reset)."""
+    games = [shooter_game(level, max_episode_steps=5000) for level in (1, 2, 3)]
+    goe = (np.arange(n_envs) % 3).astype(np.uint16)
+    return Workload(f"target-shooter-{n_envs}x{n_steps}", games, goe, n_envs, n_steps, seed=5,
+                    action_seed=5)
 
 
 BATCH_K = (5, 8, 10, 15, 20)

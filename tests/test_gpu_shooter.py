@@ -1,0 +1,93 @@
+"""Bit-exact parity of the Target Shooter levels (App. D) between the CUDA
+path and the CPU oracle: the three levels mixed in one environment, with and
+without the sticky-action / no-op-reset wrappers, across launch shapes, and
+the full benchmark workload (16,384 instances) sampled at every step."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_01764_gb300 import workloads as W
+from test_gpu_parity import full_compare, hashes, pick, sampled_run
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_01764_gb300 import build
+
+    build.build()
+    oracle.build()
+
+
+def levels(**kw):
+    return [W.shooter_game(level, **kw) for level in (1, 2, 3)]
+
+
+def test_shooter_levels_full_parity():
+    """96 instances (levels interleaved), 400 steps: level 2-3 episodes end
+    and auto-reset several times; every state, observation, reward, flag."""
+    n = 96
+    goe = (np.arange(n) % 3).astype(np.uint16)
+    env, ref = full_compare(levels(), n, 400, seed=4, action_seed=4, game_of_env=goe)
+    assert ref.records()["V"][:, 6].max() >= 1
+
+
+@pytest.mark.parametrize("launch", [
+    dict(block=256, inst_per_warp=7, steps_per_launch=32, persistent=0, use_graph=1, balance=1),
+    dict(block=128, inst_per_warp=16, steps_per_launch=8, persistent=1, use_graph=1),
+    dict(block=64, inst_per_warp=4, steps_per_launch=4, persistent=0, use_graph=1, writer_warps=2),
+])
+def test_shooter_levels_launch_shapes(launch):
+    n = 600
+    goe = (np.arange(n) % 3).astype(np.uint16)
+    full_compare(levels(max_episode_steps=150), n, 320, seed=7, action_seed=7, game_of_env=goe,
+                 launch=launch, use_step_n=True)
+
+
+def test_shooter_with_wrappers():
+    """Sticky actions (p = 0.25) and no-op resets (up to 30 steps)."""
+    n = 120
+    goe = (np.arange(n) % 3).astype(np.uint16)
+    full_compare(levels(sticky_prob=0.25, max_noops=30), n, 350, seed=8, action_seed=8,
+                 game_of_env=goe, use_step_n=True)
+
+
+def test_scripted_policy_on_gpu_matches_oracle():
+    """A closed-loop policy (chase the target, shoot when aligned) driven by
+    the GPU's own registers scores like the oracle, step for step."""
+    from paper_2510_01764_gb300 import octax
+
+    n = 48
+    goe = (np.arange(n) % 3).astype(np.uint16)
+    env = octax.Env(levels(), n, seed=2, game_of_env=goe)
+    ref = oracle.OracleEnv(levels(), n, seed=2, game_of_env=goe)
+    env.reset()
+    ref.reset()
+    total = 0.0
+    for s in range(250):
+        V = env.get_state()["V"].astype(np.int64)
+        dx, dy = V[:, 4] - V[:, 0], V[:, 5] - V[:, 1]
+        a = np.where((np.abs(dx) <= 1) & (np.abs(dy) <= 1), 4,
+                     np.where(np.abs(dx) > np.abs(dy), np.where(dx > 0, 3, 1),
+                              np.where(dy > 0, 2, 0))).astype(np.uint8)
+        _, r, d = env.step(torch.from_numpy(a).cuda())
+        _, r2, d2 = ref.step(a, obs=False)
+        assert np.array_equal(r.cpu().numpy(), r2) and np.array_equal(d.cpu().numpy(), d2)
+        total += float(r2.sum())
+    assert np.array_equal(hashes(env), ref.hashes())
+    assert total >= 3 * n
+
+
+def test_config_shooter_sampled():
+    """The benchmark workload: 16,384 instances, levels 1-3, 20,000 steps,
+    in the benchmark's launch shape."""
+    w = W.cfg_shooter()
+    sample = pick(w.n_envs, 18, 9, extra=(0, 1, 2, 53, 54, w.n_envs - 1))
+    env, n_done = sampled_run(w, chunk=64, sample=sample,
+                              launch=dict(block=256, inst_per_warp=7, steps_per_launch=32,
+                                          persistent=0, use_graph=1, balance=1))
+    assert n_done > 0
