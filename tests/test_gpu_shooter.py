@@ -39,7 +39,7 @@ def test_shooter_levels_full_parity():
 @pytest.mark.parametrize("launch", [
     dict(block=256, inst_per_warp=7, steps_per_launch=32, persistent=0, use_graph=1, balance=1),
     dict(block=128, inst_per_warp=16, steps_per_launch=8, persistent=1, use_graph=1),
-    dict(block=64, inst_per_warp=4, steps_per_launch=4, persistent=0, use_graph=1, writer_warps=2),
+    dict(block=128, inst_per_warp=8, steps_per_launch=4, persistent=0, use_graph=1, writer_warps=2),
 ])
 def test_shooter_levels_launch_shapes(launch):
     n = 600
