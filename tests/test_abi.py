@@ -133,3 +133,28 @@ def test_last_error_without_gpu(lib):
     lib.octax_num_envs.restype = C.c_int64
     lib.octax_num_envs.argtypes = [C.c_void_p]
     assert lib.octax_num_envs(None) == -1
+
+
+def test_step_entry_points_reject_null_env_without_gpu(lib):
+    """Every stepping / state entry point returns OCTAX_EINVAL with a message
+    for a null environment, before touching the device."""
+    from paper_2510_01764_gb300 import octax as o
+
+    L = o.load_library()
+    calls = {
+        "octax_reset": (None, None, None),
+        "octax_step": (None, None, None, None, None),
+        "octax_step_n": (None, 1, None, None, None, None),
+        "octax_step_n_packed": (None, 1, None, None, None, None),
+        "octax_step_host": (None, None, None, None, None),
+        "octax_step_host_packed": (None, None, None, None, None),
+        "octax_state_hash": (None, None),
+        "octax_get_state": (None, 0, 1, None),
+        "octax_set_state": (None, 0, 1, None),
+        "octax_sync": (None, 0),
+    }
+    for name, args in calls.items():
+        fn = getattr(L, name)
+        L.octax_last_error()
+        assert fn(*args) == o.EINVAL, name
+        assert name.encode() in L.octax_last_error(), name
