@@ -495,6 +495,34 @@ def test_config_divergence_sampled():
                             use_graph=1))
 
 
+def test_four_million_instances_sampled():
+    """4,194,339 instances (2^22 + 35: past every 32-bit byte offset of the
+    observation and state arrays, a ragged last group), 3 steps with
+    truncation after 2 (every instance auto-resets at once), in the
+    benchmark's launch shape; packed observations keep the output at 4.3 GB
+    per step. Sampled instances at both ends and around 2^21 and 2^22."""
+    o = octax()
+    g = W.template_game(W.TemplateParams(seed=2), max_episode_steps=2)
+    n = (1 << 22) + 35
+    sample = pick(n, 12, 11, extra=(0, 1, (1 << 21) - 1, 1 << 21, (1 << 22) - 1, 1 << 22, n - 2, n - 1))
+    env = o.Env([g], n, seed=3)
+    env.set_launch(block=256, inst_per_warp=7, steps_per_launch=32, persistent=0, use_graph=1, balance=1)
+    ref = oracle.OracleEnv([g], len(sample), seed=3, uid_of_env=sample.astype(np.uint32))
+    idx = torch.from_numpy(sample).cuda()
+    steps = 3                      # both sides start from the reset octax_create / the oracle ran
+    acts = W.actions(9, 0, steps, n, 4)
+    a_dev = torch.from_numpy(acts).cuda()
+    obs, rew, done = env.step_n_packed(a_dev)
+    o2, r2, d2, h2 = ref.rollout(acts[:, sample], obs=True, hashes=True)
+    assert np.array_equal(obs[:, idx].cpu().numpy().view(np.uint64), pack_frames(o2))
+    assert np.array_equal(rew[:, idx].cpu().numpy(), r2)
+    assert np.array_equal(done[:, idx].cpu().numpy(), d2)
+    assert int(done[1].sum().item()) == n and int(done[0].sum().item()) == 0
+    assert np.array_equal(env.state_hash()[idx].cpu().numpy().view(np.uint64), h2[-1])
+    del obs, rew, done, env
+    torch.cuda.empty_cache()
+
+
 # ----------------------------------------------------------------- packed observations
 def pack_frames(obs_u8: np.ndarray) -> np.ndarray:
     """uint8 0/1 frames [..., H, W] -> u64 words [..., H * W / 64] (bit x of a
