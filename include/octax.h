@@ -242,8 +242,19 @@ int octax_set_state(octax_env *env, int64_t first, int64_t count,
 
 /* Wait until all enqueued work finished; OCTAX_ETIMEOUT after timeout_ms
  * (negative = no limit). OCTAX_ECUDA if a kernel reported an internal
- * hand-over timeout (its outputs are then incomplete). */
+ * hand-over timeout since the last octax_sync: the outputs of the calls
+ * since then are incomplete and the state of the instances in the failed
+ * CTAs is left as it was before the failed launch. The report clears the
+ * flag, so the environment stays usable. */
 int octax_sync(octax_env *env, int timeout_ms);
+
+/* Diagnostic for the failure path of the warp-specialised kernel
+ * (writer_warps > 0): while `on` is nonzero its writer warps skip their
+ * shared-memory hand-over, so the emulator warps' bounded waits (at most
+ * about one second each) run out, the kernel records the failure and
+ * returns, and octax_sync reports OCTAX_ECUDA. No other kernel is affected.
+ * Drops the cached CUDA graphs so that the next launches see the switch. */
+int octax_debug_stall_writers(octax_env *env, int on);
 
 int octax_get_launch(const octax_env *env, octax_launch *out);
 /* EINVAL for unsupported values. */

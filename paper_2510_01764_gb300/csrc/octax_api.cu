@@ -81,6 +81,7 @@ struct octax_env {
   int counters_cap = 0;
   IO *io_d = nullptr;
   unsigned int *err_d = nullptr;  // set by a kernel whose bounded hand-over wait gave up
+  int stall_writers = 0;          // octax_debug_stall_writers
   std::map<GraphKey, cudaGraphExec_t> graphs;
   // octax_step_host staging
   uint8_t *hs_act = nullptr, *hs_obs = nullptr, *hs_done = nullptr;
@@ -316,6 +317,7 @@ StepLaunch base_launch(octax_env *e, const GroupTable *gt) {
   p.ipw = e->cfg.inst_per_warp;
   p.err = e->err_d;
   p.wrappers = uses_wrappers(e->games_h.data(), e->games_h.size());
+  p.stall_writers = e->stall_writers;
   return p;
 }
 
@@ -782,6 +784,9 @@ int octax_sync(octax_env *e, int timeout_ms) {
       r = cudaMemcpy(&err, e->err_d, sizeof err, cudaMemcpyDeviceToHost);
       if (r != cudaSuccess) return cuda_fail(r, "octax_sync");
       if (err) {
+        r = cudaMemsetAsync(e->err_d, 0, sizeof(unsigned int), e->stream);
+        if (r == cudaSuccess) r = cudaStreamSynchronize(e->stream);
+        if (r != cudaSuccess) return cuda_fail(r, "octax_sync");
         set_error("octax_sync: a kernel's shared-memory hand-over timed out; outputs are incomplete");
         return OCTAX_ECUDA;
       }
@@ -795,6 +800,19 @@ int octax_sync(octax_env *e, int timeout_ms) {
     }
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
+}
+
+int octax_debug_stall_writers(octax_env *e, int on) {
+  if (!e) {
+    set_error("octax_debug_stall_writers: null env");
+    return OCTAX_EINVAL;
+  }
+  cudaError_t r = cudaStreamSynchronize(e->stream);
+  if (r != cudaSuccess) return cuda_fail(r, "octax_debug_stall_writers");
+  for (auto &kv : e->graphs) cudaGraphExecDestroy(kv.second);
+  e->graphs.clear();
+  e->stall_writers = on ? 1 : 0;
+  return OCTAX_OK;
 }
 
 int octax_get_launch(const octax_env *e, octax_launch *out) {

@@ -120,6 +120,7 @@ struct StepLaunch {
   unsigned int *work_counter;  // non-null: persistent CTAs pull groups from it
   unsigned int *err;       // set when a bounded barrier wait gives up (specialised kernel)
   int wrappers;            // 1: some game uses sticky actions or no-op reset (kernel variant)
+  int stall_writers;       // diagnostic: writer warps skip the hand-over (specialised kernel)
 };
 
 struct ResetLaunch {

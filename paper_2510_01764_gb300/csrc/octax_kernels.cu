@@ -1052,10 +1052,18 @@ __global__ void __launch_bounds__(kMaxBlock, 2) step_kernel(const StepLaunch p) 
 // overwrites it with the reset observation, so program order keeps them
 // ordered. Slots hand over through mbarriers (full: all emulator threads
 // arrive; empty: all writer threads arrive); every wait polls a bounded
-// number of times and, if it gives up, records the failure in p.err and
-// stops the thread's work instead of hanging.
+// number of times for at most kMaxWaitNs of the global timer and, if it
+// gives up, records the failure in p.err and stops the thread's work instead
+// of hanging.
 
 constexpr uint32_t kMaxPolls = 1u << 22;
+constexpr uint64_t kMaxWaitNs = 1000000000ull;  // one second
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -1077,8 +1085,11 @@ __device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
   return ok != 0;
 }
 __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, unsigned int *err) {
-  for (uint32_t i = 0; i < kMaxPolls; ++i)
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0; i < kMaxPolls; ++i) {
     if (mbar_try(b, parity)) return true;
+    if (global_ns() - t0 > kMaxWaitNs) break;
+  }
   atomicOr(err, 1u);
   return false;
 }
@@ -1219,6 +1230,7 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
 // [ww * J/W, (ww + 1) * J/W); lane -> instance 8m + lane/4, quarter lane%4.
 __device__ void run_group_writer(const StepLaunch &p, const Group &g, const WsSmem &W, uint32_t &msg,
                                  bool &failed) {
+  if (p.stall_writers) return;  // diagnostic: never hand slots back (see octax_debug_stall_writers)
   const int t = threadIdx.x, lane = t & 31;
   const int E = (int)(blockDim.x >> 5) - p.writers;
   const int J = E * p.ipw;

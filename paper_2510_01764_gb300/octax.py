@@ -101,7 +101,7 @@ class CServerStats(C.Structure):
 EXPORTS = ("octax_create", "octax_reset", "octax_step", "octax_step_n", "octax_step_host",
            "octax_state_hash", "octax_get_state", "octax_set_state", "octax_sync",
            "octax_get_launch", "octax_set_launch", "octax_autotune", "octax_num_envs",
-           "octax_stack_frames", "octax_variant", "octax_step_n_packed", "octax_step_host_packed", "octax_device_bytes", "octax_destroy", "octax_last_error",
+           "octax_stack_frames", "octax_variant", "octax_step_n_packed", "octax_step_host_packed", "octax_debug_stall_writers", "octax_device_bytes", "octax_destroy", "octax_last_error",
            "octax_server_create", "octax_server_submit", "octax_server_wait",
            "octax_server_query", "octax_server_release", "octax_server_get_stats",
            "octax_server_destroy", "octax_rollout_static")
@@ -130,6 +130,7 @@ def load_library(path: str = LIB_PATH):
             "octax_step_host": (I32, [P, P, P, P, P]),
             "octax_step_n_packed": (I32, [P, I32, P, P, P, P]),
             "octax_step_host_packed": (I32, [P, P, P, P, P]),
+            "octax_debug_stall_writers": (I32, [P, I32]),
             "octax_state_hash": (I32, [P, P]),
             "octax_get_state": (I32, [P, I64, I64, P]),
             "octax_set_state": (I32, [P, I64, I64, P]),
@@ -375,6 +376,12 @@ class Env:
 
     def sync(self, timeout_ms: int = -1) -> None:
         check(load_library().octax_sync(self._h, timeout_ms))
+
+    def debug_stall_writers(self, on: bool) -> None:
+        """Diagnostic: make the writer warps skip their hand-over so that the
+        bounded waits of the warp-specialised kernel run out (see
+        octax_debug_stall_writers)."""
+        check(load_library().octax_debug_stall_writers(self._h, 1 if on else 0))
 
     @property
     def launch(self) -> dict:
