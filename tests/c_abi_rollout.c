@@ -6,8 +6,10 @@
  * rewards and done flags. tests/test_c_abi.py compiles it, runs it and checks
  * the hashes against the CPU oracle.
  *
- * usage: c_abi_rollout ROM N_ENVS N_STEPS SEED
+ * usage: c_abi_rollout ROM N_ENVS N_STEPS SEED [packed]
  * actions: instance i at step s takes index (7 i + 3 s) mod 5 (4 is the no-op).
+ * With "packed" it steps through octax_step_host_packed (one bit per pixel)
+ * and also prints the sum of the set observation bits of the last step.
  */
 #include <stdint.h>
 #include <stdio.h>
@@ -47,10 +49,11 @@ static uint64_t record_hash(const octax_state_record *r) {
 }
 
 int main(int argc, char **argv) {
-  if (argc != 5) {
-    fprintf(stderr, "usage: %s ROM N_ENVS N_STEPS SEED\n", argv[0]);
+  if (argc != 5 && !(argc == 6 && strcmp(argv[5], "packed") == 0)) {
+    fprintf(stderr, "usage: %s ROM N_ENVS N_STEPS SEED [packed]\n", argv[0]);
     return 2;
   }
+  const int packed = argc == 6;
   FILE *f = fopen(argv[1], "rb");
   if (!f) {
     perror("rom");
@@ -92,6 +95,7 @@ int main(int argc, char **argv) {
   }
   uint8_t *actions = malloc((size_t)n);
   uint8_t *obs = malloc((size_t)n * 4 * 32 * 64);
+  uint64_t *obs_words = malloc((size_t)n * 4 * 32 * sizeof(uint64_t));
   float *reward = malloc((size_t)n * sizeof(float));
   uint8_t *done = malloc((size_t)n);
   octax_state_record *recs = malloc((size_t)n * sizeof(octax_state_record));
@@ -99,8 +103,10 @@ int main(int argc, char **argv) {
   long done_sum = 0;
   for (int s = 0; s < steps; s++) {
     for (int64_t i = 0; i < n; i++) actions[i] = (uint8_t)((7 * i + 3 * s) % 5);
-    if (octax_step_host(env, actions, obs, reward, done) != OCTAX_OK) {
-      fprintf(stderr, "octax_step_host: %s\n", octax_last_error());
+    const int rc = packed ? octax_step_host_packed(env, actions, obs_words, reward, done)
+                          : octax_step_host(env, actions, obs, reward, done);
+    if (rc != OCTAX_OK) {
+      fprintf(stderr, "step: %s\n", octax_last_error());
       return 1;
     }
     for (int64_t i = 0; i < n; i++) {
@@ -113,10 +119,18 @@ int main(int argc, char **argv) {
     return 1;
   }
   for (int64_t i = 0; i < n; i++) printf("%016llx\n", (unsigned long long)record_hash(&recs[i]));
-  printf("reward %.0f done %ld\n", reward_sum, done_sum);
+  long lit = 0;
+  if (packed) {
+    for (size_t k = 0; k < (size_t)n * 4 * 32; k++)
+      for (uint64_t w = obs_words[k]; w; w &= w - 1) lit++;
+  } else {
+    for (size_t k = 0; k < (size_t)n * 4 * 32 * 64; k++) lit += obs[k];
+  }
+  printf("reward %.0f done %ld lit %ld\n", reward_sum, done_sum, lit);
   octax_destroy(env);
   free(actions);
   free(obs);
+  free(obs_words);
   free(reward);
   free(done);
   free(recs);

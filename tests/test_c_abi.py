@@ -23,7 +23,8 @@ def test_c_program_compiles_against_the_header(tmp_path):
 
 
 @pytest.mark.gpu
-def test_c_program_matches_oracle(tmp_path):
+@pytest.mark.parametrize("packed", [False, True])
+def test_c_program_matches_oracle(tmp_path, packed):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -40,7 +41,7 @@ def test_c_program_matches_oracle(tmp_path):
     rom_path = tmp_path / "game.ch8"
     rom_path.write_bytes(rom)
     n, steps, seed = 77, 300, 12345
-    out = subprocess.run([str(exe), str(rom_path), str(n), str(steps), str(seed)],
+    out = subprocess.run([str(exe), str(rom_path), str(n), str(steps), str(seed)] + (["packed"] if packed else []),
                          capture_output=True, text=True, check=True).stdout.split("\n")
     got = [int(line, 16) for line in out[:n]]
     summary = out[n].split()
@@ -52,9 +53,9 @@ def test_c_program_matches_oracle(tmp_path):
     i = np.arange(n)
     reward_sum, done_sum = 0.0, 0
     for s in range(steps):
-        _, r, d = ref.step(((7 * i + 3 * s) % 5).astype(np.uint8), obs=False)
+        o, r, d = ref.step(((7 * i + 3 * s) % 5).astype(np.uint8), obs=s == steps - 1)
         reward_sum += float(r.sum())
         done_sum += int(d.sum())
     assert got == [int(h) for h in ref.hashes()]
-    assert summary == ["reward", f"{reward_sum:.0f}", "done", str(done_sum)]
+    assert summary == ["reward", f"{reward_sum:.0f}", "done", str(done_sum), "lit", str(int(o.sum()))]
     assert done_sum > 0
