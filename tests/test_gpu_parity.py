@@ -299,6 +299,22 @@ def test_hand_programs_through_gpu():
     env, _ = full_compare([g], 40, 12, seed=1)
 
 
+@pytest.mark.parametrize("variant", ["chip8", "schip"])
+def test_code_as_data_through_gpu(variant):
+    """A rewritten instruction (stale in the per-CTA micro-op table, so its
+    page must be read as data) and an odd-address jump, on both variants and
+    in a launch with the 16-byte and one with the 8-byte micro-op table."""
+    from test_oracle_pins import ODD, PATCH
+    for launch in (dict(block=128, inst_per_warp=8, steps_per_launch=4, persistent=0, use_graph=1),
+                   dict(block=256, inst_per_warp=32, steps_per_launch=2, persistent=1, use_graph=0)):
+        g1 = prog(PATCH, instr_per_frame=3, frameskip=4, variant=variant)
+        g2 = GameSpec(rom=ODD, instr_per_frame=3, frameskip=4, action_set=(7, 9, 5, 8), variant=variant)
+        env, ref = full_compare([g1, g2], 64, 4, seed=2, launch=launch,
+                                game_of_env=(np.arange(64) % 2).astype(np.uint16))
+        V = env.get_state()["V"]
+        assert (V[0::2, 10] == 9).all() and (V[1::2, 12] == 7).all()
+
+
 def test_autotune_leaves_no_trace():
     o = octax()
     w = W.cfg_small()

@@ -739,3 +739,40 @@ def test_noop_count_is_uniform(oracle_lib):
     counts = np.bincount(e.records()["V"][:, 0], minlength=8)
     assert counts.sum() == 4000 and len(counts) == 8
     assert _chi2_uniform(counts) < 24.3, counts
+
+
+# ---------------------------------------------------------------- code as data
+# An instruction rewritten by FX55 runs as its new bytes; a jump to an odd
+# address fetches the opcode that straddles the word boundary (§3.2: the
+# opcode is the two bytes at PC, whatever PC is).
+PATCH = [0x6A05,  # 0x200 VA = 5        (rewritten below to 6A09: VA = 9)
+         0x7B01,  # 0x202 VB += 1
+         0x3B02,  # 0x204 skip next if VB == 2
+         0x120A,  # 0x206 first pass: go and patch
+         0x1208,  # 0x208 second pass: park here
+         0x606A,  # 0x20A V0 = 0x6A
+         0x6109,  # 0x20C V1 = 0x09
+         0xA200,  # 0x20E I = 0x200
+         0xF155,  # 0x210 RAM[0x200..0x201] = V0, V1
+         0x1200]  # 0x212 back to the rewritten instruction
+ODD = bytes([0x12, 0x03,         # 0x200 jump 0x203
+             0x00, 0x6C, 0x07,   # 0x203: 6C07 (VC = 7)
+             0x12, 0x05])        # 0x205: 1205 (park at an odd address)
+
+
+def test_rewritten_instruction_runs_as_its_new_bytes(oracle_lib):
+    m = machine(oracle_lib, PATCH)
+    m.exec(12)                     # 4 + 5 (patch) + 3 instructions
+    assert m.V[10] == 9 and m.V[11] == 2 and m.m.PC == 0x208
+    assert list(m.ram[0x200:0x202]) == [0x6A, 0x09]
+    m.exec(5)
+    assert m.m.PC == 0x208 and m.V[10] == 9
+
+
+def test_odd_pc_fetches_the_straddling_opcode(oracle_lib):
+    from chip8_prog import GameSpec
+    m = oracle_lib.Machine(GameSpec(rom=ODD, action_set=(7, 9, 5, 8)))
+    m.exec(2)
+    assert m.V[12] == 7 and m.m.PC == 0x205
+    m.exec(3)
+    assert m.m.PC == 0x205 and m.m.status == 0
