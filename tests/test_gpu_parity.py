@@ -303,10 +303,13 @@ def test_hand_programs_through_gpu():
 def test_code_as_data_through_gpu(variant):
     """A rewritten instruction (stale in the per-CTA micro-op table, so its
     page must be read as data) and an odd-address jump, on both variants and
-    in a launch with the 16-byte and one with the 8-byte micro-op table."""
+    in two launch shapes: on CHIP-8, 128 threads x 8 instances per warp use
+    the 16-byte micro-op table and 128 x 16 the 8-byte one (there the wide
+    table would cost a resident CTA per SM); Super-CHIP always uses the
+    8-byte table."""
     from test_oracle_pins import ODD, PATCH
     for launch in (dict(block=128, inst_per_warp=8, steps_per_launch=4, persistent=0, use_graph=1),
-                   dict(block=256, inst_per_warp=32, steps_per_launch=2, persistent=1, use_graph=0)):
+                   dict(block=128, inst_per_warp=16, steps_per_launch=2, persistent=1, use_graph=0)):
         g1 = prog(PATCH, instr_per_frame=3, frameskip=4, variant=variant)
         g2 = GameSpec(rom=ODD, instr_per_frame=3, frameskip=4, action_set=(7, 9, 5, 8), variant=variant)
         env, ref = full_compare([g1, g2], 64, 4, seed=2, launch=launch,
