@@ -318,6 +318,44 @@ def test_code_as_data_through_gpu(variant):
         assert (V[0::2, 10] == 9).all() and (V[1::2, 12] == 7).all()
 
 
+EDGE_PROGRAMS = [
+    # FX33 across the end of memory into page 0, FX65 back, then a sprite read
+    # from the written (dirty) page 0
+    [0x6A7B, 0xAFFE, 0xFA33, 0xAFFE, 0xF265, 0xA000, 0x6305, 0x6404, 0xD345, 0x1212],
+    # FX55 into the last page, then a sprite whose rows wrap from 0xFFF to
+    # 0x000, clipped at the right and bottom edges, then drawn at wrapped
+    # coordinates and erased (VF = 1)
+    [0x60FF, 0x6181, 0x623C, 0xAFFD, 0xF255, 0xAFFD, 0x603C, 0x611E, 0xD015,
+     0x6045, 0x6123, 0xD015, 0xD015, 0x121A],
+    # unbounded recursion: the 17th call overflows (STACK_FAULT, wraps), again and again
+    [0x2204, 0x1202, 0x7001, 0x2204],
+    # return on an empty stack, then execution from low memory
+    [0x6001, 0x00EE, 0x1204],
+    # undefined encodings and an ignored 0NNN
+    [0x8018, 0x801F, 0x5011, 0x9012, 0xE000, 0xE19F, 0xF0FF, 0xF001, 0x0123, 0x1212],
+    # BNNN past the end of memory (wraps to 0x0FE) and through low memory
+    [0x60FF, 0xBFFF],
+    # FX0A: wait for the step's key, count the presses
+    [0xF00A, 0x7101, 0x1200],
+]
+
+
+@pytest.mark.parametrize("variant,quirks", [("chip8", 0), ("chip8", 0x3F), ("schip", 0)])
+def test_edge_programs_through_gpu(variant, quirks):
+    """Memory wrap for FX33/FX55/FX65 and sprite rows, reads from written
+    pages, stack overflow and underflow, undefined opcodes, BNNN past 0xFFF,
+    FX0A with the step's key: whole-state parity at every step, seven
+    programs interleaved in one environment."""
+    games = [prog(p, instr_per_frame=10, frameskip=4, variant=variant) for p in EDGE_PROGRAMS]
+    n = 4 * len(games)
+    goe = (np.arange(n) % len(games)).astype(np.uint16)
+    env, ref = full_compare(games, n, 12, seed=3, action_seed=3, game_of_env=goe, quirks=quirks)
+    st = ref.records()["status"]
+    assert (st[2::len(games)] & oracle.ST_STACK_FAULT).all()
+    assert (st[3::len(games)] & oracle.ST_STACK_FAULT).all()
+    assert (st[4::len(games)] & oracle.ST_BAD_OP).all()
+
+
 def test_autotune_leaves_no_trace():
     o = octax()
     w = W.cfg_small()
