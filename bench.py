@@ -81,9 +81,15 @@ def whole_job_rate(world: int, n_envs: int, steps: int, ms: float) -> float:
     return world * n_envs * steps / (ms / 1e3)
 
 
-def workload(name: str) -> W.Workload:
-    return {"scale": W.cfg_scale, "small": W.cfg_small, "batch": W.cfg_batch,
-            "divergence": W.cfg_divergence, "schip": W.cfg_schip, "shooter": W.cfg_shooter}[name]()
+def workload(name: str, n_envs: int = 0) -> W.Workload:
+    """The named configuration; n_envs > 0 resizes it (profiling captures)."""
+    make = {"scale": W.cfg_scale, "small": W.cfg_small, "batch": W.cfg_batch,
+            "divergence": W.cfg_divergence, "schip": W.cfg_schip, "shooter": W.cfg_shooter}[name]
+    if n_envs > 0:
+        if name == "small":
+            raise SystemExit("--n-envs does not apply to the small configuration")
+        return make(n_envs=n_envs)
+    return make()
 
 
 def describe(config: str, w: W.Workload) -> str:
@@ -211,7 +217,7 @@ _NCU_SCALE = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 
               "usecond": 1e-6, "us": 1e-6, "msecond": 1e-3, "ms": 1e-3, "second": 1.0, "s": 1.0}
 
 
-def record_traffic(csv_path: str, config: str, launch: str, units: int) -> dict:
+def record_traffic(csv_path: str, config: str, launch: str, units: int, n_envs: int = 0) -> dict:
     """Store the step kernel's DRAM bytes and warp instructions per instance
     step, averaged over the launches of an `ncu --page raw --csv` export, in
     profiles/traffic.json under `config` (tagged with the kernel source hash)."""
@@ -231,6 +237,7 @@ def record_traffic(csv_path: str, config: str, launch: str, units: int) -> dict:
     entry = {
         "kernel_source": kernel_source_hash(),
         "captured_launch": launch,
+        "captured_n_envs": n_envs or workload(config).n_envs,
         "captured_launches": len(data),
         "captured_instance_steps_per_launch": units,
         "dram_bytes_per_launch": traffic,
@@ -267,7 +274,7 @@ def run_gpu(args) -> dict | None:
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
-    w = workload(args.config)
+    w = workload(args.config, args.n_envs)
     K, Wm = args.steps if args.steps else w.n_steps, args.warmup
     n = w.n_envs
     with torch.cuda.stream(stream):
@@ -591,7 +598,7 @@ def run_reference(args) -> dict | None:
     rank, world, _ = dist_env()
     if not run_reference_rank_gate():
         return None
-    w = workload(args.config)
+    w = workload(args.config, args.n_envs)
     threads = os.cpu_count() or 1
     K, Wm = args.steps if args.steps else w.n_steps, args.warmup
     import oracle
@@ -641,6 +648,8 @@ def main():
     ap.add_argument("--config", default="scale",
                     choices=["scale", "small", "batch", "divergence", "schip", "shooter"])
     ap.add_argument("--rollout", type=int, default=32, help="steps per octax_step_n call")
+    ap.add_argument("--n-envs", type=int, default=0,
+                    help="resize the configuration (0 = its own size); for small profiling captures")
     ap.add_argument("--launch", default="",
                     help="block,inst_per_warp,steps_per_launch,persistent,graph[,writer_warps[,balance]] "
                          "(default: autotune)")
@@ -660,7 +669,7 @@ def main():
     args = ap.parse_args()
     if args.record_traffic:
         print(json.dumps(record_traffic(args.record_traffic, args.config, args.traffic_launch,
-                                        args.traffic_units), indent=1))
+                                        args.traffic_units, args.n_envs), indent=1))
         return
     if args.impl == "reference":
         line = run_reference(args)
@@ -671,7 +680,7 @@ def main():
     if line is None:
         return
     if not args.no_cpu and line["n_gpus"] == 1:
-        w = workload(args.config)
+        w = workload(args.config, args.n_envs)
         line["cpu_baseline"] = cpu_oracle(w, args.cpu_budget, os.cpu_count() or 1)
         line["cpu_baseline"]["single_core"] = cpu_oracle(w, args.cpu_budget / 3, 1)["value"]
     print(json.dumps(line), flush=True)
