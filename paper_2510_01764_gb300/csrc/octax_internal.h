@@ -65,9 +65,8 @@ struct DevState {
   uint64_t *disp;         // [W][n]   CHIP-8 (W = 32): bit x of word y = pixel (x, y);
                           //          SCHIP (W = 128): bit x of word 2y + h = pixel (64h + x, y)
   uint64_t *dirty;        // [n]      RAM pages that differ from the ROM image
-  uint64_t *fine;         // [8][n]   written 8-byte chunks: bit c of word w = chunk 64w + c
-                          //          (exact for the dirty pages; other bits are stale;
-                          //          only stored and loaded while some page is dirty)
+  uint64_t *fine;         // [n][8]   written 8-byte chunks: bit c of word w = chunk 64w + c
+                          //          (exact for the dirty pages; other bits are stale)
   uint8_t *ram;           // [n][4096] per-instance RAM (valid on dirty pages only)
   uint32_t *ep;           // [n]      steps since reset
   uint32_t *env_steps;    // [n]      steps since creation

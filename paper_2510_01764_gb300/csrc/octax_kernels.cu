@@ -64,7 +64,7 @@ struct Ctx {
   uint32_t *stack;     // shared: this instance's entry 0; entry i at stack[i * J]
   uint32_t *V;         // shared: this instance's V0; Vx at V[x * J]
   uint8_t *ram;        // global: this instance's 4 KB RAM (dirty pages)
-  uint64_t *fine;      // shared: this instance's written-chunk word 0; word w at fine[w * J]
+  uint64_t *fine;      // global: this instance's 8 written-chunk words (dirty pages only)
   int J;
   const void *uops;      // shared: micro-op table, uint4 or uint2 entries (stage_game)
   const int4 *alu;       // shared: 8XYN coefficients, two int4 per N (stage_game)
@@ -87,14 +87,15 @@ __device__ __forceinline__ uint32_t dirty_bit(uint64_t dirty, uint32_t a) {
 }
 
 // Page copy-on-write keeps one 64-bit mask in registers; inside a dirty page
-// the 8-byte chunks actually written are marked in shared memory, so data
-// next to a written byte (sprites beside a score buffer, the code around it)
-// still reads from the shared image and decodes from the micro-op table.
-// A chunk bit is exact while its page is dirty: the page's byte of the
-// chunk mask is cleared when the page is copied.
+// the 8-byte chunks actually written are marked in a per-instance mask in
+// global memory (read only on the dirty-page paths), so data next to a
+// written byte (sprites beside a score buffer, the code around it) still
+// reads from the shared image and decodes from the micro-op table. A chunk
+// bit is exact while its page is dirty: the page's byte of the mask is
+// cleared when the page is copied.
 __device__ __forceinline__ uint32_t chunk_bit(const Ctx &C, uint32_t a) {
   const uint32_t c = (a & 0xFFFu) >> kChunkShift;
-  return (uint32_t)(C.fine[(c >> 6) * C.J] >> (c & 63u)) & 1u;
+  return (uint32_t)(C.fine[c >> 6] >> (c & 63u)) & 1u;
 }
 
 // 1 when byte a may differ from the image (its page is dirty and its chunk written).
@@ -118,10 +119,10 @@ __device__ __forceinline__ void wr8(Regs &R, const Ctx &C, uint32_t a, uint32_t 
     dst[2] = src[2];
     dst[3] = src[3];
     R.dirty |= 1ull << page;
-    C.fine[(page >> 3) * C.J] &= ~(0xFFull << ((page & 7u) * 8u));  // no chunk of it written yet
+    C.fine[page >> 3] &= ~(0xFFull << ((page & 7u) * 8u));  // no chunk of it written yet
   }
   const uint32_t c = a >> kChunkShift;
-  C.fine[(c >> 6) * C.J] |= 1ull << (c & 63u);
+  C.fine[c >> 6] |= 1ull << (c & 63u);
   C.ram[a] = (uint8_t)val;
 }
 
@@ -525,7 +526,8 @@ __device__ __forceinline__ void exec_slow(Regs &R, const Ctx &C, uint32_t op, ui
 // and written pages give the raw opcode, which takes the general path.
 template <bool kW>
 __device__ __forceinline__ uint4 fetch_uop(const Regs &R, const Ctx &C, uint32_t pc) {
-  if (!((pc & 1u) | written(R, C, pc))) {  // even PC, chunk not written: the decoded table
+  const uint32_t odd = pc & 1u;
+  if (!(odd | dirty_bit(R.dirty, pc)) || (!odd && !chunk_bit(C, pc))) {  // even PC, bytes not written
     if (kW) return static_cast<const uint4 *>(C.uops)[pc >> 1];
     const uint2 e = static_cast<const uint2 *>(C.uops)[pc >> 1];
     return make_uint4(e.x, e.y & 0xFFFFu, e.y >> 16, e.x & 0xFFFu);
@@ -809,14 +811,13 @@ struct Smem {
   int4 *alu;        // 8XYN coefficients (execute)
   uint2 *lut;       // byte of pixels -> 8 bytes of 0/1
   uint64_t *disp;
-  uint64_t *fine;   // written-chunk masks [8][J]
   uint32_t *stack;
   uint32_t *V;
 };
 
 // Shared memory of a CTA with J instances: image | game | decoded opcodes |
-// expansion table | 8XYN coefficients | display [W][J] u64 | written chunks [8][J] u64 |
-// stack [16][J] u32 | V [16][J] u32, W = 32 (CHIP-8) or 128 (SCHIP).
+// expansion table | 8XYN coefficients | display [W][J] u64 | stack [16][J] u32 | V [16][J] u32,
+// W = 32 (CHIP-8) or 128 (SCHIP).
 template <bool kS, bool kW>
 __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
   constexpr int kUopSmem = kW ? kUopSmemWide : kUopSmemNarrow;
@@ -827,8 +828,7 @@ __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
   s.lut = reinterpret_cast<uint2 *>(smem + kRamBytes + kGameSmem + kUopSmem);
   s.alu = reinterpret_cast<int4 *>(smem + kRamBytes + kGameSmem + kUopSmem + kLutSmem);
   s.disp = reinterpret_cast<uint64_t *>(smem + kRamBytes + kGameSmem + kUopSmem + kLutSmem + kAluSmem);
-  s.fine = s.disp + Disp<kS>::kWords * J;
-  s.stack = reinterpret_cast<uint32_t *>(s.fine + kFineWords * J);
+  s.stack = reinterpret_cast<uint32_t *>(s.disp + Disp<kS>::kWords * J);
   s.V = s.stack + 16 * J;
   return s;
 }
@@ -913,20 +913,6 @@ __device__ __forceinline__ void load_V(const Ctx &C, const DevState &st, int64_t
   }
 }
 
-// Written-chunk masks travel only while some page is dirty (they are read
-// only for dirty pages, and a page's byte is reset whenever it is copied).
-__device__ __forceinline__ void load_fine(const Ctx &C, const DevState &st, int64_t slot, uint64_t dirty) {
-  if (dirty)
-#pragma unroll
-    for (int w = 0; w < kFineWords; ++w) C.fine[w * C.J] = st.fine[w * st.n + slot];
-}
-
-__device__ __forceinline__ void store_fine(const Ctx &C, const DevState &st, int64_t slot, uint64_t dirty) {
-  if (dirty)
-#pragma unroll
-    for (int w = 0; w < kFineWords; ++w) st.fine[w * st.n + slot] = C.fine[w * C.J];
-}
-
 __device__ __forceinline__ void store_V(const Ctx &C, const DevState &st, int64_t slot) {
 #pragma unroll
   for (int w = 0; w < 4; ++w) {
@@ -964,11 +950,8 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
     for (int r = 0; r < Disp<kS>::kWords; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, S.fine + (mine ? j : 0), J, S.uops, S.alu, st.rpl + slot * 16};
-  if (mine) {
-    load_V(C, st, slot);
-    load_fine(C, st, slot, R.dirty);
-  }
+              st.ram + slot * (int64_t)kRamBytes, st.fine + slot * kFineWords, J, S.uops, S.alu, st.rpl + slot * 16};
+  if (mine) load_V(C, st, slot);
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
   __syncwarp();
 
@@ -1031,7 +1014,6 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
   if (active) {
     store_regs<kS>(R, st, slot);
     store_V(C, st, slot);
-    store_fine(C, st, slot, R.dirty);
     st.ep[slot] = ep;
     st.prev_score[slot] = prev;
 #pragma unroll
@@ -1187,11 +1169,8 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
     for (int r = 0; r < 32; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, S.fine + (mine ? j : 0), J, S.uops, S.alu, st.rpl + slot * 16};
-  if (mine) {
-    load_V(C, st, slot);
-    load_fine(C, st, slot, R.dirty);
-  }
+              st.ram + slot * (int64_t)kRamBytes, st.fine + slot * kFineWords, J, S.uops, S.alu, st.rpl + slot * 16};
+  if (mine) load_V(C, st, slot);
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
 
   for (int s = 0; s < p.steps && !failed; ++s) {
@@ -1265,7 +1244,6 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
   if (active && !failed) {
     store_regs<false>(R, st, slot);
     store_V(C, st, slot);
-    store_fine(C, st, slot, R.dirty);
     st.ep[slot] = ep;
     st.prev_score[slot] = prev;
 #pragma unroll
@@ -1401,7 +1379,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
     load_regs<kS>(R, st, slot);
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, S.fine + (mine ? j : 0), J, S.uops, S.alu, st.rpl + slot * 16};
+              st.ram + slot * (int64_t)kRamBytes, st.fine + slot * kFineWords, J, S.uops, S.alu, st.rpl + slot * 16};
   if (doit) reset_instance<true, kS, false>(R, C, G, p.quirks);
   const unsigned which = __ballot_sync(kFull, doit);
   if (p.obs && which) {
@@ -1413,7 +1391,6 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
   if (doit) {
     store_regs<kS>(R, st, slot);
     store_V(C, st, slot);
-    store_fine(C, st, slot, R.dirty);
     st.ep[slot] = 0;
     st.prev_score[slot] = score(R, C, G);
     if (p.init) {
@@ -1557,7 +1534,7 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
     }
   }
   st.dirty[slot] = dirty;
-  for (int w = 0; w < kFineWords; ++w) st.fine[w * st.n + slot] = fine[w];
+  for (int w = 0; w < kFineWords; ++w) st.fine[slot * kFineWords + w] = fine[w];
   st.ep[slot] = rec.episode_steps;
   st.env_steps[slot] = rec.env_steps;
   st.last_act[slot] = rec.last_action;
@@ -1586,7 +1563,7 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
 size_t step_smem_bytes(int block, int ipw, int schip, int wide) {
   const size_t J = (size_t)(block / 32) * ipw;
   return (size_t)kRamBytes + kGameSmem + (wide ? kUopSmemWide : kUopSmemNarrow) + kLutSmem + kAluSmem +
-         J * ((disp_words(schip) + kFineWords) * sizeof(uint64_t) + 32 * sizeof(uint32_t));
+         J * (disp_words(schip) * sizeof(uint64_t) + 32 * sizeof(uint32_t));
 }
 
 // Dynamic shared memory a CTA may opt into, less room for static shared data.
