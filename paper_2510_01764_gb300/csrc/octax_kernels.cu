@@ -63,8 +63,7 @@ struct Ctx {
   uint64_t *disp;      // shared: this instance's row 0; row r at disp[r * J]
   uint32_t *stack;     // shared: this instance's entry 0; entry i at stack[i * J]
   uint32_t *V;         // shared: this instance's V0; Vx at V[x * J]
-  uint8_t *ram;        // global: this instance's 4 KB RAM (dirty pages)
-  uint64_t *fine;      // global: this instance's 8 written-chunk words (dirty pages only)
+  uint8_t *ram;        // global: this instance's 4 KB RAM (dirty pages), then its written-chunk words
   int J;
   const void *uops;      // shared: micro-op table, uint4 or uint2 entries (stage_game)
   const int4 *alu;       // shared: 8XYN coefficients, two int4 per N (stage_game)
@@ -93,9 +92,13 @@ __device__ __forceinline__ uint32_t dirty_bit(uint64_t dirty, uint32_t a) {
 // reads from the shared image and decodes from the micro-op table. A chunk
 // bit is exact while its page is dirty: the page's byte of the mask is
 // cleared when the page is copied.
+__device__ __forceinline__ uint64_t *chunk_words(const Ctx &C) {
+  return reinterpret_cast<uint64_t *>(C.ram + kRamBytes);
+}
+
 __device__ __forceinline__ uint32_t chunk_bit(const Ctx &C, uint32_t a) {
   const uint32_t c = (a & 0xFFFu) >> kChunkShift;
-  return (uint32_t)(C.fine[c >> 6] >> (c & 63u)) & 1u;
+  return (uint32_t)(chunk_words(C)[c >> 6] >> (c & 63u)) & 1u;
 }
 
 // 1 when byte a may differ from the image (its page is dirty and its chunk written).
@@ -119,10 +122,10 @@ __device__ __forceinline__ void wr8(Regs &R, const Ctx &C, uint32_t a, uint32_t 
     dst[2] = src[2];
     dst[3] = src[3];
     R.dirty |= 1ull << page;
-    C.fine[page >> 3] &= ~(0xFFull << ((page & 7u) * 8u));  // no chunk of it written yet
+    chunk_words(C)[page >> 3] &= ~(0xFFull << ((page & 7u) * 8u));  // no chunk of it written yet
   }
   const uint32_t c = a >> kChunkShift;
-  C.fine[c >> 6] |= 1ull << (c & 63u);
+  chunk_words(C)[c >> 6] |= 1ull << (c & 63u);
   C.ram[a] = (uint8_t)val;
 }
 
@@ -526,8 +529,8 @@ __device__ __forceinline__ void exec_slow(Regs &R, const Ctx &C, uint32_t op, ui
 // and written pages give the raw opcode, which takes the general path.
 template <bool kW>
 __device__ __forceinline__ uint4 fetch_uop(const Regs &R, const Ctx &C, uint32_t pc) {
-  const uint32_t odd = pc & 1u;
-  if (!(odd | dirty_bit(R.dirty, pc)) || (!odd && !chunk_bit(C, pc))) {  // even PC, bytes not written
+  // even PC on a clean page (the common case), or on a dirty page in an unwritten chunk
+  if (!((pc & 1u) | dirty_bit(R.dirty, pc)) || (!(pc & 1u) && !chunk_bit(C, pc))) {
     if (kW) return static_cast<const uint4 *>(C.uops)[pc >> 1];
     const uint2 e = static_cast<const uint2 *>(C.uops)[pc >> 1];
     return make_uint4(e.x, e.y & 0xFFFFu, e.y >> 16, e.x & 0xFFFu);
@@ -950,7 +953,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
     for (int r = 0; r < Disp<kS>::kWords; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, st.fine + slot * kFineWords, J, S.uops, S.alu, st.rpl + slot * 16};
+              st.ram + slot * (int64_t)kRamStride, J, S.uops, S.alu, st.rpl + slot * 16};
   if (mine) load_V(C, st, slot);
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
   __syncwarp();
@@ -1169,7 +1172,7 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
     for (int r = 0; r < 32; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, st.fine + slot * kFineWords, J, S.uops, S.alu, st.rpl + slot * 16};
+              st.ram + slot * (int64_t)kRamStride, J, S.uops, S.alu, st.rpl + slot * 16};
   if (mine) load_V(C, st, slot);
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
 
@@ -1379,7 +1382,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
     load_regs<kS>(R, st, slot);
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, st.fine + slot * kFineWords, J, S.uops, S.alu, st.rpl + slot * 16};
+              st.ram + slot * (int64_t)kRamStride, J, S.uops, S.alu, st.rpl + slot * 16};
   if (doit) reset_instance<true, kS, false>(R, C, G, p.quirks);
   const unsigned which = __ballot_sync(kFull, doit);
   if (p.obs && which) {
@@ -1412,7 +1415,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
 // RAM byte of a slot as the program sees it.
 __device__ __forceinline__ uint8_t ram_byte(const DevState &st, const uint8_t *img, int64_t slot,
                                             uint64_t dirty, uint32_t a) {
-  return ((dirty >> (a >> kPageShift)) & 1u) ? st.ram[slot * (int64_t)kRamBytes + a] : img[a];
+  return ((dirty >> (a >> kPageShift)) & 1u) ? st.ram[slot * (int64_t)kRamStride + a] : img[a];
 }
 
 __device__ __forceinline__ uint64_t fnv_byte(uint64_t h, uint32_t b) {
@@ -1518,7 +1521,7 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
   const int game = st.game[slot];
   const uint8_t *img = images + (size_t)game * kRamBytes;
   uint64_t dirty = 0, fine[kFineWords] = {};
-  uint8_t *ram = st.ram + slot * (int64_t)kRamBytes;
+  uint8_t *ram = st.ram + slot * (int64_t)kRamStride;
   for (int page = 0; page < kRamBytes >> kPageShift; ++page) {
     bool differs = false;
     for (int b = 0; b < (1 << kPageShift); ++b) {
@@ -1534,7 +1537,7 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
     }
   }
   st.dirty[slot] = dirty;
-  for (int w = 0; w < kFineWords; ++w) st.fine[slot * kFineWords + w] = fine[w];
+  for (int w = 0; w < kFineWords; ++w) reinterpret_cast<uint64_t *>(ram + kRamBytes)[w] = fine[w];
   st.ep[slot] = rec.episode_steps;
   st.env_steps[slot] = rec.env_steps;
   st.last_act[slot] = rec.last_action;
@@ -1723,8 +1726,8 @@ cudaError_t alloc_state(DevState &st, int64_t n, int schip, void **block_out, si
   const size_t N = (size_t)n;
   // every array starts on a 256-byte boundary
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t sizes[] = {16 * N, 4 * N, 4 * N, 32 * N, 8 * (size_t)disp_words(schip) * N, 8 * N, 4096 * N,
-                          4 * N,  4 * N, 4 * N, 8 * N,  4 * N,   4 * N, 2 * N, N, N, 16 * N, 8 * kFineWords * N};
+  const size_t sizes[] = {16 * N, 4 * N, 4 * N, 32 * N, 8 * (size_t)disp_words(schip) * N, 8 * N, kRamStride * N,
+                          4 * N,  4 * N, 4 * N, 8 * N,  4 * N,   4 * N, 2 * N, N, N, 16 * N};
   size_t total = 0;
   for (size_t b : sizes) total += up(b);
   uint8_t *base = nullptr;
@@ -1735,8 +1738,8 @@ cudaError_t alloc_state(DevState &st, int64_t n, int schip, void **block_out, si
                   (void **)&st.disp, (void **)&st.dirty,     (void **)&st.ram,       (void **)&st.ep,
                   (void **)&st.env_steps, (void **)&st.prev_score, (void **)&st.key, (void **)&st.uid,
                   (void **)&st.out_row, (void **)&st.game, (void **)&st.last_act, (void **)&st.mode,
-                  (void **)&st.rpl, (void **)&st.fine};
-  for (int i = 0; i < 18; ++i) {
+                  (void **)&st.rpl};
+  for (int i = 0; i < 17; ++i) {
     *dst[i] = base + off;
     off += up(sizes[i]);
   }
