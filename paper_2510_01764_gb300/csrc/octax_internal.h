@@ -15,8 +15,6 @@ constexpr int kRamBytes = 4096;
 constexpr int kPageShift = 6;               // 64-byte RAM pages: 64 pages -> one u64 mask
 constexpr int kChunkShift = 3;              // 8-byte chunks inside the pages: 512 -> 8 u64 words
 constexpr int kFineWords = 8;
-// Per-instance RAM slot: the 4 KB RAM, then the 8 written-chunk words.
-constexpr int kRamStride = kRamBytes + 8 * kFineWords;
 constexpr int kFrameBytes = 32 * 64;        // one uint8 CHIP-8 observation frame
 constexpr int kSchipFrameBytes = 64 * 128;  // one uint8 SCHIP observation frame (the 128x64 buffer)
 constexpr uint32_t kBigFontAddr = 0x0A0;    // SCHIP 8x10 glyphs, 10 bytes each
@@ -67,9 +65,10 @@ struct DevState {
   uint64_t *disp;         // [W][n]   CHIP-8 (W = 32): bit x of word y = pixel (x, y);
                           //          SCHIP (W = 128): bit x of word 2y + h = pixel (64h + x, y)
   uint64_t *dirty;        // [n]      RAM pages that differ from the ROM image
-  uint8_t *ram;           // [n][4160] per-instance RAM (valid on dirty pages only), then 8 u64
-                          //          written-chunk words: bit c of word w = chunk 64w + c
-                          //          (exact for the dirty pages; other bits are stale)
+  uint64_t *fine;         // [8][n]   written 8-byte chunks: bit c of word w = chunk 64w + c
+                          //          (exact for the dirty pages; other bits are stale;
+                          //          only stored and loaded while some page is dirty)
+  uint8_t *ram;           // [n][4096] per-instance RAM (valid on dirty pages only)
   uint32_t *ep;           // [n]      steps since reset
   uint32_t *env_steps;    // [n]      steps since creation
   int32_t *prev_score;    // [n]      score at the end of the last step / reset
@@ -85,7 +84,7 @@ struct DevState {
 
 // Every per-slot array is set (checked on the host before each launch).
 inline bool state_complete(const DevState &s) {
-  return s.n > 0 && s.v && s.pcI && s.misc && s.stack && s.disp && s.dirty && s.ram && s.ep && s.env_steps &&
+  return s.n > 0 && s.v && s.pcI && s.misc && s.stack && s.disp && s.dirty && s.fine && s.ram && s.ep && s.env_steps &&
          s.prev_score && s.key && s.uid && s.out_row && s.game && s.last_act && s.mode && s.rpl;
 }
 

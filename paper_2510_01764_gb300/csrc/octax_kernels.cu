@@ -63,7 +63,8 @@ struct Ctx {
   uint64_t *disp;      // shared: this instance's row 0; row r at disp[r * J]
   uint32_t *stack;     // shared: this instance's entry 0; entry i at stack[i * J]
   uint32_t *V;         // shared: this instance's V0; Vx at V[x * J]
-  uint8_t *ram;        // global: this instance's 4 KB RAM (dirty pages), then its written-chunk words
+  uint8_t *ram;        // global: this instance's 4 KB RAM (dirty pages)
+  uint64_t *fine;      // shared: this instance's written-chunk word 0; word w at fine[w * J]
   int J;
   const void *uops;      // shared: micro-op table, uint4 or uint2 entries (stage_game)
   const int4 *alu;       // shared: 8XYN coefficients, two int4 per N (stage_game)
@@ -86,19 +87,14 @@ __device__ __forceinline__ uint32_t dirty_bit(uint64_t dirty, uint32_t a) {
 }
 
 // Page copy-on-write keeps one 64-bit mask in registers; inside a dirty page
-// the 8-byte chunks actually written are marked in a per-instance mask in
-// global memory (read only on the dirty-page paths), so data next to a
-// written byte (sprites beside a score buffer, the code around it) still
-// reads from the shared image and decodes from the micro-op table. A chunk
-// bit is exact while its page is dirty: the page's byte of the mask is
-// cleared when the page is copied.
-__device__ __forceinline__ uint64_t *chunk_words(const Ctx &C) {
-  return reinterpret_cast<uint64_t *>(C.ram + kRamBytes);
-}
-
+// the 8-byte chunks actually written are marked in shared memory, so a
+// sprite next to a written byte (beside a score buffer, say) is still drawn
+// from the shared image. Other reads of a dirty page use its complete copy.
+// A chunk bit is exact while its page is dirty: the page's byte of the
+// chunk mask is cleared when the page is copied.
 __device__ __forceinline__ uint32_t chunk_bit(const Ctx &C, uint32_t a) {
   const uint32_t c = (a & 0xFFFu) >> kChunkShift;
-  return (uint32_t)(chunk_words(C)[c >> 6] >> (c & 63u)) & 1u;
+  return (uint32_t)(C.fine[(c >> 6) * C.J] >> (c & 63u)) & 1u;
 }
 
 // 1 when byte a may differ from the image (its page is dirty and its chunk written).
@@ -106,9 +102,18 @@ __device__ __forceinline__ uint32_t written(const Regs &R, const Ctx &C, uint32_
   return dirty_bit(R.dirty, a) ? chunk_bit(C, a) : 0u;
 }
 
+// 1 when every byte of [a, a + len) (len <= 32, no wrap past 0xFFF) is as in the image.
+__device__ __forceinline__ bool unwritten(const Regs &R, const Ctx &C, uint32_t a, uint32_t len) {
+  if (!(dirty_bit(R.dirty, a) | dirty_bit(R.dirty, a + len - 1u))) return true;
+  bool clean = true;
+  for (uint32_t b = a & ~7u; b <= a + len - 1u; b += 8u) clean &= !written(R, C, b);
+  return clean;
+}
+
+// A byte of RAM: a dirty page's copy is complete, so no chunk test is needed.
 __device__ __forceinline__ uint32_t rd8(const Regs &R, const Ctx &C, uint32_t a) {
   a &= 0xFFFu;
-  return written(R, C, a) ? (uint32_t)C.ram[a] : img_byte(a);
+  return dirty_bit(R.dirty, a) ? (uint32_t)C.ram[a] : img_byte(a);
 }
 
 __device__ __forceinline__ void wr8(Regs &R, const Ctx &C, uint32_t a, uint32_t val) {
@@ -122,10 +127,10 @@ __device__ __forceinline__ void wr8(Regs &R, const Ctx &C, uint32_t a, uint32_t 
     dst[2] = src[2];
     dst[3] = src[3];
     R.dirty |= 1ull << page;
-    chunk_words(C)[page >> 3] &= ~(0xFFull << ((page & 7u) * 8u));  // no chunk of it written yet
+    C.fine[(page >> 3) * C.J] &= ~(0xFFull << ((page & 7u) * 8u));  // no chunk of it written yet
   }
   const uint32_t c = a >> kChunkShift;
-  chunk_words(C)[c >> 6] |= 1ull << (c & 63u);
+  C.fine[(c >> 6) * C.J] |= 1ull << (c & 63u);
   C.ram[a] = (uint8_t)val;
 }
 
@@ -161,11 +166,7 @@ __device__ __forceinline__ void draw(Regs &R, const Ctx &C, uint32_t vx, uint32_
   const bool wrap = quirks & OCTAX_QUIRK_WRAP_SPRITES;
   // the sprite spans at most two pages and three chunks: read it from the
   // image unless one of its chunks was written
-  bool clean = n == 0 || !(dirty_bit(R.dirty, I) | dirty_bit(R.dirty, I + n - 1u));
-  if (!clean) {
-    clean = true;
-    for (uint32_t a = I & ~7u; a <= I + n - 1u; a += 8u) clean &= !written(R, C, a);
-  }
+  const bool clean = n == 0 || unwritten(R, C, I, n);
   if (clean && !wrap && I + n <= (uint32_t)kRamBytes) {
     // Common case: sprite in the shared image, rows below the screen clipped,
     // no per-row checks; collision bits are OR-ed over the rows.
@@ -224,6 +225,9 @@ __device__ __forceinline__ void draw_schip(Regs &R, const Ctx &C, uint32_t vx, u
   const uint32_t x0 = vx & (gw - 1u), y0 = vy & (gh - 1u);
   const uint32_t rows = n ? n : 16u, width = n ? 8u : 16u;
   const uint32_t bx = x0 * unit, bits_w = width * unit;  // buffer column, pattern width (<= 32)
+  // sprite bytes from the shared image unless one of their chunks was written
+  const uint32_t I = R.I, nbytes = n ? n : 32u;
+  const bool from_img = I + nbytes <= (uint32_t)kRamBytes && unwritten(R, C, I, nbytes);
   uint32_t coll = 0;
   for (uint32_t r = 0; r < rows; ++r) {
     uint32_t gy = y0 + r;
@@ -231,7 +235,9 @@ __device__ __forceinline__ void draw_schip(Regs &R, const Ctx &C, uint32_t vx, u
       if (!wrap) break;
       gy -= gh;
     }
-    const uint32_t bits = n ? rd8(R, C, R.I + r) : ((rd8(R, C, R.I + 2u * r) << 8) | rd8(R, C, R.I + 2u * r + 1u));
+    uint32_t bits;
+    if (from_img) bits = n ? img_byte(I + r) : (img_byte(I + 2u * r) << 8) | img_byte(I + 2u * r + 1u);
+    else bits = n ? rd8(R, C, I + r) : ((rd8(R, C, I + 2u * r) << 8) | rd8(R, C, I + 2u * r + 1u));
     const uint32_t rev = __brev(bits) >> (32u - width);   // sprite pixel j -> bit j
     const uint64_t pat = unit == 1u ? (uint64_t)rev : (uint64_t)double_bits(rev);
     // pat << bx as a 128-bit value (lo, hi); bits past column 127 drop
@@ -529,8 +535,7 @@ __device__ __forceinline__ void exec_slow(Regs &R, const Ctx &C, uint32_t op, ui
 // and written pages give the raw opcode, which takes the general path.
 template <bool kW>
 __device__ __forceinline__ uint4 fetch_uop(const Regs &R, const Ctx &C, uint32_t pc) {
-  // even PC on a clean page (the common case), or on a dirty page in an unwritten chunk
-  if (!((pc & 1u) | dirty_bit(R.dirty, pc)) || (!(pc & 1u) && !chunk_bit(C, pc))) {
+  if (!((pc & 1u) | dirty_bit(R.dirty, pc))) {
     if (kW) return static_cast<const uint4 *>(C.uops)[pc >> 1];
     const uint2 e = static_cast<const uint2 *>(C.uops)[pc >> 1];
     return make_uint4(e.x, e.y & 0xFFFFu, e.y >> 16, e.x & 0xFFFu);
@@ -814,13 +819,14 @@ struct Smem {
   int4 *alu;        // 8XYN coefficients (execute)
   uint2 *lut;       // byte of pixels -> 8 bytes of 0/1
   uint64_t *disp;
+  uint64_t *fine;   // written-chunk masks [8][J]
   uint32_t *stack;
   uint32_t *V;
 };
 
 // Shared memory of a CTA with J instances: image | game | decoded opcodes |
-// expansion table | 8XYN coefficients | display [W][J] u64 | stack [16][J] u32 | V [16][J] u32,
-// W = 32 (CHIP-8) or 128 (SCHIP).
+// expansion table | 8XYN coefficients | display [W][J] u64 | written chunks [8][J] u64 |
+// stack [16][J] u32 | V [16][J] u32, W = 32 (CHIP-8) or 128 (SCHIP).
 template <bool kS, bool kW>
 __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
   constexpr int kUopSmem = kW ? kUopSmemWide : kUopSmemNarrow;
@@ -831,7 +837,8 @@ __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
   s.lut = reinterpret_cast<uint2 *>(smem + kRamBytes + kGameSmem + kUopSmem);
   s.alu = reinterpret_cast<int4 *>(smem + kRamBytes + kGameSmem + kUopSmem + kLutSmem);
   s.disp = reinterpret_cast<uint64_t *>(smem + kRamBytes + kGameSmem + kUopSmem + kLutSmem + kAluSmem);
-  s.stack = reinterpret_cast<uint32_t *>(s.disp + Disp<kS>::kWords * J);
+  s.fine = s.disp + Disp<kS>::kWords * J;
+  s.stack = reinterpret_cast<uint32_t *>(s.fine + kFineWords * J);
   s.V = s.stack + 16 * J;
   return s;
 }
@@ -916,6 +923,20 @@ __device__ __forceinline__ void load_V(const Ctx &C, const DevState &st, int64_t
   }
 }
 
+// Written-chunk masks travel only while some page is dirty (they are read
+// only for dirty pages, and a page's byte is reset whenever it is copied).
+__device__ __forceinline__ void load_fine(const Ctx &C, const DevState &st, int64_t slot, uint64_t dirty) {
+  if (dirty)
+#pragma unroll
+    for (int w = 0; w < kFineWords; ++w) C.fine[w * C.J] = st.fine[w * st.n + slot];
+}
+
+__device__ __forceinline__ void store_fine(const Ctx &C, const DevState &st, int64_t slot, uint64_t dirty) {
+  if (dirty)
+#pragma unroll
+    for (int w = 0; w < kFineWords; ++w) st.fine[w * st.n + slot] = C.fine[w * C.J];
+}
+
 __device__ __forceinline__ void store_V(const Ctx &C, const DevState &st, int64_t slot) {
 #pragma unroll
   for (int w = 0; w < 4; ++w) {
@@ -953,8 +974,11 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
     for (int r = 0; r < Disp<kS>::kWords; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamStride, J, S.uops, S.alu, st.rpl + slot * 16};
-  if (mine) load_V(C, st, slot);
+              st.ram + slot * (int64_t)kRamBytes, S.fine + (mine ? j : 0), J, S.uops, S.alu, st.rpl + slot * 16};
+  if (mine) {
+    load_V(C, st, slot);
+    load_fine(C, st, slot, R.dirty);
+  }
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
   __syncwarp();
 
@@ -1017,6 +1041,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
   if (active) {
     store_regs<kS>(R, st, slot);
     store_V(C, st, slot);
+    store_fine(C, st, slot, R.dirty);
     st.ep[slot] = ep;
     st.prev_score[slot] = prev;
 #pragma unroll
@@ -1172,8 +1197,11 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
     for (int r = 0; r < 32; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamStride, J, S.uops, S.alu, st.rpl + slot * 16};
-  if (mine) load_V(C, st, slot);
+              st.ram + slot * (int64_t)kRamBytes, S.fine + (mine ? j : 0), J, S.uops, S.alu, st.rpl + slot * 16};
+  if (mine) {
+    load_V(C, st, slot);
+    load_fine(C, st, slot, R.dirty);
+  }
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
 
   for (int s = 0; s < p.steps && !failed; ++s) {
@@ -1247,6 +1275,7 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
   if (active && !failed) {
     store_regs<false>(R, st, slot);
     store_V(C, st, slot);
+    store_fine(C, st, slot, R.dirty);
     st.ep[slot] = ep;
     st.prev_score[slot] = prev;
 #pragma unroll
@@ -1382,7 +1411,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
     load_regs<kS>(R, st, slot);
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamStride, J, S.uops, S.alu, st.rpl + slot * 16};
+              st.ram + slot * (int64_t)kRamBytes, S.fine + (mine ? j : 0), J, S.uops, S.alu, st.rpl + slot * 16};
   if (doit) reset_instance<true, kS, false>(R, C, G, p.quirks);
   const unsigned which = __ballot_sync(kFull, doit);
   if (p.obs && which) {
@@ -1394,6 +1423,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
   if (doit) {
     store_regs<kS>(R, st, slot);
     store_V(C, st, slot);
+    store_fine(C, st, slot, R.dirty);
     st.ep[slot] = 0;
     st.prev_score[slot] = score(R, C, G);
     if (p.init) {
@@ -1415,7 +1445,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
 // RAM byte of a slot as the program sees it.
 __device__ __forceinline__ uint8_t ram_byte(const DevState &st, const uint8_t *img, int64_t slot,
                                             uint64_t dirty, uint32_t a) {
-  return ((dirty >> (a >> kPageShift)) & 1u) ? st.ram[slot * (int64_t)kRamStride + a] : img[a];
+  return ((dirty >> (a >> kPageShift)) & 1u) ? st.ram[slot * (int64_t)kRamBytes + a] : img[a];
 }
 
 __device__ __forceinline__ uint64_t fnv_byte(uint64_t h, uint32_t b) {
@@ -1521,7 +1551,7 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
   const int game = st.game[slot];
   const uint8_t *img = images + (size_t)game * kRamBytes;
   uint64_t dirty = 0, fine[kFineWords] = {};
-  uint8_t *ram = st.ram + slot * (int64_t)kRamStride;
+  uint8_t *ram = st.ram + slot * (int64_t)kRamBytes;
   for (int page = 0; page < kRamBytes >> kPageShift; ++page) {
     bool differs = false;
     for (int b = 0; b < (1 << kPageShift); ++b) {
@@ -1537,7 +1567,7 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
     }
   }
   st.dirty[slot] = dirty;
-  for (int w = 0; w < kFineWords; ++w) reinterpret_cast<uint64_t *>(ram + kRamBytes)[w] = fine[w];
+  for (int w = 0; w < kFineWords; ++w) st.fine[w * st.n + slot] = fine[w];
   st.ep[slot] = rec.episode_steps;
   st.env_steps[slot] = rec.env_steps;
   st.last_act[slot] = rec.last_action;
@@ -1566,7 +1596,7 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
 size_t step_smem_bytes(int block, int ipw, int schip, int wide) {
   const size_t J = (size_t)(block / 32) * ipw;
   return (size_t)kRamBytes + kGameSmem + (wide ? kUopSmemWide : kUopSmemNarrow) + kLutSmem + kAluSmem +
-         J * (disp_words(schip) * sizeof(uint64_t) + 32 * sizeof(uint32_t));
+         J * ((disp_words(schip) + kFineWords) * sizeof(uint64_t) + 32 * sizeof(uint32_t));
 }
 
 // Dynamic shared memory a CTA may opt into, less room for static shared data.
@@ -1726,8 +1756,8 @@ cudaError_t alloc_state(DevState &st, int64_t n, int schip, void **block_out, si
   const size_t N = (size_t)n;
   // every array starts on a 256-byte boundary
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t sizes[] = {16 * N, 4 * N, 4 * N, 32 * N, 8 * (size_t)disp_words(schip) * N, 8 * N, kRamStride * N,
-                          4 * N,  4 * N, 4 * N, 8 * N,  4 * N,   4 * N, 2 * N, N, N, 16 * N};
+  const size_t sizes[] = {16 * N, 4 * N, 4 * N, 32 * N, 8 * (size_t)disp_words(schip) * N, 8 * N, 4096 * N,
+                          4 * N,  4 * N, 4 * N, 8 * N,  4 * N,   4 * N, 2 * N, N, N, 16 * N, 8 * kFineWords * N};
   size_t total = 0;
   for (size_t b : sizes) total += up(b);
   uint8_t *base = nullptr;
@@ -1738,8 +1768,8 @@ cudaError_t alloc_state(DevState &st, int64_t n, int schip, void **block_out, si
                   (void **)&st.disp, (void **)&st.dirty,     (void **)&st.ram,       (void **)&st.ep,
                   (void **)&st.env_steps, (void **)&st.prev_score, (void **)&st.key, (void **)&st.uid,
                   (void **)&st.out_row, (void **)&st.game, (void **)&st.last_act, (void **)&st.mode,
-                  (void **)&st.rpl};
-  for (int i = 0; i < 17; ++i) {
+                  (void **)&st.rpl, (void **)&st.fine};
+  for (int i = 0; i < 18; ++i) {
     *dst[i] = base + off;
     off += up(sizes[i]);
   }
