@@ -54,10 +54,9 @@ def step_io_bytes(w: W.Workload) -> int:
 def state_bytes(w: W.Workload) -> int:
     schip = w.games[0].variant == "schip"
     disp = 1024 if schip else 256
-    # V, PC|I, SP|timers|status, stack, display, page mask, written-chunk mask
-    # (moved only while a page is dirty: counted in full), counters, previous
-    # score and action, SCHIP mode byte
-    written = 16 + 4 + 4 + 32 + disp + 8 + 64 + 8 + 4 + 1 + (1 if schip else 0)
+    # V, PC|I, SP|timers|status, stack, display, page mask, written-address
+    # range, counters, previous score and action, SCHIP mode byte
+    written = 16 + 4 + 4 + 32 + disp + 8 + 4 + 8 + 4 + 1 + (1 if schip else 0)
     return written + (written + 16)  # written, and read back with the 16 read-only bytes
 
 

@@ -507,7 +507,7 @@ int octax_create(const octax_game *games, int n_games, const uint16_t *game_of_e
   ALLOC(st.stack, 16 * n);
   ALLOC(st.disp, (size_t)disp_words(e->schip) * n);
   ALLOC(st.dirty, n);
-  ALLOC(st.fine, (size_t)kFineWords * n);
+  ALLOC(st.wrange, n);
   ALLOC(st.ram, n * kRamBytes);
   ALLOC(st.ep, n);
   ALLOC(st.env_steps, n);
@@ -854,7 +854,7 @@ int octax_autotune(octax_env *e, int n_steps, const uint8_t *actions_dev, float 
                           {st.stack, 32 * n}, {st.disp, 8 * (size_t)disp_words(e->schip) * n}, {st.dirty, 8 * n},
                           {st.ram, 4096 * n}, {st.ep, 4 * n},     {st.env_steps, 4 * n},
                           {st.prev_score, 4 * n}, {st.last_act, n}, {st.mode, n}, {st.rpl, 16 * n},
-                          {st.fine, 8 * kFineWords * n}};
+                          {st.wrange, 4 * n}};
   size_t total = 0;
   for (const Piece &pc : pieces) total += pc.bytes;
   uint8_t *backup = nullptr, *acts = nullptr, *obs = nullptr, *done = nullptr;

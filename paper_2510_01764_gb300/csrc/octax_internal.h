@@ -13,8 +13,8 @@ namespace octax {
 
 constexpr int kRamBytes = 4096;
 constexpr int kPageShift = 6;               // 64-byte RAM pages: 64 pages -> one u64 mask
-constexpr int kChunkShift = 3;              // 8-byte chunks inside the pages: 512 -> 8 u64 words
-constexpr int kFineWords = 8;
+// Written-address range of an instance, lo | hi << 16 (lo > hi: nothing written).
+constexpr uint32_t kNoWrites = 0x0FFFu;
 constexpr int kFrameBytes = 32 * 64;        // one uint8 CHIP-8 observation frame
 constexpr int kSchipFrameBytes = 64 * 128;  // one uint8 SCHIP observation frame (the 128x64 buffer)
 constexpr uint32_t kBigFontAddr = 0x0A0;    // SCHIP 8x10 glyphs, 10 bytes each
@@ -65,9 +65,8 @@ struct DevState {
   uint64_t *disp;         // [W][n]   CHIP-8 (W = 32): bit x of word y = pixel (x, y);
                           //          SCHIP (W = 128): bit x of word 2y + h = pixel (64h + x, y)
   uint64_t *dirty;        // [n]      RAM pages that differ from the ROM image
-  uint64_t *fine;         // [8][n]   written 8-byte chunks: bit c of word w = chunk 64w + c
-                          //          (exact for the dirty pages; other bits are stale;
-                          //          only stored and loaded while some page is dirty)
+  uint32_t *wrange;       // [n]      lowest | highest << 16 RAM address written since the
+                          //          reset (kNoWrites: none): bytes outside it equal the image
   uint8_t *ram;           // [n][4096] per-instance RAM (valid on dirty pages only)
   uint32_t *ep;           // [n]      steps since reset
   uint32_t *env_steps;    // [n]      steps since creation
@@ -84,7 +83,7 @@ struct DevState {
 
 // Every per-slot array is set (checked on the host before each launch).
 inline bool state_complete(const DevState &s) {
-  return s.n > 0 && s.v && s.pcI && s.misc && s.stack && s.disp && s.dirty && s.fine && s.ram && s.ep && s.env_steps &&
+  return s.n > 0 && s.v && s.pcI && s.misc && s.stack && s.disp && s.dirty && s.wrange && s.ram && s.ep && s.env_steps &&
          s.prev_score && s.key && s.uid && s.out_row && s.game && s.last_act && s.mode && s.rpl;
 }
 
@@ -169,7 +168,7 @@ inline int uses_wrappers(const GameDev *games, size_t n) {
   return 0;
 }
 // Bytes of device state per slot (all DevState arrays).
-constexpr size_t kSlotStateBytes = 16 + 4 + 4 + 32 + 256 + 8 + 64 + 4096 + 4 + 4 + 4 + 8 + 4 + 4 + 2 + 1 + 1 + 16;
+constexpr size_t kSlotStateBytes = 16 + 4 + 4 + 32 + 256 + 8 + 4 + 4096 + 4 + 4 + 4 + 8 + 4 + 4 + 2 + 1 + 1 + 16;
 inline size_t slot_state_bytes(int schip) {
   return kSlotStateBytes + (schip ? 8 * (kSchipDispWords - kDispWords) : 0);
 }

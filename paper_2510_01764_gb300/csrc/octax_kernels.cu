@@ -64,7 +64,7 @@ struct Ctx {
   uint32_t *stack;     // shared: this instance's entry 0; entry i at stack[i * J]
   uint32_t *V;         // shared: this instance's V0; Vx at V[x * J]
   uint8_t *ram;        // global: this instance's 4 KB RAM (dirty pages)
-  uint64_t *fine;      // shared: this instance's written-chunk word 0; word w at fine[w * J]
+  uint32_t *wrange;    // shared: this instance's written-address range (kNoWrites: none)
   int J;
   const void *uops;      // shared: micro-op table, uint4 or uint2 entries (stage_game)
   const int4 *alu;       // shared: 8XYN coefficients, two int4 per N (stage_game)
@@ -86,31 +86,19 @@ __device__ __forceinline__ uint32_t dirty_bit(uint64_t dirty, uint32_t a) {
   return (uint32_t)(dirty >> ((a & 0xFFFu) >> kPageShift)) & 1u;
 }
 
-// Page copy-on-write keeps one 64-bit mask in registers; inside a dirty page
-// the 8-byte chunks actually written are marked in shared memory, so a
-// sprite next to a written byte (beside a score buffer, say) is still drawn
-// from the shared image. Other reads of a dirty page use its complete copy.
-// A chunk bit is exact while its page is dirty: the page's byte of the
-// chunk mask is cleared when the page is copied.
-__device__ __forceinline__ uint32_t chunk_bit(const Ctx &C, uint32_t a) {
-  const uint32_t c = (a & 0xFFFu) >> kChunkShift;
-  return (uint32_t)(C.fine[(c >> 6) * C.J] >> (c & 63u)) & 1u;
-}
-
-// 1 when byte a may differ from the image (its page is dirty and its chunk written).
-__device__ __forceinline__ uint32_t written(const Regs &R, const Ctx &C, uint32_t a) {
-  return dirty_bit(R.dirty, a) ? chunk_bit(C, a) : 0u;
-}
-
-// 1 when every byte of [a, a + len) (len <= 32, no wrap past 0xFFF) is as in the image.
+// Page copy-on-write keeps one 64-bit mask in registers. Beside it, shared
+// memory holds the range of RAM addresses written since the reset, so a
+// sprite on a dirty page but outside that range (beside a score buffer, say)
+// is still drawn from the shared image. Other reads of a dirty page use its
+// complete copy.
+// True when every byte of [a, a + len) (len <= 32, a + len <= 4096) is as in the image.
 __device__ __forceinline__ bool unwritten(const Regs &R, const Ctx &C, uint32_t a, uint32_t len) {
   if (!(dirty_bit(R.dirty, a) | dirty_bit(R.dirty, a + len - 1u))) return true;
-  bool clean = true;
-  for (uint32_t b = a & ~7u; b <= a + len - 1u; b += 8u) clean &= !written(R, C, b);
-  return clean;
+  const uint32_t w = *C.wrange;
+  return a + len - 1u < (w & 0xFFFFu) || a > (w >> 16);
 }
 
-// A byte of RAM: a dirty page's copy is complete, so no chunk test is needed.
+// A byte of RAM: a dirty page's copy is complete.
 __device__ __forceinline__ uint32_t rd8(const Regs &R, const Ctx &C, uint32_t a) {
   a &= 0xFFFu;
   return dirty_bit(R.dirty, a) ? (uint32_t)C.ram[a] : img_byte(a);
@@ -127,10 +115,9 @@ __device__ __forceinline__ void wr8(Regs &R, const Ctx &C, uint32_t a, uint32_t 
     dst[2] = src[2];
     dst[3] = src[3];
     R.dirty |= 1ull << page;
-    C.fine[(page >> 3) * C.J] &= ~(0xFFull << ((page & 7u) * 8u));  // no chunk of it written yet
   }
-  const uint32_t c = a >> kChunkShift;
-  C.fine[(c >> 6) * C.J] |= 1ull << (c & 63u);
+  const uint32_t w = *C.wrange;
+  *C.wrange = min(w & 0xFFFFu, a) | max(w >> 16, a) << 16;
   C.ram[a] = (uint8_t)val;
 }
 
@@ -164,9 +151,9 @@ __device__ __forceinline__ void draw(Regs &R, const Ctx &C, uint32_t vx, uint32_
                                      uint32_t quirks) {
   const uint32_t x0 = vx & 63u, y0 = vy & 31u, I = R.I;
   const bool wrap = quirks & OCTAX_QUIRK_WRAP_SPRITES;
-  // the sprite spans at most two pages and three chunks: read it from the
-  // image unless one of its chunks was written
-  const bool clean = n == 0 || unwritten(R, C, I, n);
+  // the sprite spans at most two pages: read it from the image unless a byte
+  // of it may have been written
+  const bool clean = n == 0 || (I + n <= (uint32_t)kRamBytes && unwritten(R, C, I, n));
   if (clean && !wrap && I + n <= (uint32_t)kRamBytes) {
     // Common case: sprite in the shared image, rows below the screen clipped,
     // no per-row checks; collision bits are OR-ed over the rows.
@@ -225,7 +212,7 @@ __device__ __forceinline__ void draw_schip(Regs &R, const Ctx &C, uint32_t vx, u
   const uint32_t x0 = vx & (gw - 1u), y0 = vy & (gh - 1u);
   const uint32_t rows = n ? n : 16u, width = n ? 8u : 16u;
   const uint32_t bx = x0 * unit, bits_w = width * unit;  // buffer column, pattern width (<= 32)
-  // sprite bytes from the shared image unless one of their chunks was written
+  // sprite bytes from the shared image unless one of them may have been written
   const uint32_t I = R.I, nbytes = n ? n : 32u;
   const bool from_img = I + nbytes <= (uint32_t)kRamBytes && unwritten(R, C, I, nbytes);
   uint32_t coll = 0;
@@ -660,6 +647,7 @@ __device__ __forceinline__ void reset_instance(Regs &R, const Ctx &C, const Game
   R.dt = 0;
   R.st = 0;
   R.dirty = 0;
+  *C.wrange = kNoWrites;
 #pragma unroll
   for (int i = 0; i < 16; ++i) C.stack[i * C.J] = 0;
 #pragma unroll 8
@@ -819,14 +807,14 @@ struct Smem {
   int4 *alu;        // 8XYN coefficients (execute)
   uint2 *lut;       // byte of pixels -> 8 bytes of 0/1
   uint64_t *disp;
-  uint64_t *fine;   // written-chunk masks [8][J]
+  uint32_t *wrange; // written-address ranges [J]
   uint32_t *stack;
   uint32_t *V;
 };
 
 // Shared memory of a CTA with J instances: image | game | decoded opcodes |
-// expansion table | 8XYN coefficients | display [W][J] u64 | written chunks [8][J] u64 |
-// stack [16][J] u32 | V [16][J] u32, W = 32 (CHIP-8) or 128 (SCHIP).
+// expansion table | 8XYN coefficients | display [W][J] u64 | stack [16][J] u32 | V [16][J] u32 |
+// written range [J] u32, W = 32 (CHIP-8) or 128 (SCHIP).
 template <bool kS, bool kW>
 __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
   constexpr int kUopSmem = kW ? kUopSmemWide : kUopSmemNarrow;
@@ -837,9 +825,9 @@ __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
   s.lut = reinterpret_cast<uint2 *>(smem + kRamBytes + kGameSmem + kUopSmem);
   s.alu = reinterpret_cast<int4 *>(smem + kRamBytes + kGameSmem + kUopSmem + kLutSmem);
   s.disp = reinterpret_cast<uint64_t *>(smem + kRamBytes + kGameSmem + kUopSmem + kLutSmem + kAluSmem);
-  s.fine = s.disp + Disp<kS>::kWords * J;
-  s.stack = reinterpret_cast<uint32_t *>(s.fine + kFineWords * J);
+  s.stack = reinterpret_cast<uint32_t *>(s.disp + Disp<kS>::kWords * J);
   s.V = s.stack + 16 * J;
+  s.wrange = s.V + 16 * J;
   return s;
 }
 
@@ -923,20 +911,6 @@ __device__ __forceinline__ void load_V(const Ctx &C, const DevState &st, int64_t
   }
 }
 
-// Written-chunk masks travel only while some page is dirty (they are read
-// only for dirty pages, and a page's byte is reset whenever it is copied).
-__device__ __forceinline__ void load_fine(const Ctx &C, const DevState &st, int64_t slot, uint64_t dirty) {
-  if (dirty)
-#pragma unroll
-    for (int w = 0; w < kFineWords; ++w) C.fine[w * C.J] = st.fine[w * st.n + slot];
-}
-
-__device__ __forceinline__ void store_fine(const Ctx &C, const DevState &st, int64_t slot, uint64_t dirty) {
-  if (dirty)
-#pragma unroll
-    for (int w = 0; w < kFineWords; ++w) st.fine[w * st.n + slot] = C.fine[w * C.J];
-}
-
 __device__ __forceinline__ void store_V(const Ctx &C, const DevState &st, int64_t slot) {
 #pragma unroll
   for (int w = 0; w < 4; ++w) {
@@ -974,10 +948,10 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
     for (int r = 0; r < Disp<kS>::kWords; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, S.fine + (mine ? j : 0), J, S.uops, S.alu, st.rpl + slot * 16};
+              st.ram + slot * (int64_t)kRamBytes, S.wrange + (mine ? j : 0), J, S.uops, S.alu, st.rpl + slot * 16};
   if (mine) {
     load_V(C, st, slot);
-    load_fine(C, st, slot, R.dirty);
+    *C.wrange = st.wrange[slot];
   }
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
   __syncwarp();
@@ -1041,7 +1015,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
   if (active) {
     store_regs<kS>(R, st, slot);
     store_V(C, st, slot);
-    store_fine(C, st, slot, R.dirty);
+    st.wrange[slot] = *C.wrange;
     st.ep[slot] = ep;
     st.prev_score[slot] = prev;
 #pragma unroll
@@ -1161,7 +1135,7 @@ struct WsSmem {
 __device__ __forceinline__ WsSmem carve_ws(uint8_t *smem, int J) {
   WsSmem w;
   w.base = carve<false, false>(smem, J);
-  w.ring = reinterpret_cast<uint64_t *>(w.base.V + 16 * J);
+  w.ring = reinterpret_cast<uint64_t *>(w.base.wrange + ((J + 1) & ~1));
   w.done = reinterpret_cast<uint8_t *>(w.ring + 2 * 32 * J);
   w.full = reinterpret_cast<uint64_t *>(w.done + ((2 * J + 15) & ~15));
   w.empty = w.full + 2;
@@ -1197,10 +1171,10 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
     for (int r = 0; r < 32; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, S.fine + (mine ? j : 0), J, S.uops, S.alu, st.rpl + slot * 16};
+              st.ram + slot * (int64_t)kRamBytes, S.wrange + (mine ? j : 0), J, S.uops, S.alu, st.rpl + slot * 16};
   if (mine) {
     load_V(C, st, slot);
-    load_fine(C, st, slot, R.dirty);
+    *C.wrange = st.wrange[slot];
   }
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
 
@@ -1275,7 +1249,7 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
   if (active && !failed) {
     store_regs<false>(R, st, slot);
     store_V(C, st, slot);
-    store_fine(C, st, slot, R.dirty);
+    st.wrange[slot] = *C.wrange;
     st.ep[slot] = ep;
     st.prev_score[slot] = prev;
 #pragma unroll
@@ -1411,7 +1385,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
     load_regs<kS>(R, st, slot);
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, S.fine + (mine ? j : 0), J, S.uops, S.alu, st.rpl + slot * 16};
+              st.ram + slot * (int64_t)kRamBytes, S.wrange + (mine ? j : 0), J, S.uops, S.alu, st.rpl + slot * 16};
   if (doit) reset_instance<true, kS, false>(R, C, G, p.quirks);
   const unsigned which = __ballot_sync(kFull, doit);
   if (p.obs && which) {
@@ -1423,7 +1397,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
   if (doit) {
     store_regs<kS>(R, st, slot);
     store_V(C, st, slot);
-    store_fine(C, st, slot, R.dirty);
+    st.wrange[slot] = *C.wrange;
     st.ep[slot] = 0;
     st.prev_score[slot] = score(R, C, G);
     if (p.init) {
@@ -1550,7 +1524,8 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
   for (int k = 0; k < 16; ++k) st.rpl[slot * 16 + k] = st.schip ? rec.rpl[k] : 0;
   const int game = st.game[slot];
   const uint8_t *img = images + (size_t)game * kRamBytes;
-  uint64_t dirty = 0, fine[kFineWords] = {};
+  uint64_t dirty = 0;
+  uint32_t lo = 0xFFFu, hi = 0u;
   uint8_t *ram = st.ram + slot * (int64_t)kRamBytes;
   for (int page = 0; page < kRamBytes >> kPageShift; ++page) {
     bool differs = false;
@@ -1558,7 +1533,8 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
       const int a = (page << kPageShift) + b;
       if (rec.ram[a] != img[a]) {
         differs = true;
-        fine[a >> 9] |= 1ull << ((a >> kChunkShift) & 63);
+        lo = a < (int)lo ? (uint32_t)a : lo;
+        hi = (uint32_t)a;
       }
     }
     if (differs) {
@@ -1567,7 +1543,7 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
     }
   }
   st.dirty[slot] = dirty;
-  for (int w = 0; w < kFineWords; ++w) st.fine[w * st.n + slot] = fine[w];
+  st.wrange[slot] = lo | hi << 16;  // the bytes that differ from the image lie in [lo, hi]
   st.ep[slot] = rec.episode_steps;
   st.env_steps[slot] = rec.env_steps;
   st.last_act[slot] = rec.last_action;
@@ -1596,7 +1572,7 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
 size_t step_smem_bytes(int block, int ipw, int schip, int wide) {
   const size_t J = (size_t)(block / 32) * ipw;
   return (size_t)kRamBytes + kGameSmem + (wide ? kUopSmemWide : kUopSmemNarrow) + kLutSmem + kAluSmem +
-         J * ((disp_words(schip) + kFineWords) * sizeof(uint64_t) + 32 * sizeof(uint32_t));
+         J * (disp_words(schip) * sizeof(uint64_t) + 32 * sizeof(uint32_t)) + ((J + 1) & ~(size_t)1) * sizeof(uint32_t);
 }
 
 // Dynamic shared memory a CTA may opt into, less room for static shared data.
@@ -1757,7 +1733,7 @@ cudaError_t alloc_state(DevState &st, int64_t n, int schip, void **block_out, si
   // every array starts on a 256-byte boundary
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t sizes[] = {16 * N, 4 * N, 4 * N, 32 * N, 8 * (size_t)disp_words(schip) * N, 8 * N, 4096 * N,
-                          4 * N,  4 * N, 4 * N, 8 * N,  4 * N,   4 * N, 2 * N, N, N, 16 * N, 8 * kFineWords * N};
+                          4 * N,  4 * N, 4 * N, 8 * N,  4 * N,   4 * N, 2 * N, N, N, 16 * N, 4 * N};
   size_t total = 0;
   for (size_t b : sizes) total += up(b);
   uint8_t *base = nullptr;
@@ -1768,7 +1744,7 @@ cudaError_t alloc_state(DevState &st, int64_t n, int schip, void **block_out, si
                   (void **)&st.disp, (void **)&st.dirty,     (void **)&st.ram,       (void **)&st.ep,
                   (void **)&st.env_steps, (void **)&st.prev_score, (void **)&st.key, (void **)&st.uid,
                   (void **)&st.out_row, (void **)&st.game, (void **)&st.last_act, (void **)&st.mode,
-                  (void **)&st.rpl, (void **)&st.fine};
+                  (void **)&st.rpl, (void **)&st.wrange};
   for (int i = 0; i < 18; ++i) {
     *dst[i] = base + off;
     off += up(sizes[i]);

@@ -33,7 +33,7 @@ constexpr size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t N = (size_t)kStaticMaxEnvs;
 // per-slot arrays, in the order of the pointer list in octax_rollout_static
 constexpr size_t kArr[18] = {16 * N, 4 * N, 4 * N, 32 * N, 256 * N, 8 * N, 4096 * N,
-                             4 * N,  4 * N, 4 * N, 8 * N,  4 * N,   4 * N, 2 * N, N, N, 16 * N, 8 * kFineWords * N};
+                             4 * N,  4 * N, 4 * N, 8 * N,  4 * N,   4 * N, 2 * N, N, N, 16 * N, 4 * N};
 constexpr size_t state_bytes() {
   size_t t = 0;
   for (size_t b : kArr) t += up256(b);
@@ -133,7 +133,7 @@ extern "C" int octax_rollout_static(const octax_game *game, int64_t n_envs, uint
                   (void **)&st.disp,     (void **)&st.dirty,      (void **)&st.ram,  (void **)&st.ep,
                   (void **)&st.env_steps, (void **)&st.prev_score, (void **)&st.key,  (void **)&st.uid,
                   (void **)&st.out_row,  (void **)&st.game,   (void **)&st.last_act,
-                  (void **)&st.mode,     (void **)&st.rpl,    (void **)&st.fine};
+                  (void **)&st.mode,     (void **)&st.rpl,    (void **)&st.wrange};
   for (int i = 0; i < 18; ++i) {
     *dst[i] = base + off;
     off += up256(kArr[i]);
