@@ -57,6 +57,7 @@ struct Regs {
   uint32_t key0, key1, uid;
   uint32_t last_act;  // action index applied at the previous step (sticky actions)
   uint32_t hires;     // SCHIP: 1 in 128x64 mode
+  uint32_t wrange;    // lowest | highest << 16 RAM address written since the reset
 };
 
 struct Ctx {
@@ -64,7 +65,6 @@ struct Ctx {
   uint32_t *stack;     // shared: this instance's entry 0; entry i at stack[i * J]
   uint32_t *V;         // shared: this instance's V0; Vx at V[x * J]
   uint8_t *ram;        // global: this instance's 4 KB RAM (dirty pages)
-  uint32_t *wrange;    // shared: this instance's written-address range (kNoWrites: none)
   int J;
   const void *uops;      // shared: micro-op table, uint4 or uint2 entries (stage_game)
   const int4 *alu;       // shared: 8XYN coefficients, two int4 per N (stage_game)
@@ -86,16 +86,14 @@ __device__ __forceinline__ uint32_t dirty_bit(uint64_t dirty, uint32_t a) {
   return (uint32_t)(dirty >> ((a & 0xFFFu) >> kPageShift)) & 1u;
 }
 
-// Page copy-on-write keeps one 64-bit mask in registers. Beside it, shared
-// memory holds the range of RAM addresses written since the reset, so a
-// sprite on a dirty page but outside that range (beside a score buffer, say)
-// is still drawn from the shared image. Other reads of a dirty page use its
-// complete copy.
+// Page copy-on-write keeps one 64-bit mask in registers, and beside it the
+// range of RAM addresses written since the reset, so a sprite on a dirty
+// page but outside that range (beside a score buffer, say) is still drawn
+// from the shared image. Other reads of a dirty page use its complete copy.
 // True when every byte of [a, a + len) (len <= 32, a + len <= 4096) is as in the image.
 __device__ __forceinline__ bool unwritten(const Regs &R, const Ctx &C, uint32_t a, uint32_t len) {
   if (!(dirty_bit(R.dirty, a) | dirty_bit(R.dirty, a + len - 1u))) return true;
-  const uint32_t w = *C.wrange;
-  return a + len - 1u < (w & 0xFFFFu) || a > (w >> 16);
+  return a + len - 1u < (R.wrange & 0xFFFFu) || a > (R.wrange >> 16);
 }
 
 // A byte of RAM: a dirty page's copy is complete.
@@ -116,8 +114,7 @@ __device__ __forceinline__ void wr8(Regs &R, const Ctx &C, uint32_t a, uint32_t 
     dst[3] = src[3];
     R.dirty |= 1ull << page;
   }
-  const uint32_t w = *C.wrange;
-  *C.wrange = min(w & 0xFFFFu, a) | max(w >> 16, a) << 16;
+  R.wrange = min(R.wrange & 0xFFFFu, a) | max(R.wrange >> 16, a) << 16;
   C.ram[a] = (uint8_t)val;
 }
 
@@ -647,7 +644,7 @@ __device__ __forceinline__ void reset_instance(Regs &R, const Ctx &C, const Game
   R.dt = 0;
   R.st = 0;
   R.dirty = 0;
-  *C.wrange = kNoWrites;
+  R.wrange = kNoWrites;
 #pragma unroll
   for (int i = 0; i < 16; ++i) C.stack[i * C.J] = 0;
 #pragma unroll 8
@@ -807,14 +804,13 @@ struct Smem {
   int4 *alu;        // 8XYN coefficients (execute)
   uint2 *lut;       // byte of pixels -> 8 bytes of 0/1
   uint64_t *disp;
-  uint32_t *wrange; // written-address ranges [J]
   uint32_t *stack;
   uint32_t *V;
 };
 
 // Shared memory of a CTA with J instances: image | game | decoded opcodes |
-// expansion table | 8XYN coefficients | display [W][J] u64 | stack [16][J] u32 | V [16][J] u32 |
-// written range [J] u32, W = 32 (CHIP-8) or 128 (SCHIP).
+// expansion table | 8XYN coefficients | display [W][J] u64 | stack [16][J] u32 | V [16][J] u32,
+// W = 32 (CHIP-8) or 128 (SCHIP).
 template <bool kS, bool kW>
 __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
   constexpr int kUopSmem = kW ? kUopSmemWide : kUopSmemNarrow;
@@ -827,7 +823,6 @@ __device__ __forceinline__ Smem carve(uint8_t *smem, int J) {
   s.disp = reinterpret_cast<uint64_t *>(smem + kRamBytes + kGameSmem + kUopSmem + kLutSmem + kAluSmem);
   s.stack = reinterpret_cast<uint32_t *>(s.disp + Disp<kS>::kWords * J);
   s.V = s.stack + 16 * J;
-  s.wrange = s.V + 16 * J;
   return s;
 }
 
@@ -881,6 +876,7 @@ __device__ __forceinline__ void load_regs(Regs &R, const DevState &st, int64_t s
   R.st = (misc >> 16) & 0xFFu;
   R.status = misc >> 24;
   R.dirty = st.dirty[slot];
+  R.wrange = st.wrange[slot];
   R.env_steps = st.env_steps[slot];
   R.key0 = st.key[slot];
   R.key1 = st.key[n + slot];
@@ -948,11 +944,8 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
     for (int r = 0; r < Disp<kS>::kWords; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, S.wrange + (mine ? j : 0), J, S.uops, S.alu, st.rpl + slot * 16};
-  if (mine) {
-    load_V(C, st, slot);
-    *C.wrange = st.wrange[slot];
-  }
+              st.ram + slot * (int64_t)kRamBytes, J, S.uops, S.alu, st.rpl + slot * 16};
+  if (mine) load_V(C, st, slot);
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
   __syncwarp();
 
@@ -1015,7 +1008,7 @@ __device__ void run_group(const StepLaunch &p, const Group &g, const Smem &S) {
   if (active) {
     store_regs<kS>(R, st, slot);
     store_V(C, st, slot);
-    st.wrange[slot] = *C.wrange;
+    st.wrange[slot] = R.wrange;
     st.ep[slot] = ep;
     st.prev_score[slot] = prev;
 #pragma unroll
@@ -1135,7 +1128,7 @@ struct WsSmem {
 __device__ __forceinline__ WsSmem carve_ws(uint8_t *smem, int J) {
   WsSmem w;
   w.base = carve<false, false>(smem, J);
-  w.ring = reinterpret_cast<uint64_t *>(w.base.wrange + ((J + 1) & ~1));
+  w.ring = reinterpret_cast<uint64_t *>(w.base.V + 16 * J);
   w.done = reinterpret_cast<uint8_t *>(w.ring + 2 * 32 * J);
   w.full = reinterpret_cast<uint64_t *>(w.done + ((2 * J + 15) & ~15));
   w.empty = w.full + 2;
@@ -1171,11 +1164,8 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
     for (int r = 0; r < 32; ++r) S.disp[r * J + j] = st.disp[r * n + slot];
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, S.wrange + (mine ? j : 0), J, S.uops, S.alu, st.rpl + slot * 16};
-  if (mine) {
-    load_V(C, st, slot);
-    *C.wrange = st.wrange[slot];
-  }
+              st.ram + slot * (int64_t)kRamBytes, J, S.uops, S.alu, st.rpl + slot * 16};
+  if (mine) load_V(C, st, slot);
   const uint32_t K = G.K, FS = G.frameskip, first_kept = FS - (uint32_t)p.S;
 
   for (int s = 0; s < p.steps && !failed; ++s) {
@@ -1249,7 +1239,7 @@ __device__ void run_group_emu(const StepLaunch &p, const Group &g, const WsSmem 
   if (active && !failed) {
     store_regs<false>(R, st, slot);
     store_V(C, st, slot);
-    st.wrange[slot] = *C.wrange;
+    st.wrange[slot] = R.wrange;
     st.ep[slot] = ep;
     st.prev_score[slot] = prev;
 #pragma unroll
@@ -1385,7 +1375,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
     load_regs<kS>(R, st, slot);
   }
   const Ctx C{S.disp + (mine ? j : 0), S.stack + (mine ? j : 0), S.V + (mine ? j : 0),
-              st.ram + slot * (int64_t)kRamBytes, S.wrange + (mine ? j : 0), J, S.uops, S.alu, st.rpl + slot * 16};
+              st.ram + slot * (int64_t)kRamBytes, J, S.uops, S.alu, st.rpl + slot * 16};
   if (doit) reset_instance<true, kS, false>(R, C, G, p.quirks);
   const unsigned which = __ballot_sync(kFull, doit);
   if (p.obs && which) {
@@ -1397,7 +1387,7 @@ __global__ void __launch_bounds__(kMaxBlock) reset_kernel(const ResetLaunch p) {
   if (doit) {
     store_regs<kS>(R, st, slot);
     store_V(C, st, slot);
-    st.wrange[slot] = *C.wrange;
+    st.wrange[slot] = R.wrange;
     st.ep[slot] = 0;
     st.prev_score[slot] = score(R, C, G);
     if (p.init) {
@@ -1572,7 +1562,7 @@ __global__ void set_records_kernel(const DevState st, const GameDev *games, cons
 size_t step_smem_bytes(int block, int ipw, int schip, int wide) {
   const size_t J = (size_t)(block / 32) * ipw;
   return (size_t)kRamBytes + kGameSmem + (wide ? kUopSmemWide : kUopSmemNarrow) + kLutSmem + kAluSmem +
-         J * (disp_words(schip) * sizeof(uint64_t) + 32 * sizeof(uint32_t)) + ((J + 1) & ~(size_t)1) * sizeof(uint32_t);
+         J * (disp_words(schip) * sizeof(uint64_t) + 32 * sizeof(uint32_t));
 }
 
 // Dynamic shared memory a CTA may opt into, less room for static shared data.
