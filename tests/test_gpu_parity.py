@@ -318,6 +318,8 @@ def test_code_as_data_through_gpu(variant):
         assert (V[0::2, 10] == 9).all() and (V[1::2, 12] == 7).all()
 
 
+from test_oracle_pins import SPRITE_PAGE_DATA, SPRITE_PAGE_WORDS  # noqa: E402
+
 EDGE_PROGRAMS = [
     # FX33 across the end of memory into page 0, FX65 back, then a sprite read
     # from the written (dirty) page 0
@@ -337,6 +339,9 @@ EDGE_PROGRAMS = [
     [0x60FF, 0xBFFF],
     # FX0A: wait for the step's key, count the presses
     [0xF00A, 0x7101, 0x1200],
+    # sprites on a written page: one outside the written bytes, one rewritten
+    # by FX55, one inside the written address range but unchanged
+    (SPRITE_PAGE_WORDS, SPRITE_PAGE_DATA),
 ]
 
 
@@ -346,7 +351,8 @@ def test_edge_programs_through_gpu(variant, quirks):
     pages, stack overflow and underflow, undefined opcodes, BNNN past 0xFFF,
     FX0A with the step's key: whole-state parity at every step, seven
     programs interleaved in one environment."""
-    games = [prog(p, instr_per_frame=10, frameskip=4, variant=variant) for p in EDGE_PROGRAMS]
+    games = [prog(*(p if isinstance(p, tuple) else (p,)), instr_per_frame=10, frameskip=4, variant=variant)
+             for p in EDGE_PROGRAMS]
     n = 4 * len(games)
     goe = (np.arange(n) % len(games)).astype(np.uint16)
     env, ref = full_compare(games, n, 12, seed=3, action_seed=3, game_of_env=goe, quirks=quirks)

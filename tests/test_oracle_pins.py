@@ -776,3 +776,40 @@ def test_odd_pc_fetches_the_straddling_opcode(oracle_lib):
     assert m.V[12] == 7 and m.m.PC == 0x205
     m.exec(3)
     assert m.m.PC == 0x205 and m.m.status == 0
+
+
+# Sprites on a page that the program writes (§3.2 memory, App. B DXYN): the
+# drawn rows are the RAM's current bytes, whether or not they were written.
+SPRITE_PAGE_WORDS = [0xA230,  # I = 0x230 (score buffer, same 64-byte page as the sprites)
+                     0x6A7B,  # VA = 123
+                     0xFA33,  # BCD into 0x230-0x232
+                     0xA228,  # I = sprite A (0x228-0x22C)
+                     0x6305, 0x6404,
+                     0xD345,  # draw A at (5, 4)
+                     0x60FF, 0x6181,
+                     0xA229,
+                     0xF155,  # rewrite A's rows 1-2 with FF 81
+                     0xA228, 0x6414,
+                     0xD345,  # draw A again at (5, 20)
+                     0xA22D, 0x631E,
+                     0xD343,  # draw B (0x22D-0x22F, unchanged) at (30, 20)
+                     0x1222, 0x0000, 0x0000]
+SPRITE_PAGE_DATA = bytes([0xF0, 0x90, 0xF0, 0x90, 0xF0,  # A at 0x228
+                          0x3C, 0x66, 0x3C,              # B at 0x22D
+                          0, 0, 0, 0])                   # score buffer at 0x230
+
+
+def test_sprites_on_a_written_page(oracle_lib):
+    m = machine(oracle_lib, SPRITE_PAGE_WORDS, data=SPRITE_PAGE_DATA)
+    m.exec(18)
+    assert m.m.PC == 0x222
+    assert list(m.ram[0x230:0x233]) == [1, 2, 3]
+
+    def rows(y, x, n):
+        return [int("".join(str(int(b)) for b in m.pixels[y + r, x:x + 8]), 2) for r in range(n)]
+
+    assert rows(4, 5, 5) == [0xF0, 0x90, 0xF0, 0x90, 0xF0]
+    assert rows(20, 5, 5) == [0xF0, 0xFF, 0x81, 0x90, 0xF0]
+    assert rows(20, 30, 3) == [0x3C, 0x66, 0x3C]
+    assert m.pixels.sum() == sum(bin(v).count("1") for v in (0xF0, 0x90) * 2 + (0xF0,)) \
+        + sum(bin(v).count("1") for v in (0xF0, 0xFF, 0x81, 0x90, 0xF0, 0x3C, 0x66, 0x3C))
