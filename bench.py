@@ -625,7 +625,7 @@ def run_reference(args) -> dict | None:
     acts = W.actions(w.action_seed, 0, K, m, w.games[0].n_actions) if K * m <= 2e9 else None
     t0 = time.perf_counter()
     for s in range(K):
-        row = acts[s] if acts is not None else W.actions(w.action_seed, s, s + 1, m)[0]
+        row = acts[s] if acts is not None else W.actions(w.action_seed, s, s + 1, m, w.games[0].n_actions)[0]
         env.step(row, threads=threads)
     dt = time.perf_counter() - t0
     value = m * K / dt

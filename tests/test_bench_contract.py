@@ -1,0 +1,87 @@
+"""bench.py's output contract and bookkeeping, without a GPU: the reference
+arm's JSON line (the CPU oracle on the host cores), the algorithmic byte
+counts behind the roofline, the workload descriptions, and how ncu exports
+become per-instance-step traffic."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_2510_01764_gb300 import workloads as W  # noqa: E402
+
+BASE_KEYS = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+             "scaling", "vs_baseline", "dtype", "data", "config"}
+
+
+def test_reference_arm_json_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--config", "small", "--steps", "3", "--warmup", "3", "--ref-budget", "1"],
+                         capture_output=True, text=True, check=True, cwd=ROOT, timeout=600).stdout
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert BASE_KEYS <= set(d)
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "env steps/s"
+    assert d["steps"] == 3 and d["warmup"] == 3 and d["n_gpus"] == 1 and d["value"] > 0
+    assert d["higher_is_better"] is True and d["vs_baseline"] is None
+    assert "workload" in d["config"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    e2e = d["e2e"]
+    assert e2e["value"] == d["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+@pytest.mark.parametrize("name", ["scale", "small", "batch", "divergence", "schip", "shooter"])
+def test_workload_descriptions_and_bytes(name):
+    w = bench.workload(name)
+    text = bench.describe(name, w)
+    assert str(w.n_envs) in text
+    schip = w.games[0].variant == "schip"
+    assert bench.frame_shape(w) == ((64, 128) if schip else (32, 64))
+    # observation stack + action + reward + done per env step
+    assert bench.step_io_bytes(w) == 4 * (8192 if schip else 2048) + 6
+    # state written back and read again per launch (display 1 KB for SCHIP)
+    assert bench.state_bytes(w) == (2228 if schip else 690)
+    assert bench.data_kind(name)
+
+
+def test_workload_resize():
+    assert bench.workload("divergence", 65536).n_envs == 65536
+    with pytest.raises(SystemExit):
+        bench.workload("small", 10)
+
+
+def test_record_traffic_from_an_ncu_export(tmp_path, monkeypatch):
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "feedface")
+    cols = ["Kernel Name", "dram__bytes_read.sum", "dram__bytes_write.sum", "smsp__inst_executed.sum",
+            "smsp__thread_inst_executed_per_inst_executed.ratio",
+            "smsp__sass_average_branch_targets_threads_uniform.pct", "gpu__time_duration.sum"]
+    units = ["", "Mbyte", "Gbyte", "inst", "", "%", "us"]
+    row = ["void step_kernel_chip8<1>(StepLaunch)", "8", "4", "655360", "9.5", "90", "800"]
+    csv_path = tmp_path / "raw.csv"
+    csv_path.write_text("\n".join(",".join(f'"{c}"' for c in r) for r in (cols, units, row)) + "\n")
+    e = bench.record_traffic(str(csv_path), "scale", "256,7,32,0,1,0,1", 1000)
+    assert e["kernel_source"] == "feedface" and e["captured_n_envs"] == 16384
+    assert e["dram_bytes_per_launch"] == pytest.approx(8e6 + 4e9)
+    assert e["dram_bytes_per_instance_step"] == pytest.approx((8e6 + 4e9) / 1000)
+    assert e["warp_inst_per_instance_step"] == pytest.approx(655.36)
+    assert e["captured_duration_s"] == pytest.approx(800e-6)
+    stored = json.load(open(tmp_path / "profiles" / "traffic.json"))
+    assert stored["scale"] == e
+    assert bench.profiled_traffic("scale") == e          # same source hash: used
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "changed")
+    assert bench.profiled_traffic("scale") is None       # kernel changed: not used
+
+
+def test_kernel_source_hash_ignores_comments():
+    a = "int f() { return 1; } // one\n/* block */\n"
+    b = "int f() {   return 1; }\n"
+    assert bench.strip_comments(a).split() == bench.strip_comments(b).split()
