@@ -1,8 +1,9 @@
 // liboctax device code: the vectorised CHIP-8 environment step for sm_103a.
 //
 // Mapping (one CTA = one group of block/32 * ipw instances of one game):
-//  - each warp emulates `ipw` instances, one per lane; PC/I/SP/timers/status
-//    and the 64-bit dirty-page mask live in registers; V0-VF (one u32 each),
+//  - each warp emulates `ipw` instances, one per lane; PC/I/SP/timers/status,
+//    the 64-bit dirty-page mask and the written-address range live in
+//    registers; V0-VF (one u32 each),
 //    the call stack and the bit-packed 64x32 display (one u64 per row, bit x =
 //    pixel x; Super-CHIP: two u64 per row of the 128x64 buffer) live in
 //    shared memory laid out [register|entry|row][instance],
@@ -10,8 +11,12 @@
 //  - the game's initial 4 KB RAM image (font + ROM) is staged once per CTA in
 //    shared memory and is read-only; an instance's writes go to 64-byte pages
 //    of its own RAM in global memory, tracked by the dirty mask. Fetches and
-//    loads read the shared image unless the page is dirty, and a reset only
-//    clears the mask;
+//    loads read the shared image unless the page is dirty; sprites read it
+//    whenever their bytes lie outside the range of addresses written since
+//    the reset (data packed next to a score buffer). A reset only clears the
+//    mask and the range;
+//  - observations can also be written one bit per pixel (the display words
+//    themselves), 8x fewer bytes;
 //  - dispatch limits divergence: the common opcodes (jumps, skips, loads,
 //    adds, 8XYN ALU, key tests, FX07/FX15) run through one branch-free
 //    predicated datapath that every lane executes together, with 8XYN as
