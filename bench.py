@@ -86,7 +86,8 @@ def whole_job_rate(world: int, n_envs: int, steps: int, ms: float) -> float:
 def workload(name: str, n_envs: int = 0) -> W.Workload:
     """The named configuration; n_envs > 0 resizes it (profiling captures)."""
     make = {"scale": W.cfg_scale, "small": W.cfg_small, "batch": W.cfg_batch,
-            "divergence": W.cfg_divergence, "schip": W.cfg_schip, "shooter": W.cfg_shooter}[name]
+            "divergence": W.cfg_divergence, "schip": W.cfg_schip, "shooter": W.cfg_shooter,
+            "wrappers": W.cfg_wrappers}[name]
     if n_envs > 0:
         if name == "small":
             raise SystemExit("--n-envs does not apply to the small configuration")
@@ -106,6 +107,8 @@ def describe(config: str, w: W.Workload) -> str:
         "schip": f"schip-scale: {w.n_envs} instances of the hires Super-CHIP template ROM (seed 3, "
                  f"{len(g.rom)} B), K=20, frameskip 4, obs uint8 [4,64,128], auto-reset at score>=20 "
                  "or 2,000 steps",
+        "wrappers": f"wrappers: the plain-scale workload ({w.n_envs} template instances, K=10, frameskip 4) "
+                    "with sticky actions (p = 0.25) and no-op resets (0-30 steps)",
         "shooter": f"target-shooter: {w.n_envs} instances of the Target Shooter levels 1-3 (one third each, "
                    f"{'/'.join(str(len(x.rom)) for x in w.games)} B), K=10, frameskip 4, uniform random "
                    "actions over 5, auto-reset after 10 targets or 5,000 steps",
@@ -648,7 +651,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="octax", choices=["octax", "reference"])
     ap.add_argument("--config", default="scale",
-                    choices=["scale", "small", "batch", "divergence", "schip", "shooter"])
+                    choices=["scale", "small", "batch", "divergence", "schip", "shooter", "wrappers"])
     ap.add_argument("--rollout", type=int, default=32, help="steps per octax_step_n call")
     ap.add_argument("--n-envs", type=int, default=0,
                     help="resize the configuration (0 = its own size); for small profiling captures")

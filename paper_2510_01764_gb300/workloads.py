@@ -730,6 +730,16 @@ def cfg_scale(n_envs: int = 16384, n_steps: int = 20000) -> Workload:
                     action_seed=2)
 
 
+def cfg_wrappers(n_envs: int = 16384, n_steps: int = 20000) -> Workload:
+    """The 16,384-instance template workload behind the §3.2 wrappers: sticky
+    actions with p = 0.25 and no-op resets of 0-30 steps (the values commonly
+    used for Atari agents)."""
+    w = cfg_scale(n_envs, n_steps)
+    g = replace(w.games[0], sticky_prob=0.25, max_noops=30)
+    return Workload(f"wrappers-scale-{n_envs}x{n_steps}", [g], None, n_envs, n_steps, seed=w.seed,
+                    action_seed=w.action_seed)
+
+
 def cfg_schip(n_envs: int = 16384, n_steps: int = 4000) -> Workload:
     """16,384 instances of the hires SCHIP template ROM (seed 3), K = 20, frame
     skip 4, observations uint8 [4, 64, 128], done on score >= 20 or 2,000 steps."""

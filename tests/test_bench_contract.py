@@ -37,7 +37,7 @@ def test_reference_arm_json_line():
     assert e2e["value"] == d["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
 
 
-@pytest.mark.parametrize("name", ["scale", "small", "batch", "divergence", "schip", "shooter"])
+@pytest.mark.parametrize("name", ["scale", "small", "batch", "divergence", "schip", "shooter", "wrappers"])
 def test_workload_descriptions_and_bytes(name):
     w = bench.workload(name)
     text = bench.describe(name, w)

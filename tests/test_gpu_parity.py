@@ -536,6 +536,20 @@ def test_config_scale_sampled_balanced():
     assert n_done > 0
 
 
+def test_config_wrappers_sampled():
+    """The template workload behind sticky actions (p = 0.25) and no-op resets
+    (0-30 steps), 16,384 instances x 3,000 steps in the benchmark's launch
+    shape (the wrapper kernel variant); episodes truncated at 700 steps here
+    so that every instance goes through auto-resets with no-op steps."""
+    w = W.cfg_wrappers(n_steps=3000)
+    w.games = [W.replace(w.games[0], max_episode_steps=700)]
+    sample = pick(w.n_envs, 16, 12, extra=(0, 53, 54, w.n_envs - 1))
+    env, n_done = sampled_run(w, chunk=64, sample=sample,
+                              launch=dict(block=256, inst_per_warp=7, steps_per_launch=32,
+                                          persistent=0, use_graph=1, balance=1))
+    assert n_done > 0
+
+
 @pytest.mark.parametrize("balance", [0, 1])
 def test_config_batch_sampled(balance):
     """65,536 instances over 16 ROMs (K from {5,8,10,15,20}, uneven episodes),
