@@ -874,14 +874,23 @@ int octax_autotune(octax_env *e, int n_steps, const uint8_t *actions_dev, float 
     set_error("octax_autotune: scratch allocation failed");
     return OCTAX_ENOMEM;
   }
-  size_t off = 0;
-  for (const Piece &pc : pieces) {
-    cudaMemcpyAsync(backup + off, pc.p, pc.bytes, cudaMemcpyDeviceToDevice, e->stream);
-    off += pc.bytes;
-  }
-  if (actions_dev) {
-    cudaMemcpyAsync(acts, actions_dev, (size_t)n_steps * n, cudaMemcpyDeviceToDevice, e->stream);
-  } else {  // uniform over each game's action indices (including the no-op)
+  // copy the state pieces to (save) or from (restore) the backup
+  auto copy_state = [&](bool save) {
+    size_t off = 0;
+    cudaError_t err = cudaSuccess;
+    for (const Piece &pc : pieces) {
+      const cudaError_t c =
+          save ? cudaMemcpyAsync(backup + off, pc.p, pc.bytes, cudaMemcpyDeviceToDevice, e->stream)
+               : cudaMemcpyAsync(pc.p, backup + off, pc.bytes, cudaMemcpyDeviceToDevice, e->stream);
+      if (err == cudaSuccess) err = c;
+      off += pc.bytes;
+    }
+    return err;
+  };
+  r = copy_state(true);
+  if (r == cudaSuccess && actions_dev) {
+    r = cudaMemcpyAsync(acts, actions_dev, (size_t)n_steps * n, cudaMemcpyDeviceToDevice, e->stream);
+  } else if (r == cudaSuccess) {  // uniform over each game's action indices (including the no-op)
     std::vector<uint8_t> h((size_t)n_steps * n);
     uint64_t x = 0x9E3779B97F4A7C15ull;
     for (size_t i = 0; i < h.size(); ++i) {
@@ -892,28 +901,39 @@ int octax_autotune(octax_env *e, int n_steps, const uint8_t *actions_dev, float 
       z ^= z >> 31;
       h[i] = (uint8_t)(z % 5u);
     }
-    cudaMemcpy(acts, h.data(), h.size(), cudaMemcpyHostToDevice);
+    r = cudaMemcpyAsync(acts, h.data(), h.size(), cudaMemcpyHostToDevice, e->stream);
+    if (r == cudaSuccess) r = cudaStreamSynchronize(e->stream);  // h is a local buffer
   }
   IO io{acts, obs, rew, done, e->n};
-  cudaEvent_t t0, t1;
-  cudaEventCreate(&t0);
-  cudaEventCreate(&t1);
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (r == cudaSuccess) r = cudaEventCreate(&t0);
+  if (r == cudaSuccess) r = cudaEventCreate(&t1);
   const octax_launch saved = e->cfg;
   octax_launch best = saved;
   float best_ms = 1e30f;
-  int rc = OCTAX_OK;
+  int rc = r == cudaSuccess ? OCTAX_OK : cuda_fail(r, "octax_autotune setup");
+  // Every candidate runs the same n_steps from the caller's state (restored
+  // before the warm-up and before each timed repetition), so all of them
+  // see the same phase of the workload (episode ends, resets).
   auto trial = [&](const octax_launch &c) {
     if (rc != OCTAX_OK || launch_problem(c, e->schip) || c.steps_per_launch > n_steps) return;
     e->cfg = c;
-    rc = enqueue_steps(e, c, n_steps, io);  // warm-up (graph build)
+    cudaError_t q = copy_state(false);
+    rc = q == cudaSuccess ? enqueue_steps(e, c, n_steps, io) : cuda_fail(q, "octax_autotune");  // warm-up
     float ms_min = 1e30f;
     for (int rep = 0; rep < 3 && rc == OCTAX_OK; ++rep) {
-      cudaEventRecord(t0, e->stream);
+      q = copy_state(false);
+      if (q == cudaSuccess) q = cudaEventRecord(t0, e->stream);
+      if (q != cudaSuccess) {
+        rc = cuda_fail(q, "octax_autotune");
+        break;
+      }
       rc = enqueue_steps(e, c, n_steps, io);
-      cudaEventRecord(t1, e->stream);
-      cudaEventSynchronize(t1);
+      q = cudaEventRecord(t1, e->stream);
+      if (q == cudaSuccess) q = cudaEventSynchronize(t1);
       float ms = 0;
-      cudaEventElapsedTime(&ms, t0, t1);
+      if (q == cudaSuccess) q = cudaEventElapsedTime(&ms, t0, t1);
+      if (q != cudaSuccess && rc == OCTAX_OK) rc = cuda_fail(q, "octax_autotune");
       ms_min = std::min(ms_min, ms);
     }
     if (rc == OCTAX_OK && ms_min < best_ms) {
@@ -936,21 +956,24 @@ int octax_autotune(octax_env *e, int n_steps, const uint8_t *actions_dev, float 
     for (int pers : {0, 1})
       for (int spl : {1, 2, 4, 8, 16, 32})
         trial(octax_launch{shape.block, shape.inst_per_warp, spl, pers, 1, W, shape.balance});
-  off = 0;
-  for (const Piece &pc : pieces) {
-    cudaMemcpyAsync(pc.p, backup + off, pc.bytes, cudaMemcpyDeviceToDevice, e->stream);
-    off += pc.bytes;
-  }
-  r = cudaStreamSynchronize(e->stream);
-  cudaEventDestroy(t0);
-  cudaEventDestroy(t1);
+  r = copy_state(false);
+  const cudaError_t rs = cudaStreamSynchronize(e->stream);
+  if (r == cudaSuccess) r = rs;
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
   cudaFree(backup);
   cudaFree(acts);
   cudaFree(obs);
   cudaFree(rew);
   cudaFree(done);
-  if (rc) return rc;
-  if (r != cudaSuccess) return cuda_fail(r, "octax_autotune");
+  if (rc) {
+    e->cfg = saved;
+    return rc;
+  }
+  if (r != cudaSuccess) {
+    e->cfg = saved;
+    return cuda_fail(r, "octax_autotune");
+  }
   e->cfg = best;
   if (best_ms_out) *best_ms_out = best_ms;
   return OCTAX_OK;
