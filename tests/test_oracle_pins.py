@@ -813,3 +813,25 @@ def test_sprites_on_a_written_page(oracle_lib):
     assert rows(20, 30, 3) == [0x3C, 0x66, 0x3C]
     assert m.pixels.sum() == sum(bin(v).count("1") for v in (0xF0, 0x90) * 2 + (0xF0,)) \
         + sum(bin(v).count("1") for v in (0xF0, 0xFF, 0x81, 0x90, 0xF0, 0x3C, 0x66, 0x3C))
+
+
+def test_oracle_command_line(oracle_lib, tmp_path):
+    """`python -m oracle` prints the same per-step hashes as the library."""
+    import subprocess
+    import sys
+
+    from paper_2510_01764_gb300 import workloads as W
+
+    rom = W.template_rom(W.TemplateParams(seed=3))
+    path = tmp_path / "t.ch8"
+    path.write_bytes(rom)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-m", "oracle", str(path), "--envs", "3", "--steps", "5"],
+                         capture_output=True, text=True, check=True, cwd=root).stdout.splitlines()
+    game = W.GameSpec(rom=rom, action_set=(7, 9, 5, 8), score=(W.Term("reg", 6),))
+    env = oracle_lib.OracleEnv([game], 3, seed=1)
+    env.reset()
+    _, r, d, h = env.rollout(W.actions(1, 0, 5, 3, 5), hashes=True)
+    for s in range(5):
+        assert out[s].split() == [str(s)] + [f"{int(x):016x}" for x in h[s]]
+    assert out[5].split() == ["reward", f"{float(r.sum()):.0f}", "done", str(int(d.sum()))]
