@@ -455,12 +455,21 @@ class Server:
     def submit(self, game: int, actions: np.ndarray, seed: int, out=None) -> int:
         torch = self._torch
         a = np.ascontiguousarray(actions, dtype=np.uint8)
+        if a.ndim != 2:
+            raise ValueError("actions: need uint8 [n_steps, n_envs]")
         T, n = a.shape
         if out is None:
             out = (torch.empty((T, n, self.S) + self.frame, dtype=torch.uint8, device=self.device),
                    torch.empty((T, n), dtype=torch.float32, device=self.device),
                    torch.empty((T, n), dtype=torch.uint8, device=self.device))
         obs, rew, done = out
+        # the library sees plain pointers: the sizes are checked here
+        for t, dt, shp, nm in ((obs, torch.uint8, (T, n, self.S) + self.frame, "obs"),
+                               (rew, torch.float32, (T, n), "reward"),
+                               (done, torch.uint8, (T, n), "done")):
+            if t.device != self.device or t.dtype != dt or tuple(t.shape) != shp or not t.is_contiguous():
+                raise ValueError(f"{nm}: need contiguous {dt} {shp} on {self.device}, "
+                                 f"got {t.dtype} {tuple(t.shape)} on {t.device}")
         req = CRequest(game, 0, n, T, 0, seed & 0xFFFFFFFFFFFFFFFF, a.ctypes.data,
                        obs.data_ptr(), rew.data_ptr(), done.data_ptr())
         rid = C.c_uint64()

@@ -158,3 +158,26 @@ def test_step_entry_points_reject_null_env_without_gpu(lib):
         L.octax_last_error()
         assert fn(*args) == o.EINVAL, name
         assert name.encode() in L.octax_last_error(), name
+
+
+def test_server_submit_checks_output_tensors_without_gpu():
+    """The library takes plain device pointers, so the binding checks the
+    output tensors' shape, dtype and device before a request is submitted."""
+    import numpy as np
+
+    torch = pytest.importorskip("torch")
+    from paper_2510_01764_gb300 import octax as o
+
+    srv = object.__new__(o.Server)          # no device needed: the check runs first
+    srv._torch, srv.device, srv.S, srv.frame = torch, torch.device("cpu"), 4, (32, 64)
+    T, n = 2, 8
+    good = (torch.empty((T, n, 4, 32, 64), dtype=torch.uint8), torch.empty((T, n)),
+            torch.empty((T, n), dtype=torch.uint8))
+    bad = [(torch.empty((T, n, 4, 32, 63), dtype=torch.uint8),) + good[1:],
+           (good[0], torch.empty((T, n), dtype=torch.float64), good[2]),
+           good[:2] + (torch.empty((T + 1, n), dtype=torch.uint8),)]
+    for out in bad:
+        with pytest.raises(ValueError):
+            srv.submit(0, np.zeros((T, n), np.uint8), 1, out=out)
+    with pytest.raises(ValueError):
+        srv.submit(0, np.zeros(n, np.uint8), 1, out=good)
