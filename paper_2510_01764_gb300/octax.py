@@ -361,6 +361,7 @@ class Env:
     def state_hash(self, out=None):
         torch = self._torch
         h = out if out is not None else torch.empty(self.n, dtype=torch.int64, device=self.device)
+        self._check_dev(h, torch.int64, (self.n,), "hash")
         check(load_library().octax_state_hash(self._h, _ptr(h)))
         return h
 
