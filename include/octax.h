@@ -290,9 +290,9 @@ typedef struct octax_server octax_server;
 
 typedef struct {
   int64_t memory_budget_bytes; /* device bytes for resident instance state; the
-                                  slot pool holds budget / 4,484 instances
-                                  (4,476 B of state and 8 B of per-step
-                                  buffers each; Super-CHIP: budget / 5,252)   */
+                                  slot pool holds budget / 4,476 instances
+                                  (4,468 B of state and 8 B of per-step
+                                  buffers each; Super-CHIP: budget / 5,244)   */
   int32_t block;               /* threads per CTA: 32, 64, 128, 256 (0 = 64)    */
   int32_t inst_per_warp;       /* 1, 2, 4, 8, 16, 32 (0 = 8)                    */
   int32_t max_inflight_ticks;  /* batched launches enqueued ahead, 1..8 (0 = 2) */
