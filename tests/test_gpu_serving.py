@@ -13,7 +13,7 @@ from paper_2510_01764_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-SLOT_BYTES = 4476 + 8  # >= per-slot CHIP-8 state (4,468 B) + step buffers (8 B): budgets of k slots
+SLOT_BYTES = 4476 + 8  # >= per-slot state (4,468 B) + step buffers (8 B): k * SLOT_BYTES holds >= k slots
 
 
 @pytest.fixture(scope="module", autouse=True)
