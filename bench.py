@@ -1,9 +1,11 @@
 """Benchmark of the vectorised CHIP-8 environment step on GB300.
 
-Default workload (N = 1): 16,384 instances of one seeded template ROM (seed
-2), K = 10 instructions per frame, frame skip 4, uint8 [4,32,64] observation
-stack, auto-reset on score >= 20 or 5,000 steps; K timed env steps (default
-20,000 = the whole workload) from the freshly reset state.
+Default workload (N = 1): the largest single-GPU configuration, 262,144
+instances of 64 seeded random-opcode ROMs (3,584 B each, CXNN at 10 %),
+K = 10 instructions per frame, frame skip 4, uint8 [4,32,64] observation
+stack; K timed env steps (default 2,000 = the whole workload) from the
+freshly reset state. ``--config scale|batch|schip|shooter|wrappers|small``
+selects the other workloads.
 
 One JSON line on stdout (rank 0). ``value`` is whole-job env steps/s with the
 actions already in HBM, through octax_step_n (CUDA-graph replay, launch
@@ -76,6 +78,24 @@ def max_over_ranks(values: list, device=None) -> list:
     t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return [float(v) for v in t.tolist()]
+
+
+def step_plan(steps: int, rollout: int, warmup: int) -> dict:
+    """How the K timed env steps are cut into octax_step_n calls.
+
+    T (the rollout ring's depth, the autotuner's call length) is at most the
+    step count, so a short run (``--steps 20``) tunes and times 20-step calls
+    rather than asking for more action rows than it generated. ``calls`` are
+    the [lo, hi) step ranges of the timed region (T steps each, the last one
+    ragged); ``warmup`` are the untimed step indices replayed before it (at
+    least one, cycling through the K action rows), followed by the first
+    calls again so that every graph the timed region replays exists."""
+    if steps < 1:
+        raise ValueError("need at least one timed step")
+    T = max(1, min(rollout, steps))
+    calls = [(lo, min(lo + T, steps)) for lo in range(0, steps, T)]
+    return {"T": T, "calls": calls, "warmup": [s % steps for s in range(max(warmup, 1))],
+            "warmup_calls": calls[:2]}
 
 
 def whole_job_rate(world: int, n_envs: int, steps: int, ms: float) -> float:
@@ -282,10 +302,11 @@ def run_gpu(args) -> dict | None:
     w = workload(args.config, args.n_envs)
     K, Wm = args.steps if args.steps else w.n_steps, args.warmup
     n = w.n_envs
+    plan = step_plan(K, args.rollout, Wm)
+    T, calls = plan["T"], plan["calls"]
     with torch.cuda.stream(stream):
         env = octax.Env(w.games, n, seed=w.seed, quirks=w.quirks, game_of_env=w.game_of_env,
                         device=local, stream=stream)
-        T = args.rollout
         acts_h = W.actions(w.action_seed, 0, K, n, w.games[0].n_actions)
         acts = torch.from_numpy(acts_h).to(dev)
         obs = torch.empty((T, n, 4) + frame_shape(w), dtype=torch.uint8, device=dev)
@@ -301,7 +322,6 @@ def run_gpu(args) -> dict | None:
         else:
             env.autotune(T, acts[:T])
         launch = env.launch
-        calls = [(lo, min(lo + T, K)) for lo in range(0, K, T)]
 
         def run_calls(cfg: dict | None):
             if cfg:
@@ -314,10 +334,9 @@ def run_gpu(args) -> dict | None:
             # warm-up (graph build, caches) then restore the fresh state
             if cfg:
                 env.set_launch(**cfg)
-            for lo in range(0, max(Wm, 1)):
-                s = lo % K
+            for s in plan["warmup"]:
                 env.step_n(acts[s:s + 1], out=(obs[:1], rew[:1], done[:1]))
-            for lo, hi in calls[:2]:
+            for lo, hi in plan["warmup_calls"]:
                 env.step_n(acts[lo:hi], out=(obs[:hi - lo], rew[:hi - lo], done[:hi - lo]))
             env.set_state(init_state)
             torch.cuda.synchronize(dev)
@@ -342,7 +361,7 @@ def run_gpu(args) -> dict | None:
 
         # ---- the same calls writing bit-packed observations (octax_step_n_packed)
         pobs = torch.empty((T, n) + env.packed_obs_shape, dtype=torch.int64, device=dev)
-        for lo, hi in calls[:2]:
+        for lo, hi in plan["warmup_calls"]:
             env.step_n_packed(acts[lo:hi], out=(pobs[:hi - lo], rew[:hi - lo], done[:hi - lo]))
         env.set_state(init_state)
         torch.cuda.synchronize(dev)
@@ -644,13 +663,13 @@ def run_reference(args) -> dict | None:
                     "d2h_bytes_per_step": 0}}
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=0, help="timed env steps (0 = the workload's)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="octax", choices=["octax", "reference"])
-    ap.add_argument("--config", default="scale",
+    ap.add_argument("--config", default="divergence",
                     choices=["scale", "small", "batch", "divergence", "schip", "shooter", "wrappers"])
     ap.add_argument("--rollout", type=int, default=32, help="steps per octax_step_n call")
     ap.add_argument("--n-envs", type=int, default=0,
@@ -671,7 +690,11 @@ def main():
     ap.add_argument("--traffic-launch", default="", help="launch string of the captured run")
     ap.add_argument("--traffic-units", type=int, default=0,
                     help="instance steps per captured launch (instances x steps per launch)")
-    args = ap.parse_args()
+    return ap.parse_args(argv)
+
+
+def main():
+    args = parse_args()
     if args.record_traffic:
         print(json.dumps(record_traffic(args.record_traffic, args.config, args.traffic_launch,
                                         args.traffic_units, args.n_envs), indent=1))

@@ -185,8 +185,11 @@ int octax_create(const octax_game *games, int n_games, const uint16_t *game_of_e
                  uint64_t seed, void *cuda_stream, octax_env **out);
 
 /* Reset the instances with mask_dev[i] != 0 (mask_dev NULL = all) and write
- * their observation (the reset display in every stack slot) to
- * obs_dev[i][stack_frames][H][W] (uint8 0/1; NULL = no write). H x W is 32 x 64
+ * their observation. The reset is the paper's episode start (§3.2 "ROM
+ * loading and initialization": memory image, registers, PC = 0x200) followed
+ * by the game's startup instructions (§3.3 "Initialization handling"); the
+ * reward baseline is the score after them. The observation (the reset
+ * display in every stack slot) goes to obs_dev[i][stack_frames][H][W] (uint8 0/1; NULL = no write). H x W is 32 x 64
  * for CHIP-8 and 64 x 128 for SCHIP environments. */
 int octax_reset(octax_env *env, const uint8_t *mask_dev, uint8_t *obs_dev);
 
@@ -199,14 +202,20 @@ int octax_reset(octax_env *env, const uint8_t *mask_dev, uint8_t *obs_dev);
 int octax_step(octax_env *env, const uint8_t *actions_dev, uint8_t *obs_dev,
                float *reward_dev, uint8_t *done_dev);
 
-/* n_steps steps in as few launches as the launch configuration allows
+/* n_steps steps in as few launches as the launch configuration allows. The
+ * paper steps one env step per call (§3.2, §4.2); this batched form is the
+ * "adaptive batching" that §5 names as future work for the synchronisation
+ * cost of uneven instruction counts: many steps, games with different
+ * instructions per frame and uneven episodes in one persistent or
+ * graph-replayed launch.
  * (steps_per_launch per launch, CUDA-graph replay, persistent scheduling).
  * actions_dev [n_steps][n_envs]; obs_dev [n_steps][n_envs][S][H][W];
  * reward_dev, done_dev [n_steps][n_envs]. Same results as n_steps octax_step. */
 int octax_step_n(octax_env *env, int n_steps, const uint8_t *actions_dev, uint8_t *obs_dev,
                  float *reward_dev, uint8_t *done_dev);
 
-/* octax_step_n writing packed observations, one bit per pixel instead of one
+/* octax_step_n writing packed observations (the paper's observation is a
+ * boolean frame stack, §3.2 "4-frame stacking", §4.1), one bit per pixel instead of one
  * byte (8x fewer observation bytes): obs_words_dev is uint64 [n_steps][n_envs]
  * [S][W], 16-byte aligned, with W = 32 for CHIP-8 (word y = row y, bit x =
  * pixel x) and 128 for SCHIP (word 2y + h = pixels 64h..64h+63 of row y, bit x
@@ -216,7 +225,7 @@ int octax_step_n(octax_env *env, int n_steps, const uint8_t *actions_dev, uint8_
 int octax_step_n_packed(octax_env *env, int n_steps, const uint8_t *actions_dev, uint64_t *obs_words_dev,
                         float *reward_dev, uint8_t *done_dev);
 
-/* octax_step with host buffers, synchronous. Page-locked (pinned) buffers are
+/* octax_step (§3.2) with host buffers, synchronous. Page-locked (pinned) buffers are
  * read and written by the kernel directly through their device mapping;
  * pageable buffers go through device staging buffers and copies. */
 int octax_step_host(octax_env *env, const uint8_t *actions_host, uint8_t *obs_host,
@@ -228,19 +237,25 @@ int octax_step_host_packed(octax_env *env, const uint8_t *actions_host, uint64_t
                            float *reward_host, uint8_t *done_host);
 
 /* FNV-1a 64-bit hash of each instance's canonical record (octax_state_record
- * bytes in field order, little-endian) into hash_dev [n_envs]. */
+ * bytes in field order, little-endian) into hash_dev [n_envs]. The paper
+ * defines no counterpart: this is the parity check against the CPU oracle.
+ * Asynchronous on the environment's stream; EINVAL for a NULL argument. */
 int octax_state_hash(octax_env *env, uint64_t *hash_dev);
 
 /* Copy the canonical records of instances [first, first+count) to host
- * memory. Synchronous. EINVAL if the range is outside [0, n_envs). */
+ * memory. The paper defines no counterpart (state comparison with the
+ * oracle, checkpoints). Synchronous. EINVAL if the range is outside
+ * [0, n_envs). */
 int octax_get_state(octax_env *env, int64_t first, int64_t count, octax_state_record *out_host);
 
-/* Overwrite instances [first, first+count) from records (checkpoint resume).
+/* Overwrite instances [first, first+count) from records (checkpoint resume;
+ * the paper defines no counterpart).
  * Synchronous. EINVAL if the range is outside [0, n_envs) or SP > 16. */
 int octax_set_state(octax_env *env, int64_t first, int64_t count,
                     const octax_state_record *in_host);
 
-/* Wait until all enqueued work finished; OCTAX_ETIMEOUT after timeout_ms
+/* Wait until all enqueued work finished (the paper defines no counterpart:
+ * its JAX calls block implicitly); OCTAX_ETIMEOUT after timeout_ms
  * (negative = no limit). OCTAX_ECUDA if a kernel reported an internal
  * hand-over timeout since the last octax_sync: the outputs of the calls
  * since then are incomplete and the state of the instances in the failed
@@ -248,7 +263,7 @@ int octax_set_state(octax_env *env, int64_t first, int64_t count,
  * flag, so the environment stays usable. */
 int octax_sync(octax_env *env, int timeout_ms);
 
-/* Diagnostic for the failure path of the warp-specialised kernel
+/* Diagnostic (the paper defines no counterpart) for the failure path of the warp-specialised kernel
  * (writer_warps > 0): while `on` is nonzero its writer warps skip their
  * shared-memory hand-over, so the emulator warps' bounded waits (at most
  * about one second each) run out, the kernel records the failure and
@@ -256,11 +271,13 @@ int octax_sync(octax_env *env, int timeout_ms);
  * Drops the cached CUDA graphs so that the next launches see the switch. */
 int octax_debug_stall_writers(octax_env *env, int on);
 
+/* Read / set the launch configuration (the paper defines no counterpart:
+ * XLA picks its own launches). EINVAL for unsupported values. */
 int octax_get_launch(const octax_env *env, octax_launch *out);
-/* EINVAL for unsupported values. */
 int octax_set_launch(octax_env *env, const octax_launch *cfg);
 
-/* Time candidate launch configurations (CTA size, instances per warp, steps
+/* Autotuner for the batched step (part of §5's adaptive batching; the paper
+ * defines no tuner). Times candidate launch configurations (CTA size, instances per warp, steps
  * per launch, persistence) for octax_step_n calls of n_steps steps, starting
  * from the current state, then restore that state: results are unaffected.
  * actions_dev [n_steps][n_envs] (nullable: pseudo-random indices 0..4) should
@@ -268,16 +285,21 @@ int octax_set_launch(octax_env *env, const octax_launch *cfg);
  * configuration. Synchronous. best_ms_out (nullable) receives its time. */
 int octax_autotune(octax_env *env, int n_steps, const uint8_t *actions_dev, float *best_ms_out);
 
+/* Accessors (the paper defines no counterparts); -1 / 0 for a NULL env. */
 int64_t octax_num_envs(const octax_env *env);
 int octax_stack_frames(const octax_env *env);
 /* OCTAX_VARIANT_CHIP8 or OCTAX_VARIANT_SCHIP. */
 int octax_variant(const octax_env *env);
 /* Device bytes owned by the environment. */
 size_t octax_device_bytes(const octax_env *env);
+/* Free the environment's device memory once its queued work has finished
+ * (the paper defines no counterpart). NULL is a no-op. */
 void octax_destroy(octax_env *env);
 
 /* ---- serving: continuous batching of step requests ------------------------
- * A server keeps a pool of resident emulator slots sized by a device-memory
+ * The paper defines no server; its consumers are training loops that step
+ * batches of environments (§4.1), and the request loop here batches such
+ * step requests as they arrive. A server keeps a pool of resident emulator slots sized by a device-memory
  * budget and runs its own thread and CUDA stream. Each request asks for
  * n_envs fresh instances of one game (reset with its own seed; instance i has
  * random-number identity i) stepped n_steps times with the given actions.
@@ -360,14 +382,17 @@ void octax_server_destroy(octax_server *s);
  * for OCTAX_VARIANT_SCHIP); every device that loads the
  * library holds the array (about 4.6 MB) until the process exits.
  * The first call on a device looks up the array's device address, so make it
- * before any stream capture. Every call reuses the same array: calls whose
+ * before any stream capture. The address is kept for the life of the
+ * process: do not call this entry point again on a device after
+ * cudaDeviceReset on it (the cached address belongs to the ended context). Every call reuses the same array: calls whose
  * work overlaps on the GPU (other streams, other threads) race with each
  * other and must be serialised by the caller. */
 int octax_rollout_static(const octax_game *game, int64_t n_envs, uint32_t quirks, uint64_t seed,
                          int n_steps, const uint8_t *actions_dev, uint8_t *obs_dev,
                          float *reward_dev, uint8_t *done_dev, void *cuda_stream);
 
-/* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on this thread ("" if none). The paper
+ * defines no counterpart. */
 const char *octax_last_error(void);
 
 #ifdef __cplusplus

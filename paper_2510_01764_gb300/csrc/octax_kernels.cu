@@ -1571,15 +1571,20 @@ size_t step_smem_bytes(int block, int ipw, int schip, int wide) {
 }
 
 // Dynamic shared memory a CTA may opt into, less room for static shared data.
+// Opt-in dynamic shared memory limit of the current device (less 1 KB for
+// static shared memory), queried once per device ordinal.
 size_t max_dynamic_smem() {
-  static size_t v = 0;
-  if (!v) {
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || optin <= 0)
-      optin = 99 * 1024;
-    v = (size_t)optin - 1024;
-  }
+  static std::mutex mu;
+  static std::map<int, size_t> per_dev;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = per_dev.find(dev);
+  if (it != per_dev.end()) return it->second;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || optin <= 0)
+    optin = 99 * 1024;
+  const size_t v = (size_t)optin - 1024;
+  per_dev[dev] = v;
   return v;
 }
 
@@ -1588,9 +1593,17 @@ size_t step_ws_smem_bytes(int block, int ipw) {
   return step_smem_bytes(block, ipw, 0) + 2 * 32 * 8 * J + ((2 * J + 15) & ~(size_t)15) + 4 * 8;
 }
 
+// The dynamic shared memory attribute of a kernel applies to the current
+// device only, so it is set once per device ordinal (under a lock: the
+// serving thread and user threads launch concurrently).
 static cudaError_t ensure_smem_attr() {
-  static bool done = false;
-  if (done) return cudaSuccess;
+  static std::mutex mu;
+  static std::map<int, bool> done;
+  int dev = 0;
+  cudaError_t de = cudaGetDevice(&dev);
+  if (de != cudaSuccess) return de;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return cudaSuccess;
   const size_t cap = max_dynamic_smem();
   auto lim = [&](int schip, int wide) { return (int)std::min(step_smem_bytes(kMaxBlock, 32, schip, wide), cap); };
   const struct {
@@ -1606,7 +1619,7 @@ static cudaError_t ensure_smem_attr() {
     cudaError_t e = cudaFuncSetAttribute(f.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, f.smem);
     if (e != cudaSuccess) return e;
   }
-  done = true;
+  done[dev] = true;
   return cudaSuccess;
 }
 
@@ -1614,9 +1627,11 @@ static cudaError_t ensure_smem_attr() {
 // table when it fits and keeps the narrow table's resident CTAs per SM.
 static bool use_wide(int block, int ipw, int wrappers) {
   static std::mutex mu;
-  static std::map<std::tuple<int, int, int>, bool> memo;
+  static std::map<std::tuple<int, int, int, int>, bool> memo;
+  int dev = 0;
+  cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(mu);
-  const auto key = std::make_tuple(block, ipw, wrappers);
+  const auto key = std::make_tuple(dev, block, ipw, wrappers);
   auto it = memo.find(key);
   if (it != memo.end()) return it->second;
   const size_t sw = step_smem_bytes(block, ipw, 0, 1), sn = step_smem_bytes(block, ipw, 0, 0);

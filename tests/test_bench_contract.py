@@ -85,3 +85,39 @@ def test_kernel_source_hash_ignores_comments():
     a = "int f() { return 1; } // one\n/* block */\n"
     b = "int f() {   return 1; }\n"
     assert bench.strip_comments(a).split() == bench.strip_comments(b).split()
+
+
+@pytest.mark.parametrize("steps,warmup,rollout", [(20, 5, 32), (1, 3, 32), (33, 3, 32), (2000, 3, 32),
+                                                  (64, 0, 32), (7, 9, 4)])
+def test_step_plan(steps, warmup, rollout):
+    """The timed calls cover exactly steps 0..K-1 in order, each at most T
+    long, T never exceeds K (the autotuner and the rollout ring are sized
+    from T), and every warm-up index is a valid action row."""
+    p = bench.step_plan(steps, rollout, warmup)
+    T = p["T"]
+    assert 1 <= T <= min(rollout, steps)
+    assert p["calls"][0][0] == 0 and p["calls"][-1][1] == steps
+    for (lo, hi), (lo2, _) in zip(p["calls"], p["calls"][1:]):
+        assert hi == lo2
+    assert all(0 < hi - lo <= T for lo, hi in p["calls"])
+    assert len(p["warmup"]) == max(warmup, 1) and all(0 <= s < steps for s in p["warmup"])
+    assert p["warmup_calls"] == p["calls"][:2]
+
+
+def test_step_plan_driver_command():
+    """A short run (--steps 20 --warmup 5) tunes and times one 20-step call;
+    the default run (2,000 steps) uses 32-step calls."""
+    p = bench.step_plan(20, 32, 5)
+    assert p["T"] == 20 and p["calls"] == [(0, 20)]
+    p = bench.step_plan(2000, 32, 3)
+    assert p["T"] == 32 and len(p["calls"]) == 63 and p["calls"][-1] == (1984, 2000)
+    p = bench.step_plan(33, 32, 3)
+    assert p["calls"] == [(0, 32), (32, 33)]
+    with pytest.raises(ValueError):
+        bench.step_plan(0, 32, 3)
+
+
+def test_default_config_is_the_largest_single_gpu_workload():
+    a = bench.parse_args(["--gpus", "1", "--steps", "20", "--warmup", "5"])
+    assert a.config == "divergence" and a.steps == 20 and a.warmup == 5
+    assert bench.workload(a.config).n_envs == 262144

@@ -448,14 +448,21 @@ def test_sync_timeout_is_reported():
 
 
 # ----------------------------------------------------------------- full size, sampled
-def sampled_run(w, *, chunk, sample, launch=None, use_step_n=True):
+def sampled_run(w, *, chunk, sample, launch=None, use_step_n=True, autotune=False):
     """Run the whole workload on the GPU; compare `sample` rows with the
     oracle at every step (obs, reward, done) and the state hash at every
-    chunk boundary."""
+    chunk boundary. With autotune, the launch shape is the one octax_autotune
+    picks for chunk-step calls on the first chunk of actions, as the
+    benchmark does before it times the same workload in chunk-step calls."""
     o = octax()
     env = o.Env(w.games, w.n_envs, seed=w.seed, quirks=w.quirks, game_of_env=w.game_of_env)
     if launch:
         env.set_launch(**launch)
+    if autotune:
+        a0 = torch.from_numpy(W.actions(w.action_seed, 0, chunk, w.n_envs, w.games[0].n_actions)).cuda()
+        env.autotune(chunk, a0)
+        print(f"{w.name}: autotuned launch for {chunk}-step calls: {env.launch}")
+        del a0
     goe = None if w.game_of_env is None else w.game_of_env[sample]
     ref = oracle.OracleEnv(w.games, len(sample), seed=w.seed, quirks=w.quirks, game_of_env=goe,
                            uid_of_env=sample.astype(np.uint32))
@@ -561,6 +568,49 @@ def test_config_batch_sampled(balance):
     sampled_run(w, chunk=32, sample=sample,
                 launch=dict(block=64, inst_per_warp=16, steps_per_launch=4, persistent=1,
                             use_graph=1, balance=balance))
+
+
+@pytest.mark.parametrize("T", [20, 32])
+def test_config_divergence_autotuned(T):
+    """262,144 random-opcode instances x 2,000 steps in the launch shape the
+    autotuner picks for T-step calls (T = 32: the benchmark's default; T =
+    20: a 20-step benchmark run), stepped in T-step calls like the
+    benchmark's timed region."""
+    w = W.cfg_divergence()
+    sample = pick(w.n_envs, 24, 14, extra=(0, 1, 63, 64, w.n_envs - 1))
+    sampled_run(w, chunk=T, sample=sample, autotune=True)
+
+
+@pytest.mark.parametrize("launch", [
+    dict(block=128, inst_per_warp=16, steps_per_launch=16, persistent=1, use_graph=1),
+    dict(block=128, inst_per_warp=16, steps_per_launch=32, persistent=0, use_graph=1, balance=1),
+])
+def test_config_divergence_bench_shapes(launch):
+    """The divergence workload in shapes the autotuner has picked for it."""
+    w = W.cfg_divergence()
+    sample = pick(w.n_envs, 16, 15, extra=(2, 127, w.n_envs - 2))
+    sampled_run(w, chunk=32, sample=sample, launch=launch)
+
+
+@pytest.mark.parametrize("T", [20, 32])
+def test_config_batch_autotuned(T):
+    """65,536 instances over 16 ROMs in the autotuned shape for T-step calls."""
+    w = W.cfg_batch()
+    goe = w.game_of_env
+    per_game = [np.nonzero(goe == g)[0][:1] for g in range(16)]
+    sample = np.unique(np.concatenate(per_game + [pick(w.n_envs, 8, 16)]))
+    sampled_run(w, chunk=T, sample=sample, autotune=True)
+
+
+def test_config_batch_bench_shape():
+    """The batch workload in the shape the autotuner picked for it: 128
+    threads x 16 instances per warp, 32 steps per graph-replayed launch."""
+    w = W.cfg_batch()
+    goe = w.game_of_env
+    per_game = [np.nonzero(goe == g)[0][-1:] for g in range(16)]
+    sample = np.unique(np.concatenate(per_game + [pick(w.n_envs, 8, 17)]))
+    sampled_run(w, chunk=32, sample=sample,
+                launch=dict(block=128, inst_per_warp=16, steps_per_launch=32, persistent=0, use_graph=1))
 
 
 def test_config_divergence_sampled():

@@ -13,6 +13,7 @@ import ctypes as C
 import numpy as np
 import pytest
 
+import oracle
 from paper_2510_01764_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -26,6 +27,7 @@ def _built():
     from paper_2510_01764_gb300 import build
 
     build.build()
+    oracle.build()
 
 
 def rollout_static(game, n, seed, actions, quirks=0):
@@ -71,6 +73,27 @@ def test_static_rollout_matches_step_n_twice_in_a_row():
         for x, y in zip(got, ref):
             assert torch.equal(x, y)
     assert int(got[2].sum()) >= 0
+
+
+def test_static_rollout_at_capacity_matches_step_n_and_oracle():
+    """Exactly 1,024 instances (the last CTA group full, every state array
+    used to its end), twice in a row; the second call is also checked
+    against the CPU oracle directly."""
+    game = W.template_game(W.TemplateParams(seed=6), score_limit=2, max_episode_steps=25)
+    n, seed, T = 1024, 21, 48
+    for rep in range(2):
+        acts = torch.from_numpy(W.actions(seed + rep, 0, T, n, game.n_actions + 1)).cuda()
+        got = rollout_static(game, n, seed, acts)
+        ref = reference(game, n, seed, acts)
+        for x, y in zip(got, ref):
+            assert torch.equal(x, y)
+    orc = oracle.OracleEnv([game], n, seed=seed)
+    orc.reset()
+    o2, r2, d2, _ = orc.rollout(acts.cpu().numpy(), obs=True)
+    assert np.array_equal(got[0].cpu().numpy(), o2)
+    assert np.array_equal(got[1].cpu().numpy(), r2)
+    assert np.array_equal(got[2].cpu().numpy(), d2)
+    assert int(got[2].sum()) > 0
 
 
 def test_static_rollout_rejects_oversize():
