@@ -835,3 +835,79 @@ def test_oracle_command_line(oracle_lib, tmp_path):
     for s in range(5):
         assert out[s].split() == [str(s)] + [f"{int(x):016x}" for x in h[s]]
     assert out[5].split() == ["reward", f"{float(r.sum()):.0f}", "done", str(int(d.sum()))]
+
+
+# ---------------------------------------------------------------- DXYN brute force
+def _dxyn_by_planes(bg, rows, x0, y0, wrap):
+    """App. B sprite drawing restated as plane arithmetic: the sprite's bits
+    (MSB leftmost) placed on a padded plane at (x0, y0), the overhang either
+    dropped (clip) or folded back onto the opposite edge (wrap); the display
+    becomes bg XOR plane and VF says whether the plane met a lit pixel."""
+    n = len(rows)
+    plane = np.zeros((32 + 16, 64 + 8), dtype=np.uint8)
+    if n:
+        bits = np.unpackbits(np.frombuffer(bytes(rows), dtype=np.uint8)).reshape(n, 8)
+        plane[y0:y0 + n, x0:x0 + 8] = bits
+    on = plane[:32, :64].copy()
+    if wrap:
+        on[:16, :] |= plane[32:, :64]
+        on[:, :8] |= plane[:32, 64:]
+        on[:16, :8] |= plane[32:, 64:]
+    return bg ^ on, int((bg & on).any())
+
+
+@pytest.mark.parametrize("wrap", [False, True])
+@pytest.mark.parametrize("pattern", ["full", "random", "sparse"])
+def test_dxyn_brute_force_every_position_and_height(oracle_lib, pattern, wrap):
+    """Every origin (x0, y0) of the 64x32 display and every height N = 0..15
+    (VX, VY also above 63 / 31, reduced mod 64 / 32), over backgrounds that
+    are empty, sparse, dense or a checkerboard, with and without the
+    sprite-wrap quirk: the oracle's display and VF equal the plane
+    definition above."""
+    rng = np.random.default_rng({"full": 1, "random": 2, "sparse": 3}[pattern])
+    sprite = {"full": bytes([0xFF] * 15),
+              "random": bytes(rng.integers(0, 256, 15, dtype=np.uint8)),
+              "sparse": bytes([0x81, 0x00, 0x18, 0x24, 0x00, 0x42, 0x80, 0x01, 0x00,
+                               0x10, 0x08, 0x00, 0xC0, 0x03, 0x66])}[pattern]
+    checker = (np.indices((32, 64)).sum(axis=0) % 2).astype(np.uint8)
+    bgs = [np.zeros((32, 64), np.uint8), (rng.random((32, 64)) < 0.05).astype(np.uint8),
+           (rng.random((32, 64)) < 0.5).astype(np.uint8), checker]
+    code = [0xD010 | n for n in range(16)]
+    m = machine(oracle_lib, code, data=sprite, quirks=0x10 if wrap else 0)
+    ram = np.ctypeslib.as_array(m.m.ram)
+    i_sprite = int(np.nonzero([bytes(ram[a:a + 15]) == sprite for a in range(0x200, 0x240)])[0][0]) + 0x200
+    pix = np.ctypeslib.as_array(m.m.pix)
+    hits = 0
+    for n in range(16):
+        for y0 in range(32):
+            for x0 in range(64):
+                bg = bgs[(x0 + 3 * y0 + n) % 4]
+                pix[:] = 0
+                pix[:32, :64] = bg
+                m.m.PC = 0x200 + 2 * n
+                m.m.I = i_sprite
+                m.m.V[0] = x0 + 64 * ((y0 + n) % 4)
+                m.m.V[1] = y0 + 32 * (x0 % 8)
+                m.m.V[15] = 7
+                m.exec()
+                want, vf = _dxyn_by_planes(bg, sprite[:n], x0, y0, wrap)
+                assert np.array_equal(pix[:32, :64], want), (x0, y0, n)
+                assert m.m.V[15] == vf, (x0, y0, n)
+                assert not pix[32:].any() and not pix[:, 64:].any()
+                hits += vf
+    assert hits > 1000
+
+
+def test_dxyn_sprite_rows_wrap_around_memory(oracle_lib):
+    """Sprite rows are read at (I + r) mod 4096: a 15-row sprite starting at
+    0xFF8 takes its last 7 rows from 0x000-0x006."""
+    sprite = bytes(range(0x11, 0x11 + 15 * 0x0B, 0x0B))
+    m = machine(oracle_lib, [0xD01F])
+    ram = np.ctypeslib.as_array(m.m.ram)
+    ram[0xFF8:0x1000] = np.frombuffer(sprite[:8], np.uint8)
+    ram[0x000:0x007] = np.frombuffer(sprite[8:], np.uint8)
+    m.m.I = 0xFF8
+    m.m.V[0], m.m.V[1] = 20, 9
+    m.exec()
+    want, vf = _dxyn_by_planes(np.zeros((32, 64), np.uint8), sprite, 20, 9, False)
+    assert np.array_equal(m.pixels, want) and m.m.V[15] == vf == 0
