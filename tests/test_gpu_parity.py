@@ -581,15 +581,18 @@ def test_config_divergence_autotuned(T):
     sampled_run(w, chunk=T, sample=sample, autotune=True)
 
 
-@pytest.mark.parametrize("launch", [
-    dict(block=128, inst_per_warp=16, steps_per_launch=16, persistent=1, use_graph=1),
-    dict(block=128, inst_per_warp=16, steps_per_launch=32, persistent=0, use_graph=1, balance=1),
-])
-def test_config_divergence_bench_shapes(launch):
-    """The divergence workload in shapes the autotuner has picked for it."""
+@pytest.mark.parametrize("spl,persistent,chunk", [(16, 0, 32), (16, 1, 32), (32, 0, 32), (32, 1, 32),
+                                                  (20, 0, 20), (20, 1, 20)])
+def test_config_divergence_bench_shapes(spl, persistent, chunk):
+    """The divergence workload in the shapes the autotuner picks for it
+    (128 threads x 16 instances per warp, graph replay) at 16, 20 and 32
+    steps per launch, with and without the persistent queue, stepped in
+    calls of the benchmark's length."""
     w = W.cfg_divergence()
-    sample = pick(w.n_envs, 16, 15, extra=(2, 127, w.n_envs - 2))
-    sampled_run(w, chunk=32, sample=sample, launch=launch)
+    sample = pick(w.n_envs, 12, 15 + spl + persistent, extra=(2, 127, w.n_envs - 2))
+    sampled_run(w, chunk=chunk, sample=sample,
+                launch=dict(block=128, inst_per_warp=16, steps_per_launch=spl, persistent=persistent,
+                            use_graph=1))
 
 
 @pytest.mark.parametrize("T", [20, 32])
@@ -602,15 +605,17 @@ def test_config_batch_autotuned(T):
     sampled_run(w, chunk=T, sample=sample, autotune=True)
 
 
-def test_config_batch_bench_shape():
-    """The batch workload in the shape the autotuner picked for it: 128
-    threads x 16 instances per warp, 32 steps per graph-replayed launch."""
+@pytest.mark.parametrize("block,spl,chunk", [(128, 32, 32), (256, 32, 32), (256, 20, 20)])
+def test_config_batch_bench_shape(block, spl, chunk):
+    """The batch workload in the shapes the autotuner picked for it: 128 or
+    256 threads x 16 instances per warp, 20 or 32 steps per graph-replayed
+    launch."""
     w = W.cfg_batch()
     goe = w.game_of_env
     per_game = [np.nonzero(goe == g)[0][-1:] for g in range(16)]
-    sample = np.unique(np.concatenate(per_game + [pick(w.n_envs, 8, 17)]))
-    sampled_run(w, chunk=32, sample=sample,
-                launch=dict(block=128, inst_per_warp=16, steps_per_launch=32, persistent=0, use_graph=1))
+    sample = np.unique(np.concatenate(per_game + [pick(w.n_envs, 8, 17 + block)]))
+    sampled_run(w, chunk=chunk, sample=sample,
+                launch=dict(block=block, inst_per_warp=16, steps_per_launch=spl, persistent=0, use_graph=1))
 
 
 def test_config_divergence_sampled():
