@@ -697,6 +697,34 @@ def actions(seed: int, step_lo: int, step_hi: int, n_envs: int, n_actions: int =
     return out
 
 
+def policy_params(seed: int, n_logits: int) -> dict:
+    """Seeded float32 parameters for the §4.1 actor-critic network (random
+    initialisation: normal with standard deviation sqrt(2 / fan_in) for the
+    convolutions and hidden layers, sqrt(1 / fan_in) for the two output
+    layers, biases uniform in [-0.1, 0.1]). Shapes: w1 [32,4,8,4]
+    (out, frame, kx, ky), w2 [64,32,4,4], w3 [64,64,3,3], wa1 / wc1
+    [256,1024] (input index = channel * 16 + x * 4 + y of the 64 x 4 x 4
+    features), wa2 [n_logits,256], wc2 [256], matching biases; bc2 is a
+    one-element array."""
+    g = np.random.Generator(np.random.Philox(key=seed, counter=[0, 0, 0, 7]))
+
+    def normal(shape, fan_in, gain=2.0):
+        return (g.standard_normal(shape) * np.sqrt(gain / fan_in)).astype(np.float32)
+
+    def bias(n):
+        return g.uniform(-0.1, 0.1, size=n).astype(np.float32)
+
+    return {
+        "w1": normal((32, 4, 8, 4), 4 * 8 * 4), "b1": bias(32),
+        "w2": normal((64, 32, 4, 4), 32 * 16), "b2": bias(64),
+        "w3": normal((64, 64, 3, 3), 64 * 9), "b3": bias(64),
+        "wa1": normal((256, 1024), 1024), "ba1": bias(256),
+        "wa2": normal((n_logits, 256), 256, 1.0), "ba2": bias(n_logits),
+        "wc1": normal((256, 1024), 1024), "bc1": bias(256),
+        "wc2": normal((256,), 256, 1.0), "bc2": bias(1),
+    }
+
+
 # --------------------------------------------------------------------------
 # The configurations the implementation is measured and checked on.
 
