@@ -23,11 +23,13 @@ Readings where §4.1 is silent (each also listed in the design notes):
 - actions are sampled from softmax(logits) by inverse CDF with one uniform
   number per instance and step.
 
-``forward`` computes in float64. With ``storage="bf16"`` the weights and
-every stored activation (the convolution outputs and the flattened
-features) are rounded to bfloat16 (round to nearest even) first, which is
-the storage precision of the tensor-core kernels; dot products stay
-float64. Parameter names: w1 [32,4,8,4] (out, frame, kx, ky), b1 [32];
+``forward`` computes in float64. With ``storage="bf16"`` the weights of
+the three convolutions and of the two hidden layers, and every stored
+activation (the convolution outputs, which include the flattened
+features), are rounded to bfloat16 (round to nearest even) first: the
+storage precision of the tensor-core kernels. The output layers (wa2, wc2)
+and all biases stay float32 values, as the kernels keep them; dot products
+stay float64. Parameter names: w1 [32,4,8,4] (out, frame, kx, ky), b1 [32];
 w2 [64,32,4,4], b2; w3 [64,64,3,3], b3; wa1 [256,1024], ba1; wa2 [L,256],
 ba2 [L]; wc1 [256,1024], bc1; wc2 [256], bc2 (scalar).
 """
@@ -41,6 +43,7 @@ CONV_SPECS = (  # (in channels, out channels, kernel (kx, ky), stride (sx, sy)),
     (64, 64, (3, 3), (1, 1)),
 )
 HIDDEN = 256
+BF16_WEIGHTS = ("w1", "w2", "w3", "wa1", "wc1")   # stored in bfloat16 by the tensor-core kernels
 
 
 def bf16_round(a: np.ndarray) -> np.ndarray:
@@ -89,7 +92,7 @@ def forward(params: dict, obs: np.ndarray, storage: str = "f64", features: bool 
     """Logits [n, L] and value [n] of the network for observation stacks
     obs uint8 [n, 4, 32, 64] (values 0/1)."""
     q = bf16_round if storage == "bf16" else (lambda a: np.asarray(a, dtype=np.float64))
-    p = {k: q(v) if k.startswith("w") else np.asarray(v, dtype=np.float64) for k, v in params.items()}
+    p = {k: q(v) if k in BF16_WEIGHTS else np.asarray(v, dtype=np.float64) for k, v in params.items()}
     h = to_paper_orientation(obs)
     acts = []
     for li, (_, _, _, stride) in enumerate(CONV_SPECS, start=1):

@@ -149,3 +149,25 @@ def test_bf16_storage_stays_close_to_float64():
     assert np.abs(l16 - l64).max() < 0.03 * scale
     assert np.abs(v16 - v64).max() < 0.03 * max(1.0, float(np.abs(v64).max()))
     assert np.abs(l16 - l64).max() > 0      # the rounding is really applied
+
+
+def test_bf16_storage_rounds_exactly_the_tensor_core_operands():
+    """Only the convolution and hidden-layer weights are rounded: changing
+    an output-layer weight by less than a bfloat16 ulp still moves the
+    logits, changing a conv1 weight that little does not."""
+    p = W.policy_params(11, 5)
+    obs = (np.random.default_rng(3).random((4, 4, 32, 64)) < 0.2).astype(np.uint8)
+    base, _ = P.forward(p, obs, storage="bf16")
+    q = dict(p)
+    q["wa2"] = p["wa2"] * np.float32(1 + 2 ** -12)
+    moved, _ = P.forward(q, obs, storage="bf16")
+    assert np.abs(moved - base).max() > 0
+    q = dict(p)
+    w1 = P.bf16_round(p["w1"]).astype(np.float32)
+    q["w1"] = w1 * np.float32(1 + 2 ** -12)          # rounds back to the same bfloat16
+    assert np.array_equal(P.bf16_round(q["w1"]), P.bf16_round(w1))
+    p2 = dict(p)
+    p2["w1"] = w1
+    same, _ = P.forward(q, obs, storage="bf16")
+    ref, _ = P.forward(p2, obs, storage="bf16")
+    assert np.array_equal(same, ref)
