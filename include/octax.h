@@ -391,6 +391,79 @@ int octax_rollout_static(const octax_game *game, int64_t n_envs, uint32_t quirks
                          int n_steps, const uint8_t *actions_dev, uint8_t *obs_dev,
                          float *reward_dev, uint8_t *done_dev, void *cuda_stream);
 
+/* ---- the policy network and the on-device rollout -------------------------
+ * The actor-critic network that consumes the observation stack (§4.1,
+ * "Network architecture"): three convolutions (32 filters, kernel (8,4),
+ * stride (4,2); 64 filters, 4, 2; 64 filters, 3, 1) with ReLU over the
+ * 4-frame stack in the (frame, x, y) = (4, 64, 32) orientation, VALID
+ * padding (64 x 32 -> 15 x 15 -> 6 x 6 -> 4 x 4), the 1,024 features
+ * flattened in (channel, x, y) order, then an actor head (256 ReLU units ->
+ * n_logits logits) and a critic head (256 ReLU units -> one value). The
+ * convolutions and hidden layers run on the tensor cores with bfloat16
+ * weights and activations and fp32 accumulation; the output layers and the
+ * action draw run in fp32. */
+typedef struct octax_policy octax_policy;
+
+/* Parameters, host float32 arrays in these layouts (copied at creation):
+ * w1 [32][4][8][4] (out, frame, kx, ky), b1 [32]; w2 [64][32][4][4], b2 [64];
+ * w3 [64][64][3][3], b3 [64]; wa1, wc1 [256][1024] (input index = channel * 16
+ * + x * 4 + y), ba1, bc1 [256]; wa2 [n_logits][256], ba2 [n_logits];
+ * wc2 [256], bc2 [1]. n_logits = the game's n_actions + 1 (its action
+ * indices, the no-op last), 1..17. */
+typedef struct {
+  const float *w1, *b1, *w2, *b2, *w3, *b3;
+  const float *wa1, *ba1, *wa2, *ba2;
+  const float *wc1, *bc1, *wc2, *bc2;
+  int32_t n_logits;
+} octax_policy_params;
+
+/* Create a policy on `device` for batches of up to max_envs instances (its
+ * device buffers: packed weights 1.2 MB, features 2 KB and a two-slot packed
+ * observation ring 2 KB per instance). cuda_stream: the stream of
+ * octax_policy_forward calls (NULL = a stream of its own). Synchronous.
+ * EINVAL: a NULL array, n_logits outside 1..17, max_envs outside 1..2^31. */
+int octax_policy_create(const octax_policy_params *params, int64_t max_envs, int device, void *cuda_stream,
+                        octax_policy **out);
+
+/* The network on n_envs packed observation stacks obs_words_dev [n][4][32]
+ * (the layout of octax_step_n_packed: word y of frame f = row y, bit x =
+ * pixel x; 16-byte aligned). Outputs (each nullable): logits_dev
+ * [n][n_logits] and value_dev [n] (fp32), actions_dev [n]: an action index
+ * drawn from softmax(logits) by inverse CDF, with u = (w >> 8) * 2^-24 for
+ * the Philox4x32-10 word w at key = seed (low word first) and counter =
+ * (instance index, step, 0, 0). Asynchronous on the policy's stream.
+ * EINVAL: n_envs outside 1..max_envs, unaligned input. */
+int octax_policy_forward(octax_policy *policy, int64_t n_envs, const uint64_t *obs_words_dev, uint64_t seed,
+                         uint32_t step, float *logits_dev, float *value_dev, uint8_t *actions_dev);
+
+/* The same on uint8 observation stacks obs_dev [n][4][32][64] (the layout
+ * of octax_step_n; a nonzero byte is a lit pixel). */
+int octax_policy_forward_u8(octax_policy *policy, int64_t n_envs, const uint8_t *obs_dev, uint64_t seed,
+                            uint32_t step, float *logits_dev, float *value_dev, uint8_t *actions_dev);
+
+/* On-device rollout of n_steps steps in which the policy picks every action
+ * (the acting loop of the paper's PPO training, §4.1): for step k the
+ * network runs on the current observation and draws actions (counter step =
+ * step0 + k), then the environment steps with them. Observations pass
+ * between the two as packed frames through the policy's two-slot ring
+ * (1 KB per instance; no uint8 frames are written). obs_words_dev
+ * [n][4][32] holds the current observation on entry (from octax_reset
+ * packed by the caller, or a previous rollout) and the observation after
+ * the last step on return. Outputs per step: actions_dev [n_steps][n],
+ * logits_dev [n_steps][n][n_logits] (nullable), value_dev [n_steps][n],
+ * reward_dev and done_dev [n_steps][n] as octax_step_n. Asynchronous on the
+ * environment's stream. EINVAL: not a CHIP-8 environment with 4 stacked
+ * frames, more instances than max_envs, another device. */
+int octax_rollout_policy(octax_env *env, octax_policy *policy, int n_steps, uint64_t seed, uint32_t step0,
+                         uint64_t *obs_words_dev, uint8_t *actions_dev, float *logits_dev, float *value_dev,
+                         float *reward_dev, uint8_t *done_dev);
+
+/* Wait for the policy's stream and the device; OCTAX_ECUDA (once) if a
+ * policy kernel gave up one of its bounded waits (its outputs are then
+ * incomplete). The paper defines no counterpart. */
+int octax_policy_sync(octax_policy *policy);
+void octax_policy_destroy(octax_policy *policy);
+
 /* Message of the last failed call on this thread ("" if none). The paper
  * defines no counterpart. */
 const char *octax_last_error(void);

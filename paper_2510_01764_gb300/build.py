@@ -11,7 +11,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "liboctax.so")
-SOURCES = ["octax_kernels.cu", "octax_api.cu", "octax_server.cu", "octax_static.cu"]
+SOURCES = ["octax_kernels.cu", "octax_api.cu", "octax_server.cu", "octax_static.cu", "octax_policy.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

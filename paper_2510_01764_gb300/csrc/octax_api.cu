@@ -418,6 +418,15 @@ int enqueue_steps(octax_env *e, const octax_launch &cfg, int n_steps, const IO &
   return OCTAX_OK;
 }
 
+}  // namespace
+
+namespace octax {
+cudaStream_t env_stream(const octax_env *e) { return e ? e->stream : nullptr; }
+int env_device(const octax_env *e) { return e ? e->device : -1; }
+}  // namespace octax
+
+namespace {
+
 void free_env(octax_env *e) {
   if (!e) return;
   cudaSetDevice(e->device);

@@ -1,0 +1,871 @@
+// The actor-critic network of §4.1 on the tensor cores (tcgen05, TMEM), and
+// the rollout that runs it between environment steps on the device.
+//
+// Network (§4.1): the 4-frame stack in the (frame, x, y) = (4, 64, 32)
+// orientation; conv1 32 filters (8,4)/(4,2) -> 15 x 15; conv2 64 filters 4/2
+// -> 6 x 6; conv3 64 filters 3/1 -> 4 x 4; ReLU after each; flatten; actor
+// and critic heads of 256 ReLU units; n_logits actor outputs and one value.
+// VALID convolutions; weights and stored activations in bfloat16, products
+// accumulated in fp32 (TMEM), heads' output layers in fp32 on the CUDA cores.
+//
+// Conv kernel (persistent, one CTA of 128 threads per SM). A batch of kP = 8
+// instances is processed at a time; the rows of every GEMM are
+// (grid position, instance) with the instance fastest, so one 8-row core
+// matrix of the tcgen05 no-swizzle K-major layout is one grid position of
+// all 8 instances, and a position shift is a shift of the descriptor's start
+// address by whole core matrices. Every convolution is then a sum over its
+// kernel taps of GEMMs whose A operand is the layer input at a shifted start:
+// no im2col copies.
+//  - conv1 works on 4 x 2-pixel blocks: with stride (4, 2) its (8, 4) kernel
+//    covers 2 x 2 blocks, so it is 4 taps of K = 32 (4 frames x 8 pixels)
+//    over a 16 x 16 grid of blocks, built from the packed frame bits through
+//    a byte -> 8 x bf16 table, two block rows per M tile (one output row of
+//    16 positions x 8 instances = 128 rows).
+//  - conv2 (stride 2) reads conv1's output split by the parity of x and y:
+//    tap (kx, ky) reads sub-grid (kx & 1, ky & 1) at offset (kx >> 1,
+//    ky >> 1) of an 8-wide grid. The sub-grids are kept as a band of three
+//    grid rows that slides down with conv1's output rows; each M tile covers
+//    two output rows.
+//  - conv3 (stride 1) reads conv2's output on an 8-wide grid: tap (kx, ky) is
+//    the shift kx + 8 ky.
+//  Rows whose grid position lies outside the layer's output are computed
+//  and discarded (they read padding or neighbouring positions, always inside
+//  the buffers).
+// Heads kernel: one CTA per (128-instance tile, head); K = 1024 streamed in
+// 32-wide slices through a 3-stage ring; the actor CTA also draws the action.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "octax_internal.h"
+
+struct octax_policy {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int n_logits = 0;
+  int64_t max_envs = 0;
+  int sms = 0;
+  void *w1 = nullptr, *w2 = nullptr, *w3 = nullptr, *wh = nullptr;  // packed bf16
+  float *fp = nullptr;        // biases and output layers (fp32), see FpLayout
+  uint8_t *act3 = nullptr;    // flattened features, heads' A-operand tiles
+  uint64_t *ring = nullptr;   // rollout: two packed observation slots [2][max_envs][4][32]
+  unsigned int *err = nullptr;
+};
+
+namespace octax {
+
+cudaStream_t env_stream(const octax_env *e);
+int env_device(const octax_env *e);
+
+namespace {
+
+constexpr int kP = 8;            // instances per conv batch
+constexpr int kThreads = 128;
+constexpr int kMaxLogits = 17;   // 16 keys + the no-op
+constexpr uint64_t kMaxWaitNs = 1000000000ull;
+constexpr uint32_t kMaxPolls = 1u << 24;
+
+// ---- conv kernel shared memory (bytes) -------------------------------------
+constexpr uint32_t kLutOff = 0;                            // 256 x 16: byte -> 8 bf16 of its bits
+constexpr uint32_t kW1Off = 4096;                          // conv1 B: [tap 4][chunk 4][n 32][8]
+constexpr uint32_t kW1Bytes = 4 * 4 * 32 * 16;
+constexpr uint32_t kW2Off = kW1Off + kW1Bytes;             // conv2 B: [tap 16][chunk 4][n 64][8]
+constexpr uint32_t kW2Bytes = 16 * 4 * 64 * 16;
+constexpr uint32_t kW3Bytes = 9 * 8 * 64 * 16;             // conv3 B: [tap 9][chunk 8][n 64][8]
+constexpr uint32_t kSubPos = 25;                           // band: 3 grid rows of 8 + 1 pad position
+constexpr uint32_t kSubBytes = kSubPos * 512;              // position: 4 chunks x 8 instances x 16 B
+constexpr uint32_t kAct1Bytes = 4 * kSubBytes;             // 4 parity sub-grids
+constexpr uint32_t kW3Off = kW2Off + kW2Bytes;             // W3 overlays the band (dead by then)
+constexpr uint32_t kAct1Off = kW3Off + (kW3Bytes - kAct1Bytes);
+constexpr uint32_t kXOff = kW3Off + kW3Bytes;              // frames + blocks (conv1) | conv2 output
+constexpr uint32_t kFrOff = kXOff;                         // [8 inst][4 frames][32 rows] u64
+constexpr uint32_t kBlkOff = kXOff + 8192;                 // 33 block positions x 512 B
+constexpr uint32_t kBlkBytes = 33 * 512;
+constexpr uint32_t kAct2Off = kXOff;                       // 50 positions x (8 chunks x 8 x 16 B)
+constexpr uint32_t kAct2Bytes = 50 * 1024;
+constexpr uint32_t kXBytes = kAct2Bytes > 8192 + kBlkBytes ? kAct2Bytes : 8192 + kBlkBytes;
+constexpr uint32_t kConvSmem = kXOff + kXBytes;
+static_assert(kAct1Off >= kW3Off && kAct1Off + kAct1Bytes == kXOff, "band inside the W3 region");
+static_assert(kConvSmem <= 227 * 1024, "conv kernel shared memory");
+
+// TMEM columns (fp32) of the conv kernel's accumulators.
+constexpr uint32_t kD1Col = 0, kD2Col = 64, kD3Col = 256, kConvTmemCols = 512;
+
+// ---- heads kernel -----------------------------------------------------------
+constexpr int kHeadStages = 3;
+constexpr uint32_t kHA = 128 * 32 * 2;      // A slice: 128 rows x 32 K (bf16) = 4 chunk planes
+constexpr uint32_t kHB = 256 * 32 * 2;      // B slice: 256 rows x 32 K
+constexpr uint32_t kHeadOutOff = kHeadStages * (kHA + kHB);
+constexpr uint32_t kHeadSmem = kHeadOutOff + (kMaxLogits + 1) * 256 * 4 + 2 * 256 * 4;
+constexpr uint32_t kAct3TileBytes = 128 * 1024 * 2;   // [slice 16][chunk 8][row 128][16 B]
+
+// fp32 parameter block: b1 32 | b2 64 | b3 64 | bh [2][256] | wa2 [17][256] | ba2 [17] | wc2 [256] | bc2
+struct FpLayout {
+  static constexpr int b1 = 0, b2 = 32, b3 = 96, bh = 160, wa2 = 672, ba2 = wa2 + kMaxLogits * 256,
+                       wc2 = ba2 + kMaxLogits, bc2 = wc2 + 256, total = bc2 + 1;
+};
+
+// ---- PTX helpers -------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0; i < kMaxPolls; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (global_ns() - t0 > kMaxWaitNs) break;
+  }
+  return false;
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Bulk copy global -> shared (16-byte aligned, size a multiple of 16), completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, no swizzle: start, leading-dimension (K
+// direction) and stride-dimension (M/N direction, between 8-row core
+// matrices) byte offsets; bits 46-48 hold the fixed value 0b001.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46);
+}
+// Instruction descriptor, kind::f16: fp32 accumulator, bf16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+// 32 consecutive fp32 columns of this thread's TMEM lane (warp w reads lanes 32w..32w+31).
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // .x = a (low half)
+  return *reinterpret_cast<uint32_t *>(&h);
+}
+// bias + ReLU on 8 values, packed to one 16-byte chunk of 8 bf16.
+__device__ __forceinline__ uint4 relu_chunk(const float *v, const float *bias) {
+  float o[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) o[j] = fmaxf(v[j] + bias[j], 0.0f);
+  return make_uint4(pack_bf16(o[0], o[1]), pack_bf16(o[2], o[3]), pack_bf16(o[4], o[5]), pack_bf16(o[6], o[7]));
+}
+
+__device__ __forceinline__ uint32_t philox_w0(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                              uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return c0;
+}
+
+struct ConvArgs {
+  const uint64_t *obs_words;  // [n][4][32] packed frames (or null)
+  const uint8_t *obs_u8;      // [n][4][32][64] uint8 frames (or null)
+  int64_t n;
+  const uint8_t *w1, *w2, *w3;  // packed bf16 B operands
+  const float *fp;              // FpLayout
+  uint8_t *act3;                // [tiles][16][8][128][16 B]
+  unsigned int *err;
+};
+
+// One 32-column conv1 tile or 64-column conv2/conv3 tile: issue `taps` x
+// `kks` MMAs (M = 128) accumulating into TMEM column `col`.
+struct TileSpec {
+  uint32_t a_base, a_lbo, a_sbo;
+  uint32_t b_base, b_lbo, b_sbo;
+};
+
+template <bool kU8>
+__global__ void __launch_bounds__(kThreads, 1) policy_conv_kernel(const ConvArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ __align__(8) uint64_t bars[3];  // 0: MMA completion, 1: W1 + W2, 2: W3
+  __shared__ uint32_t tmem_s;
+  __shared__ float sb[160];                  // b1 | b2 | b3
+  const int t = threadIdx.x, warp = t >> 5;
+  const uint32_t sbase = smem_u32(sm);
+  const uint32_t bar_mma = smem_u32(&bars[0]), bar_w = smem_u32(&bars[1]), bar_w3 = smem_u32(&bars[2]);
+
+  // byte -> 8 bf16 (element k = bit k): 1.0 is 0x3F80
+  for (int b = t; b < 256; b += kThreads) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      w[j] = ((b >> (2 * j)) & 1 ? 0x3F80u : 0u) | ((b >> (2 * j + 1)) & 1 ? 0x3F800000u : 0u);
+    *reinterpret_cast<uint4 *>(sm + kLutOff + 16 * b) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  for (int j = t; j < 160; j += kThreads) sb[j] = a.fp[j];
+  if (t == 0) {
+    mbar_init(bar_mma, 1);
+    mbar_init(bar_w, 1);
+    mbar_init(bar_w3, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_s)),
+                 "r"(kConvTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_s;
+  if (t == 0) {
+    mbar_expect_tx(bar_w, kW1Bytes + kW2Bytes);
+    bulk_g2s(sbase + kW1Off, a.w1, kW1Bytes, bar_w);
+    for (uint32_t o = 0; o < kW2Bytes; o += 16384) bulk_g2s(sbase + kW2Off + o, a.w2 + o, 16384, bar_w);
+  }
+  // every wait's outcome is made uniform over the block, so all threads
+  // leave the loops together
+  bool ok = !__syncthreads_or(!mbar_wait(bar_w, 0));
+  uint32_t ph_mma = 0, ph_w3 = 0;
+  const int64_t n_batches = (a.n + kP - 1) / kP;
+  const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+  const int r = t;                     // M-tile row of this thread (TMEM lane)
+  const int g = r >> 3, ri = r & 7;    // grid position in the tile, instance in the batch
+
+  auto wait_mma = [&]() -> bool {
+    const bool w_ok = mbar_wait(bar_mma, ph_mma);
+    ph_mma ^= 1u;
+    return !__syncthreads_or(!w_ok);
+  };
+
+  for (int64_t batch = blockIdx.x; batch < n_batches && ok; batch += gridDim.x) {
+    const int64_t i0 = batch * kP;
+    // ---- frames of the batch, packed (bit x of row word y = pixel (x, y))
+    uint64_t *fr = reinterpret_cast<uint64_t *>(sm + kFrOff);
+    if (!kU8) {
+      for (int q = t; q < kP * 64; q += kThreads) {   // 64 x 16 B per instance
+        const int i = q >> 6;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (i0 + i < a.n) v = __ldg(reinterpret_cast<const uint4 *>(a.obs_words + (i0 + i) * 128) + (q & 63));
+        reinterpret_cast<uint4 *>(fr)[q] = v;
+      }
+    } else {
+      for (int q = t; q < kP * 128; q += kThreads) {  // one 64-byte row each
+        const int i = q >> 7;
+        uint64_t bits = 0;
+        if (i0 + i < a.n) {
+          const uint4 *src = reinterpret_cast<const uint4 *>(a.obs_u8 + ((i0 + i) * 128 + (q & 127)) * 64);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const uint4 v = __ldg(src + c);
+            const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+              for (int bb = 0; bb < 4; ++bb)
+                bits |= (uint64_t)(((w4[k] >> (8 * bb)) & 0xFFu) != 0u) << (16 * c + 4 * k + bb);
+          }
+        }
+        fr[q] = bits;
+      }
+    }
+    __syncthreads();
+
+    // ---- conv1 rows 0..13 (row 14 is never read by conv2), conv2 in three bands
+    for (int oy = 0; oy < 14 && ok; ++oy) {
+      // blocks of block rows oy, oy + 1 (position b = bx + 16 * (by - oy)), plus one pad position
+      for (int q = t; q < 33 * 32; q += kThreads) {
+        const int b = q >> 5, c = (q >> 3) & 3, i = q & 7;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (b < 32) {
+          const int bx = b & 15, by = oy + (b >> 4);
+          const uint64_t *rows = fr + (i * 4 + c) * 32;
+          const uint32_t lo = (uint32_t)(rows[2 * by] >> (4 * bx)) & 15u;
+          const uint32_t hi = (uint32_t)(rows[2 * by + 1] >> (4 * bx)) & 15u;
+          v = *reinterpret_cast<const uint4 *>(sm + kLutOff + 16 * (lo | hi << 4));
+        }
+        *reinterpret_cast<uint4 *>(sm + kBlkOff + b * 512 + c * 128 + i * 16) = v;
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (t == 0) {
+        tc_fence_after();
+        for (int tap = 0; tap < 4; ++tap) {
+          const int dx = tap & 1, dy = tap >> 1;
+          for (int kk = 0; kk < 2; ++kk) {
+            const uint64_t ad = sdesc(sbase + kBlkOff + (dx + 16 * dy) * 512 + kk * 256, 128, 512);
+            const uint64_t bd = sdesc(sbase + kW1Off + tap * 2048 + kk * 1024, 512, 128);
+            mma_bf16(tmem + kD1Col, ad, bd, idesc_bf16(128, 32), (tap | kk) != 0);
+          }
+        }
+        mma_commit(bar_mma);
+      }
+      ok = wait_mma();
+      if (!ok) break;
+      tc_fence_after();
+      {
+        float v[32];
+        tmem_ld32(tmem + lane_base + kD1Col, v);
+        const int ox = g;
+        if (ox <= 13) {  // conv2 reads x <= 13
+          const int band = oy <= 5 ? 0 : (oy <= 9 ? 1 : 2);
+          const int slot = (oy >> 1) - 2 * band;
+          const int sg = (ox & 1) + 2 * (oy & 1);
+          uint8_t *dst = sm + kAct1Off + sg * kSubBytes + ((ox >> 1) + 8 * slot) * 512 + ri * 16;
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            *reinterpret_cast<uint4 *>(dst + c * 128) = relu_chunk(v + 8 * c, sb + 8 * c);
+        }
+      }
+      tc_fence_before();
+      if (oy == 5 || oy == 9 || oy == 13) {
+        const int tt = (oy - 5) >> 2;  // conv2 tile: output rows 2tt, 2tt + 1
+        fence_async_smem();
+        __syncthreads();
+        if (t == 0) {
+          tc_fence_after();
+          for (int tap = 0; tap < 16; ++tap) {
+            const int kx = tap & 3, ky = tap >> 2;
+            const uint32_t sg = (kx & 1) + 2 * (ky & 1);
+            const uint32_t shift = (kx >> 1) + 8 * (ky >> 1);
+            for (int kk = 0; kk < 2; ++kk) {
+              const uint64_t ad = sdesc(sbase + kAct1Off + sg * kSubBytes + shift * 512 + kk * 256, 128, 512);
+              const uint64_t bd = sdesc(sbase + kW2Off + tap * 4096 + kk * 2048, 1024, 128);
+              mma_bf16(tmem + kD2Col + 64 * tt, ad, bd, idesc_bf16(128, 64), (tap | kk) != 0);
+            }
+          }
+          mma_commit(bar_mma);
+        }
+        ok = wait_mma();
+        if (ok && tt < 2) {  // slide the band: grid row 2 becomes grid row 0
+          for (int q = t; q < 4 * 8 * 32; q += kThreads) {  // 4 sub-grids x 8 positions x 32 x 16 B
+            const int sgq = q >> 8, rem = q & 255;
+            uint4 *base = reinterpret_cast<uint4 *>(sm + kAct1Off + sgq * kSubBytes);
+            base[rem] = base[16 * 32 + rem];
+          }
+          __syncthreads();
+        }
+      }
+    }
+    if (!ok) break;
+
+    // ---- W3 into the (now dead) band region; conv2 epilogues into region X
+    if (t == 0) {
+      fence_async_smem();
+      mbar_expect_tx(bar_w3, kW3Bytes);
+      for (uint32_t o = 0; o < kW3Bytes; o += 18432) bulk_g2s(sbase + kW3Off + o, a.w3 + o, 18432, bar_w3);
+    }
+    tc_fence_after();
+    for (int tt = 0; tt < 3; ++tt) {
+      const int px = g & 7, py = 2 * tt + (g >> 3);
+      float v[32];
+      for (int h = 0; h < 2; ++h) {
+        tmem_ld32(tmem + lane_base + kD2Col + 64 * tt + 32 * h, v);
+        if (px < 6) {
+          uint8_t *dst = sm + kAct2Off + (px + 8 * py) * 1024 + ri * 16;
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            *reinterpret_cast<uint4 *>(dst + (4 * h + c) * 128) = relu_chunk(v + 8 * c, sb + 32 + 32 * h + 8 * c);
+        }
+      }
+    }
+    tc_fence_before();
+    fence_async_smem();
+    ok = !__syncthreads_or(!mbar_wait(bar_w3, ph_w3));
+    ph_w3 ^= 1u;
+    if (!ok) break;
+
+    // ---- conv3: two tiles of 16 positions (qx + 8 qy, qy in {2u, 2u + 1})
+    if (t == 0) {
+      tc_fence_after();
+      for (int u = 0; u < 2; ++u)
+        for (int tap = 0; tap < 9; ++tap) {
+          const int kx = tap % 3, ky = tap / 3;
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t ad = sdesc(sbase + kAct2Off + (16 * u + kx + 8 * ky) * 1024 + kk * 256, 128, 1024);
+            const uint64_t bd = sdesc(sbase + kW3Off + tap * 8192 + kk * 2048, 1024, 128);
+            mma_bf16(tmem + kD3Col + 64 * u, ad, bd, idesc_bf16(128, 64), (tap | kk) != 0);
+          }
+        }
+      mma_commit(bar_mma);
+    }
+    ok = wait_mma();
+    if (!ok) break;
+    tc_fence_after();
+    for (int u = 0; u < 2; ++u) {
+      const int m = 16 * u + g, qx = m & 7, qy = m >> 3;
+      const int64_t inst = i0 + ri;
+      float v[32];
+      for (int h = 0; h < 2; ++h) {
+        tmem_ld32(tmem + lane_base + kD3Col + 64 * u + 32 * h, v);
+        if (qx < 4 && inst < a.n) {
+          const int q = qx + 4 * qy;  // feature slice: k = 64 q + channel
+          uint8_t *dst = a.act3 + (inst >> 7) * (int64_t)kAct3TileBytes + q * 16384 + (inst & 127) * 16;
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            *reinterpret_cast<uint4 *>(dst + (4 * h + c) * 2048) = relu_chunk(v + 8 * c, sb + 96 + 32 * h + 8 * c);
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();  // region X and the W3 region are rewritten by the next batch
+  }
+  if (!ok && t == 0) atomicOr(a.err, 1u);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kConvTmemCols));
+}
+
+struct HeadsArgs {
+  const uint8_t *act3;
+  int64_t n;
+  const uint8_t *wh;     // [2][16 slices][8 chunks][256][16 B]
+  const float *fp;       // FpLayout
+  int L;
+  float *logits;         // [n][L] or null
+  float *value;          // [n] or null
+  uint8_t *actions;      // [n] or null
+  uint32_t key0, key1, step;
+  unsigned int *err;
+};
+
+// blockIdx.x: 128-instance tile; blockIdx.y: 0 actor, 1 critic.
+__global__ void __launch_bounds__(kThreads, 1) policy_heads_kernel(const HeadsArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ __align__(8) uint64_t full[kHeadStages], empty[kHeadStages];
+  __shared__ uint32_t tmem_s;
+  const int t = threadIdx.x, warp = t >> 5;
+  const int head = blockIdx.y;
+  const int64_t tile = blockIdx.x;
+  const uint32_t sbase = smem_u32(sm);
+  float *wout = reinterpret_cast<float *>(sm + kHeadOutOff);      // actor [L][256] or critic [256]
+  float *bias = wout + (kMaxLogits + 1) * 256;                     // [256] hidden biases, then outputs'
+  if (head == 0) {
+    for (int j = t; j < a.L * 256; j += kThreads) wout[j] = a.fp[FpLayout::wa2 + j];
+    for (int j = t; j < a.L; j += kThreads) bias[256 + j] = a.fp[FpLayout::ba2 + j];
+  } else {
+    for (int j = t; j < 256; j += kThreads) wout[j] = a.fp[FpLayout::wc2 + j];
+    if (t == 0) bias[256] = a.fp[FpLayout::bc2];
+  }
+  for (int j = t; j < 256; j += kThreads) bias[j] = a.fp[FpLayout::bh + 256 * head + j];
+  if (t == 0) {
+    for (int s = 0; s < kHeadStages; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&tmem_s)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_s;
+  const uint8_t *A = a.act3 + tile * (int64_t)kAct3TileBytes;
+  const uint8_t *B = a.wh + (int64_t)head * (16 * 8 * 256 * 16);
+  constexpr int kSlices = 32;  // K = 1024 in slices of 32 (4 chunks)
+  bool ok = true;
+  if (t == 0) {
+    auto load = [&](int s) {
+      const int st = s % kHeadStages;
+      const uint32_t f = smem_u32(&full[st]);
+      mbar_expect_tx(f, kHA + kHB);
+      bulk_g2s(sbase + st * (kHA + kHB), A + (int64_t)s * kHA, kHA, f);
+      bulk_g2s(sbase + st * (kHA + kHB) + kHA, B + (int64_t)s * kHB, kHB, f);
+    };
+    for (int s = 0; s < kHeadStages - 1; ++s) load(s);
+    for (int s = 0; s < kSlices && ok; ++s) {
+      const int st = s % kHeadStages;
+      ok = mbar_wait(smem_u32(&full[st]), (s / kHeadStages) & 1);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t a0 = sbase + st * (kHA + kHB), b0 = a0 + kHA;
+      for (int kk = 0; kk < 2; ++kk)
+        mma_bf16(tmem, sdesc(a0 + kk * 2 * 2048, 2048, 128), sdesc(b0 + kk * 2 * 4096, 4096, 128),
+                 idesc_bf16(128, 256), (s | kk) != 0);
+      mma_commit(smem_u32(&empty[st]));
+      const int nx = s + kHeadStages - 1;  // refill the stage the previous slice used
+      if (nx < kSlices) {
+        const int pst = nx % kHeadStages;
+        if (s >= 1) ok = mbar_wait(smem_u32(&empty[pst]), ((s - 1) / kHeadStages) & 1);
+        if (ok) load(nx);
+      }
+    }
+    // the last slice's MMAs complete -> every earlier one has too
+    if (ok) ok = mbar_wait(smem_u32(&empty[(kSlices - 1) % kHeadStages]), ((kSlices - 1) / kHeadStages) & 1);
+  }
+  ok = !__syncthreads_or(!ok);
+  tc_fence_after();
+  const int64_t inst = tile * 128 + t;
+  if (ok) {
+    float acc[kMaxLogits];
+#pragma unroll
+    for (int j = 0; j < kMaxLogits; ++j) acc[j] = 0.0f;
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    for (int c0 = 0; c0 < 256; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + lane_base + c0, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + bias[c0 + j], 0.0f);
+      if (head == 0) {
+#pragma unroll
+        for (int o = 0; o < kMaxLogits; ++o) {
+          if (o < a.L) {
+            float s = acc[o];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) s = fmaf(v[j], wout[o * 256 + c0 + j], s);
+            acc[o] = s;
+          }
+        }
+      } else {
+        float s = acc[0];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) s = fmaf(v[j], wout[c0 + j], s);
+        acc[0] = s;
+      }
+    }
+    if (inst < a.n) {
+      if (head == 0) {
+        float m = -INFINITY;
+#pragma unroll
+        for (int o = 0; o < kMaxLogits; ++o)
+          if (o < a.L) {
+            acc[o] += bias[256 + o];
+            m = fmaxf(m, acc[o]);
+            if (a.logits) a.logits[inst * a.L + o] = acc[o];
+          }
+        if (a.actions) {
+          // inverse CDF: the first index whose cumulative weight exceeds u * total
+          const uint32_t w = philox_w0((uint32_t)inst, a.step, 0u, 0u, a.key0, a.key1);
+          const float u = (float)(w >> 8) * 5.9604644775390625e-08f;  // 2^-24
+          float e[kMaxLogits], tot = 0.0f;
+#pragma unroll
+          for (int o = 0; o < kMaxLogits; ++o) {
+            e[o] = o < a.L ? expf(acc[o] - m) : 0.0f;
+            tot += e[o];
+          }
+          const float target = u * tot;
+          float run = 0.0f;
+          int pick = a.L - 1;
+          for (int o = 0; o < a.L; ++o) {
+            run += e[o];
+            if (target < run) {
+              pick = o;
+              break;
+            }
+          }
+          a.actions[inst] = (uint8_t)pick;
+        }
+      } else if (a.value) {
+        a.value[inst] = acc[0] + bias[256];
+      }
+    }
+  }
+  if (!ok && t == 0) atomicOr(a.err, 1u);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+}
+
+// ---- host: weight packing ----------------------------------------------------
+uint16_t bf16_bits(float f) {
+  __nv_bfloat16 h = __float2bfloat16_rn(f);
+  uint16_t b;
+  std::memcpy(&b, &h, 2);
+  return b;
+}
+
+int launch_forward(octax_policy *p, int64_t n, const uint64_t *obs_words, const uint8_t *obs_u8, uint64_t seed,
+                   uint32_t step, float *logits, float *value, uint8_t *actions, cudaStream_t s) {
+  if (n < 1 || n > p->max_envs) {
+    set_error("octax_policy: need 1 <= n_envs <= max_envs of the policy");
+    return OCTAX_EINVAL;
+  }
+  ConvArgs c{obs_words, obs_u8, n, (const uint8_t *)p->w1, (const uint8_t *)p->w2, (const uint8_t *)p->w3, p->fp,
+             p->act3, p->err};
+  const int64_t batches = (n + kP - 1) / kP;
+  const int grid = (int)std::min<int64_t>(batches, p->sms);
+  if (obs_u8)
+    policy_conv_kernel<true><<<grid, kThreads, kConvSmem, s>>>(c);
+  else
+    policy_conv_kernel<false><<<grid, kThreads, kConvSmem, s>>>(c);
+  cudaError_t r = cudaGetLastError();
+  if (r != cudaSuccess) return cuda_fail(r, "policy conv launch");
+  HeadsArgs h{p->act3, n, (const uint8_t *)p->wh, p->fp, p->n_logits, logits, value, actions,
+              (uint32_t)seed, (uint32_t)(seed >> 32), step, p->err};
+  policy_heads_kernel<<<dim3((unsigned)((n + 127) / 128), 2), kThreads, kHeadSmem, s>>>(h);
+  r = cudaGetLastError();
+  if (r != cudaSuccess) return cuda_fail(r, "policy heads launch");
+  return OCTAX_OK;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+}  // namespace octax
+
+using namespace octax;
+
+extern "C" {
+
+int octax_policy_create(const octax_policy_params *prm, int64_t max_envs, int device, void *cuda_stream,
+                        octax_policy **out) {
+  if (!out || !prm || max_envs < 1 || max_envs > ((int64_t)1 << 31) || prm->n_logits < 1 ||
+      prm->n_logits > kMaxLogits) {
+    set_error("octax_policy_create: need params, out, 1 <= max_envs <= 2^31, 1 <= n_logits <= 17");
+    return OCTAX_EINVAL;
+  }
+  *out = nullptr;
+  const float *need[] = {prm->w1, prm->b1, prm->w2, prm->b2, prm->w3, prm->b3, prm->wa1,
+                         prm->ba1, prm->wa2, prm->ba2, prm->wc1, prm->bc1, prm->wc2, prm->bc2};
+  for (const float *q : need)
+    if (!q) {
+      set_error("octax_policy_create: every parameter array is required");
+      return OCTAX_EINVAL;
+    }
+  cudaError_t r = cudaSetDevice(device);
+  if (r != cudaSuccess) return cuda_fail(r, "octax_policy_create: cudaSetDevice");
+  const int L = prm->n_logits;
+  // conv1 B: [tap (dx + 2 dy)][chunk = frame c][n 32][k' = kx + 4 ky] = w1[n][c][4 dx + kx][2 dy + ky]
+  std::vector<uint16_t> w1p(4 * 4 * 32 * 8);
+  for (int tap = 0; tap < 4; ++tap)
+    for (int c = 0; c < 4; ++c)
+      for (int n = 0; n < 32; ++n)
+        for (int k = 0; k < 8; ++k) {
+          const int kx = 4 * (tap & 1) + (k & 3), ky = 2 * (tap >> 1) + (k >> 2);
+          w1p[((tap * 4 + c) * 32 + n) * 8 + k] = bf16_bits(prm->w1[((n * 4 + c) * 8 + kx) * 4 + ky]);
+        }
+  // conv2 B: [tap (kx + 4 ky)][chunk j][n 64][e] = w2[n][8 j + e][kx][ky]
+  std::vector<uint16_t> w2p(16 * 4 * 64 * 8);
+  for (int tap = 0; tap < 16; ++tap)
+    for (int j = 0; j < 4; ++j)
+      for (int n = 0; n < 64; ++n)
+        for (int e = 0; e < 8; ++e)
+          w2p[((tap * 4 + j) * 64 + n) * 8 + e] =
+              bf16_bits(prm->w2[((n * 32 + 8 * j + e) * 4 + (tap & 3)) * 4 + (tap >> 2)]);
+  // conv3 B: [tap (kx + 3 ky)][chunk j][n 64][e] = w3[n][8 j + e][kx][ky]
+  std::vector<uint16_t> w3p(9 * 8 * 64 * 8);
+  for (int tap = 0; tap < 9; ++tap)
+    for (int j = 0; j < 8; ++j)
+      for (int n = 0; n < 64; ++n)
+        for (int e = 0; e < 8; ++e)
+          w3p[((tap * 8 + j) * 64 + n) * 8 + e] =
+              bf16_bits(prm->w3[((n * 64 + 8 * j + e) * 3 + tap % 3) * 3 + tap / 3]);
+  // heads B: [head][slice q (16)][chunk j][n 256][e]; feature k = 64 q + channel (q = qx + 4 qy),
+  // the caller's flatten index is channel * 16 + qx * 4 + qy
+  std::vector<uint16_t> whp(2 * 16 * 8 * 256 * 8);
+  for (int head = 0; head < 2; ++head) {
+    const float *W = head ? prm->wc1 : prm->wa1;
+    for (int q = 0; q < 16; ++q)
+      for (int j = 0; j < 8; ++j)
+        for (int n = 0; n < 256; ++n)
+          for (int e = 0; e < 8; ++e) {
+            const int ch = 8 * j + e, qx = q & 3, qy = q >> 2;
+            whp[((((size_t)head * 16 + q) * 8 + j) * 256 + n) * 8 + e] =
+                bf16_bits(W[(size_t)n * 1024 + ch * 16 + qx * 4 + qy]);
+          }
+  }
+  std::vector<float> fp(FpLayout::total, 0.0f);
+  std::memcpy(&fp[FpLayout::b1], prm->b1, 32 * 4);
+  std::memcpy(&fp[FpLayout::b2], prm->b2, 64 * 4);
+  std::memcpy(&fp[FpLayout::b3], prm->b3, 64 * 4);
+  std::memcpy(&fp[FpLayout::bh], prm->ba1, 256 * 4);
+  std::memcpy(&fp[FpLayout::bh + 256], prm->bc1, 256 * 4);
+  std::memcpy(&fp[FpLayout::wa2], prm->wa2, (size_t)L * 256 * 4);
+  std::memcpy(&fp[FpLayout::ba2], prm->ba2, (size_t)L * 4);
+  std::memcpy(&fp[FpLayout::wc2], prm->wc2, 256 * 4);
+  fp[FpLayout::bc2] = prm->bc2[0];
+
+  octax_policy *p = new octax_policy();
+  p->device = device;
+  p->n_logits = L;
+  p->max_envs = max_envs;
+  cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, device);
+  if (p->sms < 1) p->sms = 1;
+  const int64_t tiles = (max_envs + 127) / 128;
+  auto fail = [&](cudaError_t e, const char *what) {
+    octax_policy_destroy(p);
+    return cuda_fail(e, what);
+  };
+  if ((r = cudaMalloc(&p->w1, w1p.size() * 2)) != cudaSuccess) return fail(r, "octax_policy_create: alloc");
+  if ((r = cudaMalloc(&p->w2, w2p.size() * 2)) != cudaSuccess) return fail(r, "octax_policy_create: alloc");
+  if ((r = cudaMalloc(&p->w3, w3p.size() * 2)) != cudaSuccess) return fail(r, "octax_policy_create: alloc");
+  if ((r = cudaMalloc(&p->wh, whp.size() * 2)) != cudaSuccess) return fail(r, "octax_policy_create: alloc");
+  if ((r = cudaMalloc((void **)&p->fp, fp.size() * 4)) != cudaSuccess) return fail(r, "octax_policy_create: alloc");
+  if ((r = cudaMalloc((void **)&p->act3, (size_t)tiles * kAct3TileBytes)) != cudaSuccess)
+    return fail(r, "octax_policy_create: alloc");
+  if ((r = cudaMalloc((void **)&p->ring, (size_t)2 * max_envs * 1024)) != cudaSuccess)
+    return fail(r, "octax_policy_create: alloc");
+  if ((r = cudaMalloc((void **)&p->err, 4)) != cudaSuccess) return fail(r, "octax_policy_create: alloc");
+  if (cuda_stream) {
+    p->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if ((r = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return fail(r, "octax_policy_create: stream");
+    p->own_stream = true;
+  }
+  r = cudaMemcpy(p->w1, w1p.data(), w1p.size() * 2, cudaMemcpyHostToDevice);
+  if (r == cudaSuccess) r = cudaMemcpy(p->w2, w2p.data(), w2p.size() * 2, cudaMemcpyHostToDevice);
+  if (r == cudaSuccess) r = cudaMemcpy(p->w3, w3p.data(), w3p.size() * 2, cudaMemcpyHostToDevice);
+  if (r == cudaSuccess) r = cudaMemcpy(p->wh, whp.data(), whp.size() * 2, cudaMemcpyHostToDevice);
+  if (r == cudaSuccess) r = cudaMemcpy(p->fp, fp.data(), fp.size() * 4, cudaMemcpyHostToDevice);
+  if (r == cudaSuccess) r = cudaMemset(p->act3, 0, (size_t)tiles * kAct3TileBytes);
+  if (r == cudaSuccess) r = cudaMemset(p->ring, 0, (size_t)2 * max_envs * 1024);
+  if (r == cudaSuccess) r = cudaMemset(p->err, 0, 4);
+  if (r == cudaSuccess)
+    r = cudaFuncSetAttribute(policy_conv_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmem);
+  if (r == cudaSuccess)
+    r = cudaFuncSetAttribute(policy_conv_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmem);
+  if (r == cudaSuccess)
+    r = cudaFuncSetAttribute(policy_heads_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kHeadSmem);
+  if (r != cudaSuccess) return fail(r, "octax_policy_create: upload");
+  *out = p;
+  return OCTAX_OK;
+}
+
+int octax_policy_forward(octax_policy *p, int64_t n_envs, const uint64_t *obs_words_dev, uint64_t seed, uint32_t step,
+                         float *logits_dev, float *value_dev, uint8_t *actions_dev) {
+  if (!p || !obs_words_dev || !aligned16(obs_words_dev)) {
+    set_error("octax_policy_forward: need a policy and 16-byte aligned packed observations");
+    return OCTAX_EINVAL;
+  }
+  cudaError_t r = cudaSetDevice(p->device);
+  if (r != cudaSuccess) return cuda_fail(r, "octax_policy_forward: cudaSetDevice");
+  return launch_forward(p, n_envs, obs_words_dev, nullptr, seed, step, logits_dev, value_dev, actions_dev,
+                        p->stream);
+}
+
+int octax_policy_forward_u8(octax_policy *p, int64_t n_envs, const uint8_t *obs_dev, uint64_t seed, uint32_t step,
+                            float *logits_dev, float *value_dev, uint8_t *actions_dev) {
+  if (!p || !obs_dev || !aligned16(obs_dev)) {
+    set_error("octax_policy_forward_u8: need a policy and 16-byte aligned observations");
+    return OCTAX_EINVAL;
+  }
+  cudaError_t r = cudaSetDevice(p->device);
+  if (r != cudaSuccess) return cuda_fail(r, "octax_policy_forward_u8: cudaSetDevice");
+  return launch_forward(p, n_envs, nullptr, obs_dev, seed, step, logits_dev, value_dev, actions_dev, p->stream);
+}
+
+int octax_rollout_policy(octax_env *e, octax_policy *p, int n_steps, uint64_t seed, uint32_t step0,
+                         uint64_t *obs_words_dev, uint8_t *actions_dev, float *logits_dev, float *value_dev,
+                         float *reward_dev, uint8_t *done_dev) {
+  if (!e || !p || n_steps < 1 || !obs_words_dev || !aligned16(obs_words_dev) || !actions_dev || !value_dev ||
+      !reward_dev || !done_dev) {
+    set_error("octax_rollout_policy: need env, policy, n_steps >= 1, aligned obs_words, actions, value, "
+              "reward and done");
+    return OCTAX_EINVAL;
+  }
+  const int64_t n = octax_num_envs(e);
+  if (octax_stack_frames(e) != 4 || octax_variant(e) != OCTAX_VARIANT_CHIP8 || n > p->max_envs ||
+      env_device(e) != p->device) {
+    set_error("octax_rollout_policy: the network takes CHIP-8 environments with 4 stacked frames, at most "
+              "max_envs instances, on the policy's device");
+    return OCTAX_EINVAL;
+  }
+  cudaError_t r = cudaSetDevice(p->device);
+  if (r != cudaSuccess) return cuda_fail(r, "octax_rollout_policy: cudaSetDevice");
+  cudaStream_t s = env_stream(e);
+  const size_t obs_bytes = (size_t)n * 1024;
+  uint64_t *slot[2] = {p->ring, p->ring + (size_t)p->max_envs * 128};
+  r = cudaMemcpyAsync(slot[0], obs_words_dev, obs_bytes, cudaMemcpyDeviceToDevice, s);
+  if (r != cudaSuccess) return cuda_fail(r, "octax_rollout_policy: observation copy");
+  int cur = 0;
+  for (int k = 0; k < n_steps; ++k) {
+    uint8_t *act = actions_dev + (size_t)k * n;
+    int rc = launch_forward(p, n, slot[cur], nullptr, seed, step0 + (uint32_t)k,
+                            logits_dev ? logits_dev + (size_t)k * n * p->n_logits : nullptr,
+                            value_dev + (size_t)k * n, act, s);
+    if (rc) return rc;
+    rc = octax_step_n_packed(e, 1, act, slot[cur ^ 1], reward_dev + (size_t)k * n, done_dev + (size_t)k * n);
+    if (rc) return rc;
+    cur ^= 1;
+  }
+  r = cudaMemcpyAsync(obs_words_dev, slot[cur], obs_bytes, cudaMemcpyDeviceToDevice, s);
+  if (r != cudaSuccess) return cuda_fail(r, "octax_rollout_policy: observation copy");
+  return OCTAX_OK;
+}
+
+int octax_policy_sync(octax_policy *p) {
+  if (!p) {
+    set_error("octax_policy_sync: need a policy");
+    return OCTAX_EINVAL;
+  }
+  cudaError_t r = cudaSetDevice(p->device);
+  if (r == cudaSuccess) r = cudaStreamSynchronize(p->stream);
+  if (r == cudaSuccess) r = cudaDeviceSynchronize();
+  if (r != cudaSuccess) return cuda_fail(r, "octax_policy_sync");
+  unsigned int h = 0;
+  r = cudaMemcpy(&h, p->err, 4, cudaMemcpyDeviceToHost);
+  if (r != cudaSuccess) return cuda_fail(r, "octax_policy_sync");
+  if (h) {
+    cudaMemset(p->err, 0, 4);
+    set_error("octax_policy_sync: a policy kernel gave up a bounded wait; its outputs are incomplete");
+    return OCTAX_ECUDA;
+  }
+  return OCTAX_OK;
+}
+
+void octax_policy_destroy(octax_policy *p) {
+  if (!p) return;
+  cudaSetDevice(p->device);
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  for (void *q : {p->w1, p->w2, p->w3, p->wh, (void *)p->fp, (void *)p->act3, (void *)p->ring, (void *)p->err})
+    if (q) cudaFree(q);
+  if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+  delete p;
+}
+
+}  // extern "C"

@@ -74,6 +74,11 @@ def frame_shape(variant) -> tuple:
     """(rows, columns) of one observation frame of a variant ("chip8"/"schip" or 0/1)."""
     return (64, 128) if variant in ("schip", VARIANT_SCHIP) else (32, 64)
 
+class CPolicyParams(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("w1", "b1", "w2", "b2", "w3", "b3", "wa1", "ba1", "wa2", "ba2",
+                                          "wc1", "bc1", "wc2", "bc2")] + [("n_logits", C.c_int32)]
+
+
 class CServerConfig(C.Structure):
     _fields_ = [("memory_budget_bytes", C.c_int64), ("block", C.c_int32),
                 ("inst_per_warp", C.c_int32), ("max_inflight_ticks", C.c_int32),
@@ -104,7 +109,8 @@ EXPORTS = ("octax_create", "octax_reset", "octax_step", "octax_step_n", "octax_s
            "octax_stack_frames", "octax_variant", "octax_step_n_packed", "octax_step_host_packed", "octax_debug_stall_writers", "octax_device_bytes", "octax_destroy", "octax_last_error",
            "octax_server_create", "octax_server_submit", "octax_server_wait",
            "octax_server_query", "octax_server_release", "octax_server_get_stats",
-           "octax_server_destroy", "octax_rollout_static")
+           "octax_server_destroy", "octax_rollout_static", "octax_policy_create", "octax_policy_forward",
+           "octax_policy_forward_u8", "octax_rollout_policy", "octax_policy_sync", "octax_policy_destroy")
 
 _lib = None
 _lock = threading.Lock()
@@ -154,6 +160,12 @@ def load_library(path: str = LIB_PATH):
             "octax_server_destroy": (None, [P]),
             "octax_rollout_static": (I32, [C.POINTER(CGame), I64, C.c_uint32, C.c_uint64, I32,
                                            P, P, P, P, P]),
+            "octax_policy_create": (I32, [C.POINTER(CPolicyParams), I64, I32, P, C.POINTER(P)]),
+            "octax_policy_forward": (I32, [P, I64, P, C.c_uint64, C.c_uint32, P, P, P]),
+            "octax_policy_forward_u8": (I32, [P, I64, P, C.c_uint64, C.c_uint32, P, P, P]),
+            "octax_rollout_policy": (I32, [P, P, I32, C.c_uint64, C.c_uint32, P, P, P, P, P, P]),
+            "octax_policy_sync": (I32, [P]),
+            "octax_policy_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -508,6 +520,100 @@ class Server:
     def close(self) -> None:
         if getattr(self, "_h", None):
             load_library().octax_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Policy:
+    """The §4.1 actor-critic network on the tensor cores (octax_policy_*).
+
+    params: dict of float32 arrays in the layouts of octax_policy_params
+    (w1 [32,4,8,4], b1, w2 [64,32,4,4], b2, w3 [64,64,3,3], b3, wa1 / wc1
+    [256,1024], ba1 / bc1, wa2 [L,256], ba2 [L], wc2 [256], bc2 [1])."""
+
+    _NAMES = ("w1", "b1", "w2", "b2", "w3", "b3", "wa1", "ba1", "wa2", "ba2", "wc1", "bc1", "wc2", "bc2")
+
+    def __init__(self, params: dict, max_envs: int, *, device=None, stream=None):
+        import torch
+
+        self._torch = torch
+        L = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("liboctax needs a CUDA device")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.n_logits = int(np.asarray(params["wa2"]).shape[0])
+        self.max_envs = int(max_envs)
+        keep = {k: np.ascontiguousarray(params[k], dtype=np.float32) for k in self._NAMES}
+        cp = CPolicyParams(*[C.c_void_p(keep[k].ctypes.data) for k in self._NAMES], self.n_logits)
+        h = C.c_void_p()
+        check(L.octax_policy_create(C.byref(cp), self.max_envs, self.device.index,
+                                    C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self._h = h
+
+    def _outputs(self, n, out):
+        torch = self._torch
+        if out is None:
+            out = (torch.empty((n, self.n_logits), dtype=torch.float32, device=self.device),
+                   torch.empty(n, dtype=torch.float32, device=self.device),
+                   torch.empty(n, dtype=torch.uint8, device=self.device))
+        return out
+
+    def forward(self, obs_words, seed: int = 0, step: int = 0, out=None):
+        """Packed observations int64 [n, 4, 32] -> (logits [n, L], value [n], actions [n])."""
+        torch = self._torch
+        n = int(obs_words.shape[0])
+        if obs_words.dtype != torch.int64 or tuple(obs_words.shape) != (n, 4, 32) or not obs_words.is_contiguous():
+            raise ValueError("obs_words: need contiguous int64 [n, 4, 32]")
+        lg, v, a = self._outputs(n, out)
+        check(load_library().octax_policy_forward(self._h, n, _ptr(obs_words), seed & 0xFFFFFFFFFFFFFFFF,
+                                                  step & 0xFFFFFFFF, _ptr(lg), _ptr(v), _ptr(a)))
+        return lg, v, a
+
+    def forward_u8(self, obs, seed: int = 0, step: int = 0, out=None):
+        """uint8 observations [n, 4, 32, 64] -> (logits, value, actions)."""
+        torch = self._torch
+        n = int(obs.shape[0])
+        if obs.dtype != torch.uint8 or tuple(obs.shape) != (n, 4, 32, 64) or not obs.is_contiguous():
+            raise ValueError("obs: need contiguous uint8 [n, 4, 32, 64]")
+        lg, v, a = self._outputs(n, out)
+        check(load_library().octax_policy_forward_u8(self._h, n, _ptr(obs), seed & 0xFFFFFFFFFFFFFFFF,
+                                                     step & 0xFFFFFFFF, _ptr(lg), _ptr(v), _ptr(a)))
+        return lg, v, a
+
+    def rollout(self, env: "Env", n_steps: int, obs_words, seed: int = 0, step0: int = 0, out=None,
+                logits: bool = True):
+        """octax_rollout_policy: n_steps on-device steps in which this policy
+        acts. obs_words int64 [n, 4, 32] (updated in place to the last
+        observation). Returns (actions [T,n], logits [T,n,L] or None,
+        value [T,n], reward [T,n], done [T,n])."""
+        torch = self._torch
+        n, T = env.n, int(n_steps)
+        if obs_words.dtype != torch.int64 or tuple(obs_words.shape) != (n, 4, 32) or not obs_words.is_contiguous():
+            raise ValueError("obs_words: need contiguous int64 [n, 4, 32]")
+        if out is None:
+            out = (torch.empty((T, n), dtype=torch.uint8, device=self.device),
+                   torch.empty((T, n, self.n_logits), dtype=torch.float32, device=self.device) if logits else None,
+                   torch.empty((T, n), dtype=torch.float32, device=self.device),
+                   torch.empty((T, n), dtype=torch.float32, device=self.device),
+                   torch.empty((T, n), dtype=torch.uint8, device=self.device))
+        a, lg, v, r, d = out
+        check(load_library().octax_rollout_policy(env._h, self._h, T, seed & 0xFFFFFFFFFFFFFFFF,
+                                                  step0 & 0xFFFFFFFF, _ptr(obs_words), _ptr(a), _ptr(lg),
+                                                  _ptr(v), _ptr(r), _ptr(d)))
+        return a, lg, v, r, d
+
+    def sync(self) -> None:
+        check(load_library().octax_policy_sync(self._h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load_library().octax_policy_destroy(self._h)
             self._h = None
 
     def __del__(self):

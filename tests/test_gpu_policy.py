@@ -1,0 +1,190 @@
+"""The §4.1 actor-critic network on the tensor cores, against the float64
+oracle (oracle/policy.py), through the C-ABI.
+
+Tolerances (floating point; the environment step itself stays bit-exact):
+- against the oracle with bfloat16 storage (weights and stored activations
+  rounded as the kernels store them, products summed in float64): the
+  kernels differ only by fp32 accumulation order and the rare bfloat16
+  rounding flip it causes, so |logit or value difference| <= 2e-3 * max(1,
+  RMS of the oracle's logits);
+- against the float64 oracle: bfloat16 weights and activations (unit
+  roundoff 2^-9) through five layers, |difference| <= 5e-2 * max(1, RMS);
+- sampled actions: the kernel's draw from its own fp32 logits equals the
+  float64 inverse-CDF draw with the same uniform number wherever that number
+  lies more than 1e-5 from a CDF boundary.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import policy as P
+from paper_2510_01764_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL_BF16, TOL_F64, MARGIN = 2e-3, 5e-2, 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_01764_gb300 import build
+
+    build.build()
+    oracle.build()
+
+
+def octax():
+    from paper_2510_01764_gb300 import octax as o
+
+    return o
+
+
+def pack(obs_u8: np.ndarray) -> np.ndarray:
+    """uint8 frames [..., 32, 64] -> int64 words [..., 32] (bit x = pixel x)."""
+    b = np.packbits(obs_u8, axis=-1, bitorder="little")
+    return b.view("<u8").reshape(obs_u8.shape[:-1]).view(np.int64)
+
+
+def random_frames(n, density, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.random((n, 4, 32, 64)) < density).astype(np.uint8)
+
+
+def env_frames(n, steps, seed):
+    """Observation stacks of template games played with random actions (oracle)."""
+    g = W.template_game(W.TemplateParams(seed=seed))
+    ref = oracle.OracleEnv([g], n, seed=seed)
+    ref.reset()
+    acts = W.actions(seed, 0, steps, n, g.n_actions + 1)
+    o, _, _, _ = ref.rollout(acts, obs=True)
+    return o[-1]
+
+
+def philox_u(seed, step, n):
+    """The kernel's uniform numbers from the oracle's own Philox4x32-10:
+    key = seed (low word first), counter = (instance, step, 0, 0), word 0."""
+    k = (seed & 0xFFFFFFFF, seed >> 32)
+    words = np.array([oracle.philox4x32_10((i, step, 0, 0), k)[0] for i in range(n)], dtype=np.uint64)
+    return P.uniform_from_word(words)
+
+
+def check_outputs(params, obs, lg, v):
+    l16, v16 = P.forward(params, obs, storage="bf16")
+    l64, v64 = P.forward(params, obs)
+    scale = max(1.0, float(np.sqrt((l64 ** 2).mean())))
+    lg, v = lg.cpu().numpy().astype(np.float64), v.cpu().numpy().astype(np.float64)
+    e16 = max(np.abs(lg - l16).max(), np.abs(v - v16).max())
+    e64 = max(np.abs(lg - l64).max(), np.abs(v - v64).max())
+    print(f"n={len(obs)}: max |gpu - oracle(bf16)| = {e16:.3g}, max |gpu - oracle(f64)| = {e64:.3g}, "
+          f"logit rms {scale:.3g}")
+    assert e16 <= TOL_BF16 * scale, e16
+    assert e64 <= TOL_F64 * scale, e64
+    return l16
+
+
+@pytest.mark.parametrize("n,density,L", [(1, 0.1, 5), (8, 0.3, 5), (129, 0.05, 17), (300, 0.15, 6)])
+def test_forward_matches_oracle(n, density, L):
+    """Ragged batches of 8 and tiles of 128, packed and uint8 inputs."""
+    o = octax()
+    params = W.policy_params(10 + n, L)
+    obs = random_frames(n, density, n)
+    pol = o.Policy(params, max_envs=max(n, 64))
+    words = torch.from_numpy(pack(obs)).cuda()
+    lg, v, a = pol.forward(words, seed=5, step=3)
+    lg2, v2, a2 = pol.forward_u8(torch.from_numpy(obs).cuda(), seed=5, step=3)
+    pol.sync()
+    assert torch.equal(lg, lg2) and torch.equal(v, v2) and torch.equal(a, a2)
+    check_outputs(params, obs, lg, v)
+
+
+def test_forward_on_game_frames_and_sampling():
+    o = octax()
+    n, L = 256, 5
+    params = W.policy_params(3, L)
+    obs = env_frames(n, 30, 2)
+    pol = o.Policy(params, max_envs=n)
+    seed, step = 0x1234_5678_9ABC, 7
+    lg, v, a = pol.forward(torch.from_numpy(pack(obs)).cuda(), seed=seed, step=step)
+    pol.sync()
+    check_outputs(params, obs, lg, v)
+    u = philox_u(seed, step, n)
+    lgh = lg.cpu().numpy().astype(np.float64)
+    want = P.sample(lgh, u)
+    ok = P.cdf_margin(lgh, u) > MARGIN
+    assert ok.mean() > 0.99
+    assert np.array_equal(a.cpu().numpy()[ok], want[ok])
+    assert len(np.unique(a.cpu().numpy())) > 1
+
+
+def test_forward_full_size_sampled():
+    """16,384 instances (128 conv batches per SM wave, 128 head tiles):
+    sampled instances against the oracle."""
+    o = octax()
+    n, L = 16384, 5
+    params = W.policy_params(4, L)
+    obs = random_frames(n, 0.08, 44)
+    pol = o.Policy(params, max_envs=n)
+    lg, v, a = pol.forward(torch.from_numpy(pack(obs)).cuda(), seed=9, step=1)
+    pol.sync()
+    idx = np.unique(np.concatenate([np.random.default_rng(1).choice(n, 48, replace=False),
+                                    [0, 7, 8, 127, 128, n - 129, n - 1]]))
+    check_outputs(params, obs[idx], lg[idx], v[idx])
+
+
+def test_rollout_teacher_forced():
+    """The on-device rollout: the policy draws every action from its own
+    logits, the environment steps with them. Replaying the drawn actions in
+    the oracle environment gives bit-identical rewards, done flags and final
+    observation; at every step the logits and value match the oracle network
+    on the oracle's observation, and every draw is the inverse-CDF draw."""
+    o = octax()
+    g = W.template_game(W.TemplateParams(seed=3), score_limit=2, max_episode_steps=30)
+    n, T, L = 200, 40, g.n_actions + 1
+    params = W.policy_params(8, L)
+    env = o.Env([g], n, seed=11)
+    ref = oracle.OracleEnv([g], n, seed=11)
+    obs0 = env.reset()
+    o0 = ref.reset()
+    assert np.array_equal(obs0.cpu().numpy(), o0)
+    pol = o.Policy(params, max_envs=n)
+    words = torch.from_numpy(pack(o0)).cuda()
+    seed = 77
+    a, lg, v, r, d = pol.rollout(env, T, words, seed=seed, step0=100)
+    pol.sync()
+    env.sync()
+    a_h = a.cpu().numpy()
+    cur = o0
+    for k in range(T):
+        l16 = check_outputs(params, cur, lg[k], v[k])
+        u = philox_u(seed, 100 + k, n)
+        lgk = lg[k].cpu().numpy().astype(np.float64)
+        ok = P.cdf_margin(lgk, u) > MARGIN
+        assert np.array_equal(a_h[k][ok], P.sample(lgk, u)[ok])
+        ob, rw, dn = ref.step(a_h[k])
+        assert np.array_equal(r[k].cpu().numpy(), rw), k
+        assert np.array_equal(d[k].cpu().numpy(), dn), k
+        cur = ob
+    assert np.array_equal(words.cpu().numpy(), pack(cur))
+    assert np.array_equal(env.state_hash().cpu().numpy().view(np.uint64), ref.hashes())
+    assert int(d.sum()) > 0 and len(np.unique(a_h)) >= 3
+
+
+def test_policy_rejects_bad_arguments():
+    o = octax()
+    params = W.policy_params(1, 5)
+    bad = dict(params)
+    bad["wa2"] = np.zeros((18, 256), np.float32)
+    bad["ba2"] = np.zeros(18, np.float32)
+    with pytest.raises(o.OctaxError):
+        o.Policy(bad, max_envs=8)
+    pol = o.Policy(params, max_envs=8)
+    words = torch.zeros((9, 4, 32), dtype=torch.int64, device="cuda")
+    with pytest.raises(o.OctaxError):
+        pol.forward(words)
+    g = W.template_game(W.TemplateParams(seed=1))
+    env = o.Env([g], 16, seed=1)
+    with pytest.raises(o.OctaxError):      # more instances than max_envs
+        pol.rollout(env, 2, torch.zeros((16, 4, 32), dtype=torch.int64, device="cuda"))
