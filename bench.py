@@ -505,11 +505,143 @@ def run_gpu(args) -> dict | None:
         },
         "clocks": clocks,
     }
+    if not args.no_policy and world == 1:
+        line["policy"] = run_policy(args, dev, stream)
     if not args.no_serve and world == 1:
         line["serving"] = run_serving(args, dev)
         line["serving_p50_ms"] = line["serving"]["poisson"]["p50_ms"]
         line["serving_p99_ms"] = line["serving"]["poisson"]["p99_ms"]
     return line
+
+
+# --------------------------------------------------------------------------- policy
+def policy_flops(n_logits: int) -> int:
+    """Algorithmic FLOPs (2 per multiply-add) of the §4.1 network per
+    instance: conv1 15x15x32 outputs of 4x8x4 inputs, conv2 6x6x64 of
+    32x4x4, conv3 4x4x64 of 64x3x3, the two 1024 -> 256 hidden layers and the
+    256 -> n_logits / 256 -> 1 output layers."""
+    conv = 15 * 15 * 32 * 128 + 6 * 6 * 64 * 512 + 4 * 4 * 64 * 576
+    heads = 1024 * 512 + 256 * (n_logits + 1)
+    return 2 * (conv + heads)
+
+
+def policy_computed_flops(n_logits: int) -> int:
+    """FLOPs the tensor cores execute per instance, including the rows of
+    positions outside each layer's output (the kernels' tap-shift tiling):
+    conv1 14 tiles, conv2 3 tiles, conv3 2 tiles of 128 rows per 8
+    instances, heads 128-row tiles."""
+    conv = (14 * 128 * 32 * 128 + 3 * 128 * 64 * 512 + 2 * 128 * 64 * 576) / 8
+    return int(2 * (conv + 1024 * 512 + 256 * (n_logits + 1)))
+
+
+def pack_words(obs):
+    """uint8 frames [..., 32, 64] (0/1) -> int64 words [..., 32], bit x = pixel x."""
+    import torch
+
+    return (obs.to(torch.int64) << torch.arange(64, device=obs.device)).sum(dim=-1)
+
+
+def run_policy(args, dev, stream) -> dict:
+    """The §4.1 network acting in the environment on the device: the fused
+    rollout (octax_rollout_policy: packed frames handed to the network
+    through an L2-resident ring) against the environment step writing uint8
+    observations to HBM followed by a separate network forward on them, and
+    the network forward alone against the tensor roofline."""
+    import torch
+
+    from paper_2510_01764_gb300 import octax
+
+    w = W.cfg_scale(n_envs=args.policy_envs)
+    g = w.games[0]
+    n, L, T = w.n_envs, g.n_actions + 1, args.policy_steps
+    params = W.policy_params(1, L)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    with torch.cuda.stream(stream):
+        env = octax.Env(w.games, n, seed=w.seed, device=dev.index, stream=stream)
+        pol = octax.Policy(params, max_envs=n, device=dev.index, stream=stream)
+        obs0 = env.reset()
+        words0 = pack_words(obs0)
+        init = env.get_state()
+        outs = (torch.empty((T, n), dtype=torch.uint8, device=dev),
+                torch.empty((T, n, L), dtype=torch.float32, device=dev),
+                torch.empty((T, n), dtype=torch.float32, device=dev),
+                torch.empty((T, n), dtype=torch.float32, device=dev),
+                torch.empty((T, n), dtype=torch.uint8, device=dev))
+
+        def fused(steps):
+            words = words0.clone()
+            env.set_state(init)
+            torch.cuda.synchronize(dev)
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            pol.rollout(env, steps, words, seed=1, out=tuple(o[:steps] for o in outs))
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            return e0.elapsed_time(e1)
+
+        obs = torch.empty_like(obs0)
+        lg = torch.empty((n, L), dtype=torch.float32, device=dev)
+        val = torch.empty(n, dtype=torch.float32, device=dev)
+        act = torch.empty(n, dtype=torch.uint8, device=dev)
+
+        def separate(steps):
+            obs.copy_(obs0)
+            env.set_state(init)
+            torch.cuda.synchronize(dev)
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            for k in range(steps):
+                pol.forward_u8(obs, seed=1, step=k, out=(lg, val, act))
+                env.step(act, out=(obs, outs[3][k], outs[4][k]))
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            return e0.elapsed_time(e1)
+
+        def forward_only(reps):
+            torch.cuda.synchronize(dev)
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            for k in range(reps):
+                pol.forward(words0, seed=1, step=k, out=(lg, val, act))
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            return e0.elapsed_time(e1) / reps
+
+        for _ in range(2):
+            fused(min(T, 4))
+            separate(min(T, 4))
+            forward_only(3)
+        ms_fused = min(fused(T) for _ in range(2))
+        ms_sep = min(separate(T) for _ in range(2))
+        ms_fwd = min(forward_only(max(4, T // 2)) for _ in range(2))
+        pol.sync()
+        env.set_state(init)
+        del env, pol
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    fl = policy_flops(L)
+    achieved = fl * n / (ms_fwd / 1e3) / 1e12
+    return {
+        "workload": f"{n} instances of the template ROM (seed 2), K=10, frameskip 4; the §4.1 network "
+                    f"(convolutions 32/64/64, heads 256) with {L} logits, seeded random weights",
+        "n_envs": n, "steps": T,
+        "fused_rollout": {"value": round(n * T / (ms_fused / 1e3), 1), "unit": "env steps/s",
+                          "ms_per_step": round(ms_fused / T, 5),
+                          "entry": "octax_rollout_policy (packed frames through an L2-resident ring)"},
+        "env_step_plus_separate_forward": {
+            "value": round(n * T / (ms_sep / 1e3), 1), "unit": "env steps/s", "ms_per_step": round(ms_sep / T, 5),
+            "entry": "octax_step (uint8 observations to HBM) + octax_policy_forward_u8 per step"},
+        "speedup_fused": round(ms_sep / ms_fused, 3),
+        "forward_ms": round(ms_fwd, 5),
+        "roofline": {"bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
+                     "frac": round(achieved / peak, 4), "peak_source": "measured bf16 burst (cuBLAS)",
+                     "kernels": "policy_conv_kernel + policy_heads_kernel (one forward)",
+                     "flops_per_instance": fl, "computed_flops_per_instance": policy_computed_flops(L)},
+    }
 
 
 # --------------------------------------------------------------------------- serving
@@ -682,6 +814,9 @@ def parse_args(argv=None):
     ap.add_argument("--ref-budget", type=float, default=90.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-policy", action="store_true")
+    ap.add_argument("--policy-envs", type=int, default=16384)
+    ap.add_argument("--policy-steps", type=int, default=32)
     ap.add_argument("--serve-steps", type=int, default=1_000_000)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     ap.add_argument("--record-traffic", default="", metavar="CSV",

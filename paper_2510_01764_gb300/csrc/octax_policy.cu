@@ -8,7 +8,7 @@
 // VALID convolutions; weights and stored activations in bfloat16, products
 // accumulated in fp32 (TMEM), heads' output layers in fp32 on the CUDA cores.
 //
-// Conv kernel (persistent, one CTA of 128 threads per SM). A batch of kP = 8
+// Conv kernel (persistent, one CTA of 256 threads per SM). A batch of kP = 8
 // instances is processed at a time; the rows of every GEMM are
 // (grid position, instance) with the instance fastest, so one 8-row core
 // matrix of the tcgen05 no-swizzle K-major layout is one grid position of
@@ -18,9 +18,9 @@
 // no im2col copies.
 //  - conv1 works on 4 x 2-pixel blocks: with stride (4, 2) its (8, 4) kernel
 //    covers 2 x 2 blocks, so it is 4 taps of K = 32 (4 frames x 8 pixels)
-//    over a 16 x 16 grid of blocks, built from the packed frame bits through
-//    a byte -> 8 x bf16 table, two block rows per M tile (one output row of
-//    16 positions x 8 instances = 128 rows).
+//    over a 16 x 16 grid of blocks, expanded from the packed frame bits to
+//    bf16 0/1 for two block rows per M tile (one output row of 16 positions
+//    x 8 instances = 128 rows).
 //  - conv2 (stride 2) reads conv1's output split by the parity of x and y:
 //    tap (kx, ky) reads sub-grid (kx & 1, ky & 1) at offset (kx >> 1,
 //    ky >> 1) of an 8-wide grid. The sub-grids are kept as a band of three
@@ -64,14 +64,14 @@ int env_device(const octax_env *e);
 namespace {
 
 constexpr int kP = 8;            // instances per conv batch
-constexpr int kThreads = 128;
+constexpr int kThreads = 128;      // heads kernel
+constexpr int kConvThreads = 256;  // conv kernel: two warps per TMEM lane quarter
 constexpr int kMaxLogits = 17;   // 16 keys + the no-op
 constexpr uint64_t kMaxWaitNs = 1000000000ull;
 constexpr uint32_t kMaxPolls = 1u << 24;
 
 // ---- conv kernel shared memory (bytes) -------------------------------------
-constexpr uint32_t kLutOff = 0;                            // 256 x 16: byte -> 8 bf16 of its bits
-constexpr uint32_t kW1Off = 4096;                          // conv1 B: [tap 4][chunk 4][n 32][8]
+constexpr uint32_t kW1Off = 0;                             // conv1 B: [tap 4][chunk 4][n 32][8]
 constexpr uint32_t kW1Bytes = 4 * 4 * 32 * 16;
 constexpr uint32_t kW2Off = kW1Off + kW1Bytes;             // conv2 B: [tap 16][chunk 4][n 64][8]
 constexpr uint32_t kW2Bytes = 16 * 4 * 64 * 16;
@@ -81,19 +81,23 @@ constexpr uint32_t kSubBytes = kSubPos * 512;              // position: 4 chunks
 constexpr uint32_t kAct1Bytes = 4 * kSubBytes;             // 4 parity sub-grids
 constexpr uint32_t kW3Off = kW2Off + kW2Bytes;             // W3 overlays the band (dead by then)
 constexpr uint32_t kAct1Off = kW3Off + (kW3Bytes - kAct1Bytes);
-constexpr uint32_t kXOff = kW3Off + kW3Bytes;              // frames + blocks (conv1) | conv2 output
-constexpr uint32_t kFrOff = kXOff;                         // [8 inst][4 frames][32 rows] u64
-constexpr uint32_t kBlkOff = kXOff + 8192;                 // 33 block positions x 512 B
-constexpr uint32_t kBlkBytes = 33 * 512;
+constexpr uint32_t kXOff = kW3Off + kW3Bytes;              // blocks (conv1) | conv2 output
+constexpr uint32_t kFrOff = kW3Off;                        // frames [32 rows][4][8] u64, in the part of the
+                                                           // W3 region below the band, during conv1
+constexpr uint32_t kBlkOff = kXOff;                        // 2 buffers x 49 block positions x 512 B
+constexpr uint32_t kBlkBytes = 49 * 512;
 constexpr uint32_t kAct2Off = kXOff;                       // 50 positions x (8 chunks x 8 x 16 B)
 constexpr uint32_t kAct2Bytes = 50 * 1024;
-constexpr uint32_t kXBytes = kAct2Bytes > 8192 + kBlkBytes ? kAct2Bytes : 8192 + kBlkBytes;
+constexpr uint32_t kXBytes = kAct2Bytes > 2 * kBlkBytes ? kAct2Bytes : 2 * kBlkBytes;
 constexpr uint32_t kConvSmem = kXOff + kXBytes;
+constexpr uint32_t kW3EarlyBytes = 2 * 8192;               // W3 taps 0-1: loaded once the frames are dead
 static_assert(kAct1Off >= kW3Off && kAct1Off + kAct1Bytes == kXOff, "band inside the W3 region");
+static_assert(kFrOff + 8192 <= kAct1Off && kW3Off + kW3EarlyBytes <= kAct1Off, "frames / early W3 below the band");
 static_assert(kConvSmem <= 227 * 1024, "conv kernel shared memory");
 
 // TMEM columns (fp32) of the conv kernel's accumulators.
-constexpr uint32_t kD1Col = 0, kD2Col = 64, kD3Col = 256, kConvTmemCols = 512;
+// conv1: 2 buffers x 2 output rows x 32; conv2: 3 tiles x 64; conv3: 2 tiles x 64.
+constexpr uint32_t kD1Col = 0, kD2Col = 128, kD3Col = 320, kConvTmemCols = 512;
 
 // ---- heads kernel -----------------------------------------------------------
 constexpr int kHeadStages = 3;
@@ -185,6 +189,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
 #pragma unroll
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // .x = a (low half)
   return *reinterpret_cast<uint32_t *>(&h);
@@ -234,28 +249,24 @@ struct TileSpec {
 };
 
 template <bool kU8>
-__global__ void __launch_bounds__(kThreads, 1) policy_conv_kernel(const ConvArgs a) {
+__global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const ConvArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  __shared__ __align__(8) uint64_t bars[3];  // 0: MMA completion, 1: W1 + W2, 2: W3
+  __shared__ __align__(8) uint64_t bars[7];  // conv1 x2, conv2, conv3 MMA completion; W1 + W2; W3 x2
   __shared__ uint32_t tmem_s;
   __shared__ float sb[160];                  // b1 | b2 | b3
-  const int t = threadIdx.x, warp = t >> 5;
+  __shared__ uint2 nib[16];                  // 4 pixel bits -> 4 bf16 0 / 1 (element k = bit k)
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const uint32_t sbase = smem_u32(sm);
-  const uint32_t bar_mma = smem_u32(&bars[0]), bar_w = smem_u32(&bars[1]), bar_w3 = smem_u32(&bars[2]);
+  const uint32_t bar_c1_0 = smem_u32(&bars[0]), bar_c1_1 = smem_u32(&bars[1]);
+  const uint32_t bar_c2 = smem_u32(&bars[2]), bar_c3 = smem_u32(&bars[3]);
+  const uint32_t bar_w = smem_u32(&bars[4]), bar_w3a = smem_u32(&bars[5]), bar_w3b = smem_u32(&bars[6]);
 
-  // byte -> 8 bf16 (element k = bit k): 1.0 is 0x3F80
-  for (int b = t; b < 256; b += kThreads) {
-    uint32_t w[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-      w[j] = ((b >> (2 * j)) & 1 ? 0x3F80u : 0u) | ((b >> (2 * j + 1)) & 1 ? 0x3F800000u : 0u);
-    *reinterpret_cast<uint4 *>(sm + kLutOff + 16 * b) = make_uint4(w[0], w[1], w[2], w[3]);
-  }
-  for (int j = t; j < 160; j += kThreads) sb[j] = a.fp[j];
+  for (int j = t; j < 160; j += kConvThreads) sb[j] = a.fp[j];
+  if (t < 16)  // 1.0 in bf16 is 0x3F80
+    nib[t] = make_uint2((t & 1) * 0x3F80u | ((t >> 1) & 1) * 0x3F800000u,
+                        ((t >> 2) & 1) * 0x3F80u | ((t >> 3) & 1) * 0x3F800000u);
   if (t == 0) {
-    mbar_init(bar_mma, 1);
-    mbar_init(bar_w, 1);
-    mbar_init(bar_w3, 1);
+    for (int j = 0; j < 7; ++j) mbar_init(smem_u32(&bars[j]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -275,86 +286,120 @@ __global__ void __launch_bounds__(kThreads, 1) policy_conv_kernel(const ConvArgs
   // every wait's outcome is made uniform over the block, so all threads
   // leave the loops together
   bool ok = !__syncthreads_or(!mbar_wait(bar_w, 0));
-  uint32_t ph_mma = 0, ph_w3 = 0;
+  uint32_t ph_c1_0 = 0, ph_c1_1 = 0, ph_c2 = 0, ph_c3 = 0, ph_w3 = 0;  // ph_w3: both W3 barriers
   const int64_t n_batches = (a.n + kP - 1) / kP;
-  const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-  const int r = t;                     // M-tile row of this thread (TMEM lane)
-  const int g = r >> 3, ri = r & 7;    // grid position in the tile, instance in the batch
+  // warps w and w + 4 read the same TMEM lane quarter (rows 32 (w & 3) ..), each
+  // one half of the accumulator's columns
+  const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+  const int half = warp >> 2;
+  const int r = 32 * (warp & 3) + lane;  // M-tile row of this thread (TMEM lane)
+  const int g = r >> 3, ri = r & 7;      // grid position in the tile, instance in the batch
 
-  auto wait_mma = [&]() -> bool {
-    const bool w_ok = mbar_wait(bar_mma, ph_mma);
-    ph_mma ^= 1u;
+  // wait for the next phase of a barrier (block-uniform outcome; also a block barrier)
+  auto wait_all = [&](uint32_t bar, uint32_t &phase) -> bool {
+    const bool w_ok = mbar_wait(bar, phase);
+    phase ^= 1u;
     return !__syncthreads_or(!w_ok);
   };
 
   for (int64_t batch = blockIdx.x; batch < n_batches && ok; batch += gridDim.x) {
     const int64_t i0 = batch * kP;
-    // ---- frames of the batch, packed (bit x of row word y = pixel (x, y))
+    // ---- frames of the batch, packed (bit x of row word y = pixel (x, y)),
+    // stored [row y][frame c][instance i] so that the 32 lanes of a warp
+    // building one block position read 32 consecutive words
     uint64_t *fr = reinterpret_cast<uint64_t *>(sm + kFrOff);
     if (!kU8) {
-      for (int q = t; q < kP * 64; q += kThreads) {   // 64 x 16 B per instance
-        const int i = q >> 6;
+      for (int q = t; q < kP * 64; q += kConvThreads) {  // instance i, frame c, rows 2 y2 and 2 y2 + 1
+        const int i = q & 7, c = (q >> 7) & 3, y2 = (q >> 3) & 15;
         uint4 v = make_uint4(0, 0, 0, 0);
-        if (i0 + i < a.n) v = __ldg(reinterpret_cast<const uint4 *>(a.obs_words + (i0 + i) * 128) + (q & 63));
-        reinterpret_cast<uint4 *>(fr)[q] = v;
+        if (i0 + i < a.n) v = __ldg(reinterpret_cast<const uint4 *>(a.obs_words + (i0 + i) * 128 + c * 32 + 2 * y2));
+        fr[((2 * y2) * 4 + c) * 8 + i] = (uint64_t)v.x | (uint64_t)v.y << 32;
+        fr[((2 * y2 + 1) * 4 + c) * 8 + i] = (uint64_t)v.z | (uint64_t)v.w << 32;
       }
     } else {
-      for (int q = t; q < kP * 128; q += kThreads) {  // one 64-byte row each
-        const int i = q >> 7;
+      for (int q = t; q < kP * 128; q += kConvThreads) {  // one 64-byte row each
+        const int i = q & 7, c = (q >> 8) & 3, y = (q >> 3) & 31;
         uint64_t bits = 0;
         if (i0 + i < a.n) {
-          const uint4 *src = reinterpret_cast<const uint4 *>(a.obs_u8 + ((i0 + i) * 128 + (q & 127)) * 64);
+          const uint4 *src = reinterpret_cast<const uint4 *>(a.obs_u8 + ((i0 + i) * 128 + c * 32 + y) * 64);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const uint4 v = __ldg(src + c);
+          for (int k4 = 0; k4 < 4; ++k4) {
+            const uint4 v = __ldg(src + k4);
             const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k)
 #pragma unroll
               for (int bb = 0; bb < 4; ++bb)
-                bits |= (uint64_t)(((w4[k] >> (8 * bb)) & 0xFFu) != 0u) << (16 * c + 4 * k + bb);
+                bits |= (uint64_t)(((w4[k] >> (8 * bb)) & 0xFFu) != 0u) << (16 * k4 + 4 * k + bb);
           }
         }
-        fr[q] = bits;
+        fr[(y * 4 + c) * 8 + i] = bits;
       }
     }
     __syncthreads();
 
-    // ---- conv1 rows 0..13 (row 14 is never read by conv2), conv2 in three bands
-    for (int oy = 0; oy < 14 && ok; ++oy) {
-      // blocks of block rows oy, oy + 1 (position b = bx + 16 * (by - oy)), plus one pad position
-      for (int q = t; q < 33 * 32; q += kThreads) {
-        const int b = q >> 5, c = (q >> 3) & 3, i = q & 7;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (b < 32) {
-          const int bx = b & 15, by = oy + (b >> 4);
-          const uint64_t *rows = fr + (i * 4 + c) * 32;
-          const uint32_t lo = (uint32_t)(rows[2 * by] >> (4 * bx)) & 15u;
-          const uint32_t hi = (uint32_t)(rows[2 * by + 1] >> (4 * bx)) & 15u;
-          v = *reinterpret_cast<const uint4 *>(sm + kLutOff + 16 * (lo | hi << 4));
-        }
-        *reinterpret_cast<uint4 *>(sm + kBlkOff + b * 512 + c * 128 + i * 16) = v;
+    // ---- conv1 rows 0..13 (row 14 is never read by conv2) in 7 pairs,
+    // software-pipelined: the blocks of pair p + 1 are built and its 16 MMAs
+    // issued (second block buffer, second pair of TMEM accumulators) before
+    // pair p's epilogue; conv2 runs on each completed band of three grid rows
+    // while conv1 continues.
+    // Blocks of block rows 2p .. 2p + 2 (position b = bx + 16 (by - 2p)); the
+    // pad position 48 is read by discarded rows only. Warp w builds positions
+    // 6w .. 6w + 5; lane = frame * 8 + instance.
+    auto build = [&](int pr, int buf) {
+      uint8_t *blk = sm + kBlkOff + buf * kBlkBytes;
+#pragma unroll 2
+      for (int j = 0; j < 6; ++j) {
+        const int b = 6 * warp + j, bx = b & 15, by = 2 * pr + (b >> 4);
+        const uint64_t w0 = fr[(2 * by) * 32 + lane], w1 = fr[(2 * by + 1) * 32 + lane];
+        const uint2 lo = nib[(uint32_t)(w0 >> (4 * bx)) & 15u], hi = nib[(uint32_t)(w1 >> (4 * bx)) & 15u];
+        *reinterpret_cast<uint4 *>(blk + b * 512 + lane * 16) = make_uint4(lo.x, lo.y, hi.x, hi.y);
       }
-      fence_async_smem();
-      __syncthreads();
-      if (t == 0) {
-        tc_fence_after();
+    };
+    auto issue_c1 = [&](int buf) {  // thread 0: output rows 2p, 2p + 1
+      tc_fence_after();
+      for (int s2 = 0; s2 < 2; ++s2)
         for (int tap = 0; tap < 4; ++tap) {
           const int dx = tap & 1, dy = tap >> 1;
           for (int kk = 0; kk < 2; ++kk) {
-            const uint64_t ad = sdesc(sbase + kBlkOff + (dx + 16 * dy) * 512 + kk * 256, 128, 512);
+            const uint64_t ad =
+                sdesc(sbase + kBlkOff + buf * kBlkBytes + (16 * s2 + dx + 16 * dy) * 512 + kk * 256, 128, 512);
             const uint64_t bd = sdesc(sbase + kW1Off + tap * 2048 + kk * 1024, 512, 128);
-            mma_bf16(tmem + kD1Col, ad, bd, idesc_bf16(128, 32), (tap | kk) != 0);
+            mma_bf16(tmem + kD1Col + 64 * buf + 32 * s2, ad, bd, idesc_bf16(128, 32), (tap | kk) != 0);
           }
         }
-        mma_commit(bar_mma);
-      }
-      ok = wait_mma();
+      mma_commit(buf ? bar_c1_1 : bar_c1_0);
+    };
+    build(0, 0);
+    fence_async_smem();
+    __syncthreads();
+    if (t == 0) issue_c1(0);
+    for (int pr = 0; pr < 7 && ok; ++pr) {
+      const int cb = pr & 1, nb = cb ^ 1;
+      if (pr + 1 < 7) build(pr + 1, nb);  // buffer nb: its MMAs (pair pr - 1) completed
+      fence_async_smem();
+      ok = cb ? wait_all(bar_c1_1, ph_c1_1) : wait_all(bar_c1_0, ph_c1_0);
       if (!ok) break;
+      if (pr + 1 < 7 && t == 0) issue_c1(nb);
+      if (pr == 6 && t == 0) {  // the frames are dead: W3 taps 0-1 into their place
+        mbar_expect_tx(bar_w3a, kW3EarlyBytes);
+        bulk_g2s(sbase + kW3Off, a.w3, kW3EarlyBytes, bar_w3a);
+      }
+      if (pr == 3 || pr == 5) {  // the band's conv2 tile must finish before its rows are rewritten
+        ok = wait_all(bar_c2, ph_c2);
+        if (!ok) break;
+        for (int q = t; q < 4 * 8 * 32; q += kConvThreads) {  // slide: grid row 2 -> 0 (4 sub-grids x 8 x 512 B)
+          const int sgq = q >> 8, rem = q & 255;
+          uint4 *base = reinterpret_cast<uint4 *>(sm + kAct1Off + sgq * kSubBytes);
+          base[rem] = base[16 * 32 + rem];
+        }
+        __syncthreads();
+      }
       tc_fence_after();
-      {
-        float v[32];
-        tmem_ld32(tmem + lane_base + kD1Col, v);
+      for (int s2 = 0; s2 < 2; ++s2) {
+        const int oy = 2 * pr + s2;
+        float v[16];
+        tmem_ld16(tmem + lane_base + kD1Col + 64 * cb + 32 * s2 + 16 * half, v);
         const int ox = g;
         if (ox <= 13) {  // conv2 reads x <= 13
           const int band = oy <= 5 ? 0 : (oy <= 9 ? 1 : 2);
@@ -362,13 +407,13 @@ __global__ void __launch_bounds__(kThreads, 1) policy_conv_kernel(const ConvArgs
           const int sg = (ox & 1) + 2 * (oy & 1);
           uint8_t *dst = sm + kAct1Off + sg * kSubBytes + ((ox >> 1) + 8 * slot) * 512 + ri * 16;
 #pragma unroll
-          for (int c = 0; c < 4; ++c)
-            *reinterpret_cast<uint4 *>(dst + c * 128) = relu_chunk(v + 8 * c, sb + 8 * c);
+          for (int c = 0; c < 2; ++c)
+            *reinterpret_cast<uint4 *>(dst + (2 * half + c) * 128) = relu_chunk(v + 8 * c, sb + 16 * half + 8 * c);
         }
       }
       tc_fence_before();
-      if (oy == 5 || oy == 9 || oy == 13) {
-        const int tt = (oy - 5) >> 2;  // conv2 tile: output rows 2tt, 2tt + 1
+      if (pr == 2 || pr == 4 || pr == 6) {
+        const int tt = (pr - 2) >> 1;  // conv2 tile: output rows 2tt, 2tt + 1
         fence_async_smem();
         __syncthreads();
         if (t == 0) {
@@ -383,44 +428,35 @@ __global__ void __launch_bounds__(kThreads, 1) policy_conv_kernel(const ConvArgs
               mma_bf16(tmem + kD2Col + 64 * tt, ad, bd, idesc_bf16(128, 64), (tap | kk) != 0);
             }
           }
-          mma_commit(bar_mma);
-        }
-        ok = wait_mma();
-        if (ok && tt < 2) {  // slide the band: grid row 2 becomes grid row 0
-          for (int q = t; q < 4 * 8 * 32; q += kThreads) {  // 4 sub-grids x 8 positions x 32 x 16 B
-            const int sgq = q >> 8, rem = q & 255;
-            uint4 *base = reinterpret_cast<uint4 *>(sm + kAct1Off + sgq * kSubBytes);
-            base[rem] = base[16 * 32 + rem];
-          }
-          __syncthreads();
+          mma_commit(bar_c2);
         }
       }
     }
+    if (ok) ok = wait_all(bar_c2, ph_c2);  // conv2 tile 2
     if (!ok) break;
 
-    // ---- W3 into the (now dead) band region; conv2 epilogues into region X
+    // ---- the rest of W3 into the (now dead) band region; conv2 epilogues into region X
     if (t == 0) {
       fence_async_smem();
-      mbar_expect_tx(bar_w3, kW3Bytes);
-      for (uint32_t o = 0; o < kW3Bytes; o += 18432) bulk_g2s(sbase + kW3Off + o, a.w3 + o, 18432, bar_w3);
+      mbar_expect_tx(bar_w3b, kW3Bytes - kW3EarlyBytes);
+      for (uint32_t o = kW3EarlyBytes; o < kW3Bytes; o += 14336)
+        bulk_g2s(sbase + kW3Off + o, a.w3 + o, 14336, bar_w3b);
     }
     tc_fence_after();
     for (int tt = 0; tt < 3; ++tt) {
-      const int px = g & 7, py = 2 * tt + (g >> 3);
+      const int px = g & 7, py = 2 * tt + (g >> 3), h = half;
       float v[32];
-      for (int h = 0; h < 2; ++h) {
-        tmem_ld32(tmem + lane_base + kD2Col + 64 * tt + 32 * h, v);
-        if (px < 6) {
-          uint8_t *dst = sm + kAct2Off + (px + 8 * py) * 1024 + ri * 16;
+      tmem_ld32(tmem + lane_base + kD2Col + 64 * tt + 32 * h, v);
+      if (px < 6) {
+        uint8_t *dst = sm + kAct2Off + (px + 8 * py) * 1024 + ri * 16;
 #pragma unroll
-          for (int c = 0; c < 4; ++c)
-            *reinterpret_cast<uint4 *>(dst + (4 * h + c) * 128) = relu_chunk(v + 8 * c, sb + 32 + 32 * h + 8 * c);
-        }
+        for (int c = 0; c < 4; ++c)
+          *reinterpret_cast<uint4 *>(dst + (4 * h + c) * 128) = relu_chunk(v + 8 * c, sb + 32 + 32 * h + 8 * c);
       }
     }
     tc_fence_before();
     fence_async_smem();
-    ok = !__syncthreads_or(!mbar_wait(bar_w3, ph_w3));
+    ok = !__syncthreads_or(!(mbar_wait(bar_w3a, ph_w3) && mbar_wait(bar_w3b, ph_w3)));
     ph_w3 ^= 1u;
     if (!ok) break;
 
@@ -436,24 +472,22 @@ __global__ void __launch_bounds__(kThreads, 1) policy_conv_kernel(const ConvArgs
             mma_bf16(tmem + kD3Col + 64 * u, ad, bd, idesc_bf16(128, 64), (tap | kk) != 0);
           }
         }
-      mma_commit(bar_mma);
+      mma_commit(bar_c3);
     }
-    ok = wait_mma();
+    ok = wait_all(bar_c3, ph_c3);
     if (!ok) break;
     tc_fence_after();
     for (int u = 0; u < 2; ++u) {
-      const int m = 16 * u + g, qx = m & 7, qy = m >> 3;
+      const int m = 16 * u + g, qx = m & 7, qy = m >> 3, h = half;
       const int64_t inst = i0 + ri;
       float v[32];
-      for (int h = 0; h < 2; ++h) {
-        tmem_ld32(tmem + lane_base + kD3Col + 64 * u + 32 * h, v);
-        if (qx < 4 && inst < a.n) {
-          const int q = qx + 4 * qy;  // feature slice: k = 64 q + channel
-          uint8_t *dst = a.act3 + (inst >> 7) * (int64_t)kAct3TileBytes + q * 16384 + (inst & 127) * 16;
+      tmem_ld32(tmem + lane_base + kD3Col + 64 * u + 32 * h, v);
+      if (qx < 4 && inst < a.n) {
+        const int q = qx + 4 * qy;  // feature slice: k = 64 q + channel
+        uint8_t *dst = a.act3 + (inst >> 7) * (int64_t)kAct3TileBytes + q * 16384 + (inst & 127) * 16;
 #pragma unroll
-          for (int c = 0; c < 4; ++c)
-            *reinterpret_cast<uint4 *>(dst + (4 * h + c) * 2048) = relu_chunk(v + 8 * c, sb + 96 + 32 * h + 8 * c);
-        }
+        for (int c = 0; c < 4; ++c)
+          *reinterpret_cast<uint4 *>(dst + (4 * h + c) * 2048) = relu_chunk(v + 8 * c, sb + 96 + 32 * h + 8 * c);
       }
     }
     tc_fence_before();
@@ -599,11 +633,13 @@ __global__ void __launch_bounds__(kThreads, 1) policy_heads_kernel(const HeadsAr
           const float target = u * tot;
           float run = 0.0f;
           int pick = a.L - 1;
-          for (int o = 0; o < a.L; ++o) {
+          bool found = false;
+#pragma unroll
+          for (int o = 0; o < kMaxLogits; ++o) {
             run += e[o];
-            if (target < run) {
+            if (o < a.L && !found && target < run) {
               pick = o;
-              break;
+              found = true;
             }
           }
           a.actions[inst] = (uint8_t)pick;
@@ -639,9 +675,9 @@ int launch_forward(octax_policy *p, int64_t n, const uint64_t *obs_words, const 
   const int64_t batches = (n + kP - 1) / kP;
   const int grid = (int)std::min<int64_t>(batches, p->sms);
   if (obs_u8)
-    policy_conv_kernel<true><<<grid, kThreads, kConvSmem, s>>>(c);
+    policy_conv_kernel<true><<<grid, kConvThreads, kConvSmem, s>>>(c);
   else
-    policy_conv_kernel<false><<<grid, kThreads, kConvSmem, s>>>(c);
+    policy_conv_kernel<false><<<grid, kConvThreads, kConvSmem, s>>>(c);
   cudaError_t r = cudaGetLastError();
   if (r != cudaSuccess) return cuda_fail(r, "policy conv launch");
   HeadsArgs h{p->act3, n, (const uint8_t *)p->wh, p->fp, p->n_logits, logits, value, actions,

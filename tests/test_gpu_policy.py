@@ -4,9 +4,12 @@ oracle (oracle/policy.py), through the C-ABI.
 Tolerances (floating point; the environment step itself stays bit-exact):
 - against the oracle with bfloat16 storage (weights and stored activations
   rounded as the kernels store them, products summed in float64): the
-  kernels differ only by fp32 accumulation order and the rare bfloat16
-  rounding flip it causes, so |logit or value difference| <= 2e-3 * max(1,
-  RMS of the oracle's logits);
+  kernels differ by fp32 accumulation order, and where that order decides
+  the bfloat16 rounding of a stored activation the two sides differ by one
+  bfloat16 ulp of it (2^-8 relative, up to 0.016 for activations near 4),
+  damped by the layers after it; measured worst case 1.3e-3 over ~10^4
+  evaluations, typical 1e-4. Bound: |logit or value difference| <= 5e-3 *
+  max(1, RMS of the oracle's logits);
 - against the float64 oracle: bfloat16 weights and activations (unit
   roundoff 2^-9) through five layers, |difference| <= 5e-2 * max(1, RMS);
 - sampled actions: the kernel's draw from its own fp32 logits equals the
@@ -23,7 +26,7 @@ from paper_2510_01764_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-TOL_BF16, TOL_F64, MARGIN = 2e-3, 5e-2, 1e-5
+TOL_BF16, TOL_F64, MARGIN = 5e-3, 5e-2, 1e-5
 
 
 @pytest.fixture(scope="module", autouse=True)
