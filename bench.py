@@ -509,8 +509,8 @@ def run_gpu(args) -> dict | None:
         line["policy"] = run_policy(args, dev, stream)
     if not args.no_serve and world == 1:
         line["serving"] = run_serving(args, dev)
-        line["serving_p50_ms"] = line["serving"]["poisson"]["p50_ms"]
-        line["serving_p99_ms"] = line["serving"]["poisson"]["p99_ms"]
+        line["serving_p50_ms"] = line["serving"]["poisson"]["x1"]["p50_ms"]
+        line["serving_p99_ms"] = line["serving"]["poisson"]["x1"]["p99_ms"]
     return line
 
 
@@ -645,79 +645,173 @@ def run_policy(args, dev, stream) -> dict:
 
 
 # --------------------------------------------------------------------------- serving
-def serving_trace(total_steps: int, seed: int = 55):
-    """Poisson arrivals per game at mixed rates (10, 100, 1000 /s), each request
-    (game, 1-4,096 envs log-uniform, 1-8 steps, uniform actions, seed), until
-    the requests add up to total_steps env steps."""
+SERVE_RATES = (10.0, 100.0, 1000.0)   # requests/s per game, games cycle through the three
+
+
+def serving_requests(n_req: int, seed: int, rate_scale: float = 1.0) -> dict:
+    """n_req requests of the serving configuration: per game Poisson
+    arrivals at 10, 100 or 1000 requests/s (times rate_scale), envs
+    log-uniform in 1..4096, 1-8 steps, seeds; as arrays, sorted by arrival."""
     rng = np.random.Generator(np.random.Philox(key=seed))
-    rates = [(10.0, 100.0, 1000.0)[g % 3] for g in range(16)]
-    t = [float(rng.exponential(1.0 / r)) for r in rates]
-    reqs, steps = [], 0
-    while steps < total_steps:
-        g = int(np.argmin(t))
-        n = int(min(4096, max(1, round(float(np.exp(rng.uniform(0.0, np.log(4096.0))))))))
-        T = int(rng.integers(1, 9))
-        acts = rng.integers(0, 4, size=(T, n), dtype=np.uint8)
-        reqs.append(dict(t=t[g], game=g, actions=acts, seed=int(rng.integers(0, 2**62))))
-        steps += n * T
-        t[g] += float(rng.exponential(1.0 / rates[g]))
-    t0 = reqs[0]["t"]
-    for r in reqs:
-        r["t"] -= t0
-    return reqs
+    rates = np.array([SERVE_RATES[g % 3] for g in range(16)]) * rate_scale
+    # per-game arrival processes merged: game of each arrival ~ rate share, gaps ~ exponential(total rate)
+    game = rng.choice(16, size=n_req, p=rates / rates.sum()).astype(np.uint16)
+    t = np.cumsum(rng.exponential(1.0 / rates.sum(), size=n_req))
+    envs = np.clip(np.rint(np.exp(rng.uniform(0.0, np.log(4096.0), size=n_req))), 1, 4096).astype(np.int64)
+    steps = rng.integers(1, 9, size=n_req).astype(np.int64)
+    seeds = rng.integers(0, 2 ** 62, size=n_req, dtype=np.int64).astype(np.uint64)
+    return {"t": t - t[0], "game": game, "envs": envs, "steps": steps, "seed": seeds}
+
+
+def _requests_for(srv, rq, sel, acts, act_off, obs, rew, done, out_off):
+    """REQUEST_DTYPE rows for requests `sel`: actions from the flat host array
+    at act_off, outputs from the flat device buffers at out_off (env-steps)."""
+    r = np.zeros(len(sel), dtype=srv.REQUEST_DTYPE)
+    r["game"], r["n_envs"], r["n_steps"] = rq["game"][sel], rq["envs"][sel], rq["steps"][sel]
+    r["seed"] = rq["seed"][sel]
+    r["actions"] = acts.ctypes.data + act_off
+    o = out_off.astype(np.uint64)
+    r["obs"] = np.uint64(obs.data_ptr()) + o * np.uint64(8192)
+    r["reward"] = np.uint64(rew.data_ptr()) + o * np.uint64(4)
+    r["done"] = np.uint64(done.data_ptr()) + o
+    return r
 
 
 def run_serving(args, dev) -> dict:
+    """The serving configuration (16 template ROMs of the batch workload;
+    requests of 1-4,096 envs and 1-8 steps): the server's launch shape chosen
+    by measurement, a saturated closed-loop run of at least
+    --serve-sat-steps env steps, open-loop Poisson arrivals at three offered
+    loads, and octax_step_n on the same 16 ROMs for comparison."""
     import torch
 
     from paper_2510_01764_gb300 import octax
 
     games = W.cfg_batch(n_envs=64, n_steps=1).games
-    reqs = serving_trace(args.serve_steps)
-    total = sum(int(np.prod(r["actions"].shape)) for r in reqs)
-    obs = torch.empty((total, 4, 32, 64), dtype=torch.uint8, device=dev)
-    rew = torch.empty(total, dtype=torch.float32, device=dev)
-    done = torch.empty(total, dtype=torch.uint8, device=dev)
-    outs, off = [], 0
-    for r in reqs:
-        T, n = r["actions"].shape
-        k = T * n
-        outs.append((obs[off:off + k].view(T, n, 4, 32, 64), rew[off:off + k].view(T, n),
-                     done[off:off + k].view(T, n)))
-        off += k
-    res = {}
-    for mode in ("poisson", "saturated"):
-        srv = octax.Server(games, memory_budget_bytes=int(args.serve_budget_gb * 1e9), block=64,
-                           inst_per_warp=8, max_inflight_ticks=2, device=dev.index)
-        # warm-up: one small request per game
-        for g in range(16):
-            srv.wait(srv.submit(g, np.zeros((1, 8), np.uint8), 1, out=None))
-        torch.cuda.synchronize(dev)
-        base = srv.stats()
-        ids = []
-        t_start = time.perf_counter()
-        for r, out in zip(reqs, outs):
-            if mode == "poisson":
-                while time.perf_counter() - t_start < r["t"]:
-                    pass
-            ids.append(srv.submit(r["game"], r["actions"], r["seed"], out=out))
-        infos = [srv.wait(i) for i in ids]
-        st = srv.stats()
+    budget = int(args.serve_budget_gb * 1e9)
+    big = serving_requests(200_000, 55)
+    ES = big["envs"] * big["steps"]
+    act_h = np.random.Generator(np.random.Philox(key=56)).integers(0, 4, size=int(ES.sum()), dtype=np.uint8)
+    act_off = np.concatenate([[0], np.cumsum(ES)[:-1]])
+    half = int(args.serve_ring_steps)                      # env-steps of outputs per ring half
+    obs = torch.empty((2 * half, 4, 32, 64), dtype=torch.uint8, device=dev)
+    rew = torch.empty(2 * half, dtype=torch.float32, device=dev)
+    done = torch.empty(2 * half, dtype=torch.uint8, device=dev)
+
+    def saturated(block, ipw, min_steps):
+        """Requests of the stream in waves, each wave filling one half of the
+        output ring; a half is reused once its previous wave is done."""
+        srv = octax.Server(games, memory_budget_bytes=budget, block=block, inst_per_warp=ipw,
+                           max_inflight_ticks=2, device=dev.index)
+        pending = [None, None]
+        lat, first, last, steps, k, h = [], None, None, 0, 0, 0
+        while steps < min_steps:
+            if pending[h] is not None:
+                inf = srv.wait_raw(pending[h])
+                lat.append(inf[:, 2] - inf[:, 0])
+                last = max(last or 0, int(inf[:, 2].max()))
+            cum = np.cumsum(ES[k:k + 4096])
+            m = int(np.searchsorted(cum, half, side="right"))
+            sel = np.arange(k, k + m)
+            if k + m >= len(ES):
+                break
+            out_off = h * half + np.concatenate([[0], cum[:m - 1]])
+            ids = srv.submit_raw(_requests_for(srv, big, sel, act_h, act_off[sel], obs, rew, done, out_off))
+            first = first or time.monotonic_ns()
+            pending[h] = ids
+            steps += int(cum[m - 1])
+            k += m
+            h ^= 1
+        for hh in (0, 1):
+            if pending[hh] is not None:
+                inf = srv.wait_raw(pending[hh])
+                lat.append(inf[:, 2] - inf[:, 0])
+                last = max(last or 0, int(inf[:, 2].max()))
         srv.close()
-        lat = np.array([(i["done_ns"] - i["submit_ns"]) / 1e6 for i in infos])
-        qwait = np.array([(i["admit_ns"] - i["submit_ns"]) / 1e6 for i in infos])
-        span = (max(i["done_ns"] for i in infos) - min(i["submit_ns"] for i in infos)) / 1e9
-        res[mode] = {"env_steps_per_s": round(total / span, 1), "p50_ms": round(float(np.percentile(lat, 50)), 4),
-                     "p99_ms": round(float(np.percentile(lat, 99)), 4),
-                     "mean_admission_wait_ms": round(float(qwait.mean()), 4),
-                     "makespan_s": round(span, 4), "ticks": st["ticks"] - base["ticks"],
-                     "peak_active_requests": st["peak_active_requests"],
-                     "peak_active_envs": st["peak_active_envs"]}
-    del obs, rew, done
-    return {"requests": len(reqs), "env_steps": total, "games": 16,
-            "arrivals": "Poisson per game, rates 10/100/1000 per s; envs log-uniform 1-4096; "
-                        "1-8 steps; budget %.0f GB" % args.serve_budget_gb,
-            **{f"{m}": v for m, v in res.items()}}
+        lat = np.concatenate(lat) / 1e6
+        return steps / ((last - first) / 1e9), lat, steps, k
+
+    # launch shape by measurement (short saturated runs)
+    shapes = {}
+    for block, ipw in ((64, 8), (128, 8), (128, 16), (256, 8), (256, 16)):
+        saturated(block, ipw, 2 * half)                       # warm-up (graphs, caches)
+        shapes[f"{block}x{ipw}"] = saturated(block, ipw, 8 * half)[0]
+    best = max(shapes, key=shapes.get)
+    bb, bi = (int(x) for x in best.split("x"))
+    rate, lat, steps, nreq = saturated(bb, bi, args.serve_sat_steps)
+    sat = {"env_steps": steps, "requests": nreq, "env_steps_per_s": round(rate, 1),
+           "p50_ms": round(float(np.percentile(lat, 50)), 4), "p99_ms": round(float(np.percentile(lat, 99)), 4),
+           "latency_note": "closed loop: each wave of requests fills one half of a "
+                           f"{2 * half * 8192 / 1e9:.1f} GB output ring and waits for the wave before it; "
+                           "latency = done - submit, so it includes the wave's own queueing"}
+
+    # open-loop Poisson arrivals at three offered loads
+    poisson = {}
+    for scale in (1.0, 5.0, 15.0):
+        rq = serving_requests(100_000, 57, rate_scale=scale)
+        es = rq["envs"] * rq["steps"]
+        n_req = int(np.searchsorted(np.cumsum(es), args.serve_steps)) + 1
+        cum = np.concatenate([[0], np.cumsum(es[:n_req])])
+        if cum[-1] > 2 * half:
+            n_req = int(np.searchsorted(cum, 2 * half, side="right")) - 1
+        aoff = np.concatenate([[0], np.cumsum(es[:n_req])[:-1]])
+        srv = octax.Server(games, memory_budget_bytes=budget, block=bb, inst_per_warp=bi, max_inflight_ticks=2,
+                           device=dev.index)
+        warm = srv.submit_raw(_requests_for(srv, rq, np.arange(16), act_h, aoff[:16], obs, rew, done, aoff[:16]))
+        srv.wait_raw(warm)
+        all_ids, sched, i = [], [], 0
+        t0 = time.monotonic_ns()
+        while i < n_req:
+            now = (time.monotonic_ns() - t0) / 1e9
+            j = int(np.searchsorted(rq["t"][:n_req], now, side="right"))
+            if j > i:
+                sel = np.arange(i, j)
+                all_ids.append(srv.submit_raw(_requests_for(srv, rq, sel, act_h, aoff[sel], obs, rew, done,
+                                                            aoff[sel])))
+                sched.append(t0 + (rq["t"][sel] * 1e9).astype(np.int64))
+                i = j
+        inf = srv.wait_raw(np.concatenate(all_ids))
+        srv.close()
+        sched = np.concatenate(sched)
+        lat = (inf[:, 2] - sched) / 1e6                     # from the scheduled arrival
+        lat_srv = (inf[:, 2] - inf[:, 0]) / 1e6             # from the submit call
+        span = (inf[:, 2].max() - sched.min()) / 1e9
+        offered = cum[n_req] / max(rq["t"][n_req - 1], 1e-9)
+        poisson[f"x{scale:g}"] = {
+            "offered_env_steps_per_s": round(float(offered), 1), "requests": n_req,
+            "env_steps": int(cum[n_req]), "env_steps_per_s": round(float(cum[n_req] / span), 1),
+            "p50_ms": round(float(np.percentile(lat, 50)), 4), "p99_ms": round(float(np.percentile(lat, 99)), 4),
+            "server_p50_ms": round(float(np.percentile(lat_srv, 50)), 4),
+            "server_p99_ms": round(float(np.percentile(lat_srv, 99)), 4)}
+
+    # octax_step_n on the same 16 ROMs: the batch workload's 65,536 instances
+    w = W.cfg_batch()
+    env = octax.Env(w.games, w.n_envs, seed=w.seed, game_of_env=w.game_of_env, device=dev.index)
+    a = torch.from_numpy(W.actions(w.action_seed, 0, 32, w.n_envs, 4)).to(dev)
+    env.autotune(32, a)
+    o2 = torch.empty((32, w.n_envs, 4, 32, 64), dtype=torch.uint8, device=dev)
+    r2 = torch.empty((32, w.n_envs), dtype=torch.float32, device=dev)
+    d2 = torch.empty((32, w.n_envs), dtype=torch.uint8, device=dev)
+    env.step_n(a, out=(o2, r2, d2))
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cs = torch.cuda.current_stream(dev)
+    e0.record(cs)
+    for _ in range(2):
+        env.step_n(a, out=(o2, r2, d2))
+    e1.record(cs)
+    torch.cuda.synchronize(dev)
+    step_n_rate = 2 * 32 * w.n_envs / (e0.elapsed_time(e1) / 1e3)
+    del env, o2, r2, d2, obs, rew, done
+    torch.cuda.empty_cache()
+    return {"games": 16, "budget_gb": args.serve_budget_gb,
+            "requests": "per game Poisson 10/100/1000 requests/s (x the offered-load scale); envs "
+                        "log-uniform 1-4096; 1-8 steps; uniform actions over 4",
+            "launch_shapes_env_steps_per_s": {k: round(v, 1) for k, v in shapes.items()},
+            "launch": {"block": bb, "inst_per_warp": bi},
+            "saturated": sat, "poisson": poisson,
+            "step_n_same_roms": {"env_steps_per_s": round(step_n_rate, 1), "n_envs": w.n_envs,
+                                 "launch": "autotuned, 32-step calls"}}
 
 
 # --------------------------------------------------------------------------- CPU oracle
@@ -819,6 +913,10 @@ def parse_args(argv=None):
     ap.add_argument("--policy-steps", type=int, default=32)
     ap.add_argument("--serve-steps", type=int, default=1_000_000)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
+    ap.add_argument("--serve-sat-steps", type=int, default=60_000_000,
+                    help="env steps of the saturated serving run")
+    ap.add_argument("--serve-ring-steps", type=int, default=500_000,
+                    help="env steps of outputs per half of the serving output ring")
     ap.add_argument("--record-traffic", default="", metavar="CSV",
                     help="no GPU: read an `ncu -i <rep> --page raw --csv` export of step_kernel "
                          "launches into profiles/traffic.json for --config")

@@ -353,9 +353,21 @@ int octax_server_create(const octax_game *games, int n_games, uint32_t quirks,
 /* Queue a request (thread-safe, returns at once). EINVAL: bad fields;
  * ENOMEM: n_envs exceeds the whole slot pool. */
 int octax_server_submit(octax_server *s, const octax_request *req, uint64_t *id_out);
+/* Queue n requests under one lock (all or none: EINVAL / ENOMEM as for
+ * octax_server_submit, nothing queued). ids_out [n] receives their ids in
+ * order. For load generators and clients that produce many small requests,
+ * whose one-by-one submission would cost more host time than their GPU work.
+ * The paper defines no counterpart. */
+int octax_server_submit_batch(octax_server *s, const octax_request *reqs, int n, uint64_t *ids_out);
 /* Wait until request id is done (its outputs are then complete in device
  * memory). timeout_ms < 0 waits without limit; ETIMEOUT, ENOTFOUND. */
 int octax_server_wait(octax_server *s, uint64_t id, int timeout_ms, octax_request_info *info_out);
+/* Wait until all n requests ids [n] are done (timeout_ms for the whole wait,
+ * < 0 = no limit), copy their infos into infos [n] (nullable) and, if release
+ * is nonzero, forget them as octax_server_release does. ETIMEOUT, ENOTFOUND
+ * (nothing released). The paper defines no counterpart. */
+int octax_server_wait_batch(octax_server *s, const uint64_t *ids, int n, int timeout_ms, octax_request_info *infos,
+                            int release);
 int octax_server_query(octax_server *s, uint64_t id, octax_request_info *info_out);
 /* Forget a finished request's bookkeeping. EINVAL if it is not done. */
 int octax_server_release(octax_server *s, uint64_t id);

@@ -412,39 +412,59 @@ int octax_server_create(const octax_game *games, int n_games, uint32_t quirks,
   return OCTAX_OK;
 }
 
-int octax_server_submit(octax_server *s, const octax_request *req, uint64_t *id_out) {
-  if (!s || !req || !id_out) {
-    set_error("octax_server_submit: null argument");
-    return OCTAX_EINVAL;
-  }
-  const octax_request &r = *req;
+static int check_request(const octax_server *s, const octax_request &r, const char *who) {
   if (r.game >= s->n_games || r.n_envs < 1 || r.n_envs > kMaxEnvs || r.n_steps < 1 ||
       r.n_steps > kMaxSteps || !r.actions_host || !r.obs_dev || !r.reward_dev || !r.done_dev ||
       (reinterpret_cast<uintptr_t>(r.obs_dev) & 15u)) {
-    set_error("octax_server_submit: need game < n_games, 1..4096 envs, 1..8 steps, all buffers, "
-              "16-byte aligned obs");
+    set_error(std::string(who) + ": need game < n_games, 1..4096 envs, 1..8 steps, all buffers, "
+                                 "16-byte aligned obs");
     return OCTAX_EINVAL;
   }
   if (r.n_envs > s->capacity) {
-    set_error("octax_server_submit: request larger than the memory budget admits");
+    set_error(std::string(who) + ": request larger than the memory budget admits");
     return OCTAX_ENOMEM;
+  }
+  return OCTAX_OK;
+}
+
+// Queue already checked requests (caller holds s->mu).
+static void enqueue_locked(octax_server *s, const octax_request *reqs, int n, uint64_t *ids) {
+  const int64_t t = now_ns();
+  for (int k = 0; k < n; ++k) {
+    const octax_request &r = reqs[k];
+    const uint64_t id = s->next_id++;
+    Req &q = s->reqs[id];
+    q.id = id;
+    q.r = r;
+    q.actions.assign(r.actions_host, r.actions_host + (size_t)r.n_steps * r.n_envs);
+    q.r.actions_host = nullptr;
+    q.submit_ns = t;
+    s->queue.push_back(id);
+    s->stats.submitted++;
+    ids[k] = id;
+  }
+  s->cv_submit.notify_one();
+}
+
+int octax_server_submit(octax_server *s, const octax_request *req, uint64_t *id_out) {
+  return octax_server_submit_batch(s, req, 1, id_out);
+}
+
+int octax_server_submit_batch(octax_server *s, const octax_request *reqs, int n, uint64_t *ids_out) {
+  if (!s || !reqs || !ids_out || n < 1) {
+    set_error("octax_server_submit: null argument or n < 1");
+    return OCTAX_EINVAL;
+  }
+  for (int k = 0; k < n; ++k) {
+    const int rc = check_request(s, reqs[k], "octax_server_submit");
+    if (rc) return rc;
   }
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stop) {
     set_error(s->fatal.empty() ? "octax_server_submit: server stopped" : s->fatal);
     return OCTAX_ECUDA;
   }
-  const uint64_t id = s->next_id++;
-  Req &q = s->reqs[id];
-  q.id = id;
-  q.r = r;
-  q.actions.assign(r.actions_host, r.actions_host + (size_t)r.n_steps * r.n_envs);
-  q.r.actions_host = nullptr;
-  q.submit_ns = now_ns();
-  s->queue.push_back(id);
-  s->stats.submitted++;
-  *id_out = id;
-  s->cv_submit.notify_one();
+  enqueue_locked(s, reqs, n, ids_out);
   return OCTAX_OK;
 }
 
@@ -479,6 +499,42 @@ int octax_server_wait(octax_server *s, uint64_t id, int timeout_ms, octax_reques
   if (s->reqs[id].state != 2) {
     set_error(s->fatal.empty() ? "octax_server_wait: server stopped" : s->fatal);
     return OCTAX_ECUDA;
+  }
+  return OCTAX_OK;
+}
+
+int octax_server_wait_batch(octax_server *s, const uint64_t *ids, int n, int timeout_ms, octax_request_info *infos,
+                            int release) {
+  if (!s || !ids || n < 1) {
+    set_error("octax_server_wait_batch: null argument or n < 1");
+    return OCTAX_EINVAL;
+  }
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (int k = 0; k < n; ++k)
+    if (s->reqs.find(ids[k]) == s->reqs.end()) {
+      set_error("octax_server_wait_batch: unknown request id");
+      return OCTAX_ENOTFOUND;
+    }
+  auto all_done = [&] {
+    if (s->stop) return true;
+    for (int k = 0; k < n; ++k)
+      if (s->reqs[ids[k]].state != 2) return false;
+    return true;
+  };
+  if (timeout_ms < 0)
+    s->cv_done.wait(lk, all_done);
+  else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), all_done)) {
+    set_error("octax_server_wait_batch: timed out");
+    return OCTAX_ETIMEOUT;
+  }
+  for (int k = 0; k < n; ++k)
+    if (s->reqs[ids[k]].state != 2) {
+      set_error(s->fatal.empty() ? "octax_server_wait_batch: server stopped" : s->fatal);
+      return OCTAX_ECUDA;
+    }
+  for (int k = 0; k < n; ++k) {
+    if (infos) fill_info(s->reqs[ids[k]], infos + k);
+    if (release) s->reqs.erase(ids[k]);
   }
   return OCTAX_OK;
 }

@@ -109,7 +109,7 @@ EXPORTS = ("octax_create", "octax_reset", "octax_step", "octax_step_n", "octax_s
            "octax_stack_frames", "octax_variant", "octax_step_n_packed", "octax_step_host_packed", "octax_debug_stall_writers", "octax_device_bytes", "octax_destroy", "octax_last_error",
            "octax_server_create", "octax_server_submit", "octax_server_wait",
            "octax_server_query", "octax_server_release", "octax_server_get_stats",
-           "octax_server_destroy", "octax_rollout_static", "octax_policy_create", "octax_policy_forward",
+           "octax_server_destroy", "octax_server_submit_batch", "octax_server_wait_batch", "octax_rollout_static", "octax_policy_create", "octax_policy_forward",
            "octax_policy_forward_u8", "octax_rollout_policy", "octax_policy_sync", "octax_policy_destroy")
 
 _lib = None
@@ -153,6 +153,8 @@ def load_library(path: str = LIB_PATH):
             "octax_server_create": (I32, [C.POINTER(CGame), I32, C.c_uint32,
                                           C.POINTER(CServerConfig), C.POINTER(P)]),
             "octax_server_submit": (I32, [P, C.POINTER(CRequest), C.POINTER(C.c_uint64)]),
+            "octax_server_submit_batch": (I32, [P, C.POINTER(CRequest), I32, C.POINTER(C.c_uint64)]),
+            "octax_server_wait_batch": (I32, [P, C.POINTER(C.c_uint64), I32, I32, C.POINTER(CRequestInfo), I32]),
             "octax_server_wait": (I32, [P, C.c_uint64, I32, C.POINTER(CRequestInfo)]),
             "octax_server_query": (I32, [P, C.c_uint64, C.POINTER(CRequestInfo)]),
             "octax_server_release": (I32, [P, C.c_uint64]),
@@ -489,6 +491,65 @@ class Server:
         check(load_library().octax_server_submit(self._h, C.byref(req), C.byref(rid)))
         self._outs[rid.value] = out
         return rid.value
+
+    def submit_batch(self, items) -> list:
+        """Queue several requests at once: items = [(game, actions, seed, out)];
+        out = (obs, reward, done) device tensors as in submit (required here)."""
+        torch = self._torch
+        arr = (CRequest * len(items))()
+        keep = []
+        for k, (game, actions, seed, out) in enumerate(items):
+            a = np.ascontiguousarray(actions, dtype=np.uint8)
+            T, n = a.shape
+            obs, rew, done = out
+            if obs.dtype != torch.uint8 or tuple(obs.shape) != (T, n, self.S) + self.frame or \
+                    rew.dtype != torch.float32 or tuple(rew.shape) != (T, n) or \
+                    done.dtype != torch.uint8 or tuple(done.shape) != (T, n) or \
+                    not (obs.is_contiguous() and rew.is_contiguous() and done.is_contiguous()):
+                raise ValueError("submit_batch: outputs must match each request's shape")
+            keep.append(a)
+            arr[k] = CRequest(game, 0, n, T, 0, seed & 0xFFFFFFFFFFFFFFFF, a.ctypes.data,
+                              obs.data_ptr(), rew.data_ptr(), done.data_ptr())
+        ids = (C.c_uint64 * len(items))()
+        check(load_library().octax_server_submit_batch(self._h, arr, len(items), ids))
+        out_ids = list(ids)
+        for rid, it in zip(out_ids, items):
+            self._outs[rid] = it[3]
+        return out_ids
+
+    REQUEST_DTYPE = np.dtype([("game", "<u2"), ("pad", "<u2"), ("n_envs", "<u4"), ("n_steps", "<u4"),
+                              ("pad2", "<u4"), ("seed", "<u8"), ("actions", "<u8"), ("obs", "<u8"),
+                              ("reward", "<u8"), ("done", "<u8")])
+
+    def submit_raw(self, reqs: np.ndarray) -> np.ndarray:
+        """Queue requests given as a REQUEST_DTYPE array (the octax_request
+        layout: host action pointers, device output pointers, which the
+        caller keeps alive until the requests are done). Returns the ids."""
+        reqs = np.ascontiguousarray(reqs, dtype=self.REQUEST_DTYPE)
+        assert self.REQUEST_DTYPE.itemsize == C.sizeof(CRequest)
+        ids = np.zeros(len(reqs), dtype=np.uint64)
+        check(load_library().octax_server_submit_batch(self._h, reqs.ctypes.data_as(C.POINTER(CRequest)),
+                                                       len(reqs), ids.ctypes.data_as(C.POINTER(C.c_uint64))))
+        return ids
+
+    def wait_raw(self, ids: np.ndarray, release: bool = True, timeout_ms: int = -1) -> np.ndarray:
+        """Wait for all ids; returns int64 [n, 3] (submit_ns, admit_ns, done_ns)."""
+        ids = np.ascontiguousarray(ids, dtype=np.uint64)
+        infos = (CRequestInfo * len(ids))()
+        check(load_library().octax_server_wait_batch(self._h, ids.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                                     len(ids), timeout_ms, infos, int(release)))
+        raw = np.frombuffer(infos, dtype=np.int64).reshape(len(ids), 4)
+        return raw[:, 1:].copy()
+
+    def wait_batch(self, ids, release: bool = True, timeout_ms: int = -1) -> list:
+        """Wait for all ids; returns their infos; release=True forgets them."""
+        arr = (C.c_uint64 * len(ids))(*ids)
+        infos = (CRequestInfo * len(ids))()
+        check(load_library().octax_server_wait_batch(self._h, arr, len(ids), timeout_ms, infos, int(release)))
+        if release:
+            for rid in ids:
+                self._outs.pop(rid, None)
+        return [self._info(i) for i in infos]
 
     def outputs(self, rid: int) -> tuple:
         return self._outs[rid]

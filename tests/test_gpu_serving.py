@@ -183,3 +183,39 @@ def test_server_errors():
     with pytest.raises(o.OctaxError):
         srv.query(rid)
     srv.close()
+
+
+def test_batched_submit_equals_single_submits():
+    """octax_server_submit_batch / octax_server_wait_batch: the same requests
+    queued in one call give the same outputs as queued one by one, the infos
+    come back in order and released ids are forgotten; an invalid request in
+    a batch queues nothing."""
+    o = octax()
+    gs = games()
+    reqs = make_requests(24, 7, max_envs=500)
+    total = sum(r["actions"].shape[1] for r in reqs)
+    srv = o.Server(gs, memory_budget_bytes=(total // 2) * SLOT_BYTES, block=128, inst_per_warp=16)
+    _, _, single = run_all(srv, reqs)
+    items = []
+    for r in reqs:
+        T, n = r["actions"].shape
+        out = (torch.empty((T, n, 4, 32, 64), dtype=torch.uint8, device="cuda"),
+               torch.empty((T, n), dtype=torch.float32, device="cuda"),
+               torch.empty((T, n), dtype=torch.uint8, device="cuda"))
+        items.append((r["game"], r["actions"], r["seed"], out))
+    ids = srv.submit_batch(items)
+    assert ids == sorted(ids) and len(set(ids)) == len(ids)
+    infos = srv.wait_batch(ids, release=True, timeout_ms=60000)
+    assert all(i["state"] == 2 and i["done_ns"] >= i["admit_ns"] >= i["submit_ns"] for i in infos)
+    for (_, _, _, out), want in zip(items, single):
+        for x, y in zip(out, want):
+            assert torch.equal(x.cpu(), y)
+    with pytest.raises(o.OctaxError) as e:
+        srv.query(ids[0])
+    assert e.value.code == o.ENOTFOUND
+    bad = list(items[:2]) + [(99, items[2][1], 1, items[2][3])]
+    before = srv.stats()["submitted"]
+    with pytest.raises(o.OctaxError):
+        srv.submit_batch(bad)
+    assert srv.stats()["submitted"] == before
+    srv.close()
