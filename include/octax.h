@@ -474,6 +474,12 @@ int octax_rollout_policy(octax_env *env, octax_policy *policy, int n_steps, uint
  * policy kernel gave up one of its bounded waits (its outputs are then
  * incomplete). The paper defines no counterpart. */
 int octax_policy_sync(octax_policy *policy);
+/* Diagnostic for the policy kernels' failure path (the paper defines no
+ * counterpart): while `on` is nonzero the conv kernel skips the completion
+ * signal of its first MMA group, so that wait runs out after about one
+ * second in every CTA; the kernel records the failure and returns, and the
+ * next octax_policy_sync reports OCTAX_ECUDA. No other work is affected. */
+int octax_policy_debug_stall(octax_policy *policy, int on);
 void octax_policy_destroy(octax_policy *policy);
 
 /* Message of the last failed call on this thread ("" if none). The paper

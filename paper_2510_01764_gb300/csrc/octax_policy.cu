@@ -54,6 +54,7 @@ struct octax_policy {
   uint8_t *act3 = nullptr;    // flattened features, heads' A-operand tiles
   uint64_t *ring = nullptr;   // rollout: two packed observation slots [2][max_envs][4][32]
   unsigned int *err = nullptr;
+  int stall = 0;              // octax_policy_debug_stall
 };
 
 namespace octax {
@@ -239,6 +240,7 @@ struct ConvArgs {
   const float *fp;              // FpLayout
   uint8_t *act3;                // [tiles][16][8][128][16 B]
   unsigned int *err;
+  int stall;                    // diagnostic: the first conv1 commit is skipped (its wait runs out)
 };
 
 // One 32-column conv1 tile or 64-column conv2/conv3 tile: issue `taps` x
@@ -356,7 +358,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
         *reinterpret_cast<uint4 *>(blk + b * 512 + lane * 16) = make_uint4(lo.x, lo.y, hi.x, hi.y);
       }
     };
-    auto issue_c1 = [&](int buf) {  // thread 0: output rows 2p, 2p + 1
+    auto issue_c1 = [&](int buf, bool first) {  // thread 0: output rows 2p, 2p + 1
       tc_fence_after();
       for (int s2 = 0; s2 < 2; ++s2)
         for (int tap = 0; tap < 4; ++tap) {
@@ -368,19 +370,19 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
             mma_bf16(tmem + kD1Col + 64 * buf + 32 * s2, ad, bd, idesc_bf16(128, 32), (tap | kk) != 0);
           }
         }
-      mma_commit(buf ? bar_c1_1 : bar_c1_0);
+      if (!(a.stall && first)) mma_commit(buf ? bar_c1_1 : bar_c1_0);
     };
     build(0, 0);
     fence_async_smem();
     __syncthreads();
-    if (t == 0) issue_c1(0);
+    if (t == 0) issue_c1(0, true);
     for (int pr = 0; pr < 7 && ok; ++pr) {
       const int cb = pr & 1, nb = cb ^ 1;
       if (pr + 1 < 7) build(pr + 1, nb);  // buffer nb: its MMAs (pair pr - 1) completed
       fence_async_smem();
       ok = cb ? wait_all(bar_c1_1, ph_c1_1) : wait_all(bar_c1_0, ph_c1_0);
       if (!ok) break;
-      if (pr + 1 < 7 && t == 0) issue_c1(nb);
+      if (pr + 1 < 7 && t == 0) issue_c1(nb, false);
       if (pr == 6 && t == 0) {  // the frames are dead: W3 taps 0-1 into their place
         mbar_expect_tx(bar_w3a, kW3EarlyBytes);
         bulk_g2s(sbase + kW3Off, a.w3, kW3EarlyBytes, bar_w3a);
@@ -671,7 +673,7 @@ int launch_forward(octax_policy *p, int64_t n, const uint64_t *obs_words, const 
     return OCTAX_EINVAL;
   }
   ConvArgs c{obs_words, obs_u8, n, (const uint8_t *)p->w1, (const uint8_t *)p->w2, (const uint8_t *)p->w3, p->fp,
-             p->act3, p->err};
+             p->act3, p->err, p->stall};
   const int64_t batches = (n + kP - 1) / kP;
   const int grid = (int)std::min<int64_t>(batches, p->sms);
   if (obs_u8)
@@ -891,6 +893,15 @@ int octax_policy_sync(octax_policy *p) {
     set_error("octax_policy_sync: a policy kernel gave up a bounded wait; its outputs are incomplete");
     return OCTAX_ECUDA;
   }
+  return OCTAX_OK;
+}
+
+int octax_policy_debug_stall(octax_policy *p, int on) {
+  if (!p) {
+    set_error("octax_policy_debug_stall: need a policy");
+    return OCTAX_EINVAL;
+  }
+  p->stall = on != 0;
   return OCTAX_OK;
 }
 

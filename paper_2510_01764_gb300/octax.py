@@ -110,7 +110,8 @@ EXPORTS = ("octax_create", "octax_reset", "octax_step", "octax_step_n", "octax_s
            "octax_server_create", "octax_server_submit", "octax_server_wait",
            "octax_server_query", "octax_server_release", "octax_server_get_stats",
            "octax_server_destroy", "octax_server_submit_batch", "octax_server_wait_batch", "octax_rollout_static", "octax_policy_create", "octax_policy_forward",
-           "octax_policy_forward_u8", "octax_rollout_policy", "octax_policy_sync", "octax_policy_destroy")
+           "octax_policy_forward_u8", "octax_rollout_policy", "octax_policy_sync", "octax_policy_debug_stall",
+           "octax_policy_destroy")
 
 _lib = None
 _lock = threading.Lock()
@@ -167,6 +168,7 @@ def load_library(path: str = LIB_PATH):
             "octax_policy_forward_u8": (I32, [P, I64, P, C.c_uint64, C.c_uint32, P, P, P]),
             "octax_rollout_policy": (I32, [P, P, I32, C.c_uint64, C.c_uint32, P, P, P, P, P, P]),
             "octax_policy_sync": (I32, [P]),
+            "octax_policy_debug_stall": (I32, [P, I32]),
             "octax_policy_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
@@ -671,6 +673,10 @@ class Policy:
 
     def sync(self) -> None:
         check(load_library().octax_policy_sync(self._h))
+
+    def debug_stall(self, on: bool) -> None:
+        """Diagnostic: make the conv kernel's first wait run out (octax_policy_debug_stall)."""
+        check(load_library().octax_policy_debug_stall(self._h, int(bool(on))))
 
     def close(self) -> None:
         if getattr(self, "_h", None):

@@ -191,3 +191,30 @@ def test_policy_rejects_bad_arguments():
     env = o.Env([g], 16, seed=1)
     with pytest.raises(o.OctaxError):      # more instances than max_envs
         pol.rollout(env, 2, torch.zeros((16, 4, 32), dtype=torch.int64, device="cuda"))
+
+
+def test_bounded_wait_failure_is_reported_and_recovered():
+    """The conv kernel's waits are bounded: with its first completion signal
+    withheld (octax_policy_debug_stall) the wait runs out after about a
+    second, the kernel returns, octax_policy_sync reports OCTAX_ECUDA once,
+    and the same policy then computes correct outputs again."""
+    import time
+
+    o = octax()
+    n, L = 64, 5
+    params = W.policy_params(21, L)
+    obs = random_frames(n, 0.1, 21)
+    pol = o.Policy(params, max_envs=n)
+    words = torch.from_numpy(pack(obs)).cuda()
+    pol.debug_stall(True)
+    t0 = time.monotonic()
+    pol.forward(words)
+    with pytest.raises(o.OctaxError) as e:
+        pol.sync()
+    assert e.value.code == o.ECUDA
+    assert time.monotonic() - t0 < 30
+    pol.debug_stall(False)
+    pol.sync()                                  # the report was cleared
+    lg, v, _ = pol.forward(words)
+    pol.sync()
+    check_outputs(params, obs, lg, v)
