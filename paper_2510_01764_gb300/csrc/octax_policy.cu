@@ -8,7 +8,8 @@
 // VALID convolutions; weights and stored activations in bfloat16, products
 // accumulated in fp32 (TMEM), heads' output layers in fp32 on the CUDA cores.
 //
-// Conv kernel (persistent, one CTA of 256 threads per SM). A batch of kP = 8
+// Conv kernel (persistent, one CTA per SM: 8 warps that build operands and
+// drain accumulators, one warp that issues the MMAs and bulk copies). A batch of kP = 8
 // instances is processed at a time; the rows of every GEMM are
 // (grid position, instance) with the instance fastest, so one 8-row core
 // matrix of the tcgen05 no-swizzle K-major layout is one grid position of
@@ -19,8 +20,8 @@
 //  - conv1 works on 4 x 2-pixel blocks: with stride (4, 2) its (8, 4) kernel
 //    covers 2 x 2 blocks, so it is 4 taps of K = 32 (4 frames x 8 pixels)
 //    over a 16 x 16 grid of blocks, expanded from the packed frame bits to
-//    bf16 0/1 for two block rows per M tile (one output row of 16 positions
-//    x 8 instances = 128 rows).
+//    bf16 0/1; two output rows (16 positions x 8 instances = 128 rows each)
+//    share one N = 64 accumulator fed by the three block rows they read.
 //  - conv2 (stride 2) reads conv1's output split by the parity of x and y:
 //    tap (kx, ky) reads sub-grid (kx & 1, ky & 1) at offset (kx >> 1,
 //    ky >> 1) of an 8-wide grid. The sub-grids are kept as a band of three
@@ -66,14 +67,16 @@ namespace {
 
 constexpr int kP = 8;            // instances per conv batch
 constexpr int kThreads = 128;      // heads kernel
-constexpr int kConvThreads = 256;  // conv kernel: two warps per TMEM lane quarter
+constexpr int kConvWork = 256;               // conv kernel: 8 warps build / drain (two per TMEM lane quarter)
+constexpr int kConvThreads = kConvWork + 32; // + one warp that issues the MMAs and bulk copies
+constexpr int kIssuer = kConvWork;           // its issuing thread
 constexpr int kMaxLogits = 17;   // 16 keys + the no-op
 constexpr uint64_t kMaxWaitNs = 1000000000ull;
 constexpr uint32_t kMaxPolls = 1u << 24;
 
 // ---- conv kernel shared memory (bytes) -------------------------------------
-constexpr uint32_t kW1Off = 0;                             // conv1 B: [tap 4][chunk 4][n 32][8]
-constexpr uint32_t kW1Bytes = 4 * 4 * 32 * 16;
+constexpr uint32_t kW1Off = 0;                             // conv1 B: [j 3][dx 2][chunk 4][n 64][8]
+constexpr uint32_t kW1Bytes = 6 * 4 * 64 * 16;
 constexpr uint32_t kW2Off = kW1Off + kW1Bytes;             // conv2 B: [tap 16][chunk 4][n 64][8]
 constexpr uint32_t kW2Bytes = 16 * 4 * 64 * 16;
 constexpr uint32_t kW3Bytes = 9 * 8 * 64 * 16;             // conv3 B: [tap 9][chunk 8][n 64][8]
@@ -280,7 +283,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_s;
-  if (t == 0) {
+  if (t == kIssuer) {
     mbar_expect_tx(bar_w, kW1Bytes + kW2Bytes);
     bulk_g2s(sbase + kW1Off, a.w1, kW1Bytes, bar_w);
     for (uint32_t o = 0; o < kW2Bytes; o += 16384) bulk_g2s(sbase + kW2Off + o, a.w2 + o, 16384, bar_w);
@@ -294,6 +297,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
   // one half of the accumulator's columns
   const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
   const int half = warp >> 2;
+  const bool issuer = warp == kConvWork / 32;  // the MMA-issuing warp takes no part in building / draining
   const int r = 32 * (warp & 3) + lane;  // M-tile row of this thread (TMEM lane)
   const int g = r >> 3, ri = r & 7;      // grid position in the tile, instance in the batch
 
@@ -311,7 +315,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     // building one block position read 32 consecutive words
     uint64_t *fr = reinterpret_cast<uint64_t *>(sm + kFrOff);
     if (!kU8) {
-      for (int q = t; q < kP * 64; q += kConvThreads) {  // instance i, frame c, rows 2 y2 and 2 y2 + 1
+      for (int q = issuer ? kP * 64 : t; q < kP * 64; q += kConvWork) {  // instance i, frame c, rows 2 y2, 2 y2 + 1
         const int i = q & 7, c = (q >> 7) & 3, y2 = (q >> 3) & 15;
         uint4 v = make_uint4(0, 0, 0, 0);
         if (i0 + i < a.n) v = __ldg(reinterpret_cast<const uint4 *>(a.obs_words + (i0 + i) * 128 + c * 32 + 2 * y2));
@@ -319,7 +323,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
         fr[((2 * y2 + 1) * 4 + c) * 8 + i] = (uint64_t)v.z | (uint64_t)v.w << 32;
       }
     } else {
-      for (int q = t; q < kP * 128; q += kConvThreads) {  // one 64-byte row each
+      for (int q = issuer ? kP * 128 : t; q < kP * 128; q += kConvWork) {  // one 64-byte row each
         const int i = q & 7, c = (q >> 8) & 3, y = (q >> 3) & 31;
         uint64_t bits = 0;
         if (i0 + i < a.n) {
@@ -349,6 +353,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     // pad position 48 is read by discarded rows only. Warp w builds positions
     // 6w .. 6w + 5; lane = frame * 8 + instance.
     auto build = [&](int pr, int buf) {
+      if (issuer) return;
       uint8_t *blk = sm + kBlkOff + buf * kBlkBytes;
 #pragma unroll 2
       for (int j = 0; j < 6; ++j) {
@@ -358,39 +363,41 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
         *reinterpret_cast<uint4 *>(blk + b * 512 + lane * 16) = make_uint4(lo.x, lo.y, hi.x, hi.y);
       }
     };
-    auto issue_c1 = [&](int buf, bool first) {  // thread 0: output rows 2p, 2p + 1
+    // Both output rows of the pair in one N = 64 accumulator: block row j
+    // (shift dx) feeds row 2p through tap (dx, dy = j) and row 2p + 1 through
+    // tap (dx, dy = j - 1); W1 holds, per (j, dx), those two taps stacked
+    // over n (zeros where a tap does not apply), so each MMA reads its A tile
+    // once for 64 outputs.
+    auto issue_c1 = [&](int buf, bool first) {  // the issuing thread: output rows 2p, 2p + 1
       tc_fence_after();
-      for (int s2 = 0; s2 < 2; ++s2)
-        for (int tap = 0; tap < 4; ++tap) {
-          const int dx = tap & 1, dy = tap >> 1;
+      for (int j = 0; j < 3; ++j)
+        for (int dx = 0; dx < 2; ++dx)
           for (int kk = 0; kk < 2; ++kk) {
-            const uint64_t ad =
-                sdesc(sbase + kBlkOff + buf * kBlkBytes + (16 * s2 + dx + 16 * dy) * 512 + kk * 256, 128, 512);
-            const uint64_t bd = sdesc(sbase + kW1Off + tap * 2048 + kk * 1024, 512, 128);
-            mma_bf16(tmem + kD1Col + 64 * buf + 32 * s2, ad, bd, idesc_bf16(128, 32), (tap | kk) != 0);
+            const uint64_t ad = sdesc(sbase + kBlkOff + buf * kBlkBytes + (16 * j + dx) * 512 + kk * 256, 128, 512);
+            const uint64_t bd = sdesc(sbase + kW1Off + (2 * j + dx) * 4096 + kk * 2048, 1024, 128);
+            mma_bf16(tmem + kD1Col + 64 * buf, ad, bd, idesc_bf16(128, 64), (j | dx | kk) != 0);
           }
-        }
       if (!(a.stall && first)) mma_commit(buf ? bar_c1_1 : bar_c1_0);
     };
     build(0, 0);
     fence_async_smem();
     __syncthreads();
-    if (t == 0) issue_c1(0, true);
+    if (t == kIssuer) issue_c1(0, true);
     for (int pr = 0; pr < 7 && ok; ++pr) {
       const int cb = pr & 1, nb = cb ^ 1;
       if (pr + 1 < 7) build(pr + 1, nb);  // buffer nb: its MMAs (pair pr - 1) completed
       fence_async_smem();
       ok = cb ? wait_all(bar_c1_1, ph_c1_1) : wait_all(bar_c1_0, ph_c1_0);
       if (!ok) break;
-      if (pr + 1 < 7 && t == 0) issue_c1(nb, false);
-      if (pr == 6 && t == 0) {  // the frames are dead: W3 taps 0-1 into their place
+      if (pr + 1 < 7 && t == kIssuer) issue_c1(nb, false);
+      if (pr == 6 && t == kIssuer) {  // the frames are dead: W3 taps 0-1 into their place
         mbar_expect_tx(bar_w3a, kW3EarlyBytes);
         bulk_g2s(sbase + kW3Off, a.w3, kW3EarlyBytes, bar_w3a);
       }
       if (pr == 3 || pr == 5) {  // the band's conv2 tile must finish before its rows are rewritten
         ok = wait_all(bar_c2, ph_c2);
         if (!ok) break;
-        for (int q = t; q < 4 * 8 * 32; q += kConvThreads) {  // slide: grid row 2 -> 0 (4 sub-grids x 8 x 512 B)
+        for (int q = issuer ? 1024 : t; q < 4 * 8 * 32; q += kConvWork) {  // slide: grid row 2 -> 0 (4 x 8 x 512 B)
           const int sgq = q >> 8, rem = q & 255;
           uint4 *base = reinterpret_cast<uint4 *>(sm + kAct1Off + sgq * kSubBytes);
           base[rem] = base[16 * 32 + rem];
@@ -398,7 +405,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
         __syncthreads();
       }
       tc_fence_after();
-      for (int s2 = 0; s2 < 2; ++s2) {
+      for (int s2 = 0; s2 < 2 && !issuer; ++s2) {
         const int oy = 2 * pr + s2;
         float v[16];
         tmem_ld16(tmem + lane_base + kD1Col + 64 * cb + 32 * s2 + 16 * half, v);
@@ -418,7 +425,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
         const int tt = (pr - 2) >> 1;  // conv2 tile: output rows 2tt, 2tt + 1
         fence_async_smem();
         __syncthreads();
-        if (t == 0) {
+        if (t == kIssuer) {
           tc_fence_after();
           for (int tap = 0; tap < 16; ++tap) {
             const int kx = tap & 3, ky = tap >> 2;
@@ -438,14 +445,14 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     if (!ok) break;
 
     // ---- the rest of W3 into the (now dead) band region; conv2 epilogues into region X
-    if (t == 0) {
+    if (t == kIssuer) {
       fence_async_smem();
       mbar_expect_tx(bar_w3b, kW3Bytes - kW3EarlyBytes);
       for (uint32_t o = kW3EarlyBytes; o < kW3Bytes; o += 14336)
         bulk_g2s(sbase + kW3Off + o, a.w3 + o, 14336, bar_w3b);
     }
     tc_fence_after();
-    for (int tt = 0; tt < 3; ++tt) {
+    for (int tt = 0; tt < 3 && !issuer; ++tt) {
       const int px = g & 7, py = 2 * tt + (g >> 3), h = half;
       float v[32];
       tmem_ld32(tmem + lane_base + kD2Col + 64 * tt + 32 * h, v);
@@ -463,7 +470,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     if (!ok) break;
 
     // ---- conv3: two tiles of 16 positions (qx + 8 qy, qy in {2u, 2u + 1})
-    if (t == 0) {
+    if (t == kIssuer) {
       tc_fence_after();
       for (int u = 0; u < 2; ++u)
         for (int tap = 0; tap < 9; ++tap) {
@@ -479,7 +486,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     ok = wait_all(bar_c3, ph_c3);
     if (!ok) break;
     tc_fence_after();
-    for (int u = 0; u < 2; ++u) {
+    for (int u = 0; u < 2 && !issuer; ++u) {
       const int m = 16 * u + g, qx = m & 7, qy = m >> 3, h = half;
       const int64_t inst = i0 + ri;
       float v[32];
@@ -717,14 +724,20 @@ int octax_policy_create(const octax_policy_params *prm, int64_t max_envs, int de
   cudaError_t r = cudaSetDevice(device);
   if (r != cudaSuccess) return cuda_fail(r, "octax_policy_create: cudaSetDevice");
   const int L = prm->n_logits;
-  // conv1 B: [tap (dx + 2 dy)][chunk = frame c][n 32][k' = kx + 4 ky] = w1[n][c][4 dx + kx][2 dy + ky]
-  std::vector<uint16_t> w1p(4 * 4 * 32 * 8);
-  for (int tap = 0; tap < 4; ++tap)
-    for (int c = 0; c < 4; ++c)
-      for (int n = 0; n < 32; ++n)
-        for (int k = 0; k < 8; ++k) {
-          const int kx = 4 * (tap & 1) + (k & 3), ky = 2 * (tap >> 1) + (k >> 2);
-          w1p[((tap * 4 + c) * 32 + n) * 8 + k] = bf16_bits(prm->w1[((n * 4 + c) * 8 + kx) * 4 + ky]);
+  // conv1 B, per block row j (0..2) and shift dx: [j][dx][chunk = frame c][n 64][k' = kx + 4 ky];
+  // n < 32: w1[n][c][4 dx + kx][2 j + ky] (tap dy = j, for j <= 1), n >= 32: w1[n - 32][c][4 dx + kx][2 (j - 1) + ky]
+  // (tap dy = j - 1, for j >= 1), zero otherwise
+  std::vector<uint16_t> w1p(6 * 4 * 64 * 8, 0);
+  for (int j = 0; j < 3; ++j)
+    for (int dx = 0; dx < 2; ++dx)
+      for (int c = 0; c < 4; ++c)
+        for (int n = 0; n < 64; ++n) {
+          const int dy = n < 32 ? j : j - 1, o = n & 31;
+          if (dy < 0 || dy > 1) continue;
+          for (int k = 0; k < 8; ++k) {
+            const int kx = 4 * dx + (k & 3), ky = 2 * dy + (k >> 2);
+            w1p[(((j * 2 + dx) * 4 + c) * 64 + n) * 8 + k] = bf16_bits(prm->w1[((o * 4 + c) * 8 + kx) * 4 + ky]);
+          }
         }
   // conv2 B: [tap (kx + 4 ky)][chunk j][n 64][e] = w2[n][8 j + e][kx][ky]
   std::vector<uint16_t> w2p(16 * 4 * 64 * 8);
