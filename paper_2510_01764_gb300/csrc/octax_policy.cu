@@ -24,9 +24,10 @@
 //    share one N = 64 accumulator fed by the three block rows they read.
 //  - conv2 (stride 2) reads conv1's output split by the parity of x and y:
 //    tap (kx, ky) reads sub-grid (kx & 1, ky & 1) at offset (kx >> 1,
-//    ky >> 1) of an 8-wide grid. The sub-grids are kept as a band of three
-//    grid rows that slides down with conv1's output rows; each M tile covers
-//    two output rows.
+//    ky >> 1) of an 8-wide grid. The sub-grids are kept as a band of four
+//    grid rows that slides down by two with conv1's output rows; each M tile
+//    covers two output rows and reads three grid rows, so the next conv1
+//    pair writes the fourth while the tile computes.
 //  - conv3 (stride 1) reads conv2's output on an 8-wide grid: tap (kx, ky) is
 //    the shift kx + 8 ky.
 //  Rows whose grid position lies outside the layer's output are computed
@@ -80,22 +81,22 @@ constexpr uint32_t kW1Bytes = 6 * 4 * 64 * 16;
 constexpr uint32_t kW2Off = kW1Off + kW1Bytes;             // conv2 B: [tap 16][chunk 4][n 64][8]
 constexpr uint32_t kW2Bytes = 16 * 4 * 64 * 16;
 constexpr uint32_t kW3Bytes = 9 * 8 * 64 * 16;             // conv3 B: [tap 9][chunk 8][n 64][8]
-constexpr uint32_t kSubPos = 25;                           // band: 3 grid rows of 8 + 1 pad position
+constexpr uint32_t kSubPos = 33;                           // band: 4 grid rows of 8 + 1 pad position
 constexpr uint32_t kSubBytes = kSubPos * 512;              // position: 4 chunks x 8 instances x 16 B
 constexpr uint32_t kAct1Bytes = 4 * kSubBytes;             // 4 parity sub-grids
-constexpr uint32_t kW3Off = kW2Off + kW2Bytes;             // W3 overlays the band (dead by then)
-constexpr uint32_t kAct1Off = kW3Off + (kW3Bytes - kAct1Bytes);
-constexpr uint32_t kXOff = kW3Off + kW3Bytes;              // blocks (conv1) | conv2 output
-constexpr uint32_t kFrOff = kW3Off;                        // frames [32 rows][4][8] u64, in the part of the
-                                                           // W3 region below the band, during conv1
+constexpr uint32_t kW3Off = kW2Off + kW2Bytes;             // W3 overlays frames + band (dead by then)
+constexpr uint32_t kFrOff = kW3Off;                        // frames [32 rows][4][8] u64 during conv1
+constexpr uint32_t kAct1Off = kW3Off + 8192;
+constexpr uint32_t kW3RegionBytes = kW3Bytes > 8192 + kAct1Bytes ? kW3Bytes : 8192 + kAct1Bytes;
+constexpr uint32_t kXOff = kW3Off + kW3RegionBytes;        // blocks (conv1) | conv2 output
 constexpr uint32_t kBlkOff = kXOff;                        // 2 buffers x 49 block positions x 512 B
 constexpr uint32_t kBlkBytes = 49 * 512;
 constexpr uint32_t kAct2Off = kXOff;                       // 50 positions x (8 chunks x 8 x 16 B)
 constexpr uint32_t kAct2Bytes = 50 * 1024;
 constexpr uint32_t kXBytes = kAct2Bytes > 2 * kBlkBytes ? kAct2Bytes : 2 * kBlkBytes;
 constexpr uint32_t kConvSmem = kXOff + kXBytes;
-constexpr uint32_t kW3EarlyBytes = 2 * 8192;               // W3 taps 0-1: loaded once the frames are dead
-static_assert(kAct1Off >= kW3Off && kAct1Off + kAct1Bytes == kXOff, "band inside the W3 region");
+constexpr uint32_t kW3EarlyBytes = 8192;                   // W3 tap 0: loaded once the frames are dead
+static_assert(kAct1Off + kAct1Bytes <= kXOff && kW3Off + kW3Bytes <= kXOff, "band and W3 inside their region");
 static_assert(kFrOff + 8192 <= kAct1Off && kW3Off + kW3EarlyBytes <= kAct1Off, "frames / early W3 below the band");
 static_assert(kConvSmem <= 227 * 1024, "conv kernel shared memory");
 
@@ -204,6 +205,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&v)[16]) {
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
+// Two 16-column loads (one per address) behind a single wait, in one asm
+// statement so that no use of the registers can be scheduled before the wait.
+__device__ __forceinline__ void tmem_ld16x2(uint32_t a0, uint32_t a1, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%33];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(a0), "r"(a1)
+      : "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // .x = a (low half)
   return *reinterpret_cast<uint32_t *>(&h);
@@ -256,14 +274,14 @@ struct TileSpec {
 template <bool kU8>
 __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const ConvArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  __shared__ __align__(8) uint64_t bars[7];  // conv1 x2, conv2, conv3 MMA completion; W1 + W2; W3 x2
+  __shared__ __align__(8) uint64_t bars[8];  // conv1 x2, conv2, conv3 x2 MMA completion; W1 + W2; W3 x2
   __shared__ uint32_t tmem_s;
   __shared__ float sb[160];                  // b1 | b2 | b3
   __shared__ uint2 nib[16];                  // 4 pixel bits -> 4 bf16 0 / 1 (element k = bit k)
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const uint32_t sbase = smem_u32(sm);
   const uint32_t bar_c1_0 = smem_u32(&bars[0]), bar_c1_1 = smem_u32(&bars[1]);
-  const uint32_t bar_c2 = smem_u32(&bars[2]), bar_c3 = smem_u32(&bars[3]);
+  const uint32_t bar_c2 = smem_u32(&bars[2]), bar_c3a = smem_u32(&bars[3]), bar_c3b = smem_u32(&bars[7]);
   const uint32_t bar_w = smem_u32(&bars[4]), bar_w3a = smem_u32(&bars[5]), bar_w3b = smem_u32(&bars[6]);
 
   for (int j = t; j < 160; j += kConvThreads) sb[j] = a.fp[j];
@@ -271,7 +289,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     nib[t] = make_uint2((t & 1) * 0x3F80u | ((t >> 1) & 1) * 0x3F800000u,
                         ((t >> 2) & 1) * 0x3F80u | ((t >> 3) & 1) * 0x3F800000u);
   if (t == 0) {
-    for (int j = 0; j < 7; ++j) mbar_init(smem_u32(&bars[j]), 1);
+    for (int j = 0; j < 8; ++j) mbar_init(smem_u32(&bars[j]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -291,7 +309,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
   // every wait's outcome is made uniform over the block, so all threads
   // leave the loops together
   bool ok = !__syncthreads_or(!mbar_wait(bar_w, 0));
-  uint32_t ph_c1_0 = 0, ph_c1_1 = 0, ph_c2 = 0, ph_c3 = 0, ph_w3 = 0;  // ph_w3: both W3 barriers
+  uint32_t ph_c1_0 = 0, ph_c1_1 = 0, ph_c2 = 0, ph_c3a = 0, ph_c3b = 0, ph_w3 = 0;  // ph_w3: both W3 barriers
   const int64_t n_batches = (a.n + kP - 1) / kP;
   // warps w and w + 4 read the same TMEM lane quarter (rows 32 (w & 3) ..), each
   // one half of the accumulator's columns
@@ -355,7 +373,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     auto build = [&](int pr, int buf) {
       if (issuer) return;
       uint8_t *blk = sm + kBlkOff + buf * kBlkBytes;
-#pragma unroll 2
+#pragma unroll
       for (int j = 0; j < 6; ++j) {
         const int b = 6 * warp + j, bx = b & 15, by = 2 * pr + (b >> 4);
         const uint64_t w0 = fr[(2 * by) * 32 + lane], w1 = fr[(2 * by + 1) * 32 + lane];
@@ -394,30 +412,36 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
         mbar_expect_tx(bar_w3a, kW3EarlyBytes);
         bulk_g2s(sbase + kW3Off, a.w3, kW3EarlyBytes, bar_w3a);
       }
-      if (pr == 3 || pr == 5) {  // the band's conv2 tile must finish before its rows are rewritten
+      if (pr == 4 || pr == 6) {  // the previous tile must finish before its rows are rewritten
         ok = wait_all(bar_c2, ph_c2);
         if (!ok) break;
-        for (int q = issuer ? 1024 : t; q < 4 * 8 * 32; q += kConvWork) {  // slide: grid row 2 -> 0 (4 x 8 x 512 B)
-          const int sgq = q >> 8, rem = q & 255;
+        // slide: grid rows 2, 3 -> 0, 1 (4 sub-grids x 16 positions x 512 B)
+        for (int q = issuer ? 2048 : t; q < 4 * 16 * 32; q += kConvWork) {
+          const int sgq = q >> 9, rem = q & 511;
           uint4 *base = reinterpret_cast<uint4 *>(sm + kAct1Off + sgq * kSubBytes);
           base[rem] = base[16 * 32 + rem];
         }
         __syncthreads();
       }
       tc_fence_after();
-      for (int s2 = 0; s2 < 2 && !issuer; ++s2) {
-        const int oy = 2 * pr + s2;
-        float v[16];
-        tmem_ld16(tmem + lane_base + kD1Col + 64 * cb + 32 * s2 + 16 * half, v);
+      if (!issuer) {
+        float v[32];  // columns 16 half .. of row 2p (v[0..15]) and of row 2p + 1 (v[16..31])
+        const uint32_t d = tmem + lane_base + kD1Col + 64 * cb + 16 * half;
+        tmem_ld16x2(d, d + 32, v);
         const int ox = g;
-        if (ox <= 13) {  // conv2 reads x <= 13
-          const int band = oy <= 5 ? 0 : (oy <= 9 ? 1 : 2);
-          const int slot = (oy >> 1) - 2 * band;
-          const int sg = (ox & 1) + 2 * (oy & 1);
-          uint8_t *dst = sm + kAct1Off + sg * kSubBytes + ((ox >> 1) + 8 * slot) * 512 + ri * 16;
 #pragma unroll
-          for (int c = 0; c < 2; ++c)
-            *reinterpret_cast<uint4 *>(dst + (2 * half + c) * 128) = relu_chunk(v + 8 * c, sb + 16 * half + 8 * c);
+        for (int s2 = 0; s2 < 2; ++s2) {
+          const int oy = 2 * pr + s2;
+          if (ox <= 13) {  // conv2 reads x <= 13
+            const int band = pr < 4 ? 0 : (pr < 6 ? 1 : 2);  // band b holds grid rows 2b .. 2b + 3
+            const int slot = pr - 2 * band;                   // this pair's grid row is oy >> 1 = pr
+            const int sg = (ox & 1) + 2 * (oy & 1);
+            uint8_t *dst = sm + kAct1Off + sg * kSubBytes + ((ox >> 1) + 8 * slot) * 512 + ri * 16;
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+              *reinterpret_cast<uint4 *>(dst + (2 * half + c) * 128) =
+                  relu_chunk(v + 16 * s2 + 8 * c, sb + 16 * half + 8 * c);
+          }
         }
       }
       tc_fence_before();
@@ -441,18 +465,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
         }
       }
     }
-    if (ok) ok = wait_all(bar_c2, ph_c2);  // conv2 tile 2
-    if (!ok) break;
-
-    // ---- the rest of W3 into the (now dead) band region; conv2 epilogues into region X
-    if (t == kIssuer) {
-      fence_async_smem();
-      mbar_expect_tx(bar_w3b, kW3Bytes - kW3EarlyBytes);
-      for (uint32_t o = kW3EarlyBytes; o < kW3Bytes; o += 14336)
-        bulk_g2s(sbase + kW3Off + o, a.w3 + o, 14336, bar_w3b);
-    }
-    tc_fence_after();
-    for (int tt = 0; tt < 3 && !issuer; ++tt) {
+    // ---- conv2 epilogues into region X: tiles 0 and 1 (done) while tile 2
+    // computes; the issuing thread loads the rest of W3 over the band as soon
+    // as tile 2 is done
+    auto drain_c2 = [&](int tt) {
       const int px = g & 7, py = 2 * tt + (g >> 3), h = half;
       float v[32];
       tmem_ld32(tmem + lane_base + kD2Col + 64 * tt + 32 * h, v);
@@ -462,7 +478,23 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
         for (int c = 0; c < 4; ++c)
           *reinterpret_cast<uint4 *>(dst + (4 * h + c) * 128) = relu_chunk(v + 8 * c, sb + 32 + 32 * h + 8 * c);
       }
+    };
+    if (issuer) {
+      if (t == kIssuer && mbar_wait(bar_c2, ph_c2)) {  // (a timeout here shows in the waits below)
+        fence_async_smem();
+        mbar_expect_tx(bar_w3b, kW3Bytes - kW3EarlyBytes);
+        for (uint32_t o = kW3EarlyBytes; o < kW3Bytes; o += 16384)
+          bulk_g2s(sbase + kW3Off + o, a.w3 + o, 16384, bar_w3b);
+      }
+    } else {
+      tc_fence_after();
+      drain_c2(0);
+      drain_c2(1);
     }
+    ok = wait_all(bar_c2, ph_c2);  // conv2 tile 2
+    if (!ok) break;
+    tc_fence_after();
+    if (!issuer) drain_c2(2);
     tc_fence_before();
     fence_async_smem();
     ok = !__syncthreads_or(!(mbar_wait(bar_w3a, ph_w3) && mbar_wait(bar_w3b, ph_w3)));
@@ -470,9 +502,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     if (!ok) break;
 
     // ---- conv3: two tiles of 16 positions (qx + 8 qy, qy in {2u, 2u + 1})
+    // (one completion barrier per tile, so the first tile drains while the second computes)
     if (t == kIssuer) {
       tc_fence_after();
-      for (int u = 0; u < 2; ++u)
+      for (int u = 0; u < 2; ++u) {
         for (int tap = 0; tap < 9; ++tap) {
           const int kx = tap % 3, ky = tap / 3;
           for (int kk = 0; kk < 4; ++kk) {
@@ -481,12 +514,13 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
             mma_bf16(tmem + kD3Col + 64 * u, ad, bd, idesc_bf16(128, 64), (tap | kk) != 0);
           }
         }
-      mma_commit(bar_c3);
+        mma_commit(u ? bar_c3b : bar_c3a);
+      }
     }
-    ok = wait_all(bar_c3, ph_c3);
-    if (!ok) break;
-    tc_fence_after();
-    for (int u = 0; u < 2 && !issuer; ++u) {
+    for (int u = 0; u < 2 && ok; ++u) {
+      ok = u ? wait_all(bar_c3b, ph_c3b) : wait_all(bar_c3a, ph_c3a);
+      if (!ok || issuer) continue;
+      tc_fence_after();
       const int m = 16 * u + g, qx = m & 7, qy = m >> 3, h = half;
       const int64_t inst = i0 + ri;
       float v[32];
