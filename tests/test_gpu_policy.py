@@ -218,3 +218,52 @@ def test_bounded_wait_failure_is_reported_and_recovered():
     lg, v, _ = pol.forward(words)
     pol.sync()
     check_outputs(params, obs, lg, v)
+
+
+def test_rollouts_chain_across_calls_and_games():
+    """A rollout of 5 then one of 7 steps (step0 continuing) equals one of
+    12 steps from the same start, bit for bit (actions, logits, values,
+    rewards, done flags, final observation and state), in an environment
+    that mixes two games with different K."""
+    o = octax()
+    g1 = W.template_game(W.TemplateParams(seed=5), score_limit=2, max_episode_steps=9)
+    g2 = W.replace(W.template_game(W.TemplateParams(seed=6), max_episode_steps=7), instr_per_frame=15)
+    n, L = 300, g1.n_actions + 1
+    goe = (np.arange(n) % 2).astype(np.uint16)
+    params = W.policy_params(31, L)
+    pol = o.Policy(params, max_envs=n)
+    outs = []
+    for split in ((12,), (5, 7)):
+        env = o.Env([g1, g2], n, seed=4, game_of_env=goe)
+        words = pack_words_dev(env.reset())
+        parts, step0 = [], 10
+        for T in split:
+            parts.append(pol.rollout(env, T, words, seed=9, step0=step0))
+            step0 += T
+        pol.sync()
+        cat = [torch.cat([p[k] for p in parts]) for k in range(5)]
+        outs.append((cat, words.clone(), env.state_hash().clone()))
+    (a, w, h), (b, w2, h2) = outs
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    assert torch.equal(w, w2) and torch.equal(h, h2)
+    assert int(a[4].sum()) > 0                   # episodes ended inside the rollouts
+
+
+def pack_words_dev(obs):
+    return (obs.to(torch.int64) << torch.arange(64, device=obs.device)).sum(dim=-1)
+
+
+def test_rollout_rejects_unsupported_environments():
+    o = octax()
+    params = W.policy_params(2, 5)
+    pol = o.Policy(params, max_envs=64)
+    env = o.Env([W.schip_template_game(W.TemplateParams(seed=3))], 16, seed=1)
+    with pytest.raises(o.OctaxError) as e:          # Super-CHIP frames are 64 x 128
+        pol.rollout(env, 1, torch.zeros((16, 4, 32), dtype=torch.int64, device="cuda"))
+    assert e.value.code == o.EINVAL
+    g = W.replace(W.template_game(W.TemplateParams(seed=1)), stack_frames=2)
+    env = o.Env([g], 16, seed=1)
+    with pytest.raises(o.OctaxError) as e:
+        pol.rollout(env, 1, torch.zeros((16, 4, 32), dtype=torch.int64, device="cuda"))
+    assert e.value.code == o.EINVAL
