@@ -369,15 +369,22 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     // while conv1 continues.
     // Blocks of block rows 2p .. 2p + 2 (position b = bx + 16 (by - 2p)); the
     // pad position 48 is read by discarded rows only. Warp w builds positions
-    // 6w .. 6w + 5; lane = frame * 8 + instance.
+    // 6w .. 6w + 5; lane = frame * 8 + instance; a 16-entry table turns 4
+    // pixel bits into 4 bf16 elements.
     auto build = [&](int pr, int buf) {
       if (issuer) return;
       uint8_t *blk = sm + kBlkOff + buf * kBlkBytes;
+      // a warp's 6 positions span at most two block rows: load their row words once
+      const int r0 = (6 * warp) >> 4, r1 = (6 * warp + 5) >> 4;
+      const int y0 = 2 * (2 * pr + r0), y1 = 2 * (2 * pr + r1);
+      const uint64_t a0 = fr[y0 * 32 + lane], a1 = fr[(y0 + 1) * 32 + lane];
+      const uint64_t b0 = fr[y1 * 32 + lane], b1 = fr[(y1 + 1) * 32 + lane];
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
-        const int b = 6 * warp + j, bx = b & 15, by = 2 * pr + (b >> 4);
-        const uint64_t w0 = fr[(2 * by) * 32 + lane], w1 = fr[(2 * by + 1) * 32 + lane];
-        const uint2 lo = nib[(uint32_t)(w0 >> (4 * bx)) & 15u], hi = nib[(uint32_t)(w1 >> (4 * bx)) & 15u];
+        const int b = 6 * warp + j, bx = b & 15;
+        const bool first = (b >> 4) == r0;
+        const uint2 lo = nib[(uint32_t)((first ? a0 : b0) >> (4 * bx)) & 15u];
+        const uint2 hi = nib[(uint32_t)((first ? a1 : b1) >> (4 * bx)) & 15u];
         *reinterpret_cast<uint4 *>(blk + b * 512 + lane * 16) = make_uint4(lo.x, lo.y, hi.x, hi.y);
       }
     };
