@@ -121,3 +121,42 @@ def test_default_config_is_the_largest_single_gpu_workload():
     a = bench.parse_args(["--gpus", "1", "--steps", "20", "--warmup", "5"])
     assert a.config == "divergence" and a.steps == 20 and a.warmup == 5
     assert bench.workload(a.config).n_envs == 262144
+
+
+def test_policy_flop_counts():
+    """§4.1 layer sizes: conv1 15x15x32 of 4x8x4, conv2 6x6x64 of 32x4x4,
+    conv3 4x4x64 of 64x3x3, heads 1024 -> 2 x 256 and 256 -> L / 256 -> 1."""
+    macs = 15 * 15 * 32 * 128 + 6 * 6 * 64 * 512 + 4 * 4 * 64 * 576 + 1024 * 512 + 256 * 6
+    assert bench.policy_flops(5) == 2 * macs == 6433792
+    # the tap-shift tiling executes more (dropped rows, zero halves of conv1's stacked weights)
+    assert bench.policy_computed_flops(5) > bench.policy_flops(5)
+
+
+def test_pack_words_matches_packbits():
+    torch = pytest.importorskip("torch")
+    import numpy as np
+
+    obs = (np.random.default_rng(0).random((3, 4, 32, 64)) < 0.3).astype(np.uint8)
+    want = np.packbits(obs, axis=-1, bitorder="little").view("<u8").reshape(3, 4, 32).view(np.int64)
+    got = bench.pack_words(torch.from_numpy(obs)).numpy()
+    assert np.array_equal(got, want)
+
+
+def test_serving_request_stream():
+    """Arrivals sorted from 0, games weighted by their rates (10/100/1000 per
+    s, cycling), envs in 1..4096 (log-uniform), steps in 1..8, rate scaling
+    shortens the gaps."""
+    import numpy as np
+
+    rq = bench.serving_requests(20000, 55)
+    assert rq["t"][0] == 0 and np.all(np.diff(rq["t"]) >= 0)
+    assert rq["envs"].min() >= 1 and rq["envs"].max() <= 4096
+    assert set(np.unique(rq["steps"])) == set(range(1, 9))
+    counts = np.bincount(rq["game"], minlength=16)
+    fast = [g for g in range(16) if g % 3 == 2]
+    slow = [g for g in range(16) if g % 3 == 0]
+    assert counts[fast].min() > 20 * counts[slow].max()
+    # log-uniform sizes: about as many below 64 as above
+    assert 0.35 < (rq["envs"] < 64).mean() < 0.65
+    fast_rq = bench.serving_requests(20000, 55, rate_scale=15.0)
+    assert fast_rq["t"][-1] == pytest.approx(rq["t"][-1] / 15.0, rel=1e-9)
