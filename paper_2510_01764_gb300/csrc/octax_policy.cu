@@ -24,12 +24,19 @@
 //    share one N = 64 accumulator fed by the three block rows they read.
 //  - conv2 (stride 2) reads conv1's output split by the parity of x and y:
 //    tap (kx, ky) reads sub-grid (kx & 1, ky & 1) at offset (kx >> 1,
-//    ky >> 1) of an 8-wide grid. The sub-grids are kept as a band of four
-//    grid rows that slides down by two with conv1's output rows; each M tile
-//    covers two output rows and reads three grid rows, so the next conv1
-//    pair writes the fourth while the tile computes.
-//  - conv3 (stride 1) reads conv2's output on an 8-wide grid: tap (kx, ky) is
-//    the shift kx + 8 ky.
+//    ky >> 1) of an 8-wide grid. The taps kx and kx + 2 read the same
+//    sub-grid one position apart, so they are stacked along N (N = 128) and
+//    the drain adds columns 64..127 of row g + 1 to columns 0..63 of row g.
+//    The sub-grids are kept as a band of four grid rows that slides down by
+//    two with conv1's output rows; each M tile covers two output rows and
+//    reads three grid rows, so the next conv1 pair writes the fourth while
+//    the tile computes.
+//  - conv3 (stride 1) reads conv2's output on an 8-wide grid. The three taps
+//    kx of a kernel row ky read the same rows shifted by kx positions, so
+//    they are stacked along N (N = 192: one MMA per ky and k-step reads its A
+//    tile once for all three) and the shift is applied when draining: the
+//    output at position g sums columns 0..63 of row g, 64..127 of row g + 1
+//    and 128..191 of row g + 2.
 //  Rows whose grid position lies outside the layer's output are computed
 //  and discarded (they read padding or neighbouring positions, always inside
 //  the buffers).
@@ -78,9 +85,9 @@ constexpr uint32_t kMaxPolls = 1u << 24;
 // ---- conv kernel shared memory (bytes) -------------------------------------
 constexpr uint32_t kW1Off = 0;                             // conv1 B: [j 3][dx 2][chunk 4][n 64][8]
 constexpr uint32_t kW1Bytes = 6 * 4 * 64 * 16;
-constexpr uint32_t kW2Off = kW1Off + kW1Bytes;             // conv2 B: [tap 16][chunk 4][n 64][8]
-constexpr uint32_t kW2Bytes = 16 * 4 * 64 * 16;
-constexpr uint32_t kW3Bytes = 9 * 8 * 64 * 16;             // conv3 B: [tap 9][chunk 8][n 64][8]
+constexpr uint32_t kW2Off = kW1Off + kW1Bytes;             // conv2 B: [ky 4][kx & 1][chunk 4][n 128][8]
+constexpr uint32_t kW2Bytes = 4 * 2 * 4 * 128 * 16;
+constexpr uint32_t kW3Bytes = 3 * 8 * 192 * 16;            // conv3 B: [ky 3][chunk 8][n = 64 kx + o][8]
 constexpr uint32_t kSubPos = 33;                           // band: 4 grid rows of 8 + 1 pad position
 constexpr uint32_t kSubBytes = kSubPos * 512;              // position: 4 chunks x 8 instances x 16 B
 constexpr uint32_t kAct1Bytes = 4 * kSubBytes;             // 4 parity sub-grids
@@ -94,15 +101,23 @@ constexpr uint32_t kBlkBytes = 49 * 512;
 constexpr uint32_t kAct2Off = kXOff;                       // 50 positions x (8 chunks x 8 x 16 B)
 constexpr uint32_t kAct2Bytes = 50 * 1024;
 constexpr uint32_t kXBytes = kAct2Bytes > 2 * kBlkBytes ? kAct2Bytes : 2 * kBlkBytes;
-constexpr uint32_t kConvSmem = kXOff + kXBytes;
+// conv2 / conv3 drain exchange: rows g + 1 and g + 2 of the warps that hold
+// the last positions of a TMEM lane quarter come from the next quarter's
+// warp: [supplier 2][channel half 2][lane 8 | 16][33 floats] (rows padded
+// against bank conflicts); conv2 tiles alternate between the two parts.
+constexpr uint32_t kXbRow = 33 * 4;
+constexpr uint32_t kXb1Off = kXOff + kXBytes;              // part kx = 1: lanes 0..7
+constexpr uint32_t kXb2Off = kXb1Off + 2 * 2 * 8 * kXbRow;  // part kx = 2: lanes 0..15
+constexpr uint32_t kConvSmem = kXb2Off + 2 * 2 * 16 * kXbRow;
 constexpr uint32_t kW3EarlyBytes = 8192;                   // W3 tap 0: loaded once the frames are dead
 static_assert(kAct1Off + kAct1Bytes <= kXOff && kW3Off + kW3Bytes <= kXOff, "band and W3 inside their region");
 static_assert(kFrOff + 8192 <= kAct1Off && kW3Off + kW3EarlyBytes <= kAct1Off, "frames / early W3 below the band");
 static_assert(kConvSmem <= 227 * 1024, "conv kernel shared memory");
 
 // TMEM columns (fp32) of the conv kernel's accumulators.
-// conv1: 2 buffers x 2 output rows x 32; conv2: 3 tiles x 64; conv3: 2 tiles x 64.
-constexpr uint32_t kD1Col = 0, kD2Col = 128, kD3Col = 320, kConvTmemCols = 512;
+// conv1: 2 buffers x 2 output rows x 32; conv2: 3 tiles x 128; conv3: 2 tiles x 192
+// (over conv1's and conv2's columns, all drained before conv3 is issued).
+constexpr uint32_t kD1Col = 0, kD2Col = 128, kD3Col = 0, kConvTmemCols = 512;
 
 // ---- heads kernel -----------------------------------------------------------
 constexpr int kHeadStages = 3;
@@ -164,6 +179,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
   return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
          (1ull << 46);
 }
+// The descriptor of the same layout `bytes` further on: shared addresses stay
+// below 2^18, so the 14-bit start field takes the offset without a carry, and
+// the MMA-issuing loops add compile-time offsets to a base built once.
+__device__ __forceinline__ uint64_t sdesc_at(uint64_t base, uint32_t bytes) { return base + (bytes >> 4); }
 // Instruction descriptor, kind::f16: fp32 accumulator, bf16 A and B, both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 __host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N) {
@@ -190,20 +209,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
         "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
         "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(addr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  // the wait names the loaded registers, so no use of them is scheduled before it
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+      : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+        "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
+        "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+        "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+      :
+      : "memory");
 #pragma unroll
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(addr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 // Two 16-column loads (one per address) behind a single wait, in one asm
 // statement so that no use of the registers can be scheduled before the wait.
@@ -221,6 +236,45 @@ __device__ __forceinline__ void tmem_ld16x2(uint32_t a0, uint32_t a1, float (&v)
       : "memory");
 #pragma unroll
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+// 32 columns at each of a0, a1 (and a2) of this thread's TMEM lane, behind one wait.
+__device__ __forceinline__ void tmem_ld32x2(uint32_t a0, uint32_t a1, float (&v)[32], float (&w)[32]) {
+  uint32_t r[32], q[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(a0));
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]), "=r"(q[8]),
+        "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15]), "=r"(q[16]),
+        "=r"(q[17]), "=r"(q[18]), "=r"(q[19]), "=r"(q[20]), "=r"(q[21]), "=r"(q[22]), "=r"(q[23]), "=r"(q[24]),
+        "=r"(q[25]), "=r"(q[26]), "=r"(q[27]), "=r"(q[28]), "=r"(q[29]), "=r"(q[30]), "=r"(q[31])
+      : "r"(a1));
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+      : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+        "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
+        "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+        "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+      :
+      : "memory");
+  asm volatile(""
+      : "+r"(q[0]), "+r"(q[1]), "+r"(q[2]), "+r"(q[3]), "+r"(q[4]), "+r"(q[5]), "+r"(q[6]), "+r"(q[7]),
+        "+r"(q[8]), "+r"(q[9]), "+r"(q[10]), "+r"(q[11]), "+r"(q[12]), "+r"(q[13]), "+r"(q[14]), "+r"(q[15]),
+        "+r"(q[16]), "+r"(q[17]), "+r"(q[18]), "+r"(q[19]), "+r"(q[20]), "+r"(q[21]), "+r"(q[22]), "+r"(q[23]),
+        "+r"(q[24]), "+r"(q[25]), "+r"(q[26]), "+r"(q[27]), "+r"(q[28]), "+r"(q[29]), "+r"(q[30]), "+r"(q[31])
+      :
+      : "memory");  // after the wait (volatile statements keep their order)
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    v[j] = __uint_as_float(r[j]);
+    w[j] = __uint_as_float(q[j]);
+  }
 }
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // .x = a (low half)
@@ -317,6 +371,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
   const int half = warp >> 2;
   const bool issuer = warp == kConvWork / 32;  // the MMA-issuing warp takes no part in building / draining
   const int r = 32 * (warp & 3) + lane;  // M-tile row of this thread (TMEM lane)
+  // base descriptors of every MMA operand (the issuing loops add constant offsets)
+  const uint64_t a1d0 = sdesc(sbase + kBlkOff, 128, 512), a1d1 = sdesc(sbase + kBlkOff + kBlkBytes, 128, 512);
+  const uint64_t b1d = sdesc(sbase + kW1Off, 1024, 128);
+  const uint64_t a2d = sdesc(sbase + kAct1Off, 128, 512), b2d = sdesc(sbase + kW2Off, 2048, 128);
+  const uint64_t a3d = sdesc(sbase + kAct2Off, 128, 1024), b3d = sdesc(sbase + kW3Off, 3072, 128);
   const int g = r >> 3, ri = r & 7;      // grid position in the tile, instance in the batch
 
   // wait for the next phase of a barrier (block-uniform outcome; also a block barrier)
@@ -398,8 +457,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
       for (int j = 0; j < 3; ++j)
         for (int dx = 0; dx < 2; ++dx)
           for (int kk = 0; kk < 2; ++kk) {
-            const uint64_t ad = sdesc(sbase + kBlkOff + buf * kBlkBytes + (16 * j + dx) * 512 + kk * 256, 128, 512);
-            const uint64_t bd = sdesc(sbase + kW1Off + (2 * j + dx) * 4096 + kk * 2048, 1024, 128);
+            const uint64_t ad = sdesc_at(buf ? a1d1 : a1d0, (16 * j + dx) * 512 + kk * 256);
+            const uint64_t bd = sdesc_at(b1d, (2 * j + dx) * 4096 + kk * 2048);
             mma_bf16(tmem + kD1Col + 64 * buf, ad, bd, idesc_bf16(128, 64), (j | dx | kk) != 0);
           }
       if (!(a.stall && first)) mma_commit(buf ? bar_c1_1 : bar_c1_0);
@@ -458,16 +517,15 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
         __syncthreads();
         if (t == kIssuer) {
           tc_fence_after();
-          for (int tap = 0; tap < 16; ++tap) {
-            const int kx = tap & 3, ky = tap >> 2;
-            const uint32_t sg = (kx & 1) + 2 * (ky & 1);
-            const uint32_t shift = (kx >> 1) + 8 * (ky >> 1);
-            for (int kk = 0; kk < 2; ++kk) {
-              const uint64_t ad = sdesc(sbase + kAct1Off + sg * kSubBytes + shift * 512 + kk * 256, 128, 512);
-              const uint64_t bd = sdesc(sbase + kW2Off + tap * 4096 + kk * 2048, 1024, 128);
-              mma_bf16(tmem + kD2Col + 64 * tt, ad, bd, idesc_bf16(128, 64), (tap | kk) != 0);
+          for (int ky = 0; ky < 4; ++ky)
+            for (int px = 0; px < 2; ++px) {  // taps (px, ky) and (px + 2, ky)
+              const uint32_t sg = px + 2 * (ky & 1), shift = 8 * (ky >> 1);
+              for (int kk = 0; kk < 2; ++kk) {
+                const uint64_t ad = sdesc_at(a2d, sg * kSubBytes + shift * 512 + kk * 256);
+                const uint64_t bd = sdesc_at(b2d, (ky * 2 + px) * 8192 + kk * 4096);
+                mma_bf16(tmem + kD2Col + 128 * tt, ad, bd, idesc_bf16(128, 128), (ky | px | kk) != 0);
+              }
             }
-          }
           mma_commit(bar_c2);
         }
       }
@@ -475,10 +533,28 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     // ---- conv2 epilogues into region X: tiles 0 and 1 (done) while tile 2
     // computes; the issuing thread loads the rest of W3 over the band as soon
     // as tile 2 is done
+    // Output g (valid for px = g & 7 < 6) adds row g + 1's second half: by a
+    // shuffle, or for g = 3, 11 from the next lane quarter (rows 4, 12)
+    // through the exchange buffer.
     auto drain_c2 = [&](int tt) {
-      const int px = g & 7, py = 2 * tt + (g >> 3), h = half;
-      float v[32];
-      tmem_ld32(tmem + lane_base + kD2Col + 64 * tt + 32 * h, v);
+      const int px = g & 7, py = 2 * tt + (g >> 3), h = half, qt = warp & 3;
+      float *xb = reinterpret_cast<float *>(sm + ((tt & 1) ? kXb2Off : kXb1Off)) + ((qt >> 1) * 2 + h) * 8 * 33;
+      float v[32], w[32];
+      const uint32_t d = tmem + lane_base + kD2Col + 128 * tt + 32 * h;
+      tmem_ld32x2(d, d + 64, v, w);
+      if ((qt & 1) && lane < 8) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) xb[lane * 33 + c] = w[c];
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) w[c] = __shfl_down_sync(0xFFFFFFFFu, w[c], 8);
+      asm volatile("bar.sync 1, %0;" ::"r"(kConvWork) : "memory");
+      if (!(qt & 1) && lane >= 24) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) w[c] = xb[(lane - 24) * 33 + c];
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) v[c] += w[c];
       if (px < 6) {
         uint8_t *dst = sm + kAct2Off + (px + 8 * py) * 1024 + ri * 16;
 #pragma unroll
@@ -508,30 +584,67 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     ph_w3 ^= 1u;
     if (!ok) break;
 
-    // ---- conv3: two tiles of 16 positions (qx + 8 qy, qy in {2u, 2u + 1})
-    // (one completion barrier per tile, so the first tile drains while the second computes)
+    // ---- conv3: two tiles of 16 positions (qx + 8 qy, qy in {2u, 2u + 1}),
+    // 3 kernel rows x 4 k-steps of N = 192 each (one completion barrier per
+    // tile, so the first tile drains while the second computes)
     if (t == kIssuer) {
       tc_fence_after();
       for (int u = 0; u < 2; ++u) {
-        for (int tap = 0; tap < 9; ++tap) {
-          const int kx = tap % 3, ky = tap / 3;
+        for (int ky = 0; ky < 3; ++ky)
           for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t ad = sdesc(sbase + kAct2Off + (16 * u + kx + 8 * ky) * 1024 + kk * 256, 128, 1024);
-            const uint64_t bd = sdesc(sbase + kW3Off + tap * 8192 + kk * 2048, 1024, 128);
-            mma_bf16(tmem + kD3Col + 64 * u, ad, bd, idesc_bf16(128, 64), (tap | kk) != 0);
+            const uint64_t ad = sdesc_at(a3d, (16 * u + 8 * ky) * 1024 + kk * 256);
+            const uint64_t bd = sdesc_at(b3d, ky * 24576 + kk * 6144);
+            mma_bf16(tmem + kD3Col + 192 * u, ad, bd, idesc_bf16(128, 192), (ky | kk) != 0);
           }
-        }
         mma_commit(u ? bar_c3b : bar_c3a);
       }
     }
+    // Drain: the outputs (qx < 4) lie in lane quarters 0 and 2 (positions
+    // g = 0..3, 8..11); rows g + 1 and g + 2 come from the same warp by
+    // shuffles, or, past the quarter's end, from quarters 1 and 3 (positions
+    // 4, 5 and 12, 13, no outputs of their own) through the exchange buffer.
     for (int u = 0; u < 2 && ok; ++u) {
       ok = u ? wait_all(bar_c3b, ph_c3b) : wait_all(bar_c3a, ph_c3a);
       if (!ok || issuer) continue;
       tc_fence_after();
-      const int m = 16 * u + g, qx = m & 7, qy = m >> 3, h = half;
+      const int qt = warp & 3, h = half, sup = qt >> 1;
+      const uint32_t d = tmem + lane_base + kD3Col + 192 * u + 32 * h;
+      float *xb1 = reinterpret_cast<float *>(sm + kXb1Off) + (sup * 2 + h) * 8 * 33;
+      float *xb2 = reinterpret_cast<float *>(sm + kXb2Off) + (sup * 2 + h) * 16 * 33;
+      float v[32], w[32], x[32];
+      if (qt & 1) {  // supplier: rows 4 qt + 0, 1 for the previous quarter
+        tmem_ld32x2(d + 64, d + 128, v, w);
+        if (lane < 8) {
+#pragma unroll
+          for (int c = 0; c < 32; ++c) xb1[lane * 33 + c] = v[c];
+        }
+        if (lane < 16) {
+#pragma unroll
+          for (int c = 0; c < 32; ++c) xb2[lane * 33 + c] = w[c];
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(kConvWork) : "memory");
+        continue;
+      }
+      tmem_ld32x2(d + 64, d + 128, w, x);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        w[c] = __shfl_down_sync(0xFFFFFFFFu, w[c], 8);
+        x[c] = __shfl_down_sync(0xFFFFFFFFu, x[c], 16);
+      }
+      tmem_ld32(d, v);
+      asm volatile("bar.sync 1, %0;" ::"r"(kConvWork) : "memory");
+      if (lane >= 24) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) w[c] = xb1[(lane - 24) * 33 + c];
+      }
+      if (lane >= 16) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) x[c] = xb2[(lane - 16) * 33 + c];
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) v[c] += w[c] + x[c];
+      const int m = 16 * u + g, qx = m & 7, qy = m >> 3;
       const int64_t inst = i0 + ri;
-      float v[32];
-      tmem_ld32(tmem + lane_base + kD3Col + 64 * u + 32 * h, v);
       if (qx < 4 && inst < a.n) {
         const int q = qx + 4 * qy;  // feature slice: k = 64 q + channel
         uint8_t *dst = a.act3 + (inst >> 7) * (int64_t)kAct3TileBytes + q * 16384 + (inst & 127) * 16;
@@ -780,22 +893,28 @@ int octax_policy_create(const octax_policy_params *prm, int64_t max_envs, int de
             w1p[(((j * 2 + dx) * 4 + c) * 64 + n) * 8 + k] = bf16_bits(prm->w1[((o * 4 + c) * 8 + kx) * 4 + ky]);
           }
         }
-  // conv2 B: [tap (kx + 4 ky)][chunk j][n 64][e] = w2[n][8 j + e][kx][ky]
-  std::vector<uint16_t> w2p(16 * 4 * 64 * 8);
-  for (int tap = 0; tap < 16; ++tap)
-    for (int j = 0; j < 4; ++j)
-      for (int n = 0; n < 64; ++n)
-        for (int e = 0; e < 8; ++e)
-          w2p[((tap * 4 + j) * 64 + n) * 8 + e] =
-              bf16_bits(prm->w2[((n * 32 + 8 * j + e) * 4 + (tap & 3)) * 4 + (tap >> 2)]);
-  // conv3 B: [tap (kx + 3 ky)][chunk j][n 64][e] = w3[n][8 j + e][kx][ky]
-  std::vector<uint16_t> w3p(9 * 8 * 64 * 8);
-  for (int tap = 0; tap < 9; ++tap)
+  // conv2 B: [ky][px = kx & 1][chunk j][n = 64 (kx >> 1) + o][e] = w2[o][8 j + e][kx][ky]
+  // (taps kx and kx + 2 stacked along N)
+  std::vector<uint16_t> w2p(4 * 2 * 4 * 128 * 8);
+  for (int ky = 0; ky < 4; ++ky)
+    for (int px = 0; px < 2; ++px)
+      for (int j = 0; j < 4; ++j)
+        for (int n = 0; n < 128; ++n)
+          for (int e = 0; e < 8; ++e) {
+            const int kx = px + 2 * (n >> 6), o = n & 63;
+            w2p[((((ky * 2 + px) * 4 + j) * 128 + n) * 8) + e] =
+                bf16_bits(prm->w2[((o * 32 + 8 * j + e) * 4 + kx) * 4 + ky]);
+          }
+  // conv3 B: [ky][chunk j][n = 64 kx + o][e] = w3[o][8 j + e][kx][ky] (the three taps of a
+  // kernel row stacked along N)
+  std::vector<uint16_t> w3p(3 * 8 * 192 * 8);
+  for (int ky = 0; ky < 3; ++ky)
     for (int j = 0; j < 8; ++j)
-      for (int n = 0; n < 64; ++n)
-        for (int e = 0; e < 8; ++e)
-          w3p[((tap * 8 + j) * 64 + n) * 8 + e] =
-              bf16_bits(prm->w3[((n * 64 + 8 * j + e) * 3 + tap % 3) * 3 + tap / 3]);
+      for (int n = 0; n < 192; ++n)
+        for (int e = 0; e < 8; ++e) {
+          const int kx = n >> 6, o = n & 63;
+          w3p[((ky * 8 + j) * 192 + n) * 8 + e] = bf16_bits(prm->w3[((o * 64 + 8 * j + e) * 3 + kx) * 3 + ky]);
+        }
   // heads B: [head][slice q (16)][chunk j][n 256][e]; feature k = 64 q + channel (q = qx + 4 qy),
   // the caller's flatten index is channel * 16 + qx * 4 + qy
   std::vector<uint16_t> whp(2 * 16 * 8 * 256 * 8);
