@@ -103,16 +103,18 @@ constexpr uint32_t kAct2Bytes = 50 * 1024;
 constexpr uint32_t kXBytes = kAct2Bytes > 2 * kBlkBytes ? kAct2Bytes : 2 * kBlkBytes;
 // conv2 / conv3 drain exchange: rows g + 1 and g + 2 of the warps that hold
 // the last positions of a TMEM lane quarter come from the next quarter's
-// warp: [supplier 2][channel half 2][lane 8 | 16][33 floats] (rows padded
-// against bank conflicts); conv2 tiles alternate between the two parts.
-constexpr uint32_t kXbRow = 33 * 4;
+// warp: [supplier 2][channel half 2][lane 8 | 16][36 floats] (rows padded to
+// 144 B: 16-byte aligned, and 8 lanes' rows start in distinct bank groups);
+// conv2 tiles alternate between the two parts.
+constexpr int kXbPitch = 36;
+constexpr uint32_t kXbRow = kXbPitch * 4;
 constexpr uint32_t kXb1Off = kXOff + kXBytes;              // part kx = 1: lanes 0..7
 constexpr uint32_t kXb2Off = kXb1Off + 2 * 2 * 8 * kXbRow;  // part kx = 2: lanes 0..15
 constexpr uint32_t kConvSmem = kXb2Off + 2 * 2 * 16 * kXbRow;
 constexpr uint32_t kW3EarlyBytes = 8192;                   // W3 tap 0: loaded once the frames are dead
 static_assert(kAct1Off + kAct1Bytes <= kXOff && kW3Off + kW3Bytes <= kXOff, "band and W3 inside their region");
 static_assert(kFrOff + 8192 <= kAct1Off && kW3Off + kW3EarlyBytes <= kAct1Off, "frames / early W3 below the band");
-static_assert(kConvSmem <= 227 * 1024, "conv kernel shared memory");
+static_assert(kConvSmem + 1024 <= 227 * 1024, "conv kernel shared memory (with 1 KB of static shared data)");
 
 // TMEM columns (fp32) of the conv kernel's accumulators.
 // conv1: 2 buffers x 2 output rows x 32; conv2: 3 tiles x 128; conv3: 2 tiles x 192
@@ -274,6 +276,22 @@ __device__ __forceinline__ void tmem_ld32x2(uint32_t a0, uint32_t a1, float (&v)
   for (int j = 0; j < 32; ++j) {
     v[j] = __uint_as_float(r[j]);
     w[j] = __uint_as_float(q[j]);
+  }
+}
+// 32 floats to / from one 16-byte aligned exchange row, as 8 vector accesses.
+__device__ __forceinline__ void xrow_put(float *row, const float (&v)[32]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    reinterpret_cast<float4 *>(row)[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+}
+__device__ __forceinline__ void xrow_get(const float *row, float (&v)[32]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float4 f = reinterpret_cast<const float4 *>(row)[c];
+    v[4 * c] = f.x;
+    v[4 * c + 1] = f.y;
+    v[4 * c + 2] = f.z;
+    v[4 * c + 3] = f.w;
   }
 }
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -538,21 +556,15 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     // through the exchange buffer.
     auto drain_c2 = [&](int tt) {
       const int px = g & 7, py = 2 * tt + (g >> 3), h = half, qt = warp & 3;
-      float *xb = reinterpret_cast<float *>(sm + ((tt & 1) ? kXb2Off : kXb1Off)) + ((qt >> 1) * 2 + h) * 8 * 33;
+      float *xb = reinterpret_cast<float *>(sm + ((tt & 1) ? kXb2Off : kXb1Off)) + ((qt >> 1) * 2 + h) * 8 * kXbPitch;
       float v[32], w[32];
       const uint32_t d = tmem + lane_base + kD2Col + 128 * tt + 32 * h;
       tmem_ld32x2(d, d + 64, v, w);
-      if ((qt & 1) && lane < 8) {
-#pragma unroll
-        for (int c = 0; c < 32; ++c) xb[lane * 33 + c] = w[c];
-      }
+      if ((qt & 1) && lane < 8) xrow_put(xb + lane * kXbPitch, w);
 #pragma unroll
       for (int c = 0; c < 32; ++c) w[c] = __shfl_down_sync(0xFFFFFFFFu, w[c], 8);
       asm volatile("bar.sync 1, %0;" ::"r"(kConvWork) : "memory");
-      if (!(qt & 1) && lane >= 24) {
-#pragma unroll
-        for (int c = 0; c < 32; ++c) w[c] = xb[(lane - 24) * 33 + c];
-      }
+      if (!(qt & 1) && lane >= 24) xrow_get(xb + (lane - 24) * kXbPitch, w);
 #pragma unroll
       for (int c = 0; c < 32; ++c) v[c] += w[c];
       if (px < 6) {
@@ -609,19 +621,13 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
       tc_fence_after();
       const int qt = warp & 3, h = half, sup = qt >> 1;
       const uint32_t d = tmem + lane_base + kD3Col + 192 * u + 32 * h;
-      float *xb1 = reinterpret_cast<float *>(sm + kXb1Off) + (sup * 2 + h) * 8 * 33;
-      float *xb2 = reinterpret_cast<float *>(sm + kXb2Off) + (sup * 2 + h) * 16 * 33;
+      float *xb1 = reinterpret_cast<float *>(sm + kXb1Off) + (sup * 2 + h) * 8 * kXbPitch;
+      float *xb2 = reinterpret_cast<float *>(sm + kXb2Off) + (sup * 2 + h) * 16 * kXbPitch;
       float v[32], w[32], x[32];
       if (qt & 1) {  // supplier: rows 4 qt + 0, 1 for the previous quarter
         tmem_ld32x2(d + 64, d + 128, v, w);
-        if (lane < 8) {
-#pragma unroll
-          for (int c = 0; c < 32; ++c) xb1[lane * 33 + c] = v[c];
-        }
-        if (lane < 16) {
-#pragma unroll
-          for (int c = 0; c < 32; ++c) xb2[lane * 33 + c] = w[c];
-        }
+        if (lane < 8) xrow_put(xb1 + lane * kXbPitch, v);
+        if (lane < 16) xrow_put(xb2 + lane * kXbPitch, w);
         asm volatile("bar.sync 1, %0;" ::"r"(kConvWork) : "memory");
         continue;
       }
@@ -633,14 +639,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
       }
       tmem_ld32(d, v);
       asm volatile("bar.sync 1, %0;" ::"r"(kConvWork) : "memory");
-      if (lane >= 24) {
-#pragma unroll
-        for (int c = 0; c < 32; ++c) w[c] = xb1[(lane - 24) * 33 + c];
-      }
-      if (lane >= 16) {
-#pragma unroll
-        for (int c = 0; c < 32; ++c) x[c] = xb2[(lane - 16) * 33 + c];
-      }
+      if (lane >= 24) xrow_get(xb1 + (lane - 24) * kXbPitch, w);
+      if (lane >= 16) xrow_get(xb2 + (lane - 16) * kXbPitch, x);
 #pragma unroll
       for (int c = 0; c < 32; ++c) v[c] += w[c] + x[c];
       const int m = 16 * u + g, qx = m & 7, qy = m >> 3;
