@@ -346,7 +346,9 @@ struct TileSpec {
 template <bool kU8>
 __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const ConvArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  __shared__ __align__(8) uint64_t bars[8];  // conv1 x2, conv2, conv3 x2 MMA completion; W1 + W2; W3 x2
+  // MMA completion: conv1 x2, conv2, conv3 x2; bulk copies: W1 + W2, W3 x2; the final
+  // drain on the error path
+  __shared__ __align__(8) uint64_t bars[9];
   __shared__ uint32_t tmem_s;
   __shared__ float sb[160];                  // b1 | b2 | b3
   __shared__ uint2 nib[16];                  // 4 pixel bits -> 4 bf16 0 / 1 (element k = bit k)
@@ -361,7 +363,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     nib[t] = make_uint2((t & 1) * 0x3F80u | ((t >> 1) & 1) * 0x3F800000u,
                         ((t >> 2) & 1) * 0x3F80u | ((t >> 3) & 1) * 0x3F800000u);
   if (t == 0) {
-    for (int j = 0; j < 8; ++j) mbar_init(smem_u32(&bars[j]), 1);
+    for (int j = 0; j < 9; ++j) mbar_init(smem_u32(&bars[j]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -381,7 +383,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
   // every wait's outcome is made uniform over the block, so all threads
   // leave the loops together
   bool ok = !__syncthreads_or(!mbar_wait(bar_w, 0));
-  uint32_t ph_c1_0 = 0, ph_c1_1 = 0, ph_c2 = 0, ph_c3a = 0, ph_c3b = 0, ph_w3 = 0;  // ph_w3: both W3 barriers
+  uint32_t ph_c1_0 = 0, ph_c1_1 = 0, ph_c2 = 0, ph_c3a = 0, ph_c3b = 0, ph_w3 = 0;
+  uint32_t w3_pend = 0;  // issuing thread: W3 copies issued and not yet waited for (bit 0 early, bit 1 rest)  // ph_w3: both W3 barriers
   const int64_t n_batches = (a.n + kP - 1) / kP;
   // warps w and w + 4 read the same TMEM lane quarter (rows 32 (w & 3) ..), each
   // one half of the accumulator's columns
@@ -495,6 +498,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
       if (pr == 6 && t == kIssuer) {  // the frames are dead: W3 taps 0-1 into their place
         mbar_expect_tx(bar_w3a, kW3EarlyBytes);
         bulk_g2s(sbase + kW3Off, a.w3, kW3EarlyBytes, bar_w3a);
+        w3_pend |= 1u;
       }
       if (pr == 4 || pr == 6) {  // the previous tile must finish before its rows are rewritten
         ok = wait_all(bar_c2, ph_c2);
@@ -580,6 +584,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
         mbar_expect_tx(bar_w3b, kW3Bytes - kW3EarlyBytes);
         for (uint32_t o = kW3EarlyBytes; o < kW3Bytes; o += 16384)
           bulk_g2s(sbase + kW3Off + o, a.w3 + o, 16384, bar_w3b);
+        w3_pend |= 2u;
       }
     } else {
       tc_fence_after();
@@ -594,6 +599,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     fence_async_smem();
     ok = !__syncthreads_or(!(mbar_wait(bar_w3a, ph_w3) && mbar_wait(bar_w3b, ph_w3)));
     ph_w3 ^= 1u;
+    w3_pend = 0;
     if (!ok) break;
 
     // ---- conv3: two tiles of 16 positions (qx + 8 qy, qy in {2u, 2u + 1}),
@@ -657,6 +663,13 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     __syncthreads();  // region X and the W3 region are rewritten by the next batch
   }
   if (!ok && t == 0) atomicOr(a.err, 1u);
+  if (!ok && t == kIssuer) {  // let this thread's MMAs and bulk copies land before TMEM and shared memory go
+    mma_commit(smem_u32(&bars[8]));
+    mbar_wait(smem_u32(&bars[8]), 0);
+    mbar_wait(bar_w, 0);
+    if (w3_pend & 1u) mbar_wait(bar_w3a, ph_w3);
+    if (w3_pend & 2u) mbar_wait(bar_w3b, ph_w3);
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -679,7 +692,7 @@ struct HeadsArgs {
 // blockIdx.x: 128-instance tile; blockIdx.y: 0 actor, 1 critic.
 __global__ void __launch_bounds__(kThreads, 1) policy_heads_kernel(const HeadsArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  __shared__ __align__(8) uint64_t full[kHeadStages], empty[kHeadStages];
+  __shared__ __align__(8) uint64_t full[kHeadStages], empty[kHeadStages], fin;
   __shared__ uint32_t tmem_s;
   const int t = threadIdx.x, warp = t >> 5;
   const int head = blockIdx.y;
@@ -700,6 +713,7 @@ __global__ void __launch_bounds__(kThreads, 1) policy_heads_kernel(const HeadsAr
       mbar_init(smem_u32(&full[s]), 1);
       mbar_init(smem_u32(&empty[s]), 1);
     }
+    mbar_init(smem_u32(&fin), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -715,7 +729,9 @@ __global__ void __launch_bounds__(kThreads, 1) policy_heads_kernel(const HeadsAr
   constexpr int kSlices = 32;  // K = 1024 in slices of 32 (4 chunks)
   bool ok = true;
   if (t == 0) {
+    int loaded = 0, landed = 0;  // slices whose copies were issued / waited for
     auto load = [&](int s) {
+      loaded = s + 1;
       const int st = s % kHeadStages;
       const uint32_t f = smem_u32(&full[st]);
       mbar_expect_tx(f, kHA + kHB);
@@ -727,6 +743,7 @@ __global__ void __launch_bounds__(kThreads, 1) policy_heads_kernel(const HeadsAr
       const int st = s % kHeadStages;
       ok = mbar_wait(smem_u32(&full[st]), (s / kHeadStages) & 1);
       if (!ok) break;
+      landed = s + 1;
       tc_fence_after();
       const uint32_t a0 = sbase + st * (kHA + kHB), b0 = a0 + kHA;
       for (int kk = 0; kk < 2; ++kk)
@@ -742,6 +759,11 @@ __global__ void __launch_bounds__(kThreads, 1) policy_heads_kernel(const HeadsAr
     }
     // the last slice's MMAs complete -> every earlier one has too
     if (ok) ok = mbar_wait(smem_u32(&empty[(kSlices - 1) % kHeadStages]), ((kSlices - 1) / kHeadStages) & 1);
+    if (!ok) {  // let this thread's MMAs and copies land before TMEM and shared memory go
+      mma_commit(smem_u32(&fin));
+      mbar_wait(smem_u32(&fin), 0);
+      for (int s = landed; s < loaded; ++s) mbar_wait(smem_u32(&full[s % kHeadStages]), (s / kHeadStages) & 1);
+    }
   }
   ok = !__syncthreads_or(!ok);
   tc_fence_after();
