@@ -66,11 +66,13 @@ def env_frames(n, steps, seed):
     return o[-1]
 
 
-def philox_u(seed, step, n):
+def philox_u(seed, step, n, idx=None):
     """The kernel's uniform numbers from the oracle's own Philox4x32-10:
-    key = seed (low word first), counter = (instance, step, 0, 0), word 0."""
+    key = seed (low word first), counter = (instance, step, 0, 0), word 0
+    (for instances 0..n-1, or those in idx)."""
     k = (seed & 0xFFFFFFFF, seed >> 32)
-    words = np.array([oracle.philox4x32_10((i, step, 0, 0), k)[0] for i in range(n)], dtype=np.uint64)
+    inst = range(n) if idx is None else (int(i) for i in idx)
+    words = np.array([oracle.philox4x32_10((i, step, 0, 0), k)[0] for i in inst], dtype=np.uint64)
     return P.uniform_from_word(words)
 
 
@@ -173,6 +175,45 @@ def test_rollout_teacher_forced():
     assert np.array_equal(words.cpu().numpy(), pack(cur))
     assert np.array_equal(env.state_hash().cpu().numpy().view(np.uint64), ref.hashes())
     assert int(d.sum()) > 0 and len(np.unique(a_h)) >= 3
+
+
+def test_rollout_full_size_sampled():
+    """The rollout the bench times: 16,384 instances of its template workload
+    (seed 2), its network (weights seed 1, 5 logits) and seeds, default
+    launch. Every instance's rewards, done flags, final observation and state
+    hash match the oracle environment replaying the drawn actions; at every
+    step sampled instances' logits, value and draw match the oracle network."""
+    o = octax()
+    w = W.cfg_scale(n_envs=16384)
+    g = w.games[0]
+    n, T, L = w.n_envs, 4, g.n_actions + 1
+    params = W.policy_params(1, L)
+    env = o.Env(w.games, n, seed=w.seed)
+    ref = oracle.OracleEnv(w.games, n, seed=w.seed)
+    o0 = ref.reset()
+    assert np.array_equal(env.reset().cpu().numpy(), o0)
+    pol = o.Policy(params, max_envs=n)
+    words = torch.from_numpy(pack(o0)).cuda()
+    a, lg, v, r, d = pol.rollout(env, T, words, seed=1, step0=0)
+    pol.sync()
+    env.sync()
+    a_h = a.cpu().numpy()
+    idx = np.unique(np.concatenate([np.random.default_rng(2).choice(n, 40, replace=False),
+                                    [0, 7, 8, 127, 128, n - 129, n - 1]]))
+    cur = o0
+    for k in range(T):
+        check_outputs(params, cur[idx], lg[k][idx], v[k][idx])
+        u = philox_u(1, k, n, idx)
+        lgk = lg[k].cpu().numpy()[idx].astype(np.float64)
+        ok = P.cdf_margin(lgk, u) > MARGIN
+        assert np.array_equal(a_h[k][idx][ok], P.sample(lgk, u)[ok])
+        ob, rw, dn = ref.step(a_h[k])
+        assert np.array_equal(r[k].cpu().numpy(), rw), k
+        assert np.array_equal(d[k].cpu().numpy(), dn), k
+        cur = ob
+    assert np.array_equal(words.cpu().numpy(), pack(cur))
+    assert np.array_equal(env.state_hash().cpu().numpy().view(np.uint64), ref.hashes())
+    assert len(np.unique(a_h)) >= 3
 
 
 def test_policy_rejects_bad_arguments():
