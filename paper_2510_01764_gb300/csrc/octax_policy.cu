@@ -773,27 +773,37 @@ __global__ void __launch_bounds__(kThreads, 1) policy_heads_kernel(const HeadsAr
 #pragma unroll
     for (int j = 0; j < kMaxLogits; ++j) acc[j] = 0.0f;
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-    for (int c0 = 0; c0 < 256; c0 += 32) {
-      float v[32];
-      tmem_ld32(tmem + lane_base + c0, v);
+    // one output's dot product over 32 hidden units: the weights as 8 vector
+    // loads, four independent partial sums
+    auto dot32 = [&](const float(&h)[32], const float *w) -> float {
+      const float4 *w4 = reinterpret_cast<const float4 *>(w);
+      float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + bias[c0 + j], 0.0f);
+      for (int q = 0; q < 8; ++q) {
+        const float4 ww = w4[q];
+        s0 = fmaf(h[4 * q], ww.x, s0);
+        s1 = fmaf(h[4 * q + 1], ww.y, s1);
+        s2 = fmaf(h[4 * q + 2], ww.z, s2);
+        s3 = fmaf(h[4 * q + 3], ww.w, s3);
+      }
+      return (s0 + s1) + (s2 + s3);
+    };
+    auto chunk = [&](float(&h)[32], int c0) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) h[j] = fmaxf(h[j] + bias[c0 + j], 0.0f);
       if (head == 0) {
 #pragma unroll
-        for (int o = 0; o < kMaxLogits; ++o) {
-          if (o < a.L) {
-            float s = acc[o];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) s = fmaf(v[j], wout[o * 256 + c0 + j], s);
-            acc[o] = s;
-          }
-        }
+        for (int o = 0; o < kMaxLogits; ++o)
+          if (o < a.L) acc[o] += dot32(h, wout + o * 256 + c0);
       } else {
-        float s = acc[0];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) s = fmaf(v[j], wout[c0 + j], s);
-        acc[0] = s;
+        acc[0] += dot32(h, wout + c0);
       }
+    };
+    for (int c0 = 0; c0 < 256; c0 += 64) {  // two 32-column TMEM loads behind one wait
+      float v[32], w[32];
+      tmem_ld32x2(tmem + lane_base + c0, tmem + lane_base + c0 + 32, v, w);
+      chunk(v, c0);
+      chunk(w, c0 + 32);
     }
     if (inst < a.n) {
       if (head == 0) {
