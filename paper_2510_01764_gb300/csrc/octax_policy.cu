@@ -405,6 +405,20 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     phase ^= 1u;
     return !__syncthreads_or(!w_ok);
   };
+  // the same among the 8 worker warps only (named barrier 1), so that they
+  // need not wait for the issuing thread while it is issuing
+  auto wait_workers = [&](uint32_t bar, uint32_t &phase) -> bool {
+    const uint32_t w_ok = mbar_wait(bar, phase);
+    phase ^= 1u;
+    uint32_t any_fail;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.eq.u32 p, %1, 0;\n\tbarrier.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(any_fail)
+        : "r"(w_ok), "r"(kConvWork)
+        : "memory");
+    return !any_fail;
+  };
 
   for (int64_t batch = blockIdx.x; batch < n_batches && ok; batch += gridDim.x) {
     const int64_t i0 = batch * kP;
@@ -621,9 +635,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     // g = 0..3, 8..11); rows g + 1 and g + 2 come from the same warp by
     // shuffles, or, past the quarter's end, from quarters 1 and 3 (positions
     // 4, 5 and 12, 13, no outputs of their own) through the exchange buffer.
-    for (int u = 0; u < 2 && ok; ++u) {
-      ok = u ? wait_all(bar_c3b, ph_c3b) : wait_all(bar_c3a, ph_c3a);
-      if (!ok || issuer) continue;
+    // (the issuing warp goes on to the batch's closing barrier; the workers'
+    // outcome joins it there)
+    for (int u = 0; u < 2 && !issuer; ++u) {
+      ok = (u ? wait_workers(bar_c3b, ph_c3b) : wait_workers(bar_c3a, ph_c3a)) && ok;
+      if (!ok) continue;  // uniform among the workers
       tc_fence_after();
       const int qt = warp & 3, h = half, sup = qt >> 1;
       const uint32_t d = tmem + lane_base + kD3Col + 192 * u + 32 * h;
@@ -660,7 +676,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
       }
     }
     tc_fence_before();
-    __syncthreads();  // region X and the W3 region are rewritten by the next batch
+    ok = !__syncthreads_or(!ok);  // region X and the W3 region are rewritten by the next batch
   }
   if (!ok && t == 0) atomicOr(a.err, 1u);
   if (!ok && t == kIssuer) {  // let this thread's MMAs and bulk copies land before TMEM and shared memory go
