@@ -161,6 +161,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   }
   return false;
 }
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
@@ -347,8 +350,9 @@ template <bool kU8>
 __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const ConvArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   // MMA completion: conv1 x2, conv2, conv3 x2; bulk copies: W1 + W2, W3 x2; the final
-  // drain on the error path
-  __shared__ __align__(8) uint64_t bars[9];
+  // drain on the error path; conv1 blocks built x2 (per block buffer), band rows written
+  // (worker arrivals)
+  __shared__ __align__(8) uint64_t bars[12];
   __shared__ uint32_t tmem_s;
   __shared__ float sb[160];                  // b1 | b2 | b3
   __shared__ uint2 nib[16];                  // 4 pixel bits -> 4 bf16 0 / 1 (element k = bit k)
@@ -357,6 +361,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
   const uint32_t bar_c1_0 = smem_u32(&bars[0]), bar_c1_1 = smem_u32(&bars[1]);
   const uint32_t bar_c2 = smem_u32(&bars[2]), bar_c3a = smem_u32(&bars[3]), bar_c3b = smem_u32(&bars[7]);
   const uint32_t bar_w = smem_u32(&bars[4]), bar_w3a = smem_u32(&bars[5]), bar_w3b = smem_u32(&bars[6]);
+  const uint32_t bar_blk0 = smem_u32(&bars[9]), bar_blk1 = smem_u32(&bars[11]), bar_band = smem_u32(&bars[10]);
 
   for (int j = t; j < 160; j += kConvThreads) sb[j] = a.fp[j];
   if (t < 16)  // 1.0 in bf16 is 0x3F80
@@ -364,6 +369,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
                         ((t >> 2) & 1) * 0x3F80u | ((t >> 3) & 1) * 0x3F800000u);
   if (t == 0) {
     for (int j = 0; j < 9; ++j) mbar_init(smem_u32(&bars[j]), 1);
+    for (int j = 9; j < 12; ++j) mbar_init(smem_u32(&bars[j]), kConvWork);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -384,6 +390,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
   // leave the loops together
   bool ok = !__syncthreads_or(!mbar_wait(bar_w, 0));
   uint32_t ph_c1_0 = 0, ph_c1_1 = 0, ph_c2 = 0, ph_c3a = 0, ph_c3b = 0, ph_w3 = 0;
+  uint32_t ph_blk0 = 0, ph_blk1 = 0, ph_band = 0;  // issuing thread: conv1 blocks built, band rows written
   uint32_t w3_pend = 0;  // issuing thread: W3 copies issued and not yet waited for (bit 0 early, bit 1 rest)  // ph_w3: both W3 barriers
   const int64_t n_batches = (a.n + kP - 1) / kP;
   // warps w and w + 4 read the same TMEM lane quarter (rows 32 (w & 3) ..), each
@@ -498,74 +505,108 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
           }
       if (!(a.stall && first)) mma_commit(buf ? bar_c1_1 : bar_c1_0);
     };
-    build(0, 0);
-    fence_async_smem();
-    __syncthreads();
-    if (t == kIssuer) issue_c1(0, true);
-    for (int pr = 0; pr < 7 && ok; ++pr) {
-      const int cb = pr & 1, nb = cb ^ 1;
-      if (pr + 1 < 7) build(pr + 1, nb);  // buffer nb: its MMAs (pair pr - 1) completed
-      fence_async_smem();
-      ok = cb ? wait_all(bar_c1_1, ph_c1_1) : wait_all(bar_c1_0, ph_c1_0);
-      if (!ok) break;
-      if (pr + 1 < 7 && t == kIssuer) issue_c1(nb, false);
-      if (pr == 6 && t == kIssuer) {  // the frames are dead: W3 taps 0-1 into their place
-        mbar_expect_tx(bar_w3a, kW3EarlyBytes);
-        bulk_g2s(sbase + kW3Off, a.w3, kW3EarlyBytes, bar_w3a);
-        w3_pend |= 1u;
-      }
-      if (pr == 4 || pr == 6) {  // the previous tile must finish before its rows are rewritten
-        ok = wait_all(bar_c2, ph_c2);
-        if (!ok) break;
-        // slide: grid rows 2, 3 -> 0, 1 (4 sub-grids x 16 positions x 512 B)
-        for (int q = issuer ? 2048 : t; q < 4 * 16 * 32; q += kConvWork) {
-          const int sgq = q >> 9, rem = q & 511;
-          uint4 *base = reinterpret_cast<uint4 *>(sm + kAct1Off + sgq * kSubBytes);
-          base[rem] = base[16 * 32 + rem];
-        }
-        __syncthreads();
-      }
+    auto issue_c2 = [&](int tt) {  // the issuing thread: conv2 tile tt (output rows 2tt, 2tt + 1)
       tc_fence_after();
-      if (!issuer) {
-        float v[32];  // columns 16 half .. of row 2p (v[0..15]) and of row 2p + 1 (v[16..31])
-        const uint32_t d = tmem + lane_base + kD1Col + 64 * cb + 16 * half;
-        tmem_ld16x2(d, d + 32, v);
-        const int ox = g;
-#pragma unroll
-        for (int s2 = 0; s2 < 2; ++s2) {
-          const int oy = 2 * pr + s2;
-          if (ox <= 13) {  // conv2 reads x <= 13
-            const int band = pr < 4 ? 0 : (pr < 6 ? 1 : 2);  // band b holds grid rows 2b .. 2b + 3
-            const int slot = pr - 2 * band;                   // this pair's grid row is oy >> 1 = pr
-            const int sg = (ox & 1) + 2 * (oy & 1);
-            uint8_t *dst = sm + kAct1Off + sg * kSubBytes + ((ox >> 1) + 8 * slot) * 512 + ri * 16;
-#pragma unroll
-            for (int c = 0; c < 2; ++c)
-              *reinterpret_cast<uint4 *>(dst + (2 * half + c) * 128) =
-                  relu_chunk(v + 16 * s2 + 8 * c, sb + 16 * half + 8 * c);
+      for (int ky = 0; ky < 4; ++ky)
+        for (int px = 0; px < 2; ++px) {  // taps (px, ky) and (px + 2, ky)
+          const uint32_t sg = px + 2 * (ky & 1), shift = 8 * (ky >> 1);
+          for (int kk = 0; kk < 2; ++kk) {
+            const uint64_t ad = sdesc_at(a2d, sg * kSubBytes + shift * 512 + kk * 256);
+            const uint64_t bd = sdesc_at(b2d, (ky * 2 + px) * 8192 + kk * 4096);
+            mma_bf16(tmem + kD2Col + 128 * tt, ad, bd, idesc_bf16(128, 128), (ky | px | kk) != 0);
           }
         }
-      }
-      tc_fence_before();
-      if (pr == 2 || pr == 4 || pr == 6) {
-        const int tt = (pr - 2) >> 1;  // conv2 tile: output rows 2tt, 2tt + 1
-        fence_async_smem();
-        __syncthreads();
-        if (t == kIssuer) {
-          tc_fence_after();
-          for (int ky = 0; ky < 4; ++ky)
-            for (int px = 0; px < 2; ++px) {  // taps (px, ky) and (px + 2, ky)
-              const uint32_t sg = px + 2 * (ky & 1), shift = 8 * (ky >> 1);
-              for (int kk = 0; kk < 2; ++kk) {
-                const uint64_t ad = sdesc_at(a2d, sg * kSubBytes + shift * 512 + kk * 256);
-                const uint64_t bd = sdesc_at(b2d, (ky * 2 + px) * 8192 + kk * 4096);
-                mma_bf16(tmem + kD2Col + 128 * tt, ad, bd, idesc_bf16(128, 128), (ky | px | kk) != 0);
-              }
+      mma_commit(bar_c2);
+    };
+    // The workers and the issuing thread meet only through mbarriers here.
+    // The workers arrive on blk[p & 1] when pair p's blocks are built, which
+    // also says that pair p - 2 has been drained, so its TMEM buffer is free
+    // (one barrier per block buffer: the next arrival on it needs pair p's
+    // MMAs, issued only after the issuing thread's wait, so that thread never
+    // falls two phases behind a parity wait). They arrive on band when the
+    // band rows of pairs 2, 4 and 6 are written, and each worker waits for
+    // the MMAs itself. So the workers go on while the issuing thread sits in
+    // a full MMA queue. Every wait is bounded; one that runs out only clears
+    // r_ok, and each side still runs its whole schedule (no other side waits
+    // on it for long).
+    bool r_ok = true;
+    if (!issuer) {
+      build(0, 0);
+      fence_async_smem();
+      mbar_arrive(bar_blk0);
+      for (int pr = 0; pr < 7; ++pr) {
+        const int cb = pr & 1, nb = cb ^ 1;
+        if (pr + 1 < 7) {  // buffer nb: pair pr - 1's MMAs done (waited for last iteration)
+          build(pr + 1, nb);
+          fence_async_smem();
+          mbar_arrive(nb ? bar_blk1 : bar_blk0);
+        }
+        r_ok &= mbar_wait(cb ? bar_c1_1 : bar_c1_0, cb ? ph_c1_1 : ph_c1_0);
+        if (cb) ph_c1_1 ^= 1u; else ph_c1_0 ^= 1u;
+        if (pr == 4 || pr == 6) {  // the previous tile must finish before its rows are rewritten
+          r_ok &= mbar_wait(bar_c2, ph_c2);
+          ph_c2 ^= 1u;
+          asm volatile("bar.sync 1, %0;" ::"r"(kConvWork) : "memory");  // every worker's rows written
+          // slide: grid rows 2, 3 -> 0, 1 (4 sub-grids x 16 positions x 512 B)
+          for (int q = t; q < 4 * 16 * 32; q += kConvWork) {
+            const int sgq = q >> 9, rem = q & 511;
+            uint4 *base = reinterpret_cast<uint4 *>(sm + kAct1Off + sgq * kSubBytes);
+            base[rem] = base[16 * 32 + rem];
+          }
+          asm volatile("bar.sync 1, %0;" ::"r"(kConvWork) : "memory");
+        }
+        tc_fence_after();
+        {
+          float v[32];  // columns 16 half .. of row 2p (v[0..15]) and of row 2p + 1 (v[16..31])
+          const uint32_t d = tmem + lane_base + kD1Col + 64 * cb + 16 * half;
+          tmem_ld16x2(d, d + 32, v);
+          const int ox = g;
+#pragma unroll
+          for (int s2 = 0; s2 < 2; ++s2) {
+            const int oy = 2 * pr + s2;
+            if (ox <= 13) {  // conv2 reads x <= 13
+              const int band = pr < 4 ? 0 : (pr < 6 ? 1 : 2);  // band b holds grid rows 2b .. 2b + 3
+              const int slot = pr - 2 * band;                   // this pair's grid row is oy >> 1 = pr
+              const int sg = (ox & 1) + 2 * (oy & 1);
+              uint8_t *dst = sm + kAct1Off + sg * kSubBytes + ((ox >> 1) + 8 * slot) * 512 + ri * 16;
+#pragma unroll
+              for (int c = 0; c < 2; ++c)
+                *reinterpret_cast<uint4 *>(dst + (2 * half + c) * 128) =
+                    relu_chunk(v + 16 * s2 + 8 * c, sb + 16 * half + 8 * c);
             }
-          mma_commit(bar_c2);
+          }
+        }
+        tc_fence_before();
+        if (pr == 2 || pr == 4 || pr == 6) {
+          fence_async_smem();
+          mbar_arrive(bar_band);
         }
       }
+      // (the issuing warp skips the waits on conv2 tiles 0 and 1: two parity
+      // flips, so its ph_c2 agrees with the workers' again here)
+    } else if (t == kIssuer) {
+      for (int pr = 0; pr < 7; ++pr) {
+        const int b = pr & 1;
+        r_ok &= mbar_wait(b ? bar_blk1 : bar_blk0, b ? ph_blk1 : ph_blk0);
+        if (b) ph_blk1 ^= 1u; else ph_blk0 ^= 1u;
+        issue_c1(pr & 1, pr == 0);
+        if (pr == 6) {  // the frames are dead: W3 taps 0-1 into their place
+          mbar_expect_tx(bar_w3a, kW3EarlyBytes);
+          bulk_g2s(sbase + kW3Off, a.w3, kW3EarlyBytes, bar_w3a);
+          w3_pend |= 1u;
+        }
+        if (pr == 3 || pr == 5) {  // band rows of pairs 2 and 4 written
+          r_ok &= mbar_wait(bar_band, ph_band);
+          ph_band ^= 1u;
+          issue_c2((pr - 3) >> 1);
+        }
+      }
+      r_ok &= mbar_wait(bar_band, ph_band);  // band rows of pair 6
+      ph_band ^= 1u;
+      issue_c2(2);
     }
+    ok = !__syncthreads_or(!(ok && r_ok));
+    if (!ok) break;
     // ---- conv2 epilogues into region X: tiles 0 and 1 (done) while tile 2
     // computes; the issuing thread loads the rest of W3 over the band as soon
     // as tile 2 is done
