@@ -605,8 +605,9 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
       ph_band ^= 1u;
       issue_c2(2);
     }
-    ok = !__syncthreads_or(!(ok && r_ok));
-    if (!ok) break;
+    // (no block barrier here: the drains of conv2 tiles 0 and 1 below need
+    // only the workers' own waits, and the issuing thread may still be
+    // issuing tile 2; r_ok joins the block-wide wait on tile 2)
     // ---- conv2 epilogues into region X: tiles 0 and 1 (done) while tile 2
     // computes; the issuing thread loads the rest of W3 over the band as soon
     // as tile 2 is done
@@ -646,7 +647,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
       drain_c2(0);
       drain_c2(1);
     }
-    ok = wait_all(bar_c2, ph_c2);  // conv2 tile 2
+    {  // conv2 tile 2, and every thread's outcome so far
+      const bool w_ok = mbar_wait(bar_c2, ph_c2) && ok && r_ok;
+      ph_c2 ^= 1u;
+      ok = !__syncthreads_or(!w_ok);
+    }
     if (!ok) break;
     tc_fence_after();
     if (!issuer) drain_c2(2);
