@@ -393,6 +393,22 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
   uint32_t ph_blk0 = 0, ph_blk1 = 0, ph_band = 0;  // issuing thread: conv1 blocks built, band rows written
   uint32_t w3_pend = 0;  // issuing thread: W3 copies issued and not yet waited for (bit 0 early, bit 1 rest)  // ph_w3: both W3 barriers
   const int64_t n_batches = (a.n + kP - 1) / kP;
+  static_assert(kP * 64 == 2 * kConvWork, "two packed-frame pieces per worker");
+  // a worker's two pieces of a batch's packed frames (q = t, t + 256:
+  // instance q & 7, frame (q >> 7) & 3, rows 2 y2 and 2 y2 + 1, y2 = (q >> 3) & 15)
+  auto load_frames = [&](int64_t first, uint4 &v0, uint4 &v1) {
+    uint4 v[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int q = t + kConvWork * k, i = q & 7, c = (q >> 7) & 3, y2 = (q >> 3) & 15;
+      if (first + i < a.n)
+        v[k] = __ldg(reinterpret_cast<const uint4 *>(a.obs_words + (first + i) * 128 + c * 32 + 2 * y2));
+    }
+    v0 = v[0];
+    v1 = v[1];
+  };
+  uint4 pf[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+  bool pf_ok = false;
   // warps w and w + 4 read the same TMEM lane quarter (rows 32 (w & 3) ..), each
   // one half of the accumulator's columns
   const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
@@ -434,12 +450,16 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     // building one block position read 32 consecutive words
     uint64_t *fr = reinterpret_cast<uint64_t *>(sm + kFrOff);
     if (!kU8) {
-      for (int q = issuer ? kP * 64 : t; q < kP * 64; q += kConvWork) {  // instance i, frame c, rows 2 y2, 2 y2 + 1
-        const int i = q & 7, c = (q >> 7) & 3, y2 = (q >> 3) & 15;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (i0 + i < a.n) v = __ldg(reinterpret_cast<const uint4 *>(a.obs_words + (i0 + i) * 128 + c * 32 + 2 * y2));
-        fr[((2 * y2) * 4 + c) * 8 + i] = (uint64_t)v.x | (uint64_t)v.y << 32;
-        fr[((2 * y2 + 1) * 4 + c) * 8 + i] = (uint64_t)v.z | (uint64_t)v.w << 32;
+      // each worker's two 16-byte pieces (q = t, t + 256): loaded during the
+      // previous batch's last drain (pf_ok), else here
+      if (!issuer && !pf_ok) {
+        load_frames(i0, pf[0], pf[1]);
+      }
+      pf_ok = false;
+      for (int k = 0; k < 2 && !issuer; ++k) {  // instance i, frame c, rows 2 y2, 2 y2 + 1
+        const int q = t + kConvWork * k, i = q & 7, c = (q >> 7) & 3, y2 = (q >> 3) & 15;
+        fr[((2 * y2) * 4 + c) * 8 + i] = (uint64_t)pf[k].x | (uint64_t)pf[k].y << 32;
+        fr[((2 * y2 + 1) * 4 + c) * 8 + i] = (uint64_t)pf[k].z | (uint64_t)pf[k].w << 32;
       }
     } else {
       for (int q = issuer ? kP * 128 : t; q < kP * 128; q += kConvWork) {  // one 64-byte row each
@@ -686,6 +706,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     for (int u = 0; u < 2 && !issuer; ++u) {
       ok = (u ? wait_workers(bar_c3b, ph_c3b) : wait_workers(bar_c3a, ph_c3a)) && ok;
       if (!ok) continue;  // uniform among the workers
+      if (!kU8 && u == 1 && batch + gridDim.x < n_batches) {  // the next batch's frames, in flight during this drain
+        load_frames((batch + gridDim.x) * kP, pf[0], pf[1]);
+        pf_ok = true;
+      }
       tc_fence_after();
       const int qt = warp & 3, h = half, sup = qt >> 1;
       const uint32_t d = tmem + lane_base + kD3Col + 192 * u + 32 * h;
