@@ -41,7 +41,8 @@
 //  and discarded (they read padding or neighbouring positions, always inside
 //  the buffers).
 // Heads kernel: one CTA per (128-instance tile, head); K = 1024 streamed in
-// 32-wide slices through a 3-stage ring; the actor CTA also draws the action.
+// 32-wide slices through a 3-stage ring (one thread issues the copies,
+// another the MMAs); the actor CTA also draws the action.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -814,17 +815,25 @@ __global__ void __launch_bounds__(kThreads, 1) policy_heads_kernel(const HeadsAr
   const uint8_t *B = a.wh + (int64_t)head * (16 * 8 * 256 * 16);
   constexpr int kSlices = 32;  // K = 1024 in slices of 32 (4 chunks)
   bool ok = true;
+  // Thread 0 issues the copies, thread 32 the MMAs: each runs its own chain of
+  // waits and issues (a bulk copy or an MMA costs far more latency on the
+  // issuing thread than its bytes or its share of the tensor pipe).
+  __shared__ int s_landed;  // slices whose copies the MMA thread has waited for
+  int loaded = 0;           // thread 0: slices whose copies were issued
   if (t == 0) {
-    int loaded = 0, landed = 0;  // slices whose copies were issued / waited for
-    auto load = [&](int s) {
-      loaded = s + 1;
+    for (int s = 0; s < kSlices && ok; ++s) {
       const int st = s % kHeadStages;
+      // stage st last held slice s - kHeadStages: its MMAs must be done
+      if (s >= kHeadStages) ok = mbar_wait(smem_u32(&empty[st]), ((s / kHeadStages) - 1) & 1);
+      if (!ok) break;
       const uint32_t f = smem_u32(&full[st]);
       mbar_expect_tx(f, kHA + kHB);
       bulk_g2s(sbase + st * (kHA + kHB), A + (int64_t)s * kHA, kHA, f);
       bulk_g2s(sbase + st * (kHA + kHB) + kHA, B + (int64_t)s * kHB, kHB, f);
-    };
-    for (int s = 0; s < kHeadStages - 1; ++s) load(s);
+      loaded = s + 1;
+    }
+  } else if (t == 32) {
+    int landed = 0;
     for (int s = 0; s < kSlices && ok; ++s) {
       const int st = s % kHeadStages;
       ok = mbar_wait(smem_u32(&full[st]), (s / kHeadStages) & 1);
@@ -836,22 +845,18 @@ __global__ void __launch_bounds__(kThreads, 1) policy_heads_kernel(const HeadsAr
         mma_bf16(tmem, sdesc(a0 + kk * 2 * 2048, 2048, 128), sdesc(b0 + kk * 2 * 4096, 4096, 128),
                  idesc_bf16(128, 256), (s | kk) != 0);
       mma_commit(smem_u32(&empty[st]));
-      const int nx = s + kHeadStages - 1;  // refill the stage the previous slice used
-      if (nx < kSlices) {
-        const int pst = nx % kHeadStages;
-        if (s >= 1) ok = mbar_wait(smem_u32(&empty[pst]), ((s - 1) / kHeadStages) & 1);
-        if (ok) load(nx);
-      }
     }
     // the last slice's MMAs complete -> every earlier one has too
     if (ok) ok = mbar_wait(smem_u32(&empty[(kSlices - 1) % kHeadStages]), ((kSlices - 1) / kHeadStages) & 1);
-    if (!ok) {  // let this thread's MMAs and copies land before TMEM and shared memory go
+    if (!ok) {  // let this thread's MMAs land before TMEM goes
       mma_commit(smem_u32(&fin));
       mbar_wait(smem_u32(&fin), 0);
-      for (int s = landed; s < loaded; ++s) mbar_wait(smem_u32(&full[s % kHeadStages]), (s / kHeadStages) & 1);
     }
+    s_landed = landed;
   }
   ok = !__syncthreads_or(!ok);
+  if (!ok && t == 0)  // copies issued but never waited for land before shared memory goes
+    for (int q = s_landed; q < loaded; ++q) mbar_wait(smem_u32(&full[q % kHeadStages]), (q / kHeadStages) & 1);
   tc_fence_after();
   const int64_t inst = tile * 128 + t;
   if (ok) {
