@@ -75,7 +75,7 @@ int env_device(const octax_env *e);
 namespace {
 
 constexpr int kP = 8;            // instances per conv batch
-constexpr int kThreads = 128;      // heads kernel
+constexpr int kThreads = 256;      // heads kernel: two warps per TMEM lane quarter
 constexpr int kConvWork = 256;               // conv kernel: 8 warps build / drain (two per TMEM lane quarter)
 constexpr int kConvThreads = kConvWork + 32; // + one warp that issues the MMAs and bulk copies
 constexpr int kIssuer = kConvWork;           // its issuing thread
@@ -127,7 +127,8 @@ constexpr int kHeadStages = 3;
 constexpr uint32_t kHA = 128 * 32 * 2;      // A slice: 128 rows x 32 K (bf16) = 4 chunk planes
 constexpr uint32_t kHB = 256 * 32 * 2;      // B slice: 256 rows x 32 K
 constexpr uint32_t kHeadOutOff = kHeadStages * (kHA + kHB);
-constexpr uint32_t kHeadSmem = kHeadOutOff + (kMaxLogits + 1) * 256 * 4 + 2 * 256 * 4;
+constexpr uint32_t kHeadPartOff = kHeadOutOff + (kMaxLogits + 1) * 256 * 4 + 2 * 256 * 4;
+constexpr uint32_t kHeadSmem = kHeadPartOff + 128 * (kMaxLogits + 1) * 4;  // + partial outputs of warps 4-7
 constexpr uint32_t kAct3TileBytes = 128 * 1024 * 2;   // [slice 16][chunk 8][row 128][16 B]
 
 // fp32 parameter block: b1 32 | b2 64 | b3 64 | bh [2][256] | wa2 [17][256] | ba2 [17] | wc2 [256] | bc2
@@ -858,12 +859,17 @@ __global__ void __launch_bounds__(kThreads, 1) policy_heads_kernel(const HeadsAr
   if (!ok && t == 0)  // copies issued but never waited for land before shared memory goes
     for (int q = s_landed; q < loaded; ++q) mbar_wait(smem_u32(&full[q % kHeadStages]), (q / kHeadStages) & 1);
   tc_fence_after();
-  const int64_t inst = tile * 128 + t;
-  if (ok) {
-    float acc[kMaxLogits];
+  // warps w and w + 4 read TMEM lane quarter w & 3 (instance t & 127), each
+  // one half of the 256 hidden units; warps 4-7 hand their partial outputs
+  // over through shared memory
+  const int row = t & 127, hh = warp >> 2;
+  const int64_t inst = tile * 128 + row;
+  float *part = reinterpret_cast<float *>(sm + kHeadPartOff) + row * (kMaxLogits + 1);
+  float acc[kMaxLogits];
 #pragma unroll
-    for (int j = 0; j < kMaxLogits; ++j) acc[j] = 0.0f;
-    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+  for (int j = 0; j < kMaxLogits; ++j) acc[j] = 0.0f;
+  if (ok) {
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     // one output's dot product over 32 hidden units: the weights as 8 vector
     // loads, four independent partial sums
     auto dot32 = [&](const float(&h)[32], const float *w) -> float {
@@ -890,12 +896,21 @@ __global__ void __launch_bounds__(kThreads, 1) policy_heads_kernel(const HeadsAr
         acc[0] += dot32(h, wout + c0);
       }
     };
-    for (int c0 = 0; c0 < 256; c0 += 64) {  // two 32-column TMEM loads behind one wait
+    for (int c0 = 128 * hh; c0 < 128 * hh + 128; c0 += 64) {  // two 32-column TMEM loads behind one wait
       float v[32], w[32];
       tmem_ld32x2(tmem + lane_base + c0, tmem + lane_base + c0 + 32, v, w);
       chunk(v, c0);
       chunk(w, c0 + 32);
     }
+    if (hh) {
+#pragma unroll
+      for (int o = 0; o < kMaxLogits; ++o) part[o] = acc[o];
+    }
+  }
+  __syncthreads();
+  if (ok && !hh) {
+#pragma unroll
+    for (int o = 0; o < kMaxLogits; ++o) acc[o] += part[o];
     if (inst < a.n) {
       if (head == 0) {
         float m = -INFINITY;
