@@ -9,7 +9,9 @@
 // accumulated in fp32 (TMEM), heads' output layers in fp32 on the CUDA cores.
 //
 // Conv kernel (persistent, one CTA per SM: 8 warps that build operands and
-// drain accumulators, one warp that issues the MMAs and bulk copies). A batch of kP = 8
+// drain accumulators, and two threads in two more warps that issue the MMAs
+// and bulk copies: an MMA costs its issuing thread more time than its share of
+// the tensor pipe, so conv1's MMAs and conv2's come from different threads). A batch of kP = 8
 // instances is processed at a time; the rows of every GEMM are
 // (grid position, instance) with the instance fastest, so one 8-row core
 // matrix of the tcgen05 no-swizzle K-major layout is one grid position of
@@ -77,8 +79,9 @@ namespace {
 constexpr int kP = 8;            // instances per conv batch
 constexpr int kThreads = 256;      // heads kernel: two warps per TMEM lane quarter
 constexpr int kConvWork = 256;               // conv kernel: 8 warps build / drain (two per TMEM lane quarter)
-constexpr int kConvThreads = kConvWork + 32; // + one warp that issues the MMAs and bulk copies
-constexpr int kIssuer = kConvWork;           // its issuing thread
+constexpr int kConvThreads = kConvWork + 64; // + two warps whose first lanes issue the MMAs and bulk copies
+constexpr int kIssuer = kConvWork;           // conv1's MMAs, the W1 / W2 copies and W3's first taps
+constexpr int kIssuer2 = kConvWork + 32;     // conv2's and conv3's MMAs and the rest of W3
 constexpr int kMaxLogits = 17;   // 16 keys + the no-op
 constexpr uint64_t kMaxWaitNs = 1000000000ull;
 constexpr uint32_t kMaxPolls = 1u << 24;
@@ -352,9 +355,9 @@ template <bool kU8>
 __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const ConvArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   // MMA completion: conv1 x2, conv2, conv3 x2; bulk copies: W1 + W2, W3 x2; the final
-  // drain on the error path; conv1 blocks built x2 (per block buffer), band rows written
-  // (worker arrivals)
-  __shared__ __align__(8) uint64_t bars[12];
+  // drain on the error path (bars[8] and bars[12], one per issuing thread); conv1 blocks
+  // built x2 (per block buffer), band rows written (worker arrivals)
+  __shared__ __align__(8) uint64_t bars[13];
   __shared__ uint32_t tmem_s;
   __shared__ float sb[160];                  // b1 | b2 | b3
   __shared__ uint2 nib[16];                  // 4 pixel bits -> 4 bf16 0 / 1 (element k = bit k)
@@ -372,6 +375,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
   if (t == 0) {
     for (int j = 0; j < 9; ++j) mbar_init(smem_u32(&bars[j]), 1);
     for (int j = 9; j < 12; ++j) mbar_init(smem_u32(&bars[j]), kConvWork);
+    mbar_init(smem_u32(&bars[12]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -415,7 +419,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
   // one half of the accumulator's columns
   const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
   const int half = warp >> 2;
-  const bool issuer = warp == kConvWork / 32;  // the MMA-issuing warp takes no part in building / draining
+  const bool issuer = warp >= kConvWork / 32;  // the MMA-issuing warps take no part in building / draining
   const int r = 32 * (warp & 3) + lane;  // M-tile row of this thread (TMEM lane)
   // base descriptors of every MMA operand (the issuing loops add constant offsets)
   const uint64_t a1d0 = sdesc(sbase + kBlkOff, 128, 512), a1d1 = sdesc(sbase + kBlkOff + kBlkBytes, 128, 512);
@@ -540,17 +544,19 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
         }
       mma_commit(bar_c2);
     };
-    // The workers and the issuing thread meet only through mbarriers here.
-    // The workers arrive on blk[p & 1] when pair p's blocks are built, which
-    // also says that pair p - 2 has been drained, so its TMEM buffer is free
-    // (one barrier per block buffer: the next arrival on it needs pair p's
-    // MMAs, issued only after the issuing thread's wait, so that thread never
-    // falls two phases behind a parity wait). They arrive on band when the
-    // band rows of pairs 2, 4 and 6 are written, and each worker waits for
-    // the MMAs itself. So the workers go on while the issuing thread sits in
-    // a full MMA queue. Every wait is bounded; one that runs out only clears
-    // r_ok, and each side still runs its whole schedule (no other side waits
-    // on it for long).
+    // The workers and the two issuing threads meet only through mbarriers
+    // here. The workers arrive on blk[p & 1] when pair p's blocks are built,
+    // which also says that pair p - 2 has been drained, so its TMEM buffer is
+    // free (one barrier per block buffer: the next arrival on it needs pair
+    // p's MMAs, issued only after conv1's issuing thread has waited, so that
+    // thread never falls two phases behind a parity wait). They arrive on band
+    // when the band rows of pairs 2, 4 and 6 are written; conv2's issuing
+    // thread waits for it (the next arrival needs a conv1 pair whose MMAs come
+    // after the tile's wait in the tensor pipe's order, through the slide's
+    // wait for the tile). Each worker waits for the MMAs itself, so the
+    // workers go on while an issuing thread sits in a full MMA queue. Every
+    // wait is bounded; one that runs out only clears r_ok, and each side still
+    // runs its whole schedule (no other side waits on it for long).
     bool r_ok = true;
     if (!issuer) {
       build(0, 0);
@@ -604,8 +610,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
           mbar_arrive(bar_band);
         }
       }
-      // (the issuing warp skips the waits on conv2 tiles 0 and 1: two parity
-      // flips, so its ph_c2 agrees with the workers' again here)
+      // (the issuing warps skip the waits on conv2 tiles 0 and 1: two parity
+      // flips, so their ph_c2 agrees with the workers' again here)
     } else if (t == kIssuer) {
       for (int pr = 0; pr < 7; ++pr) {
         const int b = pr & 1;
@@ -617,21 +623,19 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
           bulk_g2s(sbase + kW3Off, a.w3, kW3EarlyBytes, bar_w3a);
           w3_pend |= 1u;
         }
-        if (pr == 3 || pr == 5) {  // band rows of pairs 2 and 4 written
-          r_ok &= mbar_wait(bar_band, ph_band);
-          ph_band ^= 1u;
-          issue_c2((pr - 3) >> 1);
-        }
       }
-      r_ok &= mbar_wait(bar_band, ph_band);  // band rows of pair 6
-      ph_band ^= 1u;
-      issue_c2(2);
+    } else if (t == kIssuer2) {  // conv2 tiles as the band fills (rows of pairs 2, 4 and 6)
+      for (int tt = 0; tt < 3; ++tt) {
+        r_ok &= mbar_wait(bar_band, ph_band);
+        ph_band ^= 1u;
+        issue_c2(tt);
+      }
     }
     // (no block barrier here: the drains of conv2 tiles 0 and 1 below need
-    // only the workers' own waits, and the issuing thread may still be
+    // only the workers' own waits, and conv2's issuing thread may still be
     // issuing tile 2; r_ok joins the block-wide wait on tile 2)
     // ---- conv2 epilogues into region X: tiles 0 and 1 (done) while tile 2
-    // computes; the issuing thread loads the rest of W3 over the band as soon
+    // computes; conv2's issuing thread loads the rest of W3 over the band as soon
     // as tile 2 is done
     // Output g (valid for px = g & 7 < 6) adds row g + 1's second half: by a
     // shuffle, or for g = 3, 11 from the next lane quarter (rows 4, 12)
@@ -657,7 +661,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
       }
     };
     if (issuer) {
-      if (t == kIssuer && mbar_wait(bar_c2, ph_c2)) {  // (a timeout here shows in the waits below)
+      if (t == kIssuer2 && mbar_wait(bar_c2, ph_c2)) {  // (a timeout here shows in the waits below)
         fence_async_smem();
         mbar_expect_tx(bar_w3b, kW3Bytes - kW3EarlyBytes);
         for (uint32_t o = kW3EarlyBytes; o < kW3Bytes; o += 16384)
@@ -703,7 +707,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     // g = 0..3, 8..11); rows g + 1 and g + 2 come from the same warp by
     // shuffles, or, past the quarter's end, from quarters 1 and 3 (positions
     // 4, 5 and 12, 13, no outputs of their own) through the exchange buffer.
-    // (the issuing warp goes on to the batch's closing barrier; the workers'
+    // (the issuing warps go on to the batch's closing barrier; the workers'
     // outcome joins it there)
     for (int u = 0; u < 2 && !issuer; ++u) {
       ok = (u ? wait_workers(bar_c3b, ph_c3b) : wait_workers(bar_c3a, ph_c3a)) && ok;
@@ -751,10 +755,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     ok = !__syncthreads_or(!ok);  // region X and the W3 region are rewritten by the next batch
   }
   if (!ok && t == 0) atomicOr(a.err, 1u);
-  if (!ok && t == kIssuer) {  // let this thread's MMAs and bulk copies land before TMEM and shared memory go
-    mma_commit(smem_u32(&bars[8]));
-    mbar_wait(smem_u32(&bars[8]), 0);
-    mbar_wait(bar_w, 0);
+  if (!ok && (t == kIssuer || t == kIssuer2)) {  // let this thread's MMAs and copies land before TMEM and shared memory go
+    const uint32_t fin = smem_u32(&bars[t == kIssuer ? 8 : 12]);
+    mma_commit(fin);
+    mbar_wait(fin, 0);
+    if (t == kIssuer) mbar_wait(bar_w, 0);
     if (w3_pend & 1u) mbar_wait(bar_w3a, ph_w3);
     if (w3_pend & 2u) mbar_wait(bar_w3b, ph_w3);
   }
