@@ -9,9 +9,10 @@
 // accumulated in fp32 (TMEM), heads' output layers in fp32 on the CUDA cores.
 //
 // Conv kernel (persistent, one CTA per SM: 8 warps that build operands and
-// drain accumulators, and two threads in two more warps that issue the MMAs
-// and bulk copies: an MMA costs its issuing thread more time than its share of
-// the tensor pipe, so conv1's MMAs and conv2's come from different threads). A batch of kP = 8
+// drain accumulators, and three threads in three more warps that issue the
+// MMAs and bulk copies: an MMA costs its issuing thread more time than its
+// share of the tensor pipe, so conv1's even pairs, its odd pairs and conv2's
+// tiles come from different threads). A batch of kP = 8
 // instances is processed at a time; the rows of every GEMM are
 // (grid position, instance) with the instance fastest, so one 8-row core
 // matrix of the tcgen05 no-swizzle K-major layout is one grid position of
@@ -79,9 +80,10 @@ namespace {
 constexpr int kP = 8;            // instances per conv batch
 constexpr int kThreads = 256;      // heads kernel: two warps per TMEM lane quarter
 constexpr int kConvWork = 256;               // conv kernel: 8 warps build / drain (two per TMEM lane quarter)
-constexpr int kConvThreads = kConvWork + 64; // + two warps whose first lanes issue the MMAs and bulk copies
-constexpr int kIssuer = kConvWork;           // conv1's MMAs, the W1 / W2 copies and W3's first taps
-constexpr int kIssuer2 = kConvWork + 32;     // conv2's and conv3's MMAs and the rest of W3
+constexpr int kConvThreads = kConvWork + 96; // + three warps whose first lanes issue the MMAs and bulk copies
+constexpr int kIssuer = kConvWork;           // conv1's even pairs, conv3, the W1 / W2 copies and W3's first taps
+constexpr int kIssuer2 = kConvWork + 32;     // conv2's tiles and the rest of W3
+constexpr int kIssuer3 = kConvWork + 64;     // conv1's odd pairs
 constexpr int kMaxLogits = 17;   // 16 keys + the no-op
 constexpr uint64_t kMaxWaitNs = 1000000000ull;
 constexpr uint32_t kMaxPolls = 1u << 24;
@@ -355,9 +357,9 @@ template <bool kU8>
 __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const ConvArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   // MMA completion: conv1 x2, conv2, conv3 x2; bulk copies: W1 + W2, W3 x2; the final
-  // drain on the error path (bars[8] and bars[12], one per issuing thread); conv1 blocks
+  // drain on the error path (bars[8], [12], [13], one per issuing thread); conv1 blocks
   // built x2 (per block buffer), band rows written (worker arrivals)
-  __shared__ __align__(8) uint64_t bars[13];
+  __shared__ __align__(8) uint64_t bars[14];
   __shared__ uint32_t tmem_s;
   __shared__ float sb[160];                  // b1 | b2 | b3
   __shared__ uint2 nib[16];                  // 4 pixel bits -> 4 bf16 0 / 1 (element k = bit k)
@@ -376,6 +378,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     for (int j = 0; j < 9; ++j) mbar_init(smem_u32(&bars[j]), 1);
     for (int j = 9; j < 12; ++j) mbar_init(smem_u32(&bars[j]), kConvWork);
     mbar_init(smem_u32(&bars[12]), 1);
+    mbar_init(smem_u32(&bars[13]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -548,8 +551,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     // here. The workers arrive on blk[p & 1] when pair p's blocks are built,
     // which also says that pair p - 2 has been drained, so its TMEM buffer is
     // free (one barrier per block buffer: the next arrival on it needs pair
-    // p's MMAs, issued only after conv1's issuing thread has waited, so that
-    // thread never falls two phases behind a parity wait). They arrive on band
+    // p's MMAs, issued only after the issuing thread of pairs p & 1 has
+    // waited, so it never falls two phases behind a parity wait). They arrive on band
     // when the band rows of pairs 2, 4 and 6 are written; conv2's issuing
     // thread waits for it (the next arrival needs a conv1 pair whose MMAs come
     // after the tile's wait in the tensor pipe's order, through the slide's
@@ -612,8 +615,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
       }
       // (the issuing warps skip the waits on conv2 tiles 0 and 1: two parity
       // flips, so their ph_c2 agrees with the workers' again here)
-    } else if (t == kIssuer) {
-      for (int pr = 0; pr < 7; ++pr) {
+    } else if (t == kIssuer || t == kIssuer3) {  // conv1's even / odd pairs
+      for (int pr = t == kIssuer ? 0 : 1; pr < 7; pr += 2) {
         const int b = pr & 1;
         r_ok &= mbar_wait(b ? bar_blk1 : bar_blk0, b ? ph_blk1 : ph_blk0);
         if (b) ph_blk1 ^= 1u; else ph_blk0 ^= 1u;
@@ -755,8 +758,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     ok = !__syncthreads_or(!ok);  // region X and the W3 region are rewritten by the next batch
   }
   if (!ok && t == 0) atomicOr(a.err, 1u);
-  if (!ok && (t == kIssuer || t == kIssuer2)) {  // let this thread's MMAs and copies land before TMEM and shared memory go
-    const uint32_t fin = smem_u32(&bars[t == kIssuer ? 8 : 12]);
+  if (!ok && (t == kIssuer || t == kIssuer2 || t == kIssuer3)) {  // let this thread's MMAs and copies land
+    const uint32_t fin = smem_u32(&bars[t == kIssuer ? 8 : (t == kIssuer2 ? 12 : 13)]);
     mma_commit(fin);
     mbar_wait(fin, 0);
     if (t == kIssuer) mbar_wait(bar_w, 0);
