@@ -560,6 +560,7 @@ def run_policy(args, dev, stream) -> dict:
         env = octax.Env(w.games, n, seed=w.seed, device=dev.index, stream=stream)
         pol = octax.Policy(params, max_envs=n, device=dev.index, stream=stream)
         obs0 = env.reset()
+        env.autotune(1)  # both legs step the environment one step per call
         words0 = pack_words(obs0)
         init = env.get_state()
         outs = (torch.empty((T, n), dtype=torch.uint8, device=dev),
