@@ -395,12 +395,12 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
     bulk_g2s(sbase + kW1Off, a.w1, kW1Bytes, bar_w);
     for (uint32_t o = 0; o < kW2Bytes; o += 16384) bulk_g2s(sbase + kW2Off + o, a.w2 + o, 16384, bar_w);
   }
-  // every wait's outcome is made uniform over the block, so all threads
-  // leave the loops together
+  // every exit from the batch loop tests ok right after a block-wide
+  // reduction of every thread's outcome, so all threads leave it together
   bool ok = !__syncthreads_or(!mbar_wait(bar_w, 0));
-  uint32_t ph_c1_0 = 0, ph_c1_1 = 0, ph_c2 = 0, ph_c3a = 0, ph_c3b = 0, ph_w3 = 0;
-  uint32_t ph_blk0 = 0, ph_blk1 = 0, ph_band = 0;  // issuing thread: conv1 blocks built, band rows written
-  uint32_t w3_pend = 0;  // issuing thread: W3 copies issued and not yet waited for (bit 0 early, bit 1 rest)  // ph_w3: both W3 barriers
+  uint32_t ph_c1_0 = 0, ph_c1_1 = 0, ph_c2 = 0, ph_c3a = 0, ph_c3b = 0, ph_w3 = 0;  // ph_w3: both W3 barriers
+  uint32_t ph_blk0 = 0, ph_blk1 = 0, ph_band = 0;  // issuing threads: conv1 blocks built, band rows written
+  uint32_t w3_pend = 0;  // issuing threads: W3 copies issued and not yet waited for (bit 0 early, bit 1 rest)
   const int64_t n_batches = (a.n + kP - 1) / kP;
   static_assert(kP * 64 == 2 * kConvWork, "two packed-frame pieces per worker");
   // a worker's two pieces of a batch's packed frames (q = t, t + 256:
