@@ -309,10 +309,13 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t *>(&h);
 }
 // bias + ReLU on 8 values, packed to one 16-byte chunk of 8 bf16.
+// (bias: 16-byte aligned shared memory, read as two vectors)
 __device__ __forceinline__ uint4 relu_chunk(const float *v, const float *bias) {
+  const float4 b0 = reinterpret_cast<const float4 *>(bias)[0], b1 = reinterpret_cast<const float4 *>(bias)[1];
+  const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
   float o[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) o[j] = fmaxf(v[j] + bias[j], 0.0f);
+  for (int j = 0; j < 8; ++j) o[j] = fmaxf(v[j] + bb[j], 0.0f);
   return make_uint4(pack_bf16(o[0], o[1]), pack_bf16(o[2], o[3]), pack_bf16(o[4], o[5]), pack_bf16(o[6], o[7]));
 }
 
@@ -361,7 +364,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) policy_conv_kernel(const Conv
   // built x2 (per block buffer), band rows written (worker arrivals)
   __shared__ __align__(8) uint64_t bars[14];
   __shared__ uint32_t tmem_s;
-  __shared__ float sb[160];                  // b1 | b2 | b3
+  __shared__ __align__(16) float sb[160];    // b1 | b2 | b3 (offsets used are multiples of 8)
   __shared__ uint2 nib[16];                  // 4 pixel bits -> 4 bf16 0 / 1 (element k = bit k)
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const uint32_t sbase = smem_u32(sm);
