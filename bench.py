@@ -98,6 +98,23 @@ def step_plan(steps: int, rollout: int, warmup: int) -> dict:
             "warmup_calls": calls[:2]}
 
 
+# Output ring that the default rollout length may fill (observations, rewards
+# and done flags of one octax_step_n call).
+ROLLOUT_RING_BYTES = 36e9
+
+
+def default_rollout(n_envs: int, io_bytes: int, budget: float = ROLLOUT_RING_BYTES) -> int:
+    """Env steps per octax_step_n call when --rollout is not given: the
+    longest power of two from 32 (the paper's PPO rollout, §4.1) up to 256
+    whose output ring, n_envs x io_bytes per step, fits in ``budget``; never
+    below 32. A launch lasts until its slowest warp is done, so longer calls
+    (and the longer launches they allow) spread the stragglers' wait."""
+    T = 32
+    while T < 256 and 2 * T * n_envs * io_bytes <= budget:
+        T *= 2
+    return T
+
+
 def whole_job_rate(world: int, n_envs: int, steps: int, ms: float) -> float:
     """Env steps/s of the whole job: every replica ran n_envs x steps."""
     return world * n_envs * steps / (ms / 1e3)
@@ -302,7 +319,7 @@ def run_gpu(args) -> dict | None:
     w = workload(args.config, args.n_envs)
     K, Wm = args.steps if args.steps else w.n_steps, args.warmup
     n = w.n_envs
-    plan = step_plan(K, args.rollout, Wm)
+    plan = step_plan(K, args.rollout or default_rollout(n, step_io_bytes(w)), Wm)
     T, calls = plan["T"], plan["calls"]
     with torch.cuda.stream(stream):
         env = octax.Env(w.games, n, seed=w.seed, quirks=w.quirks, game_of_env=w.game_of_env,
@@ -898,7 +915,9 @@ def parse_args(argv=None):
     ap.add_argument("--impl", default="octax", choices=["octax", "reference"])
     ap.add_argument("--config", default="divergence",
                     choices=["scale", "small", "batch", "divergence", "schip", "shooter", "wrappers"])
-    ap.add_argument("--rollout", type=int, default=32, help="steps per octax_step_n call")
+    ap.add_argument("--rollout", type=int, default=0,
+                    help="steps per octax_step_n call (0 = the longest of 32..256 whose output "
+                         "ring fits in 36 GB)")
     ap.add_argument("--n-envs", type=int, default=0,
                     help="resize the configuration (0 = its own size); for small profiling captures")
     ap.add_argument("--launch", default="",

@@ -162,7 +162,7 @@ typedef struct {
 typedef struct {
   int32_t block;             /* emulator threads per CTA: 32, 64, 128 or 256    */
   int32_t inst_per_warp;     /* instances emulated per warp: 1..32                */
-  int32_t steps_per_launch;  /* octax_step_n: env steps per kernel launch 1..64  */
+  int32_t steps_per_launch;  /* octax_step_n: env steps per kernel launch 1..256 */
   int32_t persistent;        /* 1: resident CTAs pull instance groups off a queue */
   int32_t use_graph;         /* 1: octax_step_n replays a captured CUDA graph     */
   int32_t writer_warps;      /* 0, 1, 2, 4 or 8 observation-writer warps         */
@@ -278,7 +278,8 @@ int octax_set_launch(octax_env *env, const octax_launch *cfg);
 
 /* Autotuner for the batched step (part of §5's adaptive batching; the paper
  * defines no tuner). Times candidate launch configurations (CTA size, instances per warp, steps
- * per launch, persistence) for octax_step_n calls of n_steps steps, starting
+ * per launch from 1 to 256 and n_steps itself, persistence, writer warps) for
+ * octax_step_n calls of n_steps steps, starting
  * from the current state, then restore that state: results are unaffected.
  * actions_dev [n_steps][n_envs] (nullable: pseudo-random indices 0..4) should
  * be representative, since divergence depends on them. Keeps the fastest

@@ -189,7 +189,7 @@ int wave_of(const octax_env *e, const octax_launch &c) {
 
 const char *launch_problem(const octax_launch &c, int schip) {
   if (!block_ok(c.block) || !ipw_ok(c.inst_per_warp)) return "block in {32,64,128,256}, inst_per_warp in {1,...,32}";
-  if (c.steps_per_launch < 1 || c.steps_per_launch > 64) return "steps_per_launch 1..64";
+  if (c.steps_per_launch < 1 || c.steps_per_launch > 256) return "steps_per_launch 1..256";
   if ((c.persistent != 0 && c.persistent != 1) || (c.use_graph != 0 && c.use_graph != 1) ||
       (c.balance != 0 && c.balance != 1))
     return "flags 0/1";
@@ -959,11 +959,17 @@ int octax_autotune(octax_env *e, int n_steps, const uint8_t *actions_dev, float 
         const int J = b / 32 * ipw;
         if (J >= 8 && J <= 256) trial(octax_launch{b, ipw, std::min(32, n_steps), 0, 1, 0, bal});
       }
-  // stage 2: writer warps, persistence and steps per launch around the best shape
+  // stage 2: writer warps, persistence and steps per launch around the best
+  // shape. Launches up to 256 steps and the call length itself are
+  // candidates: a launch ends with its slowest warp, and on workloads whose
+  // instances now and then run a long sequential stretch (no-op resets) the
+  // longer launch spreads that wait over more steps.
   const octax_launch shape = best;
+  std::vector<int> spls = {1, 2, 4, 8, 16, 32, 64, 128, 256};
+  if (n_steps <= 256 && std::find(spls.begin(), spls.end(), n_steps) == spls.end()) spls.push_back(n_steps);
   for (int W : {0, 1, 2, 4})
     for (int pers : {0, 1})
-      for (int spl : {1, 2, 4, 8, 16, 32})
+      for (int spl : spls)
         trial(octax_launch{shape.block, shape.inst_per_warp, spl, pers, 1, W, shape.balance});
   r = copy_state(false);
   const cudaError_t rs = cudaStreamSynchronize(e->stream);

@@ -104,6 +104,29 @@ def test_step_plan(steps, warmup, rollout):
     assert p["warmup_calls"] == p["calls"][:2]
 
 
+def test_default_rollout_by_workload():
+    """With no --rollout, each configuration gets the longest power-of-two
+    rollout from 32 to 256 whose output ring fits the 36 GB budget: the
+    16,384-instance CHIP-8 workloads 256 steps, the 65,536-instance batch and
+    the Super-CHIP workload (4x larger frames) 64, the 262,144-instance
+    default 32; the driver's 20-step command still times one 20-step call."""
+    rings = {}
+    for name, T_want in [("scale", 256), ("wrappers", 256), ("shooter", 256), ("small", 256),
+                         ("schip", 64), ("batch", 64), ("divergence", 32)]:
+        w = bench.workload(name)
+        io = bench.step_io_bytes(w)
+        T = bench.default_rollout(w.n_envs, io)
+        assert T == T_want, name
+        assert T == 32 or T * w.n_envs * io <= bench.ROLLOUT_RING_BYTES
+        rings[name] = T * w.n_envs * io
+    assert max(rings.values()) < 70e9  # the 32-step floor at 262,144 instances
+    w = bench.workload("divergence")
+    p = bench.step_plan(20, bench.default_rollout(w.n_envs, bench.step_io_bytes(w)), 5)
+    assert p["T"] == 20 and p["calls"] == [(0, 20)]
+    assert bench.default_rollout(1, 1) == 256 and bench.default_rollout(10**9, 10**4) == 32
+    assert bench.parse_args([]).rollout == 0
+
+
 def test_step_plan_driver_command():
     """A short run (--steps 20 --warmup 5) tunes and times one 20-step call;
     the default run (2,000 steps) uses 32-step calls."""

@@ -557,6 +557,38 @@ def test_config_wrappers_sampled():
     assert n_done > 0
 
 
+@pytest.mark.parametrize("spl", [64, 128, 256])
+def test_config_wrappers_long_launches(spl):
+    """The wrappers workload (episodes truncated at 700 steps, so every
+    instance resets through its no-op steps) in launches of 64, 128 and 256
+    steps inside 256-step calls, the benchmark's default call length for
+    16,384 instances; 3,000 steps, so the last call and its launches are
+    ragged."""
+    w = W.cfg_wrappers(n_steps=3000)
+    w.games = [W.replace(w.games[0], max_episode_steps=700)]
+    sample = pick(w.n_envs, 12, 40 + spl, extra=(0, 55, 56, w.n_envs - 1))
+    env, n_done = sampled_run(w, chunk=256, sample=sample,
+                              launch=dict(block=256, inst_per_warp=7, steps_per_launch=spl,
+                                          persistent=0, use_graph=1, balance=1))
+    assert n_done > 0
+
+
+@pytest.mark.parametrize("config", ["wrappers", "scale"])
+def test_config_autotuned_256(config):
+    """The 16,384-instance workloads (the full 20,000-step scale workload;
+    the wrappers one with episodes truncated at 700 steps) in the shape the
+    autotuner picks for 256-step calls, whose candidates now include
+    launches of up to 256 steps."""
+    if config == "wrappers":
+        w = W.cfg_wrappers(n_steps=3000)
+        w.games = [W.replace(w.games[0], max_episode_steps=700)]
+    else:
+        w = W.cfg_scale()
+    sample = pick(w.n_envs, 16, 50 + len(config), extra=(1, 111, 112, w.n_envs - 1))
+    env, n_done = sampled_run(w, chunk=256, sample=sample, autotune=True)
+    assert n_done > 0
+
+
 @pytest.mark.parametrize("balance", [0, 1])
 def test_config_batch_sampled(balance):
     """65,536 instances over 16 ROMs (K from {5,8,10,15,20}, uneven episodes),
@@ -595,9 +627,10 @@ def test_config_divergence_bench_shapes(spl, persistent, chunk):
                             use_graph=1))
 
 
-@pytest.mark.parametrize("T", [20, 32])
+@pytest.mark.parametrize("T", [20, 32, 64])
 def test_config_batch_autotuned(T):
-    """65,536 instances over 16 ROMs in the autotuned shape for T-step calls."""
+    """65,536 instances over 16 ROMs in the autotuned shape for T-step calls
+    (64: the benchmark's default call length for this workload)."""
     w = W.cfg_batch()
     goe = w.game_of_env
     per_game = [np.nonzero(goe == g)[0][:1] for g in range(16)]

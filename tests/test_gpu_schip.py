@@ -177,3 +177,12 @@ def test_schip_packed_observations():
     assert np.array_equal(obs.cpu().numpy().view(np.uint64), pack_frames(o2))
     assert np.array_equal(rew.cpu().numpy(), r2) and np.array_equal(done.cpu().numpy(), d2)
     assert np.array_equal(hashes(env), ref.hashes())
+
+
+def test_schip_scale_autotuned_64():
+    """The 16,384-instance hires workload (4,000 steps) in the shape the
+    autotuner picks for the benchmark's default 64-step calls."""
+    w = W.cfg_schip()
+    sample = pick(w.n_envs, 10, 27, extra=(1, 111, w.n_envs - 1))
+    env, n_done = sampled_run(w, chunk=64, sample=sample, autotune=True)
+    assert n_done > 0

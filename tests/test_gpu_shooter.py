@@ -91,3 +91,13 @@ def test_config_shooter_sampled():
                               launch=dict(block=256, inst_per_warp=7, steps_per_launch=32,
                                           persistent=0, use_graph=1, balance=1))
     assert n_done > 0
+
+
+def test_config_shooter_autotuned_256():
+    """The benchmark workload in the shape the autotuner picks for its
+    default 256-step calls (launches of up to 256 steps among the
+    candidates)."""
+    w = W.cfg_shooter()
+    sample = pick(w.n_envs, 12, 19, extra=(3, 111, 112, w.n_envs - 1))
+    env, n_done = sampled_run(w, chunk=256, sample=sample, autotune=True)
+    assert n_done > 0
