@@ -85,6 +85,14 @@ def test_config_small_full_parity():
                  n_actions=4)
 
 
+def test_config_small_autotuned():
+    """The small configuration (64 instances, 1,000 steps) in the shape the
+    autotuner picks for 256-step calls (CTAs of fewer than 8 instances are
+    candidates at this size), every instance compared at every step."""
+    w = W.cfg_small()
+    sampled_run(w, chunk=256, sample=np.arange(w.n_envs), autotune=True)
+
+
 @pytest.mark.parametrize("launch", [
     dict(block=32, inst_per_warp=32, steps_per_launch=1, persistent=0, use_graph=0),
     dict(block=64, inst_per_warp=32, steps_per_launch=4, persistent=0, use_graph=1),
@@ -104,6 +112,9 @@ def test_config_small_full_parity():
     dict(block=256, inst_per_warp=8, steps_per_launch=3, persistent=1, use_graph=0, balance=1),
     dict(block=128, inst_per_warp=16, steps_per_launch=2, persistent=0, use_graph=1, writer_warps=2,
          balance=1),
+    dict(block=128, inst_per_warp=3, steps_per_launch=5, persistent=0, use_graph=1),
+    dict(block=32, inst_per_warp=1, steps_per_launch=16, persistent=0, use_graph=1, balance=1),
+    dict(block=256, inst_per_warp=2, steps_per_launch=64, persistent=1, use_graph=1),
 ])
 def test_launch_configurations_agree(launch):
     w = W.cfg_small()

@@ -47,6 +47,9 @@ def test_schip_template_full_parity():
     dict(block=64, inst_per_warp=8, steps_per_launch=4, persistent=0, use_graph=1, balance=1),
     dict(block=128, inst_per_warp=7, steps_per_launch=3, persistent=1, use_graph=1),
     dict(block=256, inst_per_warp=4, steps_per_launch=8, persistent=0, use_graph=1),
+    dict(block=64, inst_per_warp=1, steps_per_launch=6, persistent=0, use_graph=1),
+    dict(block=128, inst_per_warp=2, steps_per_launch=60, persistent=1, use_graph=1, balance=1),
+    dict(block=32, inst_per_warp=3, steps_per_launch=4, persistent=0, use_graph=0),
 ])
 def test_schip_launch_configurations(launch):
     full_compare([template(score_limit=4, max_episode_steps=50)], 150, 60, seed=5, action_seed=5,
