@@ -89,11 +89,15 @@ def test_alone_equals_in_mix():
         env.close()
 
 
-def test_requests_match_oracle():
+@pytest.mark.parametrize("shape", [None, (64, 1), (32, 2), (128, 4)])
+def test_requests_match_oracle(shape):
+    """Requests against the oracle, with the server's default CTA shape and
+    with warps of 1, 2 and 4 instances (whose frames all 32 lanes write)."""
     o = octax()
     gs = games()
     reqs = make_requests(6, 2, max_envs=64)
-    srv = o.Server(gs, memory_budget_bytes=10000 * SLOT_BYTES)
+    kw = {} if shape is None else dict(block=shape[0], inst_per_warp=shape[1])
+    srv = o.Server(gs, memory_budget_bytes=10000 * SLOT_BYTES, **kw)
     _, _, outs = run_all(srv, reqs, stagger_s=0.0005)
     srv.close()
     for r, got in zip(reqs, outs):
