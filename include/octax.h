@@ -306,9 +306,11 @@ void octax_destroy(octax_env *env);
  * random-number identity i) stepped n_steps times with the given actions.
  * Queued requests are admitted first-in first-out as slots free up; every
  * scheduling tick launches one step kernel over all admitted requests, each
- * at its own step, so requests that arrive while others run join the next
- * tick. Results are identical to running the request alone (octax_create +
- * octax_step with the same seed). */
+ * at its own step, advancing them all by the fewest steps any of them has
+ * left (at least one), so requests that arrive while others run join the
+ * next tick, and a request that runs alone takes one launch. Results are
+ * identical to running the request alone (octax_create + octax_step with the
+ * same seed). */
 typedef struct octax_server octax_server;
 
 typedef struct {

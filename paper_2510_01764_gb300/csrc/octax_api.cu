@@ -953,14 +953,11 @@ int octax_autotune(octax_env *e, int n_steps, const uint8_t *actions_dev, float 
   // stage 1: CTA shape (threads x instances per warp) and balanced waves,
   // plain kernel, up to 32 steps per launch (long launches rank shapes as
   // they will run)
-  // CTAs of fewer than 8 instances (down to one per warp) are candidates only
-  // when the instances are too few to give every SM a few CTAs of 8.
-  const int min_j = e->n <= 4096 ? 1 : 8;
   for (int b : {32, 64, 128, 256})
-    for (int ipw : {32, 16, 8, 7, 6, 4, 2, 1})
+    for (int ipw : {32, 16, 8, 7, 6, 4})
       for (int bal : {0, 1}) {
         const int J = b / 32 * ipw;
-        if (J >= min_j && J <= 256) trial(octax_launch{b, ipw, std::min(32, n_steps), 0, 1, 0, bal});
+        if (J >= 8 && J <= 256) trial(octax_launch{b, ipw, std::min(32, n_steps), 0, 1, 0, bal});
       }
   // stage 2: writer warps, persistence and steps per launch around the best
   // shape. Launches up to 256 steps and the call length itself are

@@ -696,30 +696,12 @@ __device__ __forceinline__ void capture_frame(const uint64_t *disp_warp, int J, 
                                               int lane, int ipw, const uint2 *lut);
 
 // CHIP-8 frame (32 rows x 64 bytes): lanes 4i..4i+3 write the four 16-pixel
-// quarters of one row of instance i (8 instances per pass). A warp of at
-// most 4 instances spreads each instance's rows over 32 / P lanes instead
-// (P = 4, 2 or 1 instances in its one pass; lane group g of an instance
-// writes rows g, g + 32 / (4P), ...), so that no lane idles while the
-// frames of a few instances are written.
+// quarters of one row of instance i (8 instances per pass).
 template <>
 __device__ __forceinline__ void capture_frame<false>(const uint64_t *disp_warp, int J, uint8_t *frame,
                                                      int lane, int ipw, const uint2 *lut) {
   const uint64_t mine = reinterpret_cast<uint64_t>(frame);
   const uint32_t q = lane & 3;
-  if (ipw <= 4) {
-    const int per = ipw > 2 ? 4 : ipw;        // instances in the pass: 4, 2 or 1
-    const int lpi = 32 / per;                 // lanes per instance: 8, 16 or 32
-    const int rstep = lpi >> 2;               // rows between a lane's stores
-    const int src = lane / lpi;
-    const uint64_t base = __shfl_sync(kFull, mine, src);
-    if (base) {
-      const uint64_t *col = disp_warp + src;
-      uint8_t *dst = reinterpret_cast<uint8_t *>(base) + q * 16u;
-      for (int r = (lane & (lpi - 1)) >> 2; r < 32; r += rstep)
-        __stcs(reinterpret_cast<uint4 *>(dst + r * 64), expand16(col[r * J], q, lut));
-    }
-    return;
-  }
   const int passes = (ipw + 7) >> 3;
   for (int m = 0; m < passes; ++m) {
     const int src = 8 * m + (lane >> 2);
@@ -734,26 +716,12 @@ __device__ __forceinline__ void capture_frame<false>(const uint64_t *disp_warp, 
 }
 
 // SCHIP frame (64 rows x 128 bytes): lanes 8i..8i+7 write the eight 16-pixel
-// chunks of one row of instance i (4 instances per pass). A warp of one or
-// two instances spreads each instance's rows over 32 or 16 lanes instead.
+// chunks of one row of instance i (4 instances per pass).
 template <>
 __device__ __forceinline__ void capture_frame<true>(const uint64_t *disp_warp, int J, uint8_t *frame,
                                                     int lane, int ipw, const uint2 *lut) {
   const uint64_t mine = reinterpret_cast<uint64_t>(frame);
   const uint32_t q = lane & 7, h = q >> 2;
-  if (ipw <= 2) {
-    const int lpi = 32 / ipw;                 // lanes per instance: 16 or 32
-    const int rstep = lpi >> 3;               // rows between a lane's stores
-    const int src = lane / lpi;
-    const uint64_t base = __shfl_sync(kFull, mine, src);
-    if (base) {
-      const uint64_t *col = disp_warp + src;
-      uint8_t *dst = reinterpret_cast<uint8_t *>(base) + q * 16u;
-      for (int r = (lane & (lpi - 1)) >> 3; r < 64; r += rstep)
-        __stcs(reinterpret_cast<uint4 *>(dst + r * 128), expand16(col[(2 * r + h) * J], q & 3u, lut));
-    }
-    return;
-  }
   const int passes = (ipw + 3) >> 2;
   for (int m = 0; m < passes; ++m) {
     const int src = 4 * m + (lane >> 3);

@@ -176,8 +176,10 @@ void finish_tick(octax_server *s, TickBuf &t) {
   s->cv_done.notify_all();
 }
 
-// One scheduling round: admit, then launch one batched step over all running
-// requests. Returns false when there was nothing to launch.
+// One scheduling round: admit, then launch one batched step kernel over all
+// running requests, advancing each by the fewest steps any of them has left
+// (so that none runs past its last step). Returns false when there was
+// nothing to launch.
 bool tick(octax_server *s) {
   TickBuf &t = s->ticks[s->tick_no % s->depth];
   if (t.pending) {  // ring slot still in flight: wait for it
@@ -202,6 +204,8 @@ bool tick(octax_server *s) {
     for (uint64_t id : s->running) run.push_back(&s->reqs[id]);
   }
   if (run.empty()) return false;
+  uint32_t k_steps = kMaxSteps;  // steps of this tick
+  for (Req *q : run) k_steps = std::min<uint32_t>(k_steps, q->r.n_steps - q->steps_done);
   const int B = s->J;  // instances per CTA
   size_t n_groups = 0, n_rgroups = 0;
   for (Req *q : run) n_groups += (q->r.n_envs + B - 1) / B;
@@ -266,7 +270,7 @@ bool tick(octax_server *s) {
   p.n_groups = (int)g;
   p.io_table = t.d_io;
   p.step0 = 0;
-  p.steps = 1;
+  p.steps = (int)k_steps;
   p.S = s->S;
   p.quirks = s->quirks;
   p.ipw = s->ipw;
@@ -288,7 +292,7 @@ bool tick(octax_server *s) {
     int64_t envs = 0;
     std::vector<uint64_t> still;
     for (Req *q : run) {
-      q->steps_done++;
+      q->steps_done += k_steps;
       envs += q->r.n_envs;
       if (q->steps_done == q->r.n_steps) {
         t.completing.push_back(q->id);
@@ -299,7 +303,7 @@ bool tick(octax_server *s) {
     }
     s->running.swap(still);
     s->stats.ticks++;
-    s->stats.env_steps += envs;
+    s->stats.env_steps += envs * (int64_t)k_steps;
     s->stats.peak_active_envs = std::max(s->stats.peak_active_envs, envs);
     s->stats.peak_active_requests = std::max<int64_t>(s->stats.peak_active_requests, (int64_t)run.size());
   }

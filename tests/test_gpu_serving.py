@@ -223,3 +223,24 @@ def test_batched_submit_equals_single_submits():
         srv.submit_batch(bad)
     assert srv.stats()["submitted"] == before
     srv.close()
+
+
+def test_lone_request_takes_one_launch():
+    """A request that runs alone advances all its steps in one tick (the
+    tick takes the fewest steps any running request has left), with the
+    oracle's results; a mix still matches the oracle step by step."""
+    o = octax()
+    gs = games()
+    srv = o.Server(gs, memory_budget_bytes=5000 * SLOT_BYTES)
+    rng = np.random.default_rng(9)
+    acts = rng.integers(0, 5, size=(8, 300), dtype=np.uint8)
+    ids, _, outs = run_all(srv, [dict(game=2, actions=acts, seed=77)])
+    st = srv.stats()
+    assert st["ticks"] == 1 and st["env_steps"] == 8 * 300
+    ref = oracle.OracleEnv(gs, 300, seed=77, game_of_env=np.full(300, 2, np.uint16))
+    ref.reset()
+    ob, rw, dn, _ = ref.rollout(acts, obs=True)
+    assert np.array_equal(outs[0][0].numpy(), ob)
+    assert np.array_equal(outs[0][1].numpy(), rw)
+    assert np.array_equal(outs[0][2].numpy(), dn)
+    srv.close()
